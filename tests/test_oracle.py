@@ -1,0 +1,423 @@
+"""Pins for the CPU oracle (no GPU).
+
+Each test ties the oracle to something other than itself: closed forms of the
+z-normalised distance, a brute-force numpy evaluation of the definitions, a
+numerical minimisation of the paper's lower-bound expression, the exactness
+claim of the pruned method, planted structure, and the decision logic of the
+paper's worked example.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ helpers
+
+def znorm_windows(x, l):
+    """All z-normalised windows of length l (population std), by numpy."""
+    W = np.lib.stride_tricks.sliding_window_view(np.asarray(x, float), l)
+    return (W - W.mean(1, keepdims=True)) / W.std(1, keepdims=True)
+
+
+def brute_matrix_profile(x, l, num=1, den=4, m_max=1):
+    """Brute force: Euclidean distances between z-normalised windows."""
+    Z = znorm_windows(x, l)
+    nl = len(Z)
+    E = math.ceil(l * num / den)
+    D = np.sqrt(((Z[:, None, :] - Z[None, :, :]) ** 2).sum(-1))
+    I = np.arange(nl)
+    D[np.abs(I[:, None] - I[None, :]) <= E] = np.inf
+    order = np.lexsort((np.broadcast_to(I, D.shape), D), axis=1)
+    nnj = order[:, :m_max]
+    nnd = np.take_along_axis(D, nnj, 1)
+    return nnd[:, 0], nnj[:, 0], nnd, nnj, D
+
+
+# ---------------------------------------------------------------- distance
+
+def test_exclusion_zone_is_ceil():
+    for l in range(2, 200):
+        assert oracle.excl(l, 1, 4) == math.ceil(l / 4)
+        assert oracle.excl(l, 1, 2) == math.ceil(l / 2)
+
+
+def test_window_stats_population():
+    x = workloads.random_walk(500, 11)
+    for l, i in [(7, 0), (64, 100), (128, 372)]:
+        mu, sd = oracle.window_stats(x, l, i)
+        assert mu == pytest.approx(np.mean(x[i:i + l]), rel=1e-13)
+        assert sd == pytest.approx(np.std(x[i:i + l]), rel=1e-12)   # ddof=0
+
+
+def test_distance_formula_matches_znormalised_euclidean():
+    # Eq. DIST (through the correlation) against the definition of the
+    # z-normalised Euclidean distance, two different formulas.
+    rng = np.random.default_rng(0)
+    x = workloads.random_walk(2000, 3)
+    for _ in range(200):
+        l = int(rng.integers(4, 300))
+        i, j = rng.integers(0, len(x) - l + 1, 2)
+        a = oracle.dist(x, l, i, j)
+        zi, zj = znorm_windows(x[i:i + l], l)[0], znorm_windows(x[j:j + l], l)[0]
+        assert a == pytest.approx(np.linalg.norm(zi - zj), rel=1e-9, abs=1e-9)
+        assert a == pytest.approx(oracle.dist_direct(x, l, i, j), rel=1e-9, abs=1e-9)
+
+
+def test_distance_closed_forms():
+    l = 64
+    t = np.arange(3 * l, dtype=float)
+    s = np.sin(2 * np.pi * t / l)
+    # identical windows one period apart: q = 1, d = 0
+    assert oracle.dist(s, l, 0, l) == pytest.approx(0.0, abs=1e-6)
+    # a quarter period apart: sin against cos over whole periods, q = 0, d = sqrt(2 l)
+    assert oracle.dist(s, l, 0, l // 4) == pytest.approx(math.sqrt(2 * l), rel=1e-12)
+    # half a period apart: the negated window, q = -1, d = 2 sqrt(l)
+    assert oracle.dist(s, l, 0, l // 2) == pytest.approx(2 * math.sqrt(l), rel=1e-12)
+    # an affine copy (positive scale) is at distance 0
+    rng = np.random.default_rng(5)
+    p = rng.standard_normal(40)
+    x = np.concatenate([p, rng.standard_normal(30), 3.5 * p - 7.0])
+    assert oracle.dist(x, 40, 0, 70) == pytest.approx(0.0, abs=1e-6)
+    # a negative scale is at the maximum 2 sqrt(l)
+    x2 = np.concatenate([p, rng.standard_normal(30), -0.25 * p + 1.0])
+    assert oracle.dist(x2, 40, 0, 70) == pytest.approx(2 * math.sqrt(40), rel=1e-12)
+
+
+def test_distance_range_symmetry_identity():
+    rng = np.random.default_rng(1)
+    x = workloads.ar2(1500, 9)
+    for _ in range(300):
+        l = int(rng.integers(3, 200))
+        i, j = rng.integers(0, len(x) - l + 1, 2)
+        d = oracle.dist(x, l, i, j)
+        assert 0.0 <= d <= 2 * math.sqrt(l) + 1e-12
+        assert d == oracle.dist(x, l, j, i)
+        assert oracle.dist(x, l, i, i) == pytest.approx(0.0, abs=1e-6)
+
+
+def test_flat_window_reading():
+    x = np.concatenate([np.full(50, 2.5), workloads.random_walk(100, 4), np.full(50, -1.0)])
+    l = 20
+    assert oracle.pearson(x, l, 0, 170) == 1.0          # both flat
+    assert oracle.dist(x, l, 0, 170) == 0.0
+    assert oracle.pearson(x, l, 0, 80) == 0.0           # one flat
+    assert oracle.dist(x, l, 0, 80) == pytest.approx(math.sqrt(2 * l))
+
+
+# ---------------------------------------------------------- matrix profile
+
+@pytest.mark.parametrize("l,num,den", [(16, 1, 4), (24, 1, 2), (9, 1, 4)])
+def test_matrix_profile_brute_force(l, num, den):
+    x = workloads.random_walk(180, 21)
+    mp, ip, nnd, nnj = oracle.matrix_profile(x, l, m_max=3, num=num, den=den)
+    bmp, bip, bnnd, bnnj, _ = brute_matrix_profile(x, l, num, den, m_max=3)
+    np.testing.assert_allclose(mp, bmp, rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(nnd, bnnd, rtol=1e-9, atol=1e-9)
+    # indices agree except where competing distances are within rounding
+    bad = ip != bip
+    assert bad.sum() <= 2
+
+
+def test_matrix_profile_exclusion_respected():
+    x = workloads.ar2(400, 2)
+    for l in (10, 33):
+        E = oracle.excl(l)
+        mp, ip, nnd, nnj = oracle.matrix_profile(x, l, m_max=4)
+        i = np.arange(len(mp))
+        assert np.all(np.abs(nnj - i[:, None]) > E)
+        prof = oracle.distance_profile(x, l, 100)
+        assert np.all(np.isinf(prof[100 - E:100 + E + 1]))
+        assert np.all(np.isfinite(np.delete(prof, np.arange(100 - E, 100 + E + 1))))
+
+
+def test_row_matches_matrix_profile():
+    x = workloads.random_walk(300, 8)
+    mp, ip, nnd, nnj = oracle.matrix_profile(x, 30, m_max=2)
+    for i in (0, 17, 150, 270):
+        r = oracle.row(x, 30, i, m_max=2)
+        assert r[0] == mp[i] and r[1] == ip[i]
+        np.testing.assert_array_equal(r[2], nnd[i])
+
+
+# ------------------------------------------------------------- lower bound
+
+def _lb_numeric(x, l, k, row, other):
+    """Minimise Eq. LB-min over (mu', sigma') numerically. ``row`` is the
+    window whose longer extension is known, ``other`` the one whose last k
+    values are treated as unknown."""
+    from scipy.optimize import minimize
+    tr = x[row:row + l]
+    to = x[other:other + l]
+    zr = (tr - tr.mean()) / tr.std()
+    s_l = tr.std()
+    s_lk = x[row:row + l + k].std()
+
+    def f(v):
+        mu, logs = v
+        return np.sum(((to - mu) / math.exp(logs) - zr) ** 2)
+
+    best = np.inf
+    for mu0 in (to.mean(), to.mean() + to.std()):
+        for ls0 in (math.log(to.std()), math.log(to.std()) + 3.0, math.log(to.std()) + 8.0):
+            r = minimize(f, [mu0, ls0], method="Nelder-Mead",
+                         options=dict(xatol=1e-12, fatol=1e-14, maxiter=20000, maxfev=40000))
+            best = min(best, r.fun)
+    return s_l / s_lk * math.sqrt(max(best, 0.0))
+
+
+def test_lower_bound_closed_form_is_the_minimum():
+    pytest.importorskip("scipy")
+    x = workloads.random_walk(600, 12)
+    rng = np.random.default_rng(3)
+    checked_pos = checked_neg = 0
+    for _ in range(40):
+        l, k = 24, int(rng.integers(1, 10))
+        row, other = rng.integers(0, len(x) - l - k, 2)
+        q = oracle.pearson(x, l, row, other)
+        s_l = oracle.window_stats(x, l, row)[1]
+        s_lk = oracle.window_stats(x, l + k, row)[1]
+        closed = oracle.lower_bound(l, q, s_l, s_lk)
+        num = _lb_numeric(x, l, k, row, other)
+        if q > 0:
+            checked_pos += 1
+            assert closed == pytest.approx(num, rel=1e-4, abs=1e-6)
+        else:
+            checked_neg += 1
+            # q <= 0: the infimum is approached as sigma' -> inf
+            assert closed <= num + 1e-6
+            assert closed == pytest.approx(num, rel=2e-2)
+    assert checked_pos > 5 and checked_neg > 5
+
+
+def test_lower_bound_never_exceeds_true_distance():
+    # The reason the bound exists: LB(d^{l+k}) <= d^{l+k} for every k >= 1,
+    # with either window as the row.
+    for series in (workloads.random_walk(900, 1), workloads.ar2(900, 2), workloads.ecg_like(900, 3)):
+        rng = np.random.default_rng(7)
+        for _ in range(300):
+            l = int(rng.integers(8, 80))
+            k = int(rng.integers(1, 60))
+            i, j = rng.integers(0, len(series) - l - k, 2)
+            if i == j:
+                continue
+            q = oracle.pearson(series, l, i, j)
+            d = oracle.dist(series, l + k, i, j)
+            for row in (i, j):
+                lb = oracle.lower_bound(l, q, oracle.window_stats(series, l, row)[1],
+                                        oracle.window_stats(series, l + k, row)[1])
+                assert lb <= d * (1 + 1e-12) + 1e-6   # sqrt of rounding in 1-q^2
+
+
+def test_lower_bound_rank_preservation():
+    # The ranking of a row's lower-bound profile is the same for every k.
+    x = workloads.random_walk(700, 5)
+    l, row = 32, 300
+    cols = [j for j in range(len(x) - l - 40) if abs(j - row) > 8]
+    q = np.array([oracle.pearson(x, l, row, j) for j in cols])
+    s_l = oracle.window_stats(x, l, row)[1]
+    ref = None
+    for k in (1, 2, 5, 17, 40):
+        s_lk = oracle.window_stats(x, l + k, row)[1]
+        lb = np.array([oracle.lower_bound(l, qq, s_l, s_lk) for qq in q])
+        order = np.lexsort((np.array(cols), lb))
+        if ref is None:
+            ref = order
+        assert np.array_equal(order, ref)
+
+
+def test_worked_example_decisions():
+    # Example 2: only the decisions are pinned (the example's series is absent).
+    g = json.load(open(os.path.join(GOLDEN, "example2_certification.json")))
+    for r in g["rows"]:
+        assert oracle.row_valid([r["minDist"]], 1, r["maxLB"]) == r["valid"]
+    gl = g["global"]
+    assert (gl["minDistAbs"] < gl["minLbAbs"]) == gl["motif_found"]
+    # strictness: a tie is not valid
+    assert not oracle.row_valid([3.0], 1, 3.0)
+    # m-th best match: needs m stored distances below the bound
+    assert oracle.row_valid([1.0, 2.0, 2.9], 3, 3.0)
+    assert not oracle.row_valid([1.0, 2.0], 3, 3.0)
+
+
+# ------------------------------------------------------------------ VALMP
+
+def test_valmp_single_length_is_matrix_profile():
+    x = workloads.random_walk(400, 6)
+    l = 40
+    v = oracle.valmp_plain(x, l, l)
+    mp, ip, _, _ = oracle.matrix_profile(x, l)
+    np.testing.assert_array_equal(v["dist"], mp)
+    np.testing.assert_array_equal(v["nn"], ip)
+    np.testing.assert_allclose(v["norm"], mp / math.sqrt(l), rtol=1e-15)
+    assert np.all(v["len"] == l)
+
+
+def test_valmp_brute_force_all_lengths():
+    x = workloads.ar2(160, 13)
+    lmin, lmax = 12, 19
+    v = oracle.valmp_plain(x, lmin, lmax)
+    n0 = len(x) - lmin + 1
+    best = np.full(n0, np.inf)
+    blen = np.zeros(n0, int)
+    for l in range(lmin, lmax + 1):
+        bmp = brute_matrix_profile(x, l)[0]
+        nd = bmp / math.sqrt(l)
+        for i in range(len(bmp)):
+            if nd[i] < best[i] - 1e-9:
+                best[i], blen[i] = nd[i], l
+    np.testing.assert_allclose(v["norm"], best, rtol=1e-9)
+    assert np.mean(v["len"] == blen) > 0.98
+
+
+@pytest.mark.parametrize("gen,n,lmin,lmax,p,m_max", [
+    ("rw", 500, 20, 34, 5, 1),
+    ("rw", 420, 16, 24, 8, 3),
+    ("ar2", 450, 18, 30, 5, 2),
+    ("ecg", 900, 40, 60, 4, 1),
+    ("planted", 1200, 30, 44, 5, 2),
+])
+def test_pruned_equals_independent_lengths(gen, n, lmin, lmax, p, m_max):
+    if gen == "rw":
+        x = workloads.random_walk(n, 31)
+    elif gen == "ar2":
+        x = workloads.ar2(n, 32)
+    elif gen == "ecg":
+        x = workloads.ecg_like(n, 33, period=40.0)
+    else:
+        x, _ = workloads.planted_walk(n, 34, motif_lengths=(30, 36), lmax=60)
+    pl = oracle.valmp_plain(x, lmin, lmax, m_max=m_max, keep_nn=True)
+    pr = oracle.valmod_pruned(x, lmin, lmax, p, m_max=m_max, keep_nn=True)
+    for key in ("dist", "norm", "len", "nn"):
+        np.testing.assert_array_equal(pl[key], pr[key])
+    np.testing.assert_array_equal(pl["nnd"], pr["nnd"])
+    np.testing.assert_array_equal(pl["nnj"], pr["nnj"])
+    st = pr["stats"]
+    assert np.all(st[:, 1] + st[:, 2] == st[:, 0])
+    assert st[0, 2] == st[0, 0]                   # everything computed at lmin
+    assert st[1:, 1].sum() > 0                    # the bound certified some rows
+
+
+def test_pruned_prunes_on_periodic_data():
+    # On quasi-periodic data most rows stay certified (the paper's regime).
+    x = workloads.ecg_like(2000, 40, period=50.0)
+    pr = oracle.valmod_pruned(x, 50, 60, 8)
+    st = pr["stats"]
+    assert st[1:, 2].sum() < 0.2 * st[1:, 0].sum()
+
+
+# ---------------------------------------------------------------- read-outs
+
+def test_topk_motif_planted_pair():
+    rng = np.random.default_rng(17)
+    pat = np.cumsum(rng.standard_normal(48))
+    x = workloads.random_walk(1500, 18)
+    x[300:348] = 2.0 * pat + 5.0
+    x[1000:1048] = 0.5 * pat - 3.0 + 1e-4 * rng.standard_normal(48)
+    v = oracle.valmp_plain(x, 40, 48)
+    mot = oracle.topk_motifs(v, 3)
+    a, b, L, d, nd = mot[0]
+    assert (a, b) == (300, 1000) and L == 48
+    assert d < 0.01
+
+
+def test_topk_motif_greedy_properties():
+    x = workloads.random_walk(700, 19)
+    v = oracle.valmp_plain(x, 20, 30)
+    k = 8
+    mot = oracle.topk_motifs(v, k)
+    assert len(mot) == k
+    nds = [m[4] for m in mot]
+    assert nds == sorted(nds)
+
+    def conflict(m1, m2):
+        E = max(oracle.excl(m1[2]), oracle.excl(m2[2]))
+        return any(abs(u - w) <= E for u in m1[:2] for w in m2[:2])
+
+    for i in range(k):
+        for j in range(i):
+            assert not conflict(mot[i], mot[j])
+    # maximality: every VALMP entry better than the last accepted one either
+    # is an accepted pair or conflicts with an accepted pair listed before it
+    order = np.lexsort((np.arange(len(v["norm"])), v["norm"]))
+    last = mot[-1][4]
+    for i in order:
+        if v["norm"][i] > last:
+            break
+        cand = (min(i, v["nn"][i]), max(i, v["nn"][i]), v["len"][i])
+        if any(cand == m[:3] for m in mot):
+            continue
+        assert any(conflict(cand, m) for m in mot if m[4] <= v["norm"][i])
+
+
+def test_discord_planted_spike():
+    x = workloads.ecg_like(3000, 41, period=60.0)
+    x[1700] += 3.0
+    l = 60
+    mp, ip, nnd, nnj = oracle.matrix_profile(x, l)
+    top = oracle.discords_one_length(mp, l, 3)
+    o = top[0][0]
+    assert o <= 1700 < o + l
+
+
+def test_discord_table_merge_and_exclusion():
+    x = workloads.ar2(600, 23)
+    lmin, lmax, k, m_max = 16, 22, 4, 2
+    pl = oracle.valmp_plain(x, lmin, lmax, m_max=m_max, keep_nn=True)
+    dk = oracle.discords(len(x), lmin, lmax, k, m_max, pl["nnd"], pl["nnj"])
+    n0 = len(x) - lmin + 1
+    for m in range(m_max):
+        for r in range(k):
+            L = dk["len"][r, m]
+            assert lmin <= L <= lmax
+            # the winning length's own ranking has this offset at rank r
+            nl = len(x) - L + 1
+            sc = pl["nnd"][L - lmin, :nl, m]
+            per = oracle.discords_one_length(sc, L, k, pl["nnj"][L - lmin, :nl, m])
+            assert per[r][0] == dk["off"][r, m]
+            assert dk["norm"][r, m] == pytest.approx(per[r][1] / math.sqrt(L))
+            # no other length scores higher at this rank (ties go to the later length)
+            for l2 in range(lmin, lmax + 1):
+                nl2 = len(x) - l2 + 1
+                per2 = oracle.discords_one_length(pl["nnd"][l2 - lmin, :nl2, m], l2, k)
+                if len(per2) > r:
+                    v2 = per2[r][1] / math.sqrt(l2)
+                    assert v2 <= dk["norm"][r, m] + 1e-15
+                    if l2 > L:
+                        assert v2 < dk["norm"][r, m]
+        # per-length picks are pairwise non-trivial and descending
+        for l2 in range(lmin, lmax + 1):
+            nl2 = len(x) - l2 + 1
+            per2 = oracle.discords_one_length(pl["nnd"][l2 - lmin, :nl2, m], l2, k)
+            sc = [p[1] for p in per2]
+            assert sc == sorted(sc, reverse=True)
+            offs = [p[0] for p in per2]
+            E = oracle.excl(l2)
+            assert all(abs(a - b) > E for a in offs for b in offs if a != b)
+    assert n0 > 0
+
+
+def test_planted_workload_recovered_small():
+    # A scaled-down planted series: the top motif is one of the planted pairs
+    # and the top discord covers a planted discord.
+    x, info = workloads.planted_walk(6000, 44, motif_lengths=(60, 80), lmax=100)
+    v = oracle.valmp_plain(x, 64, 72, keep_nn=True)
+    mot = oracle.topk_motifs(v, 3)
+    planted = [(a, b) for a, b, L in info.motifs]
+    hit = False
+    for a, b, L, d, nd in mot[:2]:
+        for pa, pb in planted:
+            if abs(a - pa) <= 20 and abs(b - pb) <= 20:
+                hit = True
+    assert hit
+    dk = oracle.discords(len(x), 64, 72, 3, 1, v["nnd"], v["nnj"])
+    offs = dk["off"][:, 0]
+    lens = dk["len"][:, 0]
+    assert any(o <= info.spike < o + L or o <= info.level_shift < o + L for o, L in zip(offs, lens))
