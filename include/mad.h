@@ -1,0 +1,194 @@
+/*
+ * mad.h -- C ABI of the GB300 (sm_103a) exact variable-length matrix profile.
+ *
+ * The library computes, on one GPU, what the VALMOD / MAD method of
+ * "Matrix Profile Goes MAD" computes:
+ *   - the z-normalised matrix profile of a data series at every length of a
+ *     range [lmin, lmax] (Problem 1, variable-length motif pair discovery),
+ *     using the paper's lower bound (Eq. LB) to skip rows whose p stored
+ *     entries already certify the result (Algorithms 1, 3, 4, 10);
+ *   - the variable-length matrix profile VALMP (Algorithm 2) and its top-k
+ *     length-normalised motif pairs (Sec. 3, Algorithm 5);
+ *   - the variable-length Top-k m-th discord table dkm_{lmin,lmax}
+ *     (Problem 3, Algorithms 7-9).
+ *
+ * Conventions (all calls):
+ *   - Offsets are 0-based. A window (subsequence) of length l starting at i
+ *     covers x[i .. i+l-1]; n_l = n - l + 1 windows exist at length l.
+ *   - A pair (i, j) is a trivial match at length l iff |i - j| <= E(l),
+ *     E(l) = ceil(l * excl_num / excl_den) (Sec. 2 "exclusion zone"; the paper
+ *     uses l/2, the default here is l/4).
+ *   - Distances are z-normalised Euclidean distances (Eq. DIST), with the
+ *     population standard deviation. A window whose values are all equal is
+ *     "flat": two flat windows are at distance 0, a flat and a non-flat
+ *     window at sqrt(2 l).
+ *   - Every call returns a mad_status; no C++ exception crosses the ABI.
+ *     After an error, mad_last_error(ctx) describes it (ctx may be NULL for
+ *     errors of mad_create*; then a thread-local message is returned).
+ *   - Host pointers are caller-owned and only read/written during the call.
+ *     Device pointers passed to mad_create_device stay caller-owned and must
+ *     remain valid until mad_destroy.
+ *   - Every call is synchronous with respect to the host: when it returns,
+ *     all GPU work it issued on the context's stream has completed.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef MAD_H
+#define MAD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define MAD_API __attribute__((visibility("default")))
+#else
+#define MAD_API
+#endif
+
+typedef struct mad_ctx mad_ctx;
+
+typedef enum {
+    MAD_OK = 0,
+    MAD_EINVAL = 1,     /* invalid argument (sizes, ranges, NULL pointers) */
+    MAD_ENOMEM = 2,     /* device or host allocation failed */
+    MAD_ECUDA = 3,      /* a CUDA runtime call failed */
+    MAD_ESTATE = 4,     /* call out of order (e.g. read-out before profile) */
+    MAD_ETIMEOUT = 5,   /* a bounded device-side wait ran out */
+    MAD_EINTERNAL = 6   /* an internal consistency check failed */
+} mad_status;
+
+/* Arithmetic of the dominant matrix-profile kernel.
+ *   MAD_FP64: FP64 everywhere (the plain reference path on the GPU).
+ *   MAD_FP32: the O(n^2) diagonal (QT) recurrence in FP32 on centred
+ *             co-moments, re-seeded from direct dot products every band of
+ *             rows; window statistics, the per-row stored entries, the
+ *             length extension, the bound test and the reported distances
+ *             of the stored entries stay FP64. Distances agree with FP64
+ *             within 1e-4 * sqrt(l). */
+typedef enum { MAD_FP64 = 0, MAD_FP32 = 1 } mad_precision;
+
+typedef struct mad_options {
+    int32_t excl_num;       /* exclusion zone numerator   (0 with excl_den 0: 1/4) */
+    int32_t excl_den;       /* exclusion zone denominator */
+    int32_t precision;      /* mad_precision, default MAD_FP64 */
+    int32_t k_max;          /* discord table rows (ranks) kept, default 10, <= 64 */
+    int32_t m_max;          /* discord table columns (m-th best match), default 1; must be <= p */
+    int32_t keep_profiles;  /* nonzero: keep every per-length matrix profile and m-th best
+                               match table for mad_matrix_profile (|L| * n_lmin * (1 + m_max)
+                               doubles and offsets; meant for small inputs) */
+    int32_t mode;           /* 0 (only mode): every row the bound cannot certify is recomputed,
+                               so every per-length result is exact for every offset */
+    int32_t reserved;       /* must be 0 */
+    void *stream;           /* cudaStream_t to issue work on; NULL = the legacy default stream */
+} mad_options;
+
+/* One motif pair: windows a < b of length len. */
+typedef struct {
+    int64_t a, b;
+    int32_t len;
+    int32_t reserved;
+    double dist;            /* z-normalised Euclidean distance at len */
+    double norm_dist;       /* dist * sqrt(1 / len) (Sec. 3) */
+    double dist_recheck;    /* the same distance recomputed directly in FP64 (two-pass
+                               statistics, centred dot product) on the GPU */
+} mad_motif;
+
+/* One cell <d*, o*, l*> of dkm_{lmin,lmax}: the Top-rank m-th discord. */
+typedef struct {
+    int64_t off;            /* o*: window offset (-1 if the cell is empty) */
+    int64_t nn;             /* offset of its m-th best match at len */
+    int32_t len;            /* l* (0 if the cell is empty) */
+    int32_t rank;           /* 1-based rank k */
+    int32_t m;              /* 1-based column m */
+    int32_t reserved;
+    double dist;            /* its m-th best-match distance at len */
+    double norm_dist;       /* d* = dist / sqrt(len) */
+    double dist_recheck;    /* the m-th best-match distance recomputed on the GPU from a
+                               full FP64 distance profile (two-pass statistics per window) */
+} mad_discord;
+
+/* Pruning counters of one length (Sec. 6.3 "valid / non-valid / recomputed"). */
+typedef struct {
+    int32_t len;
+    int32_t reserved;
+    int64_t rows;           /* windows alive at len (n_len) */
+    int64_t certified;      /* rows whose stored entries certified the result */
+    int64_t recomputed;     /* rows whose full distance profile was recomputed */
+    int64_t tiles;          /* band x column-range units the recompute kernel ran */
+    int64_t passes;         /* recompute kernel passes (1 + candidate-list refills) */
+} mad_length_stats;
+
+/* Create a context for one series copied from host memory (FP64, n values).
+ * Needs n >= 4. On success *out owns all device memory it allocates. */
+MAD_API mad_status mad_create(const double *host_series, int64_t n, const mad_options *opt,
+                              mad_ctx **out);
+
+/* Same, for a series already in device memory: dtype 0 = FP64, 1 = FP32
+ * (widened to FP64 on the device). The caller keeps ownership of
+ * dev_series; it must stay valid until mad_destroy. */
+MAD_API mad_status mad_create_device(const void *dev_series, int32_t dtype, int64_t n,
+                                     const mad_options *opt, mad_ctx **out);
+
+/* Create one context over `count` independent host series (series[s] has
+ * n[s] values), profiled together by mad_profile_batch. */
+MAD_API mad_status mad_create_batch(const double *const *series, const int64_t *n, int32_t count,
+                                    const mad_options *opt, mad_ctx **out);
+
+/* Compute the exact variable-length matrix profile over [lmin, lmax] keeping
+ * p entries per row (Algorithm 1 VALMOD with the Top-k m-th discord table
+ * of Algorithm 7). Requires 2 <= lmin <= lmax, 1 <= p <= 64, m_max <= p, and
+ * n - lmax + 1 > 2 E(lmax) + 2 (every window keeps a non-trivial neighbour).
+ * A context may be profiled again (results are replaced). */
+MAD_API mad_status mad_profile(mad_ctx *ctx, int32_t lmin, int32_t lmax, int32_t p);
+
+/* Batched form: lmin[s], lmax[s] per series of a mad_create_batch context. */
+MAD_API mad_status mad_profile_batch(mad_ctx *ctx, const int32_t *lmin, const int32_t *lmax,
+                                     int32_t p);
+
+/* Top-k length-normalised motif pairs of series `series` from VALMP: offsets
+ * visited by (norm_dist, offset) ascending, a pair accepted unless one of its
+ * offsets lies within max(E(len), E(len')) of an offset of an accepted pair.
+ * Writes up to k entries to out (caller array of k) and their count to
+ * *n_out (fewer than k is not an error). MAD_ESTATE before mad_profile. */
+MAD_API mad_status mad_motifs(mad_ctx *ctx, int32_t series, int32_t k, mad_motif *out,
+                              int32_t *n_out);
+
+/* The k x m block (ranks 1..k, columns 1..m) of dkm_{lmin,lmax}: per length
+ * and column, offsets ranked by m-th best-match distance descending (ties:
+ * smaller offset) with pairwise non-trivial picks; across lengths each cell
+ * keeps the largest dist / sqrt(len), ties to the longer length (Alg. 9).
+ * out must hold k * m entries, written rank-major (out[(r-1)*m + (c-1)]);
+ * *n_out = k * m. Requires k <= k_max, m <= m_max. */
+MAD_API mad_status mad_discords(mad_ctx *ctx, int32_t series, int32_t k, int32_t m,
+                                mad_discord *out, int32_t *n_out);
+
+/* Copy VALMP of series `series` to host arrays of n - lmin + 1 entries:
+ * raw distance, normalised distance, length, nearest-neighbour offset. */
+MAD_API mad_status mad_valmp(mad_ctx *ctx, int32_t series, double *dist, double *norm,
+                             int32_t *len, int64_t *nn);
+
+/* Copy the matrix profile of series `series` at one length len in
+ * [lmin, lmax] (needs keep_profiles): mp/ip have n_len entries, nnd/nnj
+ * n_len * m_max (row-major, m fastest). Any output pointer may be NULL. */
+MAD_API mad_status mad_matrix_profile(mad_ctx *ctx, int32_t series, int32_t len, double *mp,
+                                      int64_t *ip, double *nnd, int64_t *nnj);
+
+/* Per-length pruning counters of series `series`: writes min(cap, |L|)
+ * entries and |L| to *n_out. */
+MAD_API mad_status mad_stats(mad_ctx *ctx, int32_t series, mad_length_stats *out, int32_t cap,
+                             int32_t *n_out);
+
+/* Human-readable description of the last error on ctx (or of the calling
+ * thread's last mad_create* error when ctx is NULL). Never NULL. */
+MAD_API const char *mad_last_error(const mad_ctx *ctx);
+
+/* Release the context and its device memory. NULL-safe. */
+MAD_API void mad_destroy(mad_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MAD_H */

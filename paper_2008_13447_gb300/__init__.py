@@ -1,0 +1,215 @@
+"""Python binding of the GB300 exact variable-length matrix profile library.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``_build/libmad.so`` behind the C ABI of ``include/mad.h``. The functions
+below carry the ABI's names. There is no CPU fallback: if the library is
+missing the import of any function raises.
+
+Typical use::
+
+    import numpy as np, paper_2008_13447_gb300 as mad
+    ctx = mad.mad_create(x, precision=mad.MAD_FP32, k_max=5, m_max=1)
+    mad.mad_profile(ctx, 256, 512, 5)
+    motifs = mad.mad_motifs(ctx, 0, 5)
+    discords = mad.mad_discords(ctx, 0, 5, 1)
+    mad.mad_destroy(ctx)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libmad.so")
+
+MAD_OK, MAD_EINVAL, MAD_ENOMEM, MAD_ECUDA, MAD_ESTATE, MAD_ETIMEOUT, MAD_EINTERNAL = range(7)
+MAD_FP64, MAD_FP32 = 0, 1
+STATUS_NAMES = {0: "MAD_OK", 1: "MAD_EINVAL", 2: "MAD_ENOMEM", 3: "MAD_ECUDA", 4: "MAD_ESTATE",
+                5: "MAD_ETIMEOUT", 6: "MAD_EINTERNAL"}
+ABI_FUNCTIONS = ("mad_create", "mad_create_device", "mad_create_batch", "mad_profile", "mad_profile_batch",
+                 "mad_motifs", "mad_discords", "mad_valmp", "mad_matrix_profile", "mad_stats",
+                 "mad_last_error", "mad_destroy")
+
+
+class mad_options(C.Structure):
+    _fields_ = [("excl_num", C.c_int32), ("excl_den", C.c_int32), ("precision", C.c_int32),
+                ("k_max", C.c_int32), ("m_max", C.c_int32), ("keep_profiles", C.c_int32),
+                ("mode", C.c_int32), ("reserved", C.c_int32), ("stream", C.c_void_p)]
+
+
+class mad_motif(C.Structure):
+    _fields_ = [("a", C.c_int64), ("b", C.c_int64), ("len", C.c_int32), ("reserved", C.c_int32),
+                ("dist", C.c_double), ("norm_dist", C.c_double), ("dist_recheck", C.c_double)]
+
+
+class mad_discord(C.Structure):
+    _fields_ = [("off", C.c_int64), ("nn", C.c_int64), ("len", C.c_int32), ("rank", C.c_int32),
+                ("m", C.c_int32), ("reserved", C.c_int32), ("dist", C.c_double), ("norm_dist", C.c_double),
+                ("dist_recheck", C.c_double)]
+
+
+class mad_length_stats(C.Structure):
+    _fields_ = [("len", C.c_int32), ("reserved", C.c_int32), ("rows", C.c_int64), ("certified", C.c_int64),
+                ("recomputed", C.c_int64), ("tiles", C.c_int64), ("passes", C.c_int64)]
+
+
+class MadError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+_lib = None
+
+
+def library() -> C.CDLL:
+    """Load ``libmad.so`` (built by ``build.py``). Raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libmad.so not built (run paper_2008_13447_gb300/build.py): %s" % LIB_PATH)
+        lib = C.CDLL(LIB_PATH)
+        P, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        sig = {
+            "mad_create": [P, i64, C.POINTER(mad_options), C.POINTER(P)],
+            "mad_create_device": [P, i32, i64, C.POINTER(mad_options), C.POINTER(P)],
+            "mad_create_batch": [C.POINTER(P), C.POINTER(i64), i32, C.POINTER(mad_options), C.POINTER(P)],
+            "mad_profile": [P, i32, i32, i32],
+            "mad_profile_batch": [P, C.POINTER(i32), C.POINTER(i32), i32],
+            "mad_motifs": [P, i32, i32, C.POINTER(mad_motif), C.POINTER(i32)],
+            "mad_discords": [P, i32, i32, i32, C.POINTER(mad_discord), C.POINTER(i32)],
+            "mad_valmp": [P, i32, P, P, P, P],
+            "mad_matrix_profile": [P, i32, i32, P, P, P, P],
+            "mad_stats": [P, i32, C.POINTER(mad_length_stats), i32, C.POINTER(i32)],
+        }
+        for name, args in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        lib.mad_last_error.argtypes = [P]
+        lib.mad_last_error.restype = C.c_char_p
+        lib.mad_destroy.argtypes = [P]
+        lib.mad_destroy.restype = None
+        _lib = lib
+    return _lib
+
+
+def _check(status, ctx):
+    if status != MAD_OK:
+        raise MadError(status, library().mad_last_error(ctx).decode())
+
+
+def _options(precision=MAD_FP64, excl=(1, 4), k_max=10, m_max=1, keep_profiles=False, stream=None):
+    o = mad_options()
+    o.excl_num, o.excl_den = excl
+    o.precision = precision
+    o.k_max = k_max
+    o.m_max = m_max
+    o.keep_profiles = 1 if keep_profiles else 0
+    o.mode = 0
+    o.reserved = 0
+    if stream is not None:
+        o.stream = stream if isinstance(stream, int) else stream.cuda_stream
+    return o
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def mad_create(series, **opts):
+    """Create a context from a host FP64 series (numpy array)."""
+    x = np.ascontiguousarray(series, dtype=np.float64)
+    o = _options(**opts)
+    ctx = C.c_void_p()
+    _check(library().mad_create(_p(x), len(x), C.byref(o), C.byref(ctx)), None)
+    return ctx
+
+
+def mad_create_device(tensor, **opts):
+    """Create a context from a CUDA tensor (torch, float64 or float32,
+    contiguous). The tensor must outlive the context."""
+    import torch
+    if not (tensor.is_cuda and tensor.is_contiguous() and tensor.dim() == 1):
+        raise ValueError("need a contiguous 1-D CUDA tensor")
+    dtype = {torch.float64: 0, torch.float32: 1}[tensor.dtype]
+    o = _options(**opts)
+    ctx = C.c_void_p()
+    _check(library().mad_create_device(C.c_void_p(tensor.data_ptr()), dtype, tensor.numel(), C.byref(o),
+                                       C.byref(ctx)), None)
+    return ctx
+
+
+def mad_create_batch(series_list, **opts):
+    xs = [np.ascontiguousarray(s, dtype=np.float64) for s in series_list]
+    ptrs = (C.c_void_p * len(xs))(*[x.ctypes.data for x in xs])
+    ns = (C.c_int64 * len(xs))(*[len(x) for x in xs])
+    o = _options(**opts)
+    ctx = C.c_void_p()
+    _check(library().mad_create_batch(ptrs, ns, len(xs), C.byref(o), C.byref(ctx)), None)
+    return ctx
+
+
+def mad_profile(ctx, lmin, lmax, p):
+    _check(library().mad_profile(ctx, lmin, lmax, p), ctx)
+
+
+def mad_profile_batch(ctx, lmin, lmax, p):
+    a = (C.c_int32 * len(lmin))(*lmin)
+    b = (C.c_int32 * len(lmax))(*lmax)
+    _check(library().mad_profile_batch(ctx, a, b, p), ctx)
+
+
+def mad_motifs(ctx, series, k):
+    """Top-k motif pairs: list of dicts (a, b, len, dist, norm_dist, dist_recheck)."""
+    out = (mad_motif * k)()
+    n = C.c_int32()
+    _check(library().mad_motifs(ctx, series, k, out, C.byref(n)), ctx)
+    return [dict(a=m.a, b=m.b, len=m.len, dist=m.dist, norm_dist=m.norm_dist, dist_recheck=m.dist_recheck)
+            for m in out[:n.value]]
+
+
+def mad_discords(ctx, series, k, m):
+    """The k x m block of the discord table: list (rank-major) of dicts."""
+    out = (mad_discord * (k * m))()
+    n = C.c_int32()
+    _check(library().mad_discords(ctx, series, k, m, out, C.byref(n)), ctx)
+    return [dict(off=d.off, nn=d.nn, len=d.len, rank=d.rank, m=d.m, dist=d.dist, norm_dist=d.norm_dist,
+                 dist_recheck=d.dist_recheck) for d in out[:n.value]]
+
+
+def mad_valmp(ctx, series, n0):
+    """VALMP arrays of n0 = n - lmin + 1 entries: dict(dist, norm, len, nn)."""
+    d, nd = np.empty(n0), np.empty(n0)
+    ln, nn = np.empty(n0, np.int32), np.empty(n0, np.int64)
+    _check(library().mad_valmp(ctx, series, _p(d), _p(nd), _p(ln), _p(nn)), ctx)
+    return dict(dist=d, norm=nd, len=ln, nn=nn)
+
+
+def mad_matrix_profile(ctx, series, length, n, m_max=1):
+    """Matrix profile at one length (context made with keep_profiles=True):
+    (mp, ip, nnd[n_l, m_max], nnj[n_l, m_max])."""
+    nl = n - length + 1
+    mp, ip = np.empty(nl), np.empty(nl, np.int64)
+    nnd, nnj = np.empty((nl, m_max)), np.empty((nl, m_max), np.int64)
+    _check(library().mad_matrix_profile(ctx, series, length, _p(mp), _p(ip), _p(nnd), _p(nnj)), ctx)
+    return mp, ip, nnd, nnj
+
+
+def mad_stats(ctx, series, cap=1 << 16):
+    out = (mad_length_stats * cap)()
+    n = C.c_int32()
+    _check(library().mad_stats(ctx, series, out, cap, C.byref(n)), ctx)
+    return [dict(len=s.len, rows=s.rows, certified=s.certified, recomputed=s.recomputed, tiles=s.tiles,
+                 passes=s.passes) for s in out[:min(n.value, cap)]]
+
+
+def mad_last_error(ctx=None):
+    return library().mad_last_error(ctx).decode()
+
+
+def mad_destroy(ctx):
+    if ctx is not None:
+        library().mad_destroy(ctx)

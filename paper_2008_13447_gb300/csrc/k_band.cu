@@ -1,0 +1,358 @@
+// k_band.cu -- the matrix-profile kernel: diagonal (QT) recurrence over R x R
+// tiles, wavefront across warps, per-row candidate selection.
+//
+// What it computes (Algorithm 3 ComputeMatrixProfile, restricted to the rows
+// of the active bands): for every row r of a band and every column j, the
+// centred co-moment C(r, j) by the recurrence along diagonals
+//     C(r, j) = C(r-1, j-1) + df_{r-1} dg_{j-1} + df_{j-1} dg_{r-1}
+// (the mean-centred form of QT[j] = QT[j-1] - t_{j-1} t_{i-1} + t_{j+l-1} t_{i+l-1}),
+// started at every tile's top row and left column from direct dot products
+// (the "seed" rows). Instead of a distance it evaluates the row key
+// key = C(r, j) / sqrt(M2_j): within a row the key orders columns exactly
+// like the correlation q, hence like Eq. DIST and like Eq. LB (the p smallest
+// lower bounds of a row are its p largest correlations).
+//
+// Two modes:
+//  - append: every non-trivial cell whose key exceeds the row's threshold is
+//    appended to the row's candidate list (the threshold is a proven lower
+//    bound on the row's p-th best key, so the list holds the row's top-p);
+//  - bins: per row, the maximum key over the columns of each chunk index
+//    modulo p is recorded; the smallest of those p maxima is a lower bound on
+//    the row's p-th best key (p distinct columns), used as the first
+//    threshold at lmin.
+//
+// Layout: a band is R = 32 * RPL * NW consecutive rows. Lane t of warp w
+// owns rows rfirst(w) + t*RPL + [0, RPL); all lanes of a warp walk the same
+// column j at a time, so the row r's predecessor C(r-1, j-1) sits in the
+// same lane (previous row, previous column) or in lane t-1 (one shuffle), and
+// the first row of warp w takes it from warp w-1 through shared memory, one
+// chunk of CH columns behind (a wavefront over the warps, one barrier per
+// chunk). Per-column data (df, dg, inv) is staged per chunk in shared memory
+// and read as broadcasts.
+#include "kernels.cuh"
+
+namespace mad {
+
+// ------------------------------------------------------------------ seeds
+
+template <typename T>
+__global__ void k_seed(SeedArgs<T> A);
+
+// FP64 seeds: the centred dot product evaluated directly in FP64.
+template <>
+__global__ void k_seed<double>(SeedArgs<double> A)
+{
+    extern __shared__ double sh_d[];
+    const int l = A.l;
+    double *arow = sh_d;                  // centred row window (l)
+    const int k = A.krows[blockIdx.y];
+    const int64_t kr = (int64_t)k * A.R;
+    const int64_t a = (k == 0) ? 0 : kr - 1;
+    const double mua = A.mu[a];
+    for (int t = threadIdx.x; t < l; t += blockDim.x) arow[t] = A.x[a + t] - mua;
+    __syncthreads();
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= A.spitch) return;
+    int64_t ra, c;
+    if (k == 0) { ra = 0; c = j; }
+    else if (j == 0) { ra = kr; c = 0; }
+    else { ra = kr - 1; c = j - 1; }
+    double s = 0.0;
+    if (c < A.nl && ra < A.nl) {
+        const double muc = A.mu[c];
+        if (ra == a) {
+            for (int t = 0; t < l; ++t) s = fma(arow[t], A.x[c + t] - muc, s);
+        } else {
+            const double mur = A.mu[ra];
+            for (int t = 0; t < l; ++t) s = fma(A.x[ra + t] - mur, A.x[c + t] - muc, s);
+        }
+    }
+    A.seed[(int64_t)k * A.spitch + j] = s;
+}
+
+// FP32 seeds: the row window is centred in FP64 and rounded; the column
+// windows are shifted by one constant per block of columns (close to their
+// means) and rounded; the dot product runs in FP32 and the shift is removed
+// exactly to first order with the FP32 sum of the rounded row window.
+template <>
+__global__ void k_seed<float>(SeedArgs<float> A)
+{
+    extern __shared__ float sh_f[];
+    const int l = A.l;
+    const int B = blockDim.x;
+    float *arow = sh_f;                   // l
+    float *ycol = sh_f + l;               // B + l
+    __shared__ float s_asum;
+    const int k = A.krows[blockIdx.y];
+    const int64_t kr = (int64_t)k * A.R;
+    const int64_t a = (k == 0) ? 0 : kr - 1;
+    const int64_t jb = (int64_t)blockIdx.x * B;
+    // first column window of this block and its shift
+    const int64_t cb = (k == 0) ? jb : (jb > 0 ? jb - 1 : 0);
+    const int64_t cshift = cb < A.nl ? cb : A.nl - 1;
+    const double shift = A.mu[cshift];
+    const double mua = A.mu[a];
+    for (int t = threadIdx.x; t < l; t += B) arow[t] = (float)(A.x[a + t] - mua);
+    for (int u = threadIdx.x; u < B + l; u += B) {
+        const int64_t idx = cb + u;
+        ycol[u] = idx < A.nl + l - 1 ? (float)(A.x[idx] - shift) : 0.0f;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float s = 0.0f;
+        for (int t = threadIdx.x; t < l; t += 32) s += arow[t];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) s_asum = s;
+    }
+    __syncthreads();
+    const int64_t j = jb + threadIdx.x;
+    if (j >= A.spitch) return;
+    int64_t ra, c;
+    if (k == 0) { ra = 0; c = j; }
+    else if (j == 0) { ra = kr; c = 0; }
+    else { ra = kr - 1; c = j - 1; }
+    float out = 0.0f;
+    if (c < A.nl && ra < A.nl) {
+        if (ra == a) {
+            const float *y = ycol + (c - cb);
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+            int t = 0;
+            for (; t + 3 < l; t += 4) {
+                s0 = fmaf(arow[t], y[t], s0);
+                s1 = fmaf(arow[t + 1], y[t + 1], s1);
+                s2 = fmaf(arow[t + 2], y[t + 2], s2);
+                s3 = fmaf(arow[t + 3], y[t + 3], s3);
+            }
+            for (; t < l; ++t) s0 = fmaf(arow[t], y[t], s0);
+            const double corr = (double)s_asum * (A.mu[c] - shift);
+            out = (float)(((double)s0 + (double)s1) + ((double)s2 + (double)s3) - corr);
+        } else {
+            // the single (kR, 0) entry: direct FP64
+            const double mur = A.mu[ra], muc = A.mu[c];
+            double s = 0.0;
+            for (int t = 0; t < l; ++t) s = fma(A.x[ra + t] - mur, A.x[c + t] - muc, s);
+            out = (float)s;
+        }
+    }
+    A.seed[(int64_t)k * A.spitch + j] = out;
+}
+
+template <typename T>
+void launch_seed(const SeedArgs<T> &a, cudaStream_t s)
+{
+    const int B = 256;
+    dim3 grid((unsigned)((a.spitch + B - 1) / B), (unsigned)a.nk);
+    size_t sm = sizeof(T) == 8 ? sizeof(double) * a.l : sizeof(float) * (2 * a.l + B);
+    k_seed<T><<<grid, B, sm, s>>>(a);
+}
+template void launch_seed<float>(const SeedArgs<float> &, cudaStream_t);
+template void launch_seed<double>(const SeedArgs<double> &, cudaStream_t);
+
+// ------------------------------------------------------------- band kernel
+
+template <typename T> __device__ __forceinline__ T neg_inf();
+template <> __device__ __forceinline__ float neg_inf<float>() { return -__int_as_float(0x7f800000); }
+template <> __device__ __forceinline__ double neg_inf<double>() { return -__longlong_as_double(0x7ff0000000000000LL); }
+
+__device__ __forceinline__ float to_float_rd(float v) { return v; }
+__device__ __forceinline__ float to_float_rd(double v) { return __double2float_rd(v); }
+
+// IEEE maxNum: a NaN operand (a padded column) is ignored.
+__device__ __forceinline__ float fmax_t(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double fmax_t(double a, double b) { return fmax(a, b); }
+
+template <typename T, int RPL, int NW, bool BINS, bool DIAG>
+__device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *cbuf, T tp, T *bout, int lane, int w,
+                                           int64_t cs, int64_t rbase, T (&C)[RPL], const T (&dfr)[RPL],
+                                           const T (&dgr)[RPL], const T (&th)[RPL], T (&runmax)[RPL])
+{
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        const Col<T> cd = cbuf[c];
+        T v = __shfl_up_sync(0xffffffffu, C[RPL - 1], 1);
+        const T vt = __shfl_sync(0xffffffffu, tp, c);
+        if (lane == 0) v = vt;
+#pragma unroll
+        for (int a = RPL - 1; a >= 1; --a) C[a] = fma(dfr[a], cd.dg, fma(cd.df, dgr[a], C[a - 1]));
+        C[0] = fma(dfr[0], cd.dg, fma(cd.df, dgr[0], v));
+        if (w < NW - 1 && lane == 31) bout[c] = C[RPL - 1];
+        const int64_t j = cs + c;
+        if (!BINS) {
+            bool hit = false;
+#pragma unroll
+            for (int a = 0; a < RPL; ++a) {
+                bool h = C[a] * cd.inv > th[a];
+                if (DIAG) h = h && nontrivial(rbase + a, j, A.E);
+                hit |= h;
+            }
+            if (hit) {
+#pragma unroll
+                for (int a = 0; a < RPL; ++a) {
+                    const T key = C[a] * cd.inv;
+                    if (key > th[a] && nontrivial(rbase + a, j, A.E)) {
+                        const int64_t r = rbase + a;
+                        const int slot = atomicAdd(&A.ccnt[r], 1);
+                        if (slot < A.cap) {
+                            A.ckey[r * A.cap + slot] = key;
+                            A.cj[r * A.cap + slot] = (int32_t)j;
+                        }
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < RPL; ++a) {
+                T key = C[a] * cd.inv;
+                if (DIAG && !nontrivial(rbase + a, j, A.E)) key = neg_inf<T>();
+                runmax[a] = fmax_t(runmax[a], key);   // NaN keys (padding) are ignored
+            }
+        }
+    }
+}
+
+template <typename T, int RPL, int NW, bool BINS>
+__global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
+{
+    constexpr int R = 32 * RPL * NW;
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    Col<T> *colbuf = reinterpret_cast<Col<T> *>(smem_raw);        // [NW][CH]
+    T *bbuf = reinterpret_cast<T *>(colbuf + NW * CH);             // [NW][2][CH]
+    int *sbins = reinterpret_cast<int *>(bbuf + NW * 2 * CH);      // [R][p] (bins mode)
+    __shared__ int s_unit;
+
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nb = *A.nbands;
+    const int64_t total = (int64_t)nb * A.ngroups;
+    const int NEG_ORD = f2ord(-__int_as_float(0x7f800000));
+
+    if (BINS)
+        for (int t = threadIdx.x; t < R * A.p; t += blockDim.x) sbins[t] = NEG_ORD;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_unit = atomicAdd(A.unit_ctr, 1);
+        __syncthreads();
+        const int64_t u = s_unit;
+        __syncthreads();
+        if (u >= total) break;
+        const int g = (int)(u / nb);
+        const int band = A.bands[u % nb];
+        const int64_t i0 = (int64_t)band * R;
+        const int64_t c0 = (int64_t)g * A.group_w;
+        if (c0 >= A.nl) continue;
+        const int64_t c1 = c0 + A.group_w < A.nl ? c0 + A.group_w : A.nl;
+        const int nchunk = (int)((c1 - c0 + CH - 1) / CH);
+        const int64_t rfirst = i0 + (int64_t)w * 32 * RPL;
+        const int64_t rbase = rfirst + lane * RPL;
+        const T *sleft = A.seed + (c0 / R) * A.spitch;
+        const T *stop = A.seed + (int64_t)band * A.spitch;
+
+        T C[RPL], dfr[RPL], dgr[RPL], th[RPL], runmax[RPL];
+#pragma unroll
+        for (int a = 0; a < RPL; ++a) {
+            const int64_t r = rbase + a;
+            const Col<T> cr = A.col[r];
+            dfr[a] = cr.df;
+            dgr[a] = cr.dg;
+            th[a] = A.thr[r];
+            C[a] = sleft[r + 1];
+            runmax[a] = neg_inf<T>();
+        }
+        T carry = sleft[rfirst];
+
+        for (int s = 0; s < nchunk + NW - 1; ++s) {
+            const int q = s - w;
+            if (q >= 0 && q < nchunk) {
+                const int64_t cs = c0 + (int64_t)q * CH;
+                Col<T> *cbuf = colbuf + w * CH;
+                cbuf[lane] = A.col[cs + lane];
+                T tp;
+                if (w == 0) {
+                    tp = stop[cs + lane];
+                } else {
+                    const T *bb = bbuf + (w * 2 + (q & 1)) * CH;
+                    const T prev = bb[lane == 0 ? 0 : lane - 1];
+                    tp = lane == 0 ? carry : prev;
+                    carry = bb[CH - 1];
+                }
+                __syncwarp();
+                T *bout = bbuf + ((w + 1 < NW ? w + 1 : 0) * 2 + (q & 1)) * CH;
+                // does this warp's row range meet the exclusion zone in this chunk?
+                const int64_t rlo = rfirst, rhi = rfirst + 32 * RPL - 1;
+                const bool diag = (cs <= rhi + A.E) && (cs + CH - 1 >= rlo - A.E);
+                if (diag)
+                    band_chunk<T, RPL, NW, BINS, true>(A, cbuf, tp, bout, lane, w, cs, rbase, C, dfr, dgr, th, runmax);
+                else
+                    band_chunk<T, RPL, NW, BINS, false>(A, cbuf, tp, bout, lane, w, cs, rbase, C, dfr, dgr, th, runmax);
+                if (BINS) {
+                    const int bin = (int)((cs / CH) % A.p);
+#pragma unroll
+                    for (int a = 0; a < RPL; ++a) {
+                        atomicMax(&sbins[(w * 32 * RPL + lane * RPL + a) * A.p + bin], f2ord(to_float_rd(runmax[a])));
+                        runmax[a] = neg_inf<T>();
+                    }
+                }
+                __syncwarp();
+            }
+            __syncthreads();
+        }
+        if (BINS) {
+            for (int t = threadIdx.x; t < R * A.p; t += blockDim.x) {
+                const int64_t r = i0 + t / A.p;
+                if (r < A.nl && sbins[t] != NEG_ORD) atomicMax(&A.bins[r * A.p + (t % A.p)], sbins[t]);
+                sbins[t] = NEG_ORD;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <typename T>
+size_t band_smem(bool bins_mode, int p)
+{
+    constexpr int RPL = BandGeo<T>::RPL, NW = BandGeo<T>::NW;
+    size_t s = (size_t)NW * CH * sizeof(Col<T>) + (size_t)NW * 2 * CH * sizeof(T);
+    if (bins_mode) s += (size_t)32 * RPL * NW * p * sizeof(int);
+    return s;
+}
+
+template <typename T>
+static void *band_fn(bool bins)
+{
+    constexpr int RPL = BandGeo<T>::RPL, NW = BandGeo<T>::NW;
+    return bins ? (void *)k_band<T, RPL, NW, true> : (void *)k_band<T, RPL, NW, false>;
+}
+
+template <typename T>
+int band_occupancy(bool bins_mode, int p)
+{
+    constexpr int NW = BandGeo<T>::NW;
+    const void *fn = band_fn<T>(bins_mode);
+    const size_t sm = band_smem<T>(bins_mode, p);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int blocks = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, NW * 32, sm);
+    return blocks;
+}
+
+template <typename T>
+void launch_band(const BandArgs<T> &a, bool bins_mode, int grid, cudaStream_t s)
+{
+    constexpr int RPL = BandGeo<T>::RPL, NW = BandGeo<T>::NW;
+    const size_t sm = band_smem<T>(bins_mode, a.p);
+    if (bins_mode) {
+        cudaFuncSetAttribute(k_band<T, RPL, NW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_band<T, RPL, NW, true><<<grid, NW * 32, sm, s>>>(a);
+    } else {
+        cudaFuncSetAttribute(k_band<T, RPL, NW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_band<T, RPL, NW, false><<<grid, NW * 32, sm, s>>>(a);
+    }
+}
+
+template void launch_band<float>(const BandArgs<float> &, bool, int, cudaStream_t);
+template void launch_band<double>(const BandArgs<double> &, bool, int, cudaStream_t);
+template int band_occupancy<float>(bool, int);
+template int band_occupancy<double>(bool, int);
+template size_t band_smem<float>(bool, int);
+template size_t band_smem<double>(bool, int);
+
+}  // namespace mad

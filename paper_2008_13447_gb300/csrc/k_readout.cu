@@ -1,0 +1,343 @@
+// k_readout.cu -- discord table per length (Sec. 6: dkm_l and its merge into
+// dkm_{lmin,lmax}, Algorithms 8 and 9), top-k motif pairs from VALMP
+// (Sec. 3 length normalisation, Algorithm 5's best pairs), and FP64 re-checks
+// of the reported distances.
+#include "kernels.cuh"
+
+namespace mad {
+
+__device__ __forceinline__ double ninf() { return -__longlong_as_double(0x7ff0000000000000LL); }
+__device__ __forceinline__ double dinf() { return __longlong_as_double(0x7ff0000000000000LL); }
+
+// (v, i) ordering for discords: larger v first, then smaller i.
+__device__ __forceinline__ bool better_desc(double v, int32_t i, double w, int32_t j)
+{
+    return v > w || (v == w && i >= 0 && (j < 0 || i < j));
+}
+// (v, i) ordering for motifs: smaller v first, then smaller i.
+__device__ __forceinline__ bool better_asc(double v, int32_t i, double w, int32_t j)
+{
+    return v < w || (v == w && i >= 0 && (j < 0 || i < j));
+}
+
+template <bool DESC>
+__device__ void block_best(double &v, int32_t &i)
+{
+    __shared__ double sv[32];
+    __shared__ int32_t si[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        const double w = __shfl_xor_sync(0xffffffffu, v, o);
+        const int32_t j = __shfl_xor_sync(0xffffffffu, i, o);
+        if (DESC ? better_desc(w, j, v, i) : better_asc(w, j, v, i)) { v = w; i = j; }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) { sv[wid] = v; si[wid] = i; }
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < nw ? sv[lane] : (DESC ? ninf() : dinf());
+        i = lane < nw ? si[lane] : -1;
+        for (int o = 16; o > 0; o >>= 1) {
+            const double w = __shfl_xor_sync(0xffffffffu, v, o);
+            const int32_t j = __shfl_xor_sync(0xffffffffu, i, o);
+            if (DESC ? better_desc(w, j, v, i) : better_asc(w, j, v, i)) { v = w; i = j; }
+        }
+        if (lane == 0) { sv[0] = v; si[0] = i; }
+    }
+    __syncthreads();
+    v = sv[0];
+    i = si[0];
+    __syncthreads();
+}
+
+// ------------------------------------------------------------- discords
+
+constexpr int DBLK = 256;
+
+// Per block of DBLK offsets and column m: the best (score desc, offset asc)
+// m-th best-match distance. Offsets without an m-th best match are skipped.
+__global__ void k_disc_blockmax(const double *nnd, int64_t n0, int64_t nl, int nblk, double *bval, int32_t *bidx)
+{
+    const int m = blockIdx.y, b = blockIdx.x;
+    const int64_t i = (int64_t)b * DBLK + threadIdx.x;
+    double v = ninf();
+    int32_t ix = -1;
+    if (i < nl) {
+        const double s = nnd[m * n0 + i];
+        if (isfinite(s)) { v = s; ix = (int32_t)i; }
+    }
+    block_best<true>(v, ix);
+    if (threadIdx.x == 0) {
+        bval[m * nblk + b] = v;
+        bidx[m * nblk + b] = ix;
+    }
+}
+
+// Column m of dkm_l by greedy selection: repeatedly take the best remaining
+// offset and exclude every offset within E(l) of it (the picks of a length
+// must not be trivial matches of one another); then merge rank by rank into
+// dkm_{lmin,lmax}, keeping the largest dist / sqrt(l) and letting a later
+// (longer) length win ties (Algorithm 9's ">=").
+__global__ void k_disc_greedy(const double *nnd, const int32_t *nnj, int64_t n0, int64_t nl, int l, int64_t E,
+                              int k_max, int m_max, const double *bval, const int32_t *bidx, int nblk, DiscTable tab)
+{
+    extern __shared__ unsigned char sm_raw[];
+    double *bv = reinterpret_cast<double *>(sm_raw);
+    int32_t *bi = reinterpret_cast<int32_t *>(bv + nblk);
+    __shared__ int32_t picks[KMAX];
+    const int m = blockIdx.x;
+    const double *score = nnd + (int64_t)m * n0;
+    for (int t = threadIdx.x; t < nblk; t += blockDim.x) {
+        bv[t] = bval[m * nblk + t];
+        bi[t] = bidx[m * nblk + t];
+    }
+    __syncthreads();
+    const double f = sqrt((double)l);
+    for (int r = 0; r < k_max; ++r) {
+        double v = ninf();
+        int32_t g = -1;
+        for (int t = threadIdx.x; t < nblk; t += blockDim.x)
+            if (better_desc(bv[t], bi[t], v, g)) { v = bv[t]; g = bi[t]; }
+        block_best<true>(v, g);
+        if (g < 0) break;
+        if (threadIdx.x == 0) {
+            picks[r] = g;
+            const int cell = r * m_max + m;
+            const double d = score[g];
+            const double nd = d / f;
+            if (tab.len[cell] == 0 || nd >= tab.norm[cell]) {
+                tab.norm[cell] = nd;
+                tab.dist[cell] = d;
+                tab.off[cell] = g;
+                tab.len[cell] = l;
+                tab.nn[cell] = nnj[(int64_t)m * n0 + g];
+            }
+        }
+        __syncthreads();
+        // refresh the blocks that meet [g - E, g + E]
+        const int64_t lo = g - E < 0 ? 0 : g - E;
+        const int64_t hi = g + E >= nl ? nl - 1 : g + E;
+        for (int64_t blk = lo / DBLK; blk <= hi / DBLK; ++blk) {
+            double w = ninf();
+            int32_t wi = -1;
+            if (threadIdx.x < DBLK) {
+                const int64_t e = blk * DBLK + threadIdx.x;
+                if (e < nl) {
+                    bool free = true;
+                    for (int q = 0; q <= r; ++q) {
+                        const int64_t d = e - picks[q];
+                        free &= (d > E || -d > E);
+                    }
+                    const double s = score[e];
+                    if (free && isfinite(s)) { w = s; wi = (int32_t)e; }
+                }
+            }
+            block_best<true>(w, wi);
+            if (threadIdx.x == 0) { bv[blk] = w; bi[blk] = wi; }
+            __syncthreads();
+        }
+    }
+}
+
+void launch_discords_length(const double *nnd, const int32_t *nnj, int64_t n0, int64_t nl, int l, int64_t E,
+                            int k_max, int m_max, double *bval, int32_t *bidx, DiscTable tab, cudaStream_t s)
+{
+    const int nblk = (int)((nl + DBLK - 1) / DBLK);
+    k_disc_blockmax<<<dim3(nblk, m_max), DBLK, 0, s>>>(nnd, n0, nl, nblk, bval, bidx);
+    const size_t sm = (size_t)nblk * (sizeof(double) + sizeof(int32_t));
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_disc_greedy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_disc_greedy<<<m_max, 1024, sm, s>>>(nnd, nnj, n0, nl, l, E, k_max, m_max, bval, bidx, nblk, tab);
+}
+
+// --------------------------------------------------------------- motifs
+
+// One greedy round over VALMP: the best (normalised distance asc, offset asc)
+// entry whose pair {i, nn_i} does not come within max(E(len), E(len')) of an
+// accepted pair. acc holds (a, b, len) of the r accepted pairs.
+__global__ void k_motif_blockmin(Valmp vm, int64_t n0, int num, int den, const int32_t *acc, int r, double *bval,
+                                 int32_t *bidx)
+{
+    const int64_t i = (int64_t)blockIdx.x * DBLK + threadIdx.x;
+    double v = dinf();
+    int32_t ix = -1;
+    if (i < n0 && vm.len[i] > 0 && vm.nn[i] >= 0 && isfinite(vm.norm[i])) {
+        const int64_t a = i, b = vm.nn[i];
+        const int L = vm.len[i];
+        bool ok = true;
+        for (int q = 0; q < r && ok; ++q) {
+            const int64_t a2 = acc[3 * q], b2 = acc[3 * q + 1];
+            int64_t E = excl_zone(L, num, den), E2 = excl_zone(acc[3 * q + 2], num, den);
+            if (E2 > E) E = E2;
+            ok = llabs(a - a2) > E && llabs(a - b2) > E && llabs(b - a2) > E && llabs(b - b2) > E;
+        }
+        if (ok) { v = vm.norm[i]; ix = (int32_t)i; }
+    }
+    block_best<false>(v, ix);
+    if (threadIdx.x == 0) {
+        bval[blockIdx.x] = v;
+        bidx[blockIdx.x] = ix;
+    }
+}
+
+__global__ void k_motif_pick(Valmp vm, const double *bval, const int32_t *bidx, int nblk, int32_t *acc, int r,
+                             int32_t *picked)
+{
+    double v = dinf();
+    int32_t g = -1;
+    for (int t = threadIdx.x; t < nblk; t += blockDim.x)
+        if (better_asc(bval[t], bidx[t], v, g)) { v = bval[t]; g = bidx[t]; }
+    block_best<false>(v, g);
+    if (threadIdx.x == 0) {
+        picked[r] = g;
+        if (g >= 0) {
+            const int32_t nn = vm.nn[g];
+            acc[3 * r] = g < nn ? g : nn;
+            acc[3 * r + 1] = g < nn ? nn : g;
+            acc[3 * r + 2] = vm.len[g];
+        }
+    }
+}
+
+void launch_motif_round(const Valmp &vm, int64_t n0, int num, int den, int32_t *acc, int r, double *bval,
+                        int32_t *bidx, int32_t *picked, cudaStream_t s)
+{
+    const int nblk = (int)((n0 + DBLK - 1) / DBLK);
+    k_motif_blockmin<<<nblk, DBLK, 0, s>>>(vm, n0, num, den, acc, r, bval, bidx);
+    k_motif_pick<<<1, 1024, 0, s>>>(vm, bval, bidx, nblk, acc, r, picked);
+}
+
+// --------------------------------------------------------------- re-checks
+
+__device__ double block_sum(double v)
+{
+    __shared__ double sh[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    v = 0.0;
+    if (wid == 0) {
+        v = lane < nw ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[0] = v;
+    }
+    __syncthreads();
+    v = sh[0];
+    __syncthreads();
+    return v;
+}
+
+__device__ bool window_flat(const double *x, int64_t i, int l)
+{
+    int diff = 0;
+    for (int t = threadIdx.x + 1; t < l; t += blockDim.x) diff |= (x[i + t] != x[i]);
+    return !__syncthreads_or(diff);
+}
+
+// Eq. DIST for windows a, b at length L straight from two-pass statistics and
+// the centred dot product, in FP64 (one block per pair).
+__device__ double direct_dist(const double *x, int64_t a, int64_t b, int L)
+{
+    const bool fa = window_flat(x, a, L), fb = window_flat(x, b, L);
+    if (fa || fb) return (fa && fb) ? 0.0 : sqrt(2.0 * L);
+    double sa = 0.0, sb = 0.0;
+    for (int t = threadIdx.x; t < L; t += blockDim.x) { sa += x[a + t]; sb += x[b + t]; }
+    const double ma = block_sum(sa) / L, mb = block_sum(sb) / L;
+    double va = 0.0, vb = 0.0, cab = 0.0;
+    for (int t = threadIdx.x; t < L; t += blockDim.x) {
+        const double da = x[a + t] - ma, db = x[b + t] - mb;
+        va = fma(da, da, va);
+        vb = fma(db, db, vb);
+        cab = fma(da, db, cab);
+    }
+    va = block_sum(va);
+    vb = block_sum(vb);
+    cab = block_sum(cab);
+    double q = cab / sqrt(va * vb);
+    q = q > 1.0 ? 1.0 : (q < -1.0 ? -1.0 : q);
+    return sqrt(2.0 * L * (1.0 - q));
+}
+
+__global__ void k_recheck_pairs(const double *x, const int32_t *pairs, double *out)
+{
+    const int64_t a = pairs[3 * blockIdx.x], b = pairs[3 * blockIdx.x + 1];
+    const int L = pairs[3 * blockIdx.x + 2];
+    const double d = direct_dist(x, a, b, L);
+    if (threadIdx.x == 0) out[blockIdx.x] = d;
+}
+
+void launch_recheck_pairs(const double *x, int64_t n, const int32_t *pairs, int npairs, double *out, cudaStream_t s)
+{
+    (void)n;
+    if (npairs > 0) k_recheck_pairs<<<npairs, 256, 0, s>>>(x, pairs, out);
+}
+
+// m-th best-match distance of window `off` at length L from a full FP64
+// distance profile (two-pass statistics for every window), one block per
+// cell. Each thread keeps its own m smallest (distance, offset) pairs; the
+// block then extracts the overall m smallest one at a time.
+__global__ void k_recheck_discords(const double *x, int64_t n, const int32_t *cells, int num, int den, double *out)
+{
+    const int64_t off = cells[3 * blockIdx.x];
+    const int L = cells[3 * blockIdx.x + 1];
+    const int m = cells[3 * blockIdx.x + 2];
+    const int64_t nl = n - L + 1;
+    const int64_t E = excl_zone(L, num, den);
+    const bool fo = window_flat(x, off, L);
+    double so = 0.0;
+    for (int t = threadIdx.x; t < L; t += blockDim.x) so += x[off + t];
+    const double mo = block_sum(so) / L;
+    double vo = 0.0;
+    for (int t = threadIdx.x; t < L; t += blockDim.x) { const double d = x[off + t] - mo; vo = fma(d, d, vo); }
+    vo = block_sum(vo);
+    double best[MAXP];
+    int32_t bj[MAXP];
+    int nb = 0;
+    for (int64_t j = threadIdx.x; j < nl; j += blockDim.x) {
+        const int64_t dd = j - off;
+        if (!(dd > E || -dd > E)) continue;
+        double s = 0.0;
+        bool fj = true;
+        for (int t = 0; t < L; ++t) { s += x[j + t]; fj &= (x[j + t] == x[j]); }
+        double d;
+        if (fo || fj) {
+            d = (fo && fj) ? 0.0 : sqrt(2.0 * L);
+        } else {
+            const double mj = s / L;
+            double vj = 0.0, c = 0.0;
+            for (int t = 0; t < L; ++t) {
+                const double a = x[j + t] - mj;
+                vj = fma(a, a, vj);
+                c = fma(x[off + t] - mo, a, c);
+            }
+            double q = c / sqrt(vo * vj);
+            q = q > 1.0 ? 1.0 : (q < -1.0 ? -1.0 : q);
+            d = sqrt(2.0 * L * (1.0 - q));
+        }
+        if (nb < m || d < best[m - 1]) {
+            int b = nb < m ? nb++ : m - 1;
+            while (b > 0 && best[b - 1] > d) { best[b] = best[b - 1]; bj[b] = bj[b - 1]; --b; }
+            best[b] = d;
+            bj[b] = (int32_t)j;
+        }
+    }
+    int head = 0;
+    double res = dinf();
+    for (int r = 0; r < m; ++r) {
+        double v = head < nb ? best[head] : dinf();
+        int32_t ix = head < nb ? bj[head] : -1;
+        block_best<false>(v, ix);
+        if (head < nb && bj[head] == ix && ix >= 0) ++head;
+        res = v;
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = res;
+}
+
+void launch_recheck_discords(const double *x, int64_t n, const int32_t *cells, int ncells, int num, int den,
+                             double *out, cudaStream_t s)
+{
+    if (ncells > 0) k_recheck_discords<<<ncells, 256, 0, s>>>(x, n, cells, num, den, out);
+}
+
+}  // namespace mad

@@ -1,0 +1,465 @@
+// k_rows.cu -- per-row work of each length: extension of the stored entries
+// and the bound test (Algorithm 4 / Algorithm 10 row loops), selection of the
+// new top-p after a recompute (Algorithm 3's heap of p smallest lower
+// bounds), the flat-window rows, and the compaction of rows to recompute.
+//
+// All per-row arithmetic is FP64; one thread handles one row (rows are
+// independent, the per-row state is stored structure-of-arrays so that a
+// warp's accesses are coalesced).
+#include "kernels.cuh"
+
+namespace mad {
+
+__device__ __forceinline__ double pinf() { return __longlong_as_double(0x7ff0000000000000LL); }
+
+// Insert (q, j) into arrays sorted by q descending, j ascending; n entries.
+__device__ __forceinline__ void ins_qj(double *qs, int32_t *js, int n, double q, int32_t j)
+{
+    int t = n;
+    while (t > 0 && (qs[t - 1] < q || (qs[t - 1] == q && js[t - 1] > j))) {
+        qs[t] = qs[t - 1];
+        js[t] = js[t - 1];
+        --t;
+    }
+    qs[t] = q;
+    js[t] = j;
+}
+
+// Algorithm 2 (updateVALMP) for one row: strict improvement of the
+// length-normalised distance; lengths ascend, so ties keep the shorter one.
+__device__ __forceinline__ void valmp_update(const Valmp &vm, int64_t i, double d, int32_t j, int l)
+{
+    const double nd = d * sqrt(1.0 / l);
+    if (vm.len[i] == 0 || nd < vm.norm[i]) {
+        vm.dist[i] = d;
+        vm.norm[i] = nd;
+        vm.len[i] = l;
+        vm.nn[i] = j;
+    }
+}
+
+// Write the row's m-th best matches (entries sorted by distance ascending).
+__device__ __forceinline__ void write_nn(const LenOut &o, int64_t n0, int64_t i, int m_max, const double *d,
+                                         const int32_t *j, int cnt)
+{
+    for (int m = 0; m < m_max; ++m) {
+        o.nnd[m * n0 + i] = m < cnt ? d[m] : pinf();
+        o.nnj[m * n0 + i] = m < cnt ? j[m] : -1;
+    }
+}
+
+
+// Exact FP64 centred co-moment of windows i and j at length l.
+__device__ double comoment(const double *x, int64_t i, int64_t j, int l, double mui, double muj)
+{
+    double s = 0.0;
+    for (int t = 0; t < l; ++t) s = fma(x[i + t] - mui, x[j + t] - muj, s);
+    return s;
+}
+
+// ------------------------------------------------------------ extension
+//
+// For one length l > lmin and every row i < n_l:
+//  - each stored entry (j, C) is extended by one Welford co-moment step
+//    C += (l-1)/l (x_{i+l-1} - mu_i(l-1)) (x_{j+l-1} - mu_j(l-1))
+//    (updateDistAndLB); entries that became trivial matches or fell off the
+//    end are dropped for good (they can only stay trivial / out of range);
+//  - the row's bound is B = bnum_i / sigma_i(l) (Eq. LB with the factor
+//    sigma_i(l_b) / sigma_i(l) common to the row, rank preservation);
+//  - the row is certified iff at least m_max entries remain and the m_max-th
+//    smallest distance, evaluated pessimistically (correlation lowered by
+//    the entries' error bound), is strictly below B;
+//  - certified rows write their matrix profile, m-th best matches and VALMP;
+//    the others are flagged for recompute with the threshold
+//    key > (theta_q - dq_band) sqrt(M2_i), theta_q being a proven lower bound
+//    on the row's p-th best correlation at l (the p-th best of p distinct
+//    exactly evaluated partners).
+template <typename T>
+__device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i)
+{
+    const int l = A.l;
+    const int64_t n0 = A.n0, E = A.E;
+    if (A.run[i] >= l) {                 // flat at l: handled by k_flat_rows
+        A.st.flag[i] = ROW_FLAT;
+        A.thr[i] = T(pinf());
+        return 2;
+    }
+    const double m2i = A.m2[i];
+    const double xi = A.x[i + l - 1] - A.mu_prev[i];
+    const double wgt = (l - 1.0) / l;
+
+    double qs[MAXP];
+    int32_t js[MAXP];
+    int cnt = 0;
+    for (int e = 0; e < A.p; ++e) {
+        const int32_t j = A.st.ent_j[e * n0 + i];
+        if (j < 0) continue;
+        if (j >= A.nl || !nontrivial(i, j, E)) {
+            A.st.ent_j[e * n0 + i] = -1;
+            continue;
+        }
+        const double c = fma(wgt * xi, A.x[j + l - 1] - A.mu_prev[j], A.st.ent_c[e * n0 + i]);
+        A.st.ent_c[e * n0 + i] = c;
+        const bool flat_j = A.run[j] >= l;
+        ins_qj(qs, js, cnt, corr(c, m2i, A.m2[j], false, flat_j), j);
+        ++cnt;
+    }
+    const double sig = sqrt(m2i / l);
+    const double B = A.st.bnum[i] / sig;
+    const int m = A.m_max;
+    const bool ok = cnt >= m && dist_from_q(qs[m - 1] - A.dq_entry, l) < B;
+    if (ok) {
+        double ds[MAXP];
+        for (int e = 0; e < cnt; ++e) ds[e] = dist_from_q(qs[e], l);
+        // correlation order is distance order (ties: smaller offset)
+        write_nn(A.out, n0, i, m, ds, js, cnt);
+        valmp_update(A.vm, i, ds[0], js[0], l);
+        A.st.flag[i] = ROW_DONE;
+        A.thr[i] = T(pinf());
+        return 1;
+    }
+    // theta_q: p-th best among p distinct, exactly evaluated partners (the
+    // remaining entries, lowered by their error bound, then partners next
+    // to the exclusion zone evaluated directly in FP64)
+    double qlow[MAXP];
+    int nlow = 0;
+    for (int e = 0; e < cnt; ++e) qlow[nlow++] = qs[e] - A.dq_entry;
+    const int64_t ntc = nontrivial_count(i, A.nl, E);
+    double theta = -pinf();
+    if (ntc > A.p) {
+        const double mui = A.mu[i];
+        for (int64_t t = 1; nlow < A.p && t <= A.nl; ++t) {
+            for (int side = 0; side < 2 && nlow < A.p; ++side) {
+                const int64_t j = side == 0 ? i + E + t : i - E - t;
+                if (j < 0 || j >= A.nl) continue;
+                bool have = false;
+                for (int e = 0; e < cnt; ++e) have |= (js[e] == j);
+                if (have) continue;
+                const bool flat_j = A.run[j] >= l;
+                const double c = flat_j ? 0.0 : comoment(A.x, i, j, l, mui, A.mu[j]);
+                qlow[nlow++] = corr(c, m2i, A.m2[j], false, flat_j);
+            }
+        }
+        if (nlow >= A.p) {
+            for (int a = 1; a < nlow; ++a) {
+                const double v = qlow[a];
+                int b = a;
+                while (b > 0 && qlow[b - 1] < v) { qlow[b] = qlow[b - 1]; --b; }
+                qlow[b] = v;
+            }
+            theta = qlow[A.p - 1] - A.dq_band;
+        }
+    }
+    A.st.flag[i] = ROW_RECOMPUTE;
+    if (theta == -pinf()) {
+        A.thr[i] = T(-pinf());
+    } else {
+        // key units: key = q sqrt(M2_i); never round the threshold upwards
+        const double tk = theta * sqrt(m2i);
+        T tt = T(tk);
+        if ((double)tt > tk) tt = T(tk - fabs(tk) * 1e-6);
+        A.thr[i] = tt;
+    }
+    return 2;
+}
+
+template <typename T>
+__global__ void k_extend(ExtArgs<T> A)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int cat = 0;
+    if (i < A.n0) {
+        if (i >= A.nl) {
+            A.st.flag[i] = ROW_DONE;
+            A.thr[i] = T(pinf());
+        } else {
+            cat = extend_row(A, i);
+        }
+    }
+    const unsigned mask = __activemask();
+    const unsigned b1 = __ballot_sync(mask, cat == 1), b2 = __ballot_sync(mask, cat == 2);
+    if ((threadIdx.x & 31) == __ffs(mask) - 1) {
+        if (b1) atomicAdd(&A.out.stats[1], (unsigned long long)__popc(b1));
+        if (b2) atomicAdd(&A.out.stats[2], (unsigned long long)__popc(b2));
+    }
+}
+
+template <typename T>
+void launch_extend(const ExtArgs<T> &a, cudaStream_t s)
+{
+    const int B = 128;
+    k_extend<T><<<(unsigned)((a.n0 + B - 1) / B), B, 0, s>>>(a);
+}
+template void launch_extend<float>(const ExtArgs<float> &, cudaStream_t);
+template void launch_extend<double>(const ExtArgs<double> &, cudaStream_t);
+
+// ---------------------------------------------------------------- merge
+//
+// After the band kernel: for every row flagged for recompute, select the p
+// largest keys (ties: smaller offset) among its candidates. They are the
+// row's new stored entries at base length l (the p smallest Eq. LB values,
+// Algorithm 3 lines storing into listDP); the row's matrix profile value and
+// m-th best matches at l come from them; the bound numerator is
+// sqrt(l (1 - max(q_p + dq_band, 0)^2)) * sigma_i(l) (+inf when the row has
+// at most p non-trivial partners, all of them stored).
+// A candidate list that overflowed is replaced by a tighter threshold (the
+// p-th best key among the kept candidates, p distinct columns) and the row
+// stays flagged for another pass.
+template <typename T>
+__global__ void k_merge(MergeArgs<T> A)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= A.nl) return;
+    if (A.st.flag[i] != ROW_RECOMPUTE) return;
+    const int l = A.l;
+    const int64_t n0 = A.n0, E = A.E;
+    const int cap = A.cap;
+    const int p = A.p;
+    const int cnt = A.ccnt[i];
+    const int64_t ntc = nontrivial_count(i, A.nl, E);
+    const int need = (int)(ntc < p ? ntc : p);
+    const T *kk = A.ckey + i * cap;
+    const int32_t *jj = A.cj + i * cap;
+
+    if (cnt > cap || cnt < need) {
+        // refill: p-th best key among the kept candidates, or no threshold
+        T th = T(-pinf());
+        if (cnt > cap) {
+            T best[MAXP];
+            int nb = 0;
+            for (int c = 0; c < cap; ++c) {
+                const T v = kk[c];
+                if (nb < p) {
+                    int b = nb++;
+                    while (b > 0 && best[b - 1] < v) { best[b] = best[b - 1]; --b; }
+                    best[b] = v;
+                } else if (v > best[p - 1]) {
+                    int b = p - 1;
+                    while (b > 0 && best[b - 1] < v) { best[b] = best[b - 1]; --b; }
+                    best[b] = v;
+                }
+            }
+            // keys >= best[p-1] are wanted again: threshold one step below it
+            const T v = best[p - 1];
+            th = v - (v > T(0) ? v : -v) * T(1e-6) - T(1e-30);
+            if (!(th > A.thr[i])) th = A.thr[i];
+        }
+        A.thr[i] = th;
+        A.ccnt[i] = 0;
+        atomicAdd(A.overflow, 1u);
+        return;
+    }
+    // top-p by key desc, offset asc
+    T bk[MAXP];
+    int32_t bj[MAXP];
+    int nb = 0;
+    for (int c = 0; c < cnt; ++c) {
+        const T v = kk[c];
+        const int32_t j = jj[c];
+        if (nb == p && !(v > bk[p - 1] || (v == bk[p - 1] && j < bj[p - 1]))) continue;
+        int b = nb < p ? nb++ : p - 1;
+        while (b > 0 && (bk[b - 1] < v || (bk[b - 1] == v && bj[b - 1] > j))) {
+            bk[b] = bk[b - 1];
+            bj[b] = bj[b - 1];
+            --b;
+        }
+        bk[b] = v;
+        bj[b] = j;
+    }
+    const double m2i = A.m2[i];
+    const double sqm2i = sqrt(m2i);
+    double qs[MAXP];
+    int32_t js[MAXP];
+    int nq = 0;
+    for (int e = 0; e < p; ++e) {
+        if (e < nb) {
+            const int32_t j = bj[e];
+            const double inv = (double)A.col[j].inv;
+            const bool flat_j = A.run[j] >= l;
+            const double c = (flat_j || inv == 0.0) ? 0.0 : (double)bk[e] / inv;
+            A.st.ent_j[e * n0 + i] = j;
+            A.st.ent_c[e * n0 + i] = c;
+            ins_qj(qs, js, nq, corr(c, m2i, A.m2[j], false, flat_j), j);
+            ++nq;
+        } else {
+            A.st.ent_j[e * n0 + i] = -1;
+            A.st.ent_c[e * n0 + i] = 0.0;
+        }
+    }
+    double ds[MAXP];
+    for (int e = 0; e < nq; ++e) ds[e] = dist_from_q(qs[e], l);
+    write_nn(A.out, n0, i, A.m_max, ds, js, nq);
+    if (nq > 0) valmp_update(A.vm, i, ds[0], js[0], l);
+    A.st.base[i] = l;
+    const double sig = sqm2i / sqrt((double)l);
+    if (ntc <= p) {
+        A.st.bnum[i] = pinf();
+    } else {
+        double qp = (double)bk[p - 1] / sqm2i + A.dq_band;
+        qp = qp > 1.0 ? 1.0 : (qp < 0.0 ? 0.0 : qp);
+        A.st.bnum[i] = sqrt((double)l * (1.0 - qp * qp)) * sig;
+    }
+    A.st.flag[i] = ROW_DONE;
+    A.thr[i] = T(pinf());
+    A.ccnt[i] = 0;
+}
+
+template <typename T>
+void launch_merge(const MergeArgs<T> &a, cudaStream_t s)
+{
+    const int B = 128;
+    k_merge<T><<<(unsigned)((a.nl + B - 1) / B), B, 0, s>>>(a);
+}
+template void launch_merge<float>(const MergeArgs<float> &, cudaStream_t);
+template void launch_merge<double>(const MergeArgs<double> &, cudaStream_t);
+
+// First threshold at lmin from the interleaved maxima: the smallest of the
+// p bin maxima (p distinct columns) lower-bounds the p-th best key; rows
+// with an empty bin get no threshold.
+template <typename T>
+__global__ void k_theta_bins(const int *bins, int64_t nl, int p, const double *m2, double dq_band, T *thr)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nl) return;
+    float mn = __int_as_float(0x7f800000);
+    for (int b = 0; b < p; ++b) mn = fminf(mn, ord2f(bins[i * p + b]));
+    double th = (double)mn;
+    if (mn == -__int_as_float(0x7f800000) || mn != mn) {
+        thr[i] = T(-pinf());
+        return;
+    }
+    // bins hold keys rounded down; widen by the key error and one FP32 step
+    th -= dq_band * sqrt(m2[i]) + fabs(th) * 1e-6;
+    thr[i] = T(th);
+}
+
+template <typename T>
+void launch_theta_bins(const int *bins, int64_t nl, int p, const double *m2, double dq_band, T *thr, cudaStream_t s)
+{
+    const int B = 256;
+    k_theta_bins<T><<<(unsigned)((nl + B - 1) / B), B, 0, s>>>(bins, nl, p, m2, dq_band, thr);
+}
+template void launch_theta_bins<float>(const int *, int64_t, int, const double *, double, float *, cudaStream_t);
+template void launch_theta_bins<double>(const int *, int64_t, int, const double *, double, double *, cudaStream_t);
+
+// ----------------------------------------------------------- flat rows
+//
+// A flat row correlates 1 with every other flat window and 0 with the rest:
+// its p entries are the first flat non-trivial partners, then the first
+// non-flat ones; its co-moments are exactly 0 and its bound is 0 (recomputed
+// at every length while it stays flat). One warp per row.
+__global__ void k_flat_rows(FlatArgs A)
+{
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= A.nl) return;
+    if (A.st.flag[i] != ROW_FLAT) return;
+    const int l = A.l;
+    const int64_t n0 = A.n0, E = A.E;
+    const int p = A.p;
+    int32_t js[MAXP];
+    double qs[MAXP];
+    int nf = 0;
+    for (int pass = 0; pass < 2 && nf < p; ++pass) {
+        const bool want_flat = pass == 0;
+        for (int64_t base = 0; base < A.nl && nf < p; base += 32) {
+            const int64_t j = base + lane;
+            const bool ok = j < A.nl && nontrivial(i, j, E) && ((A.run[j] >= l) == want_flat);
+            unsigned b = __ballot_sync(0xffffffffu, ok);
+            while (b && nf < p) {
+                const int t = __ffs(b) - 1;
+                b &= b - 1;
+                js[nf] = (int32_t)(base + t);
+                qs[nf] = want_flat ? 1.0 : 0.0;
+                ++nf;
+            }
+        }
+    }
+    if (lane != 0) return;
+    double ds[MAXP];
+    for (int e = 0; e < p; ++e) {
+        A.st.ent_j[e * n0 + i] = e < nf ? js[e] : -1;
+        A.st.ent_c[e * n0 + i] = 0.0;
+    }
+    for (int e = 0; e < nf; ++e) ds[e] = dist_from_q(qs[e], l);
+    write_nn(A.out, n0, i, A.m_max, ds, js, nf);
+    if (nf > 0) valmp_update(A.vm, i, ds[0], js[0], l);
+    A.st.base[i] = l;
+    A.st.bnum[i] = 0.0;
+    A.st.flag[i] = ROW_DONE;
+}
+
+void launch_flat_rows(const FlatArgs &a, cudaStream_t s)
+{
+    const int B = 256;
+    const int64_t thr = a.nl * 32;
+    k_flat_rows<<<(unsigned)((thr + B - 1) / B), B, 0, s>>>(a);
+}
+
+// lmin: every row is recomputed; flat rows go to k_flat_rows.
+__global__ void k_init_flags(const int32_t *run, int64_t n0, int l, int32_t *flag, unsigned long long *stats)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n0) return;
+    flag[i] = run[i] >= l ? ROW_FLAT : ROW_RECOMPUTE;
+    const unsigned mask = __activemask();
+    if ((threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(&stats[2], (unsigned long long)__popc(mask));
+}
+
+// Rows not flagged for recompute take no candidates.
+template <typename T>
+__global__ void k_mask_thr_t(const int32_t *flag, int64_t n0, T *thr)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n0 && flag[i] != ROW_RECOMPUTE) thr[i] = T(pinf());
+}
+template <typename T>
+void launch_mask_thr(const int32_t *flag, int64_t n0, T *thr, cudaStream_t s)
+{
+    k_mask_thr_t<T><<<(unsigned)((n0 + 255) / 256), 256, 0, s>>>(flag, n0, thr);
+}
+template void launch_mask_thr<float>(const int32_t *, int64_t, float *, cudaStream_t);
+template void launch_mask_thr<double>(const int32_t *, int64_t, double *, cudaStream_t);
+
+// ------------------------------------------------------------ compaction
+// Bands (R consecutive rows) holding at least one row to recompute.
+__global__ void k_compact_bands(const int32_t *flag, int64_t nl, int R, int32_t *bands, int32_t *nbands)
+{
+    const int64_t b = blockIdx.x;
+    const int64_t r0 = b * R;
+    int any = 0;
+    for (int64_t r = r0 + threadIdx.x; r < r0 + R && r < nl; r += blockDim.x) any |= (flag[r] == ROW_RECOMPUTE);
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0 && any) {
+        const int slot = atomicAdd(nbands, 1);
+        bands[slot] = (int32_t)b;
+    }
+}
+
+void launch_compact_bands(const int32_t *flag, int64_t nl, int R, int32_t *bands, int32_t *nbands, cudaStream_t s)
+{
+    const int64_t nb = (nl + R - 1) / R;
+    cudaMemsetAsync(nbands, 0, sizeof(int32_t), s);
+    k_compact_bands<<<(unsigned)nb, 256, 0, s>>>(flag, nl, R, bands, nbands);
+}
+
+template <typename T>
+__global__ void k_fill(T *p, int64_t n, T v)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+template <typename T>
+void launch_fill(T *p, int64_t n, T v, cudaStream_t s)
+{
+    if (n <= 0) return;
+    const int B = 256;
+    int64_t g = (n + B - 1) / B;
+    if (g > 65536) g = 65536;
+    k_fill<T><<<(unsigned)g, B, 0, s>>>(p, n, v);
+}
+template void launch_fill<float>(float *, int64_t, float, cudaStream_t);
+template void launch_fill<double>(double *, int64_t, double, cudaStream_t);
+template void launch_fill<int32_t>(int32_t *, int64_t, int32_t, cudaStream_t);
+
+}  // namespace mad

@@ -1,0 +1,177 @@
+// kernels.cuh -- argument structs and declarations of the device kernels.
+#pragma once
+#include "mad_internal.cuh"
+
+namespace mad {
+
+// ---------------------------------------------------------------- k_stats.cu
+__global__ void k_flat_runs(const double *x, int64_t n, int cap, int32_t *run);
+__global__ void k_stats_init(const double *x, int64_t nl, int l, double *mu, double *m2);
+__global__ void k_stats_step(const double *x, int64_t nl, int l, const double *mu_o, const double *m2_o,
+                             double *mu_n, double *m2_n);
+template <typename T>
+void launch_coldata(const double *x, int64_t nl, int64_t npad, int l, const double *mu, const double *m2,
+                    const int32_t *run, Col<T> *col, cudaStream_t s);
+__global__ void k_widen_f32(const float *in, int64_t n, double *out);
+
+// ----------------------------------------------------------------- k_band.cu
+// Seed rows of the diagonal recurrence. Seed row k (band start kR) holds,
+// for every column j, the value that precedes cell (kR, j) on its diagonal:
+//   S_k[j] = C(kR - 1, j - 1)            for k >= 1, j >= 1
+//   S_k[j] = C(kR, j)                    for k == 0 or j == 0
+// (the second line makes the recurrence start exactly at the first row /
+// column, whose virtual predecessors carry df = dg = 0). By symmetry of C,
+// S_k[r] is also the value preceding cell (r, kR), the left edge of column
+// block k. Entries whose column is past the last window are 0.
+template <typename T> struct SeedArgs {
+    const double *x;
+    const double *mu;       // window means at l
+    int64_t nl;
+    int l;
+    int R;
+    const int32_t *krows;   // seed rows to compute
+    int nk;
+    int64_t spitch;         // elements per seed row
+    T *seed;
+};
+template <typename T> void launch_seed(const SeedArgs<T> &a, cudaStream_t s);
+
+template <typename T> struct BandArgs {
+    const Col<T> *col;      // per-window recurrence data, rows and columns
+    const T *seed;          // seed rows (pitch spitch)
+    int64_t spitch;
+    const T *thr;           // per-row key threshold (+inf: row not wanted)
+    const int32_t *bands;   // active band ids
+    const int32_t *nbands;  // number of active bands (device)
+    int32_t *unit_ctr;      // work counter, zero before launch
+    int64_t nl;
+    int l;
+    int64_t E;
+    int64_t group_w;        // columns per work unit (multiple of the band height)
+    int ngroups;
+    // candidate lists (append mode)
+    T *ckey;
+    int32_t *cj;
+    int32_t *ccnt;
+    int cap;
+    // per-row interleaved maxima (bins mode)
+    int *bins;
+    int p;
+};
+template <typename T> void launch_band(const BandArgs<T> &a, bool bins_mode, int grid, cudaStream_t s);
+template <typename T> int band_occupancy(bool bins_mode, int p);
+template <typename T> size_t band_smem(bool bins_mode, int p);
+
+// ----------------------------------------------------------------- k_rows.cu
+// Per-row state kept across lengths (structure of arrays, n0 = n - lmin + 1):
+//   ent_j[e * n0 + i], ent_c[e * n0 + i] : the p stored entries of row i
+//       (partner offset, -1 if empty; centred co-moment at the current length)
+//   base[i]  : length l_b at which the entries were selected
+//   bnum[i]  : bound numerator  sqrt(l_b (1 - max(q_p, 0)^2)) * sigma_i(l_b)
+//              (+inf when every non-trivial partner is stored); the bound at
+//              length l is bnum[i] / sigma_i(l) (Eq. LB, rank preservation)
+struct RowState {
+    int32_t *ent_j;
+    double *ent_c;
+    int32_t *base;
+    double *bnum;
+    int32_t *flag;
+};
+
+struct Valmp {
+    double *dist;
+    double *norm;
+    int32_t *len;
+    int32_t *nn;
+};
+
+struct LenOut {
+    double *nnd;            // [m][n0] m-th best-match distance at the current length
+    int32_t *nnj;           // [m][n0] its offset
+    unsigned long long *stats;  // this length's counters (5)
+};
+
+template <typename T> struct ExtArgs {
+    const double *x;
+    int64_t n0, nl;
+    int l;
+    int64_t E;
+    int p, m_max;
+    const double *mu_prev;  // means at l-1
+    const double *mu;       // means at l
+    const double *m2;       // M2 at l
+    const int32_t *run;
+    RowState st;
+    Valmp vm;
+    LenOut out;
+    T *thr;
+    double dq_entry;        // correlation error bound of stored entries
+    double dq_band;         // correlation error bound of the band kernel's keys
+};
+template <typename T> void launch_extend(const ExtArgs<T> &a, cudaStream_t s);
+
+template <typename T> struct MergeArgs {
+    int64_t n0, nl;
+    int l;
+    int64_t E;
+    int p, m_max, cap;
+    const double *m2;
+    const int32_t *run;
+    const Col<T> *col;
+    const T *ckey;
+    const int32_t *cj;
+    int32_t *ccnt;
+    T *thr;
+    RowState st;
+    Valmp vm;
+    LenOut out;
+    double dq_band;
+    unsigned int *overflow;
+};
+template <typename T> void launch_merge(const MergeArgs<T> &a, cudaStream_t s);
+
+template <typename T>
+void launch_theta_bins(const int *bins, int64_t nl, int p, const double *m2, double dq_band, T *thr,
+                       cudaStream_t s);
+
+struct FlatArgs {
+    int64_t n0, nl;
+    int l;
+    int64_t E;
+    int p, m_max;
+    const int32_t *run;
+    RowState st;
+    Valmp vm;
+    LenOut out;
+};
+void launch_flat_rows(const FlatArgs &a, cudaStream_t s);
+
+__global__ void k_init_flags(const int32_t *run, int64_t n0, int l, int32_t *flag, unsigned long long *stats);
+template <typename T> void launch_mask_thr(const int32_t *flag, int64_t n0, T *thr, cudaStream_t s);
+
+void launch_compact_bands(const int32_t *flag, int64_t nl, int R, int32_t *bands, int32_t *nbands,
+                          cudaStream_t s);
+
+template <typename T>
+void launch_fill(T *p, int64_t n, T v, cudaStream_t s);
+
+// ------------------------------------------------------------- k_readout.cu
+struct DiscTable {          // k_max x m_max cells, rank-major
+    double *norm;
+    double *dist;
+    int32_t *off;
+    int32_t *len;
+    int32_t *nn;
+};
+void launch_discords_length(const double *nnd, const int32_t *nnj, int64_t n0, int64_t nl, int l, int64_t E,
+                            int k_max, int m_max, double *bval, int32_t *bidx, DiscTable tab, cudaStream_t s);
+
+void launch_motif_round(const Valmp &vm, int64_t n0, int num, int den, int32_t *acc /* 3 ints per pick */,
+                        int r, double *bval, int32_t *bidx, int32_t *picked, cudaStream_t s);
+
+void launch_recheck_pairs(const double *x, int64_t n, const int32_t *pairs /* a,b,len */, int npairs,
+                          double *out, cudaStream_t s);
+void launch_recheck_discords(const double *x, int64_t n, const int32_t *cells /* off,len,m */, int ncells,
+                             int num, int den, double *out, cudaStream_t s);
+
+}  // namespace mad

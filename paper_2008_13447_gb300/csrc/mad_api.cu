@@ -1,0 +1,783 @@
+// mad_api.cu -- the C ABI (include/mad.h) and the per-length schedule of the
+// exact variable-length matrix profile (Algorithm 1 VALMOD driving Algorithms
+// 3, 4 and 10, with the discord table of Algorithm 7).
+//
+// Schedule of one profile over [lmin, lmax] (per series):
+//   lmin : window statistics; every row is recomputed: seed rows, an
+//          interleaved-maxima pass for a first per-row threshold, the
+//          candidate pass, selection of each row's top-p entries (repeated
+//          for rows whose candidate list overflowed), flat rows, discords.
+//   l > lmin : one Welford step of the statistics; extension of the stored
+//          entries with the bound test; the same recompute steps for the rows
+//          the bound did not certify; discords.
+// Device memory is owned by the context; PyTorch (or any caller) only
+// supplies the series and the stream.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mad.h"
+#include "kernels.cuh"
+
+using namespace mad;
+
+namespace {
+
+thread_local std::string g_create_err;
+
+struct Series {
+    int64_t n = 0;
+    double *x = nullptr;
+    bool own_x = true;
+    // result of the last profile
+    bool profiled = false;
+    int lmin = 0, lmax = 0, p = 0, m_max = 1, k_max = 10;
+    int64_t n0 = 0;
+    std::vector<void *> allocs;
+    Valmp vm{};
+    DiscTable tab{};
+    double *keep_nnd = nullptr;
+    int32_t *keep_nnj = nullptr;
+    std::vector<mad_length_stats> stats;
+};
+
+}  // namespace
+
+struct mad_ctx {
+    mad_options opt{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    std::vector<Series> series;
+    std::string err;
+};
+
+namespace {
+
+struct Fail {
+    mad_status st;
+};
+
+void set_err(mad_ctx *c, const std::string &m)
+{
+    if (c) c->err = m;
+    else g_create_err = m;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            set_err(ctx, std::string(#call) + ": " + cudaGetErrorString(e_));                      \
+            throw Fail{e_ == cudaErrorMemoryAllocation ? MAD_ENOMEM : MAD_ECUDA};                  \
+        }                                                                                          \
+    } while (0)
+
+#define REQUIRE(cond, msg)                                                                         \
+    do {                                                                                           \
+        if (!(cond)) {                                                                             \
+            set_err(ctx, msg);                                                                     \
+            throw Fail{MAD_EINVAL};                                                                \
+        }                                                                                          \
+    } while (0)
+
+template <typename P>
+P *dalloc(mad_ctx *ctx, Series &s, size_t count)
+{
+    void *p = nullptr;
+    CK(cudaMalloc(&p, count * sizeof(P) > 0 ? count * sizeof(P) : 1));
+    s.allocs.push_back(p);
+    return static_cast<P *>(p);
+}
+
+void free_profile(Series &s)
+{
+    for (void *p : s.allocs) cudaFree(p);
+    s.allocs.clear();
+    s.profiled = false;
+    s.keep_nnd = nullptr;
+    s.keep_nnj = nullptr;
+}
+
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+mad_options defaults(const mad_options *o)
+{
+    mad_options r{};
+    if (o) r = *o;
+    if (r.excl_num == 0 && r.excl_den == 0) { r.excl_num = 1; r.excl_den = 4; }
+    if (r.k_max == 0) r.k_max = 10;
+    if (r.m_max == 0) r.m_max = 1;
+    return r;
+}
+
+void check_options(mad_ctx *ctx, const mad_options &o)
+{
+    REQUIRE(o.excl_num >= 0 && o.excl_den >= 1, "exclusion zone needs excl_num >= 0 and excl_den >= 1");
+    REQUIRE(o.precision == MAD_FP64 || o.precision == MAD_FP32, "precision must be MAD_FP64 or MAD_FP32");
+    REQUIRE(o.k_max >= 1 && o.k_max <= KMAX, "k_max must be in [1, 64]");
+    REQUIRE(o.m_max >= 1 && o.m_max <= MAXP, "m_max must be in [1, 64]");
+    REQUIRE(o.mode == 0, "mode must be 0");
+    REQUIRE(o.reserved == 0, "reserved option field must be 0");
+}
+
+void init_ctx(mad_ctx *ctx, const mad_options *opt)
+{
+    ctx->opt = defaults(opt);
+    check_options(ctx, ctx->opt);
+    ctx->stream = static_cast<cudaStream_t>(ctx->opt.stream);
+    CK(cudaGetDevice(&ctx->device));
+    CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+}
+
+// ------------------------------------------------------------- profile
+
+template <typename T>
+struct Precision;
+template <>
+struct Precision<double> {
+    // Correlation error bounds used by the bound tests and thresholds: FP64
+    // recurrences over at most one band of rows from FP64 seeds.
+    static constexpr double dq_entry = 1e-10, dq_band = 1e-10;
+};
+template <>
+struct Precision<float> {
+    // FP32 recurrence over at most one band (2048 rows) from FP32 seeds.
+    static constexpr double dq_entry = 3e-5, dq_band = 3e-5;
+};
+
+template <typename T>
+void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
+{
+    const mad_options &o = ctx->opt;
+    cudaStream_t st = ctx->stream;
+    const int num = o.excl_num, den = o.excl_den;
+    const int64_t n = s.n;
+    REQUIRE(lmin >= 2 && lmin <= lmax, "need 2 <= lmin <= lmax");
+    REQUIRE((int64_t)lmax < n, "lmax must be smaller than the series length");
+    REQUIRE(p >= 1 && p <= MAXP, "p must be in [1, 64]");
+    REQUIRE(o.m_max <= p, "m_max must not exceed p (the paper's p >= m)");
+    const int64_t Emax = excl_zone(lmax, num, den);
+    REQUIRE(n - lmax + 1 > 2 * Emax + 2, "series too short for lmax and the exclusion zone (need n-lmax+1 > 2E(lmax)+2)");
+    REQUIRE(n < (int64_t)INT32_MAX - 4096, "series longer than 2^31 - 4096 samples");
+
+    free_profile(s);
+    s.lmin = lmin;
+    s.lmax = lmax;
+    s.p = p;
+    s.m_max = o.m_max;
+    s.k_max = o.k_max;
+    const int64_t n0 = n - lmin + 1;
+    s.n0 = n0;
+    const int m_max = o.m_max, k_max = o.k_max;
+    const int nL = lmax - lmin + 1;
+    constexpr int R = band_rows<T>();
+    const int64_t K = (n0 + R - 1) / R;
+    const int64_t npad = round_up(n0, R) + R + CH;
+    const int64_t spitch = round_up(n0, R) + R + CH;
+    const int cap = p * 8 > 32 ? p * 8 : 32;
+
+    // ---- buffers
+    int32_t *run = dalloc<int32_t>(ctx, s, n);
+    double *mu[2] = {dalloc<double>(ctx, s, n0), dalloc<double>(ctx, s, n0)};
+    double *m2[2] = {dalloc<double>(ctx, s, n0), dalloc<double>(ctx, s, n0)};
+    Col<T> *col = dalloc<Col<T>>(ctx, s, npad);
+    T *seed = dalloc<T>(ctx, s, K * spitch);
+    T *thr = dalloc<T>(ctx, s, npad);
+    RowState rs{dalloc<int32_t>(ctx, s, (size_t)p * n0), dalloc<double>(ctx, s, (size_t)p * n0),
+                dalloc<int32_t>(ctx, s, n0), dalloc<double>(ctx, s, n0), dalloc<int32_t>(ctx, s, n0)};
+    Valmp vm{dalloc<double>(ctx, s, n0), dalloc<double>(ctx, s, n0), dalloc<int32_t>(ctx, s, n0),
+             dalloc<int32_t>(ctx, s, n0)};
+    T *ckey = dalloc<T>(ctx, s, (size_t)n0 * cap);
+    int32_t *cj = dalloc<int32_t>(ctx, s, (size_t)n0 * cap);
+    int32_t *ccnt = dalloc<int32_t>(ctx, s, n0);
+    int *bins = dalloc<int>(ctx, s, (size_t)n0 * p);
+    int32_t *bands = dalloc<int32_t>(ctx, s, K);
+    int32_t *counters = dalloc<int32_t>(ctx, s, 4);   // nbands, unit counter, overflow
+    int32_t *krows = dalloc<int32_t>(ctx, s, K);
+    double *nnd = dalloc<double>(ctx, s, (size_t)m_max * n0);
+    int32_t *nnj = dalloc<int32_t>(ctx, s, (size_t)m_max * n0);
+    const int64_t nblk = (n0 + 255) / 256;
+    double *bval = dalloc<double>(ctx, s, (size_t)m_max * nblk);
+    int32_t *bidx = dalloc<int32_t>(ctx, s, (size_t)m_max * nblk);
+    unsigned long long *dstats = dalloc<unsigned long long>(ctx, s, (size_t)nL * 5);
+    DiscTable tab{dalloc<double>(ctx, s, (size_t)k_max * m_max), dalloc<double>(ctx, s, (size_t)k_max * m_max),
+                  dalloc<int32_t>(ctx, s, (size_t)k_max * m_max), dalloc<int32_t>(ctx, s, (size_t)k_max * m_max),
+                  dalloc<int32_t>(ctx, s, (size_t)k_max * m_max)};
+    if (o.keep_profiles) {
+        s.keep_nnd = dalloc<double>(ctx, s, (size_t)nL * m_max * n0);
+        s.keep_nnj = dalloc<int32_t>(ctx, s, (size_t)nL * m_max * n0);
+    }
+    int32_t *nbands_d = counters, *unit_ctr = counters + 1;
+    unsigned int *overflow = reinterpret_cast<unsigned int *>(counters + 2);
+
+    // ---- one-off initialisation
+    {
+        std::vector<int32_t> kr(K);
+        for (int64_t k = 0; k < K; ++k) kr[k] = (int32_t)k;
+        CK(cudaMemcpyAsync(krows, kr.data(), K * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    }
+    CK(cudaMemsetAsync(dstats, 0, (size_t)nL * 5 * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(vm.len, 0, n0 * sizeof(int32_t), st));
+    CK(cudaMemsetAsync(tab.len, 0, (size_t)k_max * m_max * sizeof(int32_t), st));
+    CK(cudaMemsetAsync(ccnt, 0, n0 * sizeof(int32_t), st));
+    CK(cudaMemsetAsync(rs.ent_j, 0xff, (size_t)p * n0 * sizeof(int32_t), st));
+    CK(cudaMemsetAsync(rs.ent_c, 0, (size_t)p * n0 * sizeof(double), st));
+    launch_fill<T>(thr, npad, T(INFINITY), st);
+    k_flat_runs<<<1024, 256, 0, st>>>(s.x, n, lmax, run);
+    k_stats_init<<<(unsigned)((n0 + 255) / 256), 256, 0, st>>>(s.x, n0, lmin, mu[0], m2[0]);
+    CK(cudaGetLastError());
+
+    const int occ_band = band_occupancy<T>(false, p);
+    const int occ_bins = band_occupancy<T>(true, p);
+    REQUIRE(occ_band > 0 && occ_bins > 0, "band kernel does not fit on this device");
+    const int grid_band = ctx->num_sms * occ_band;
+    const int grid_bins = ctx->num_sms * occ_bins;
+    // columns per work unit: a multiple of R, ~8 units per resident CTA when possible
+    int64_t G = (K * K) / (8 * (int64_t)grid_band);
+    if (G < 1) G = 1;
+    if (G > K) G = K;
+    const int64_t group_w = G * R;
+
+    BandArgs<T> ba{};
+    ba.col = col;
+    ba.seed = seed;
+    ba.spitch = spitch;
+    ba.thr = thr;
+    ba.bands = bands;
+    ba.nbands = nbands_d;
+    ba.unit_ctr = unit_ctr;
+    ba.group_w = group_w;
+    ba.ckey = ckey;
+    ba.cj = cj;
+    ba.ccnt = ccnt;
+    ba.cap = cap;
+    ba.bins = bins;
+    ba.p = p;
+
+    int cur = 0;
+    s.stats.assign(nL, mad_length_stats{});
+    std::vector<unsigned long long> host_tiles(nL, 0), host_passes(nL, 0);
+
+    for (int l = lmin; l <= lmax; ++l) {
+        const int li = l - lmin;
+        const int64_t nl = n - l + 1;
+        const int64_t E = excl_zone(l, num, den);
+        LenOut lo{nnd, nnj, dstats + (size_t)li * 5};
+        if (l > lmin) {
+            k_stats_step<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(s.x, nl, l, mu[cur], m2[cur], mu[cur ^ 1],
+                                                                      m2[cur ^ 1]);
+            cur ^= 1;
+        }
+        launch_coldata<T>(s.x, nl, npad, l, mu[cur], m2[cur], run, col, st);
+        CK(cudaGetLastError());
+
+        if (l == lmin) {
+            // every row recomputed; flat rows apart
+            launch_fill<int32_t>(rs.flag, n0, ROW_RECOMPUTE, st);
+            k_init_flags<<<(unsigned)((n0 + 255) / 256), 256, 0, st>>>(run, n0, l, rs.flag, lo.stats);
+        } else {
+            ExtArgs<T> ea{};
+            ea.x = s.x;
+            ea.n0 = n0;
+            ea.nl = nl;
+            ea.l = l;
+            ea.E = E;
+            ea.p = p;
+            ea.m_max = m_max;
+            ea.mu_prev = mu[cur ^ 1];
+            ea.mu = mu[cur];
+            ea.m2 = m2[cur];
+            ea.run = run;
+            ea.st = rs;
+            ea.vm = vm;
+            ea.out = lo;
+            ea.thr = thr;
+            ea.dq_entry = Precision<T>::dq_entry;
+            ea.dq_band = Precision<T>::dq_band;
+            launch_extend<T>(ea, st);
+        }
+        CK(cudaGetLastError());
+
+        launch_compact_bands(rs.flag, nl, R, bands, nbands_d, st);
+        int32_t nb_active = 0;
+        CK(cudaMemcpyAsync(&nb_active, nbands_d, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+
+        if (nb_active > 0) {
+            SeedArgs<T> sa{s.x, mu[cur], nl, l, R, krows, (int)K, spitch, seed};
+            launch_seed<T>(sa, st);
+            ba.nl = nl;
+            ba.l = l;
+            ba.E = E;
+            ba.ngroups = (int)((nl + group_w - 1) / group_w);
+            if (l == lmin) {
+                // first thresholds from interleaved maxima
+                launch_fill<int32_t>(bins, (int64_t)n0 * p, (int32_t)0x807fffff, st);  // ord(-inf)
+                CK(cudaMemsetAsync(unit_ctr, 0, sizeof(int32_t), st));
+                launch_band<T>(ba, true, grid_bins, st);
+                launch_theta_bins<T>(bins, nl, p, m2[cur], Precision<T>::dq_band, thr, st);
+                launch_mask_thr<T>(rs.flag, n0, thr, st);
+                CK(cudaGetLastError());
+            }
+            MergeArgs<T> ma{};
+            ma.n0 = n0;
+            ma.nl = nl;
+            ma.l = l;
+            ma.E = E;
+            ma.p = p;
+            ma.m_max = m_max;
+            ma.cap = cap;
+            ma.m2 = m2[cur];
+            ma.run = run;
+            ma.col = col;
+            ma.ckey = ckey;
+            ma.cj = cj;
+            ma.ccnt = ccnt;
+            ma.thr = thr;
+            ma.st = rs;
+            ma.vm = vm;
+            ma.out = lo;
+            ma.dq_band = Precision<T>::dq_band;
+            ma.overflow = overflow;
+            int passes = 0;
+            for (;;) {
+                CK(cudaMemsetAsync(unit_ctr, 0, sizeof(int32_t), st));
+                CK(cudaMemsetAsync(overflow, 0, sizeof(unsigned int), st));
+                launch_band<T>(ba, false, grid_band, st);
+                launch_merge<T>(ma, st);
+                CK(cudaGetLastError());
+                ++passes;
+                host_tiles[li] += (unsigned long long)nb_active * ba.ngroups;
+                unsigned int ovf = 0;
+                CK(cudaMemcpyAsync(&ovf, overflow, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                if (ovf == 0) break;
+                if (passes >= 64) {
+                    set_err(ctx, "candidate lists kept overflowing");
+                    throw Fail{MAD_EINTERNAL};
+                }
+                launch_compact_bands(rs.flag, nl, R, bands, nbands_d, st);
+                CK(cudaMemcpyAsync(&nb_active, nbands_d, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                if (nb_active == 0) break;
+            }
+            host_passes[li] = passes;
+        }
+        FlatArgs fa{n0, nl, l, E, p, m_max, run, rs, vm, lo};
+        launch_flat_rows(fa, st);
+        launch_discords_length(nnd, nnj, n0, nl, l, E, k_max, m_max, bval, bidx, tab, st);
+        if (o.keep_profiles) {
+            CK(cudaMemcpyAsync(s.keep_nnd + (size_t)li * m_max * n0, nnd, (size_t)m_max * n0 * sizeof(double),
+                               cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(s.keep_nnj + (size_t)li * m_max * n0, nnj, (size_t)m_max * n0 * sizeof(int32_t),
+                               cudaMemcpyDeviceToDevice, st));
+        }
+        CK(cudaGetLastError());
+    }
+    std::vector<unsigned long long> hs((size_t)nL * 5);
+    CK(cudaMemcpyAsync(hs.data(), dstats, hs.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int li = 0; li < nL; ++li) {
+        mad_length_stats &q = s.stats[li];
+        q.len = lmin + li;
+        q.rows = n - (lmin + li) + 1;
+        q.certified = (int64_t)hs[li * 5 + 1];
+        q.recomputed = (int64_t)hs[li * 5 + 2];
+        q.tiles = (int64_t)host_tiles[li];
+        q.passes = (int64_t)host_passes[li];
+    }
+    s.vm = vm;
+    s.tab = tab;
+    s.profiled = true;
+}
+
+Series &get_series(mad_ctx *ctx, int32_t idx)
+{
+    if (idx < 0 || idx >= (int32_t)ctx->series.size()) {
+        set_err(ctx, "series index out of range");
+        throw Fail{MAD_EINVAL};
+    }
+    return ctx->series[idx];
+}
+
+void profile_one(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
+{
+    if (ctx->opt.precision == MAD_FP32) profile_series<float>(ctx, s, lmin, lmax, p);
+    else profile_series<double>(ctx, s, lmin, lmax, p);
+}
+
+template <typename F>
+mad_status run_guarded(mad_ctx *ctx, F &&f)
+{
+    try {
+        if (ctx) {
+            cudaSetDevice(ctx->device);
+            ctx->err.clear();
+        }
+        f();
+        return MAD_OK;
+    } catch (const Fail &e) {
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        set_err(ctx, "host allocation failed");
+        return MAD_ENOMEM;
+    } catch (...) {
+        set_err(ctx, "internal error");
+        return MAD_EINTERNAL;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- the ABI
+
+extern "C" {
+
+MAD_API mad_status mad_create(const double *host_series, int64_t n, const mad_options *opt, mad_ctx **out)
+{
+    if (!out) { g_create_err = "out is NULL"; return MAD_EINVAL; }
+    *out = nullptr;
+    const double *const ser[1] = {host_series};
+    const int64_t ns[1] = {n};
+    return mad_create_batch(ser, ns, 1, opt, out);
+}
+
+MAD_API mad_status mad_create_batch(const double *const *series, const int64_t *n, int32_t count,
+                                    const mad_options *opt, mad_ctx **out)
+{
+    if (!out) { g_create_err = "out is NULL"; return MAD_EINVAL; }
+    *out = nullptr;
+    mad_ctx *c = new (std::nothrow) mad_ctx;
+    if (!c) { g_create_err = "host allocation failed"; return MAD_ENOMEM; }
+    mad_ctx *ctx = nullptr;   // errors before success go to the thread-local message
+    mad_status r = run_guarded(ctx, [&] {
+        REQUIRE(series != nullptr && n != nullptr && count >= 1, "need count >= 1 series");
+        for (int32_t s = 0; s < count; ++s) {
+            REQUIRE(series[s] != nullptr, "series pointer is NULL");
+            REQUIRE(n[s] >= 4, "series needs at least 4 samples");
+        }
+        {
+            mad_options chk = defaults(opt);
+            check_options(ctx, chk);
+        }
+        init_ctx(c, opt);
+        cudaSetDevice(c->device);
+        c->series.resize(count);
+        for (int32_t s = 0; s < count; ++s) {
+            Series &S = c->series[s];
+            S.n = n[s];
+            void *p = nullptr;
+            CK(cudaMalloc(&p, n[s] * sizeof(double)));
+            S.x = static_cast<double *>(p);
+            S.own_x = true;
+            CK(cudaMemcpyAsync(S.x, series[s], n[s] * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        }
+        CK(cudaStreamSynchronize(c->stream));
+    });
+    if (r != MAD_OK) {
+        if (!c->err.empty()) g_create_err = c->err;
+        mad_destroy(c);
+        return r;
+    }
+    *out = c;
+    return MAD_OK;
+}
+
+MAD_API mad_status mad_create_device(const void *dev_series, int32_t dtype, int64_t n, const mad_options *opt,
+                                     mad_ctx **out)
+{
+    if (!out) { g_create_err = "out is NULL"; return MAD_EINVAL; }
+    *out = nullptr;
+    mad_ctx *c = new (std::nothrow) mad_ctx;
+    if (!c) { g_create_err = "host allocation failed"; return MAD_ENOMEM; }
+    mad_ctx *ctx = nullptr;
+    mad_status r = run_guarded(ctx, [&] {
+        REQUIRE(dev_series != nullptr, "device series pointer is NULL");
+        REQUIRE(dtype == 0 || dtype == 1, "dtype must be 0 (FP64) or 1 (FP32)");
+        REQUIRE(n >= 4, "series needs at least 4 samples");
+        {
+            mad_options chk = defaults(opt);
+            check_options(ctx, chk);
+        }
+        init_ctx(c, opt);
+        cudaSetDevice(c->device);
+        c->series.resize(1);
+        Series &S = c->series[0];
+        S.n = n;
+        if (dtype == 0) {
+            S.x = const_cast<double *>(static_cast<const double *>(dev_series));
+            S.own_x = false;
+        } else {
+            void *p = nullptr;
+            CK(cudaMalloc(&p, n * sizeof(double)));
+            S.x = static_cast<double *>(p);
+            S.own_x = true;
+            k_widen_f32<<<256, 256, 0, c->stream>>>(static_cast<const float *>(dev_series), n, S.x);
+            CK(cudaGetLastError());
+        }
+        CK(cudaStreamSynchronize(c->stream));
+    });
+    if (r != MAD_OK) {
+        if (!c->err.empty()) g_create_err = c->err;
+        mad_destroy(c);
+        return r;
+    }
+    *out = c;
+    return MAD_OK;
+}
+
+MAD_API mad_status mad_profile(mad_ctx *ctx, int32_t lmin, int32_t lmax, int32_t p)
+{
+    if (!ctx) { g_create_err = "ctx is NULL"; return MAD_EINVAL; }
+    return run_guarded(ctx, [&] {
+        REQUIRE(ctx->series.size() == 1, "context holds several series: use mad_profile_batch");
+        profile_one(ctx, ctx->series[0], lmin, lmax, p);
+    });
+}
+
+MAD_API mad_status mad_profile_batch(mad_ctx *ctx, const int32_t *lmin, const int32_t *lmax, int32_t p)
+{
+    if (!ctx) { g_create_err = "ctx is NULL"; return MAD_EINVAL; }
+    return run_guarded(ctx, [&] {
+        REQUIRE(lmin != nullptr && lmax != nullptr, "lmin / lmax arrays are NULL");
+        for (size_t s = 0; s < ctx->series.size(); ++s) profile_one(ctx, ctx->series[s], lmin[s], lmax[s], p);
+    });
+}
+
+MAD_API mad_status mad_motifs(mad_ctx *ctx, int32_t series, int32_t k, mad_motif *out, int32_t *n_out)
+{
+    if (!ctx) { g_create_err = "ctx is NULL"; return MAD_EINVAL; }
+    return run_guarded(ctx, [&] {
+        Series &s = get_series(ctx, series);
+        REQUIRE(out != nullptr && n_out != nullptr, "output pointers are NULL");
+        REQUIRE(k >= 1 && k <= 4096, "k must be in [1, 4096]");
+        if (!s.profiled) {
+            set_err(ctx, "mad_motifs before mad_profile");
+            throw Fail{MAD_ESTATE};
+        }
+        cudaStream_t st = ctx->stream;
+        const int64_t nblk = (s.n0 + 255) / 256;
+        std::vector<void *> tmp;
+        auto talloc = [&](size_t bytes) {
+            void *p = nullptr;
+            CK(cudaMalloc(&p, bytes));
+            tmp.push_back(p);
+            return p;
+        };
+        try {
+            int32_t *acc = (int32_t *)talloc(sizeof(int32_t) * 3 * k);
+            int32_t *picked = (int32_t *)talloc(sizeof(int32_t) * k);
+            double *bval = (double *)talloc(sizeof(double) * nblk);
+            int32_t *bidx = (int32_t *)talloc(sizeof(int32_t) * nblk);
+            double *rd = (double *)talloc(sizeof(double) * k);
+            for (int r = 0; r < k; ++r)
+                launch_motif_round(s.vm, s.n0, ctx->opt.excl_num, ctx->opt.excl_den, acc, r, bval, bidx, picked, st);
+            CK(cudaGetLastError());
+            std::vector<int32_t> hp(k), ha(3 * k);
+            CK(cudaMemcpyAsync(hp.data(), picked, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(ha.data(), acc, sizeof(int32_t) * 3 * k, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            int got = 0;
+            while (got < k && hp[got] >= 0) ++got;
+            launch_recheck_pairs(s.x, s.n, acc, got, rd, st);
+            std::vector<double> hd(s.n0), hn(s.n0), hr(k);
+            if (got > 0) CK(cudaMemcpyAsync(hr.data(), rd, sizeof(double) * got, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(hd.data(), s.vm.dist, sizeof(double) * s.n0, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(hn.data(), s.vm.norm, sizeof(double) * s.n0, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            for (int r = 0; r < got; ++r) {
+                mad_motif &m = out[r];
+                m.a = ha[3 * r];
+                m.b = ha[3 * r + 1];
+                m.len = ha[3 * r + 2];
+                m.reserved = 0;
+                m.dist = hd[hp[r]];
+                m.norm_dist = hn[hp[r]];
+                m.dist_recheck = hr[r];
+            }
+            *n_out = got;
+        } catch (...) {
+            for (void *p : tmp) cudaFree(p);
+            throw;
+        }
+        for (void *p : tmp) cudaFree(p);
+    });
+}
+
+MAD_API mad_status mad_discords(mad_ctx *ctx, int32_t series, int32_t k, int32_t m, mad_discord *out,
+                                int32_t *n_out)
+{
+    if (!ctx) { g_create_err = "ctx is NULL"; return MAD_EINVAL; }
+    return run_guarded(ctx, [&] {
+        Series &s = get_series(ctx, series);
+        REQUIRE(out != nullptr && n_out != nullptr, "output pointers are NULL");
+        if (!s.profiled) {
+            set_err(ctx, "mad_discords before mad_profile");
+            throw Fail{MAD_ESTATE};
+        }
+        REQUIRE(k >= 1 && k <= s.k_max, "k must be in [1, k_max]");
+        REQUIRE(m >= 1 && m <= s.m_max, "m must be in [1, m_max]");
+        cudaStream_t st = ctx->stream;
+        const size_t cells = (size_t)s.k_max * s.m_max;
+        std::vector<double> nd(cells), dd(cells);
+        std::vector<int32_t> off(cells), len(cells), nn(cells);
+        CK(cudaMemcpyAsync(nd.data(), s.tab.norm, cells * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(dd.data(), s.tab.dist, cells * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(off.data(), s.tab.off, cells * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(len.data(), s.tab.len, cells * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(nn.data(), s.tab.nn, cells * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        std::vector<int32_t> req;
+        std::vector<int> where;
+        for (int r = 0; r < k; ++r)
+            for (int c = 0; c < m; ++c) {
+                const size_t cell = (size_t)r * s.m_max + c;
+                if (len[cell] > 0) {
+                    req.push_back(off[cell]);
+                    req.push_back(len[cell]);
+                    req.push_back(c + 1);
+                    where.push_back(r * m + c);
+                }
+            }
+        std::vector<double> rec(where.size(), NAN);
+        if (!where.empty()) {
+            void *dreq = nullptr, *dout = nullptr;
+            CK(cudaMalloc(&dreq, req.size() * sizeof(int32_t)));
+            cudaError_t e2 = cudaMalloc(&dout, where.size() * sizeof(double));
+            if (e2 != cudaSuccess) { cudaFree(dreq); CK(e2); }
+            cudaMemcpyAsync(dreq, req.data(), req.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+            launch_recheck_discords(s.x, s.n, (const int32_t *)dreq, (int)where.size(), ctx->opt.excl_num,
+                                    ctx->opt.excl_den, (double *)dout, st);
+            cudaError_t e3 = cudaMemcpyAsync(rec.data(), dout, where.size() * sizeof(double),
+                                             cudaMemcpyDeviceToHost, st);
+            cudaError_t e4 = cudaStreamSynchronize(st);
+            cudaFree(dreq);
+            cudaFree(dout);
+            CK(e3);
+            CK(e4);
+            CK(cudaGetLastError());
+        }
+        size_t w = 0;
+        for (int r = 0; r < k; ++r)
+            for (int c = 0; c < m; ++c) {
+                const size_t cell = (size_t)r * s.m_max + c;
+                mad_discord &q = out[r * m + c];
+                q.rank = r + 1;
+                q.m = c + 1;
+                q.reserved = 0;
+                if (len[cell] > 0) {
+                    q.off = off[cell];
+                    q.nn = nn[cell];
+                    q.len = len[cell];
+                    q.dist = dd[cell];
+                    q.norm_dist = nd[cell];
+                    q.dist_recheck = rec[w++];
+                } else {
+                    q.off = -1;
+                    q.nn = -1;
+                    q.len = 0;
+                    q.dist = NAN;
+                    q.norm_dist = NAN;
+                    q.dist_recheck = NAN;
+                }
+            }
+        *n_out = k * m;
+    });
+}
+
+MAD_API mad_status mad_valmp(mad_ctx *ctx, int32_t series, double *dist, double *norm, int32_t *len, int64_t *nn)
+{
+    if (!ctx) { g_create_err = "ctx is NULL"; return MAD_EINVAL; }
+    return run_guarded(ctx, [&] {
+        Series &s = get_series(ctx, series);
+        if (!s.profiled) {
+            set_err(ctx, "mad_valmp before mad_profile");
+            throw Fail{MAD_ESTATE};
+        }
+        cudaStream_t st = ctx->stream;
+        std::vector<int32_t> j32(s.n0);
+        if (dist) CK(cudaMemcpyAsync(dist, s.vm.dist, s.n0 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (norm) CK(cudaMemcpyAsync(norm, s.vm.norm, s.n0 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (len) CK(cudaMemcpyAsync(len, s.vm.len, s.n0 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        if (nn) CK(cudaMemcpyAsync(j32.data(), s.vm.nn, s.n0 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (nn)
+            for (int64_t i = 0; i < s.n0; ++i) nn[i] = j32[i];
+    });
+}
+
+MAD_API mad_status mad_matrix_profile(mad_ctx *ctx, int32_t series, int32_t len, double *mp, int64_t *ip,
+                                      double *nnd, int64_t *nnj)
+{
+    if (!ctx) { g_create_err = "ctx is NULL"; return MAD_EINVAL; }
+    return run_guarded(ctx, [&] {
+        Series &s = get_series(ctx, series);
+        if (!s.profiled) {
+            set_err(ctx, "mad_matrix_profile before mad_profile");
+            throw Fail{MAD_ESTATE};
+        }
+        REQUIRE(s.keep_nnd != nullptr, "profile was computed without keep_profiles");
+        REQUIRE(len >= s.lmin && len <= s.lmax, "len outside [lmin, lmax]");
+        cudaStream_t st = ctx->stream;
+        const int64_t nl = s.n - len + 1, n0 = s.n0;
+        const int M = s.m_max;
+        std::vector<double> d((size_t)M * n0);
+        std::vector<int32_t> j((size_t)M * n0);
+        const size_t off = (size_t)(len - s.lmin) * M * n0;
+        CK(cudaMemcpyAsync(d.data(), s.keep_nnd + off, d.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(j.data(), s.keep_nnj + off, j.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int64_t i = 0; i < nl; ++i) {
+            if (mp) mp[i] = d[i];
+            if (ip) ip[i] = j[i];
+            for (int m = 0; m < M; ++m) {
+                if (nnd) nnd[i * M + m] = d[(size_t)m * n0 + i];
+                if (nnj) nnj[i * M + m] = j[(size_t)m * n0 + i];
+            }
+        }
+    });
+}
+
+MAD_API mad_status mad_stats(mad_ctx *ctx, int32_t series, mad_length_stats *out, int32_t cap, int32_t *n_out)
+{
+    if (!ctx) { g_create_err = "ctx is NULL"; return MAD_EINVAL; }
+    return run_guarded(ctx, [&] {
+        Series &s = get_series(ctx, series);
+        if (!s.profiled) {
+            set_err(ctx, "mad_stats before mad_profile");
+            throw Fail{MAD_ESTATE};
+        }
+        REQUIRE(n_out != nullptr && (out != nullptr || cap == 0), "output pointers are NULL");
+        const int32_t nL = (int32_t)s.stats.size();
+        for (int32_t i = 0; i < nL && i < cap; ++i) out[i] = s.stats[i];
+        *n_out = nL;
+    });
+}
+
+MAD_API const char *mad_last_error(const mad_ctx *ctx)
+{
+    if (!ctx) return g_create_err.c_str();
+    return ctx->err.c_str();
+}
+
+MAD_API void mad_destroy(mad_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    for (Series &s : ctx->series) {
+        free_profile(s);
+        if (s.own_x && s.x) cudaFree(s.x);
+        s.x = nullptr;
+    }
+    delete ctx;
+}
+
+}  // extern "C"

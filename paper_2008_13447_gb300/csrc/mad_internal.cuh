@@ -1,0 +1,83 @@
+// mad_internal.cuh -- device-side definitions shared by the kernels of the
+// exact variable-length matrix profile (VALMOD / MAD).
+//
+// Notation follows the paper: series x[0..n), window length l, n_l = n-l+1
+// windows, exclusion half-width E(l). For a window i the kernels keep its
+// mean mu_i and centred second moment M2_i = sum_t (x_{i+t} - mu_i)^2
+// (= l sigma_i^2, population sigma). The correlation of windows i and j is
+// q = C(i,j) / sqrt(M2_i M2_j) with the centred co-moment
+// C(i,j) = sum_t (x_{i+t} - mu_i)(x_{j+t} - mu_j), and Eq. DIST gives
+// d = sqrt(2 l (1 - q)).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mad {
+
+constexpr int CH = 32;              // columns per wavefront chunk (one per lane)
+constexpr int MAXP = 64;            // largest p (entries kept per row)
+constexpr int KMAX = 64;            // largest discord-table rank count
+
+// Rows per lane / warps per CTA of the diagonal band kernel. A band holds
+// R = 32 * RPL * NW consecutive rows, which is also the re-seed period of
+// every diagonal (each diagonal is restarted from a direct dot product at
+// the top or left edge of every R x R tile).
+template <typename T> struct BandGeo;
+template <> struct BandGeo<float> { static constexpr int RPL = 8, NW = 8; };   // R = 2048
+template <> struct BandGeo<double> { static constexpr int RPL = 4, NW = 8; };  // R = 1024
+template <typename T> constexpr int band_rows() { return 32 * BandGeo<T>::RPL * BandGeo<T>::NW; }
+
+// Per-window data the band kernel reads for column j (and for row j):
+//   df = df_{j-1} = (x_{j-1+l} - x_{j-1}) / 2
+//   dg = dg_{j-1} = (x_{j-1+l} - mu_j) + (x_{j-1} - mu_{j-1})
+//   inv = 1 / sqrt(M2_j)  (0 for a flat window, NaN past the last window)
+// with df_{-1} = dg_{-1} = 0 for the virtual window before the first.
+// The centred co-moment then obeys, along every diagonal,
+//   C(i, j) = C(i-1, j-1) + df_{i-1} dg_{j-1} + df_{j-1} dg_{i-1}.
+template <typename T> struct __align__(4 * sizeof(T)) Col { T df, dg, inv, pad; };
+
+// Row flags of the per-length pipeline.
+enum : int32_t { ROW_DONE = 0, ROW_RECOMPUTE = 1, ROW_FLAT = 2 };
+
+// Order-preserving maps from floating point to signed integers (for
+// atomicMax on shared or global memory).
+__device__ __forceinline__ int f2ord(float f)
+{
+    int i = __float_as_int(f);
+    return i >= 0 ? i : (i ^ 0x7fffffff);
+}
+__device__ __forceinline__ float ord2f(int i) { return __int_as_float(i >= 0 ? i : (i ^ 0x7fffffff)); }
+
+__host__ __device__ __forceinline__ int64_t excl_zone(int l, int num, int den)
+{
+    return ((int64_t)l * num + den - 1) / den;
+}
+
+__device__ __forceinline__ bool nontrivial(int64_t i, int64_t j, int64_t E)
+{
+    int64_t d = i - j;
+    return d > E || -d > E;
+}
+
+// Number of non-trivial partners of window i among n_l windows.
+__device__ __forceinline__ int64_t nontrivial_count(int64_t i, int64_t nl, int64_t E)
+{
+    int64_t lo = i - E < 0 ? 0 : i - E;
+    int64_t hi = i + E > nl - 1 ? nl - 1 : i + E;
+    return nl - (hi - lo + 1);
+}
+
+__device__ __forceinline__ double clamp_q(double q) { return q > 1.0 ? 1.0 : (q < -1.0 ? -1.0 : q); }
+
+// Eq. DIST from the correlation.
+__device__ __forceinline__ double dist_from_q(double q, int l) { return sqrt(2.0 * l * (1.0 - clamp_q(q))); }
+
+// Correlation with the flat-window reading: two flat windows correlate 1, a
+// flat and a non-flat window 0.
+__device__ __forceinline__ double corr(double C, double m2i, double m2j, bool flat_i, bool flat_j)
+{
+    if (flat_i || flat_j) return (flat_i && flat_j) ? 1.0 : 0.0;
+    return clamp_q(C / sqrt(m2i * m2j));
+}
+
+}  // namespace mad

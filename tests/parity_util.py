@@ -1,0 +1,96 @@
+"""Helpers that compare the CUDA path with the CPU oracle."""
+import math
+
+import numpy as np
+
+import oracle
+import paper_2008_13447_gb300 as mad
+
+
+def tol_for(prec, l, d_ref):
+    """Distance tolerance: FP64 1e-9 relative, FP32 1e-4 sqrt(l) absolute."""
+    if prec == mad.MAD_FP64:
+        return 1e-9 * np.maximum(np.abs(d_ref), 1e-3)
+    return 1e-4 * math.sqrt(l) + 0.0 * d_ref
+
+
+def check_index_choice(x, l, i, j_gpu, d_ref, tol, num, den):
+    """An index that differs from the oracle's must be a valid, non-trivial
+    partner whose oracle distance ties the oracle's value within tol."""
+    E = oracle.excl(l, num, den)
+    assert abs(int(j_gpu) - int(i)) > E, (l, i, j_gpu)
+    assert 0 <= j_gpu < len(x) - l + 1
+    d = oracle.dist(x, l, int(i), int(j_gpu))
+    assert abs(d - d_ref) <= tol + 1e-12, (l, i, j_gpu, d, d_ref)
+
+
+def run_gpu(x, lmin, lmax, p, prec, m_max=1, k_max=5, excl=(1, 4)):
+    ctx = mad.mad_create(x, precision=prec, k_max=k_max, m_max=m_max, excl=excl, keep_profiles=True)
+    try:
+        mad.mad_profile(ctx, lmin, lmax, p)
+        n = len(x)
+        prof = {l: mad.mad_matrix_profile(ctx, 0, l, n, m_max) for l in range(lmin, lmax + 1)}
+        vm = mad.mad_valmp(ctx, 0, n - lmin + 1)
+        mot = mad.mad_motifs(ctx, 0, k_max)
+        dis = mad.mad_discords(ctx, 0, k_max, m_max)
+        st = mad.mad_stats(ctx, 0)
+    finally:
+        mad.mad_destroy(ctx)
+    return prof, vm, mot, dis, st
+
+
+def compare_all(x, lmin, lmax, p, prec, m_max=1, k_max=5, excl=(1, 4)):
+    num, den = excl
+    ref = oracle.valmp_plain(x, lmin, lmax, m_max=m_max, num=num, den=den, keep_nn=True)
+    prof, vm, mot, dis, st = run_gpu(x, lmin, lmax, p, prec, m_max, k_max, excl)
+    n = len(x)
+    n0 = n - lmin + 1
+    worst = 0.0
+    idx_mismatch = 0
+    for l in range(lmin, lmax + 1):
+        nl = n - l + 1
+        mp, ip, nnd, nnj = prof[l]
+        rd = ref["nnd"][l - lmin, :nl, :]
+        rj = ref["nnj"][l - lmin, :nl, :]
+        tol = tol_for(prec, l, rd)
+        err = np.abs(nnd - rd)
+        assert np.all(np.isfinite(nnd)), l
+        bad = err > tol
+        assert not bad.any(), (l, np.argwhere(bad)[:5], nnd[bad][:5], rd[bad][:5])
+        worst = max(worst, float((err / (tol if np.ndim(tol) else tol)).max()))
+        np.testing.assert_array_equal(mp, nnd[:, 0])
+        for m in range(m_max):
+            diff = np.nonzero(nnj[:, m] != rj[:, m])[0]
+            idx_mismatch += len(diff)
+            for i in diff[:50]:
+                t = tol if np.ndim(tol) == 0 else tol[i, m]
+                check_index_choice(x, l, i, nnj[i, m], rd[i, m], t, num, den)
+    # VALMP
+    tolv = tol_for(prec, lmax, ref["dist"])
+    assert np.all(np.abs(vm["dist"] - ref["dist"]) <= tolv)
+    ln_bad = np.nonzero(vm["len"] != ref["len"])[0]
+    for i in ln_bad:
+        # a different length is only allowed on a near-tie of normalised distances
+        assert abs(vm["norm"][i] - ref["norm"][i]) <= (np.max(tolv) if np.ndim(tolv) else tolv)
+    # stats invariants
+    for s in st:
+        assert s["certified"] + s["recomputed"] == s["rows"], s
+    assert st[0]["recomputed"] == st[0]["rows"]
+    # motifs from the oracle's VALMP
+    rm = oracle.topk_motifs(ref, k_max, num, den)
+    assert len(mot) == len(rm)
+    for g, r in zip(mot, rm):
+        tn = 1e-4 if prec == mad.MAD_FP32 else 1e-9 * max(1.0, r[4])
+        assert abs(g["norm_dist"] - r[4]) <= tn, (g, r)
+        assert abs(g["dist"] - g["dist_recheck"]) <= (1e-4 * math.sqrt(g["len"]) if prec == mad.MAD_FP32 else 1e-9 * max(1.0, g["dist"]))
+    # discords
+    rdk = oracle.discords(n, lmin, lmax, k_max, m_max, ref["nnd"], ref["nnj"], num, den)
+    for c in dis:
+        r, m = c["rank"] - 1, c["m"] - 1
+        if rdk["len"][r, m] == 0:
+            assert c["len"] == 0
+            continue
+        t = 1e-4 if prec == mad.MAD_FP32 else 1e-9 * max(1.0, rdk["norm"][r, m])
+        assert abs(c["norm_dist"] - rdk["norm"][r, m]) <= t, (c, rdk["norm"][r, m])
+        assert abs(c["dist"] - c["dist_recheck"]) <= (1e-4 * math.sqrt(c["len"]) if prec == mad.MAD_FP32 else 1e-9 * max(1.0, c["dist"]))
+    return dict(worst=worst, idx_mismatch=idx_mismatch, stats=st, motifs=mot, ref_motifs=rm)
