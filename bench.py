@@ -1,0 +1,356 @@
+#!/usr/bin/env python3
+"""Benchmark of the exact variable-length matrix profile on GB300.
+
+One step = the whole hot path over one synthetic workload: mad_profile over
+[lmin, lmax] (window statistics, the diagonal-recurrence matrix profile with
+top-p candidates, length extension with the Eq. LB bound test, recomputes,
+VALMP, per-length discord tables) plus the read-outs (top-k motifs and the
+Top-k m-th discords with their FP64 re-checks).
+
+Metric: distance cells per second over all lengths, sum over series of
+n^2 * |L|, per step. The default workload is the planted random walk
+(n = 65536, l in [256, 512], p = 5). Input series stay resident in HBM
+between steps; L2 (129 MB) is flushed between timed steps by writing a
+512 MB buffer.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Rank 0 prints one JSON line. Under torchrun every rank profiles its own
+replica of the workload (the path has no exchange step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "distance cells/s over all lengths (n^2*|L|)"
+UNIT = "cells/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+OPS_PER_CELL = 4            # FFMA, FFMA (recurrence), FMUL (key), FSETP (threshold test)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="planted65k")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the plain FP64 GPU path")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -------------------------------------------------------------- helpers
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("k_band.cu", "kernels.cuh", "mad_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2008_13447_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(cells_per_launch):
+    """DRAM bytes per band-kernel launch from the committed ncu summary,
+    scaled by cells; None if absent or taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "band_kernel_traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    return d["dram_bytes_per_cell"] * cells_per_launch
+
+
+def cpu_oracle_sample(w, seconds):
+    """Time the CPU oracle (plain definitions, OpenMP over windows) on a
+    bounded sample of the workload: full distance profiles of sampled
+    windows at sampled lengths of the range."""
+    import numpy as np
+    import oracle
+    x = w.series[0]
+    n = len(x)
+    lmin, lmax = w.lmin[0], w.lmax[0]
+    lengths = sorted(set(int(v) for v in np.linspace(lmin, lmax, 5)))
+    threads = oracle.num_threads()
+    rng = np.random.default_rng(0)
+    # calibrate on a few rows, then size the sample to the budget
+    l0 = lengths[len(lengths) // 2]
+    rows = rng.integers(0, n - lmax + 1, threads)
+    t = time.perf_counter()
+    oracle.rows(x, l0, rows)
+    per_row = (time.perf_counter() - t) / len(rows) * threads
+    nrows = max(threads, int(seconds / max(per_row, 1e-6) * threads / len(lengths)))
+    cells = 0
+    t0 = time.perf_counter()
+    for l in lengths:
+        rows = rng.integers(0, n - l + 1, nrows)
+        oracle.rows(x, l, rows)
+        cells += nrows * (n - l + 1)
+    dt = time.perf_counter() - t0
+    return {"value": cells / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d windows x %d lengths (%s) of %s: full FP64 distance profiles by definition, "
+                      "%.1f s" % (nrows, len(lengths), ",".join(map(str, lengths)), w.name, dt),
+            "seconds": dt, "cells": cells}
+
+
+# ------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import workloads
+    w = workloads.make(args.workload)
+    per = max(2.0, min(20.0, 90.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_sample(w, per / 4)
+    vals, secs, samp = [], 0.0, None
+    for _ in range(args.steps):
+        r = cpu_oracle_sample(w, per)
+        vals.append(r["value"])
+        secs += r["seconds"]
+        samp = r
+    value = statistics.median(vals)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": args.workload},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": samp["cores"], "kind": "oracle",
+                            "sample": samp["sample"]},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- our arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    import paper_2008_13447_gb300 as mad
+    import workloads
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    w = workloads.make(args.workload)
+    assert len(w.series) == 1, "bench drives single-series workloads"
+    x = w.series[0]
+    n, lmin, lmax, p, k, m = len(x), w.lmin[0], w.lmax[0], w.p, w.k, w.m
+    prec = mad.MAD_FP32 if args.precision == "fp32" else mad.MAD_FP64
+    xt = torch.tensor(x, device=dev, dtype=torch.float64)
+    ctx = mad.mad_create_device(xt, precision=prec, k_max=k, m_max=m, stream=stream)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        mad.mad_profile(ctx, lmin, lmax, p)
+        mad.mad_motifs(ctx, 0, k)
+        mad.mad_discords(ctx, 0, k, m)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    band_ms = band_cells = launches = 0
+    band_launches = 0
+    for s in range(args.steps):
+        flush.fill_(s & 0xff)
+        torch.cuda.synchronize()
+        ev[s][0].record(stream)
+        step()
+        ev[s][1].record(stream)
+        torch.cuda.synchronize()
+        st = mad.mad_stats(ctx, 0)
+        band_ms += sum(q["band_ms"] for q in st)
+        band_cells += sum(q["band_cells"] for q in st)
+        launches += sum(q["launches"] for q in st)
+        band_launches += sum(q["passes"] + (1 if q["len"] == lmin else 0) for q in st if q["band_cells"] > 0)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if pg:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    cells = w.cells
+    value = cells * world / (ms_per_step / 1e3)
+
+    # read-out launches per step (motif rounds, pair re-check, discord re-check)
+    launches_per_step = launches / args.steps + 2 * k + 1 + 1
+
+    # roofline of the dominant kernel (band kernel): FP32 ALU instructions
+    peak_mhz = (clk or {}).get("sm_max_mhz", 2070.0)
+    peak_ops = SM_COUNT * FP32_LANES_PER_SM * peak_mhz * 1e6
+    achieved_ops = band_cells * OPS_PER_CELL / (band_ms / 1e3) if band_ms > 0 else 0.0
+    cells_per_launch = band_cells / max(1, band_launches)
+    traffic = measured_traffic(cells_per_launch)
+    roof = {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+            "frac": achieved_ops / peak_ops if peak_ops else None, "traffic": traffic,
+            "kernel": "k_band (FP32 diagonal recurrence, append mode)" if prec == mad.MAD_FP32
+            else "k_band (FP64)",
+            "ops_per_cell": OPS_PER_CELL, "band_cells_per_step": band_cells / args.steps,
+            "band_ms_per_step": band_ms / args.steps}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32" if prec == mad.MAD_FP32 else "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "n": n, "lmin": lmin, "lmax": lmax, "p": p, "k": k, "m": m,
+                      "exclusion": "ceil(l/4)", "precision": args.precision, "cells_per_step": cells,
+                      "l2": "flushed between timed steps (512 MB write)", "parallelism": "replicas"},
+           "roofline": roof, "gpu_launches": int(round(launches_per_step * args.steps)),
+           "clocks": clk}
+
+    # plain FP64 GPU path, one step, for the comparison the metric names
+    if rank == 0 and not args.no_fp64_path and prec == mad.MAD_FP32:
+        c64 = mad.mad_create_device(xt, precision=mad.MAD_FP64, k_max=k, m_max=m, stream=stream)
+        try:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.fill_(7)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            mad.mad_profile(c64, lmin, lmax, p)
+            mad.mad_motifs(c64, 0, k)
+            mad.mad_discords(c64, 0, k, m)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms64 = e0.elapsed_time(e1)
+            out["fp64_path"] = {"value": cells / (ms64 / 1e3), "ms_per_step": ms64,
+                                "speedup_of_fp32": (cells / (ms_per_step / 1e3)) / (cells / (ms64 / 1e3))}
+        finally:
+            mad.mad_destroy(c64)
+
+    # end to end through the public API with host buffers (pinned input)
+    pinned = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    xh = pinned.numpy()
+    n0 = n - lmin + 1
+    e2e_ms = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c2 = mad.mad_create(xh, precision=prec, k_max=k, m_max=m, stream=stream)
+        try:
+            mad.mad_profile(c2, lmin, lmax, p)
+            mot = mad.mad_motifs(c2, 0, k)
+            dis = mad.mad_discords(c2, 0, k, m)
+            vm = mad.mad_valmp(c2, 0, n0)
+        finally:
+            mad.mad_destroy(c2)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e = min(e2e_ms)
+    d2h = n0 * (8 + 8 + 4 + 4) + k * 56 + k * m * 56
+    out["e2e"] = {"value": cells * world / (e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": n * 8,
+                  "d2h_bytes_per_step": d2h, "ms_per_step": e2e}
+    out["result"] = {"top_motif": {k2: mot[0][k2] for k2 in ("a", "b", "len", "dist", "dist_recheck")} if mot else None,
+                     "top_discord": {k2: dis[0][k2] for k2 in ("off", "len", "dist", "dist_recheck")} if dis else None,
+                     "valmp_len_mean": float(vm["len"].mean())}
+    mad.mad_destroy(ctx)
+    if rank == 0 and not args.no_cpu_baseline:
+        cb = cpu_oracle_sample(w, args.cpu_seconds)
+        out["cpu_baseline"] = {k2: cb[k2] for k2 in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

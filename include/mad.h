@@ -118,6 +118,13 @@ typedef struct {
     int64_t recomputed;     /* rows whose full distance profile was recomputed */
     int64_t tiles;          /* band x column-range units the recompute kernel ran */
     int64_t passes;         /* recompute kernel passes (1 + candidate-list refills) */
+    int64_t band_cells;     /* cells the matrix-profile (band) kernel evaluated at this length:
+                               rows of its active bands x columns, summed over passes */
+    int64_t launches;       /* GPU kernel launches issued for this length */
+    double band_ms;         /* device time of those band-kernel launches (CUDA events recorded
+                               on the context's stream around each launch) */
+    double fp32_dq_max;     /* MAD_FP32: largest |q_FP32 - q_FP64| among stored entries that were
+                               re-evaluated in FP64 at this length (0 when none / MAD_FP64) */
 } mad_length_stats;
 
 /* Create a context for one series copied from host memory (FP64, n values).

@@ -23,7 +23,7 @@ _lib = None
 
 __all__ = [
     "build", "excl", "window_stats", "pearson", "dist", "dist_direct", "lower_bound", "row_valid",
-    "distance_profile", "matrix_profile", "row", "valmp_plain", "valmod_pruned",
+    "distance_profile", "matrix_profile", "row", "rows", "num_threads", "valmp_plain", "valmod_pruned",
     "topk_motifs", "discords_one_length", "discords",
 ]
 
@@ -60,6 +60,8 @@ def _L():
             "orc_distance_profile": (None, [P, i64, C.c_int, C.c_int, C.c_int, i64, P]),
             "orc_matrix_profile": (None, [P, i64, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P, P]),
             "orc_row": (None, [P, i64, C.c_int, C.c_int, C.c_int, C.c_int, i64, P, P, P, P]),
+            "orc_rows": (None, [P, i64, C.c_int, C.c_int, C.c_int, P, i64, P, P]),
+            "orc_num_threads": (C.c_int, []),
             "orc_valmp_plain": (None, [P, i64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                        P, P, P, P, P, P]),
             "orc_valmod_pruned": (None, [P, i64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
@@ -144,6 +146,20 @@ def row(x, l, i, m_max=1, num=1, den=4):
     nnd, nnj = np.empty(m_max), np.empty(m_max, np.int64)
     _L().orc_row(_p(x), len(x), l, num, den, m_max, i, C.byref(mp), C.byref(ip), _p(nnd), _p(nnj))
     return mp.value, ip.value, nnd, nnj
+
+
+def rows(x, l, row_list, num=1, den=4):
+    """Matrix-profile value and index of the listed windows at length l
+    (parallel over windows): (mp, ip)."""
+    x = _f64(x)
+    r = np.ascontiguousarray(row_list, np.int64)
+    mp, ip = np.empty(len(r)), np.empty(len(r), np.int64)
+    _L().orc_rows(_p(x), len(x), l, num, den, _p(r), len(r), _p(mp), _p(ip))
+    return mp, ip
+
+
+def num_threads() -> int:
+    return int(_L().orc_num_threads())
 
 
 def _valmp_out(n0):

@@ -33,6 +33,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <omp.h>
 
 typedef int64_t i64;
 
@@ -212,6 +213,38 @@ void orc_row(const double *x, i64 n, int l, int num, int den, int m_max, i64 i,
     }
     free(prof);
     free(buf);
+}
+
+/* orc_row for a list of windows at one length, in parallel over windows
+ * (same definitions; used to time the oracle on a sample of a workload). */
+void orc_rows(const double *x, i64 n, int l, int num, int den, const i64 *rows, i64 nrows, double *mp, i64 *ip)
+{
+    i64 nl = n - l + 1;
+#pragma omp parallel
+    {
+        double *prof = (double *)malloc(sizeof(double) * (size_t)nl);
+        dj_t *buf = (dj_t *)malloc(sizeof(dj_t) * (size_t)nl);
+#pragma omp for schedule(dynamic, 1)
+        for (i64 r = 0; r < nrows; ++r) {
+            orc_distance_profile(x, n, l, num, den, rows[r], prof);
+            i64 c = sorted_profile(prof, nl, buf);
+            mp[r] = c > 0 ? buf[0].d : INFINITY;
+            ip[r] = c > 0 ? buf[0].j : -1;
+        }
+        free(prof);
+        free(buf);
+    }
+}
+
+int orc_num_threads(void)
+{
+    int t = 1;
+#pragma omp parallel
+    {
+#pragma omp single
+        t = omp_get_num_threads();
+    }
+    return t;
 }
 
 /* Algorithm 2 (updateVALMP) applied to one length: for i < n_l, if

@@ -52,7 +52,9 @@ class mad_discord(C.Structure):
 
 class mad_length_stats(C.Structure):
     _fields_ = [("len", C.c_int32), ("reserved", C.c_int32), ("rows", C.c_int64), ("certified", C.c_int64),
-                ("recomputed", C.c_int64), ("tiles", C.c_int64), ("passes", C.c_int64)]
+                ("recomputed", C.c_int64), ("tiles", C.c_int64), ("passes", C.c_int64),
+                ("band_cells", C.c_int64), ("launches", C.c_int64), ("band_ms", C.c_double),
+                ("fp32_dq_max", C.c_double)]
 
 
 class MadError(RuntimeError):
@@ -203,7 +205,8 @@ def mad_stats(ctx, series, cap=1 << 16):
     n = C.c_int32()
     _check(library().mad_stats(ctx, series, out, cap, C.byref(n)), ctx)
     return [dict(len=s.len, rows=s.rows, certified=s.certified, recomputed=s.recomputed, tiles=s.tiles,
-                 passes=s.passes) for s in out[:min(n.value, cap)]]
+                 passes=s.passes, band_cells=s.band_cells, launches=s.launches, band_ms=s.band_ms,
+                 fp32_dq_max=s.fp32_dq_max) for s in out[:min(n.value, cap)]]
 
 
 def mad_last_error(ctx=None):

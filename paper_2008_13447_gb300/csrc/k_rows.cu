@@ -286,6 +286,40 @@ __global__ void k_merge(MergeArgs<T> A)
             A.st.ent_c[e * n0 + i] = 0.0;
         }
     }
+    // Entries at a small distance are re-evaluated directly in FP64: near
+    // d = 0 the distance amplifies any error of q (d^2 = 2 l (1 - q)).
+    if (A.d_refine > 0.0) {
+        const double mui = A.mu[i];
+        double dqmax = 0.0;
+        bool changed = false;
+        for (int e = 0; e < nq; ++e) {
+            if (!(dist_from_q(qs[e], l) < A.d_refine)) continue;
+            const int32_t j = js[e];
+            if (A.run[j] >= l) continue;
+            const double c = comoment(A.x, i, j, l, mui, A.mu[j]);
+            const double q = corr(c, m2i, A.m2[j], false, false);
+            dqmax = fmax(dqmax, fabs(q - qs[e]));
+            qs[e] = q;
+            changed = true;
+            for (int f = 0; f < p; ++f)
+                if (A.st.ent_j[f * n0 + i] == j) A.st.ent_c[f * n0 + i] = c;
+        }
+        if (changed) {
+            for (int a = 1; a < nq; ++a) {   // restore (q desc, j asc) order
+                const double q = qs[a];
+                const int32_t j = js[a];
+                int b = a;
+                while (b > 0 && (qs[b - 1] < q || (qs[b - 1] == q && js[b - 1] > j))) {
+                    qs[b] = qs[b - 1];
+                    js[b] = js[b - 1];
+                    --b;
+                }
+                qs[b] = q;
+                js[b] = j;
+            }
+            atomicMax(&A.out.stats[3], (unsigned long long)__double_as_longlong(dqmax));
+        }
+    }
     double ds[MAXP];
     for (int e = 0; e < nq; ++e) ds[e] = dist_from_q(qs[e], l);
     write_nn(A.out, n0, i, A.m_max, ds, js, nq);

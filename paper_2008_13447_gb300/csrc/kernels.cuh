@@ -88,7 +88,8 @@ struct Valmp {
 struct LenOut {
     double *nnd;            // [m][n0] m-th best-match distance at the current length
     int32_t *nnj;           // [m][n0] its offset
-    unsigned long long *stats;  // this length's counters (5)
+    unsigned long long *stats;  // this length's counters: [1] certified, [2] recomputed,
+                                //   [3] largest |q_band - q_FP64| seen on re-evaluated entries (bits)
 };
 
 template <typename T> struct ExtArgs {
@@ -111,10 +112,12 @@ template <typename T> struct ExtArgs {
 template <typename T> void launch_extend(const ExtArgs<T> &a, cudaStream_t s);
 
 template <typename T> struct MergeArgs {
+    const double *x;
     int64_t n0, nl;
     int l;
     int64_t E;
     int p, m_max, cap;
+    const double *mu;
     const double *m2;
     const int32_t *run;
     const Col<T> *col;
@@ -126,6 +129,7 @@ template <typename T> struct MergeArgs {
     Valmp vm;
     LenOut out;
     double dq_band;
+    double d_refine;        // entries closer than this are re-evaluated directly in FP64
     unsigned int *overflow;
 };
 template <typename T> void launch_merge(const MergeArgs<T> &a, cudaStream_t s);

@@ -7,11 +7,21 @@ import oracle
 import paper_2008_13447_gb300 as mad
 
 
+# FP64 correlation rounding floor: d^2 = 2 l (1 - q), so an error dq in q
+# moves d^2 by 2 l dq whatever d is; near d = 0 that dominates 1e-9 * d.
+DQ64 = 1e-12
+
+
 def tol_for(prec, l, d_ref):
-    """Distance tolerance: FP64 1e-9 relative, FP32 1e-4 sqrt(l) absolute."""
+    """Distance tolerance. FP64: 1e-9 relative, with the floor that a 1e-12
+    error of the correlation puts on d (|d1^2 - d2^2| <= 2 l dq, i.e.
+    |d1 - d2| <= 2 l dq / (d1 + d2) <= sqrt(2 l dq)). FP32: 1e-4 sqrt(l)
+    absolute."""
+    d = np.abs(np.asarray(d_ref, dtype=float))
     if prec == mad.MAD_FP64:
-        return 1e-9 * np.maximum(np.abs(d_ref), 1e-3)
-    return 1e-4 * math.sqrt(l) + 0.0 * d_ref
+        floor = 2 * l * DQ64 / np.maximum(2 * d, math.sqrt(2 * l * DQ64))
+        return 1e-9 * d + floor
+    return 1e-4 * math.sqrt(l) + 0.0 * d
 
 
 def check_index_choice(x, l, i, j_gpu, d_ref, tol, num, den):
@@ -66,12 +76,20 @@ def compare_all(x, lmin, lmax, p, prec, m_max=1, k_max=5, excl=(1, 4)):
                 t = tol if np.ndim(tol) == 0 else tol[i, m]
                 check_index_choice(x, l, i, nnj[i, m], rd[i, m], t, num, den)
     # VALMP
+    # normalised distance d / sqrt(l): tolerance divided by sqrt(l)
+    tn = 1e-4 if prec == mad.MAD_FP32 else tol_for(prec, lmax, ref["norm"] * math.sqrt(lmin)) / math.sqrt(lmin)
+    assert np.all(np.abs(vm["norm"] - ref["norm"]) <= tn), np.max(np.abs(vm["norm"] - ref["norm"]))
+    same = vm["len"] == ref["len"]
     tolv = tol_for(prec, lmax, ref["dist"])
-    assert np.all(np.abs(vm["dist"] - ref["dist"]) <= tolv)
-    ln_bad = np.nonzero(vm["len"] != ref["len"])[0]
-    for i in ln_bad:
-        # a different length is only allowed on a near-tie of normalised distances
-        assert abs(vm["norm"][i] - ref["norm"][i]) <= (np.max(tolv) if np.ndim(tolv) else tolv)
+    tolv = tolv[same] if np.ndim(tolv) else tolv
+    assert np.all(np.abs(vm["dist"][same] - ref["dist"][same]) <= tolv)
+    # a different length is only allowed on a near-tie of normalised distances,
+    # and the reported distance must be that length's distance
+    for i in np.nonzero(~same)[0][:50]:
+        L = int(vm["len"][i])
+        assert lmin <= L <= lmax
+        d = oracle.dist(x, L, i, int(vm["nn"][i]))
+        assert abs(d - vm["dist"][i]) <= tol_for(prec, L, d) + 1e-12
     # stats invariants
     for s in st:
         assert s["certified"] + s["recomputed"] == s["rows"], s
@@ -80,9 +98,9 @@ def compare_all(x, lmin, lmax, p, prec, m_max=1, k_max=5, excl=(1, 4)):
     rm = oracle.topk_motifs(ref, k_max, num, den)
     assert len(mot) == len(rm)
     for g, r in zip(mot, rm):
-        tn = 1e-4 if prec == mad.MAD_FP32 else 1e-9 * max(1.0, r[4])
+        tn = 1e-4 if prec == mad.MAD_FP32 else float(tol_for(prec, r[2], r[3])) / math.sqrt(r[2]) + 1e-15
         assert abs(g["norm_dist"] - r[4]) <= tn, (g, r)
-        assert abs(g["dist"] - g["dist_recheck"]) <= (1e-4 * math.sqrt(g["len"]) if prec == mad.MAD_FP32 else 1e-9 * max(1.0, g["dist"]))
+        assert abs(g["dist"] - g["dist_recheck"]) <= float(tol_for(prec, g["len"], g["dist_recheck"]))
     # discords
     rdk = oracle.discords(n, lmin, lmax, k_max, m_max, ref["nnd"], ref["nnj"], num, den)
     for c in dis:
@@ -90,7 +108,7 @@ def compare_all(x, lmin, lmax, p, prec, m_max=1, k_max=5, excl=(1, 4)):
         if rdk["len"][r, m] == 0:
             assert c["len"] == 0
             continue
-        t = 1e-4 if prec == mad.MAD_FP32 else 1e-9 * max(1.0, rdk["norm"][r, m])
+        t = 1e-4 if prec == mad.MAD_FP32 else float(tol_for(prec, c["len"], rdk["dist"][r, m])) / math.sqrt(c["len"]) + 1e-15
         assert abs(c["norm_dist"] - rdk["norm"][r, m]) <= t, (c, rdk["norm"][r, m])
-        assert abs(c["dist"] - c["dist_recheck"]) <= (1e-4 * math.sqrt(c["len"]) if prec == mad.MAD_FP32 else 1e-9 * max(1.0, c["dist"]))
+        assert abs(c["dist"] - c["dist_recheck"]) <= float(tol_for(prec, c["len"], c["dist_recheck"]))
     return dict(worst=worst, idx_mismatch=idx_mismatch, stats=st, motifs=mot, ref_motifs=rm)

@@ -55,7 +55,7 @@ int main(void){
   printf("%zu %zu %zu\n", sizeof(mad_options), offsetof(mad_options, stream), offsetof(mad_options, keep_profiles));
   printf("%zu %zu\n", sizeof(mad_motif), offsetof(mad_motif, dist_recheck));
   printf("%zu %zu\n", sizeof(mad_discord), offsetof(mad_discord, dist_recheck));
-  printf("%zu %zu\n", sizeof(mad_length_stats), offsetof(mad_length_stats, passes));
+  printf("%zu %zu %zu\n", sizeof(mad_length_stats), offsetof(mad_length_stats, passes), offsetof(mad_length_stats, fp32_dq_max));
   return 0; }
 '''
     import tempfile
@@ -68,7 +68,8 @@ int main(void){
     want = [C.sizeof(mad.mad_options), mad.mad_options.stream.offset, mad.mad_options.keep_profiles.offset,
             C.sizeof(mad.mad_motif), mad.mad_motif.dist_recheck.offset,
             C.sizeof(mad.mad_discord), mad.mad_discord.dist_recheck.offset,
-            C.sizeof(mad.mad_length_stats), mad.mad_length_stats.passes.offset]
+            C.sizeof(mad.mad_length_stats), mad.mad_length_stats.passes.offset,
+            mad.mad_length_stats.fp32_dq_max.offset]
     assert [int(g) for g in got] == want
 
 
