@@ -161,10 +161,40 @@ __device__ __forceinline__ float to_float_rd(double v) { return __double2float_r
 __device__ __forceinline__ float fmax_t(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double fmax_t(double a, double b) { return fmax(a, b); }
 
+// Insert (key, j) into a row's top-p list in shared memory (only the lane
+// owning the row touches it). The list keeps the p largest keys seen; among
+// equal keys the smaller offset wins (columns arrive in increasing j, and an
+// equal key never replaces a kept one). th is the row's current threshold:
+// max(lower bound given at launch, smallest kept key once p are kept).
+template <typename T>
+__device__ __forceinline__ void topp_insert(T *K, int32_t *J, int32_t &cnt, int p, T key, int32_t j, T &th)
+{
+    if (cnt < p) {
+        K[cnt] = key;
+        J[cnt] = j;
+        ++cnt;
+        if (cnt == p) {
+            T mn = K[0];
+            for (int e = 1; e < p; ++e) mn = K[e] < mn ? K[e] : mn;
+            th = mn > th ? mn : th;
+        }
+        return;
+    }
+    int m = 0;
+    for (int e = 1; e < p; ++e)
+        if (K[e] < K[m] || (K[e] == K[m] && J[e] > J[m])) m = e;
+    K[m] = key;
+    J[m] = j;
+    T mn = K[0];
+    for (int e = 1; e < p; ++e) mn = K[e] < mn ? K[e] : mn;
+    th = mn > th ? mn : th;
+}
+
 template <typename T, int RPL, int NW, bool BINS, bool DIAG>
 __device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *cbuf, T tp, T *bout, int lane, int w,
-                                           int64_t cs, int64_t rbase, T (&C)[RPL], const T (&dfr)[RPL],
-                                           const T (&dgr)[RPL], const T (&th)[RPL], T (&runmax)[RPL])
+                                           int64_t cs, int64_t rbase, int rl0, T (&C)[RPL], const T (&dfr)[RPL],
+                                           const T (&dgr)[RPL], T (&th)[RPL], T (&runmax)[RPL], T *lkey,
+                                           int32_t *lj, int32_t *lcnt)
 {
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
@@ -176,26 +206,24 @@ __device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *c
         for (int a = RPL - 1; a >= 1; --a) C[a] = fma(dfr[a], cd.dg, fma(cd.df, dgr[a], C[a - 1]));
         C[0] = fma(dfr[0], cd.dg, fma(cd.df, dgr[0], v));
         if (w < NW - 1 && lane == 31) bout[c] = C[RPL - 1];
-        const int64_t j = cs + c;
         if (!BINS) {
             bool hit = false;
 #pragma unroll
             for (int a = 0; a < RPL; ++a) {
                 bool h = C[a] * cd.inv > th[a];
-                if (DIAG) h = h && nontrivial(rbase + a, j, A.E);
+                if (DIAG) h = h && nontrivial(rbase + a, cs + c, A.E);
                 hit |= h;
             }
             if (hit) {
+                const int32_t j = (int32_t)(cs + c);
 #pragma unroll
                 for (int a = 0; a < RPL; ++a) {
                     const T key = C[a] * cd.inv;
                     if (key > th[a] && nontrivial(rbase + a, j, A.E)) {
-                        const int64_t r = rbase + a;
-                        const int slot = atomicAdd(&A.ccnt[r], 1);
-                        if (slot < A.cap) {
-                            A.ckey[r * A.cap + slot] = key;
-                            A.cj[r * A.cap + slot] = (int32_t)j;
-                        }
+                        const int rl = rl0 + a;
+                        int32_t cnt = lcnt[rl];
+                        topp_insert<T>(lkey + rl * A.p, lj + rl * A.p, cnt, A.p, key, j, th[a]);
+                        lcnt[rl] = cnt;
                     }
                 }
             }
@@ -203,7 +231,7 @@ __device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *c
 #pragma unroll
             for (int a = 0; a < RPL; ++a) {
                 T key = C[a] * cd.inv;
-                if (DIAG && !nontrivial(rbase + a, j, A.E)) key = neg_inf<T>();
+                if (DIAG && !nontrivial(rbase + a, cs + c, A.E)) key = neg_inf<T>();
                 runmax[a] = fmax_t(runmax[a], key);   // NaN keys (padding) are ignored
             }
         }
@@ -217,16 +245,22 @@ __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
     extern __shared__ __align__(32) unsigned char smem_raw[];
     Col<T> *colbuf = reinterpret_cast<Col<T> *>(smem_raw);        // [NW][CH]
     T *bbuf = reinterpret_cast<T *>(colbuf + NW * CH);             // [NW][2][CH]
-    int *sbins = reinterpret_cast<int *>(bbuf + NW * 2 * CH);      // [R][p] (bins mode)
+    unsigned char *tail = reinterpret_cast<unsigned char *>(bbuf + NW * 2 * CH);
+    // bins mode: int [R][nbins];  top-p mode: T [R][p], int32 [R][p], int32 [R]
+    int *sbins = reinterpret_cast<int *>(tail);
+    T *lkey = reinterpret_cast<T *>(tail);
+    int32_t *lj = reinterpret_cast<int32_t *>(lkey + R * A.p);
+    int32_t *lcnt = lj + R * A.p;
     __shared__ int s_unit;
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nb = *A.nbands;
     const int64_t total = (int64_t)nb * A.ngroups;
     const int NEG_ORD = f2ord(-__int_as_float(0x7f800000));
+    const int nbins = A.nbins;
 
     if (BINS)
-        for (int t = threadIdx.x; t < R * A.p; t += blockDim.x) sbins[t] = NEG_ORD;
+        for (int t = threadIdx.x; t < R * nbins; t += blockDim.x) sbins[t] = NEG_ORD;
 
     for (;;) {
         if (threadIdx.x == 0) s_unit = atomicAdd(A.unit_ctr, 1);
@@ -243,6 +277,7 @@ __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
         const int nchunk = (int)((c1 - c0 + CH - 1) / CH);
         const int64_t rfirst = i0 + (int64_t)w * 32 * RPL;
         const int64_t rbase = rfirst + lane * RPL;
+        const int rl0 = w * 32 * RPL + lane * RPL;
         const T *sleft = A.seed + (c0 / R) * A.spitch;
         const T *stop = A.seed + (int64_t)band * A.spitch;
 
@@ -256,6 +291,7 @@ __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
             th[a] = A.thr[r];
             C[a] = sleft[r + 1];
             runmax[a] = neg_inf<T>();
+            if (!BINS) lcnt[rl0 + a] = 0;
         }
         T carry = sleft[rfirst];
 
@@ -280,14 +316,16 @@ __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
                 const int64_t rlo = rfirst, rhi = rfirst + 32 * RPL - 1;
                 const bool diag = (cs <= rhi + A.E) && (cs + CH - 1 >= rlo - A.E);
                 if (diag)
-                    band_chunk<T, RPL, NW, BINS, true>(A, cbuf, tp, bout, lane, w, cs, rbase, C, dfr, dgr, th, runmax);
+                    band_chunk<T, RPL, NW, BINS, true>(A, cbuf, tp, bout, lane, w, cs, rbase, rl0, C, dfr, dgr, th,
+                                                       runmax, lkey, lj, lcnt);
                 else
-                    band_chunk<T, RPL, NW, BINS, false>(A, cbuf, tp, bout, lane, w, cs, rbase, C, dfr, dgr, th, runmax);
+                    band_chunk<T, RPL, NW, BINS, false>(A, cbuf, tp, bout, lane, w, cs, rbase, rl0, C, dfr, dgr, th,
+                                                        runmax, lkey, lj, lcnt);
                 if (BINS) {
-                    const int bin = (int)((cs / CH) % A.p);
+                    const int bin = (int)((cs / CH) % nbins);
 #pragma unroll
                     for (int a = 0; a < RPL; ++a) {
-                        atomicMax(&sbins[(w * 32 * RPL + lane * RPL + a) * A.p + bin], f2ord(to_float_rd(runmax[a])));
+                        atomicMax(&sbins[(rl0 + a) * nbins + bin], f2ord(to_float_rd(runmax[a])));
                         runmax[a] = neg_inf<T>();
                     }
                 }
@@ -296,63 +334,86 @@ __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
             __syncthreads();
         }
         if (BINS) {
-            for (int t = threadIdx.x; t < R * A.p; t += blockDim.x) {
-                const int64_t r = i0 + t / A.p;
-                if (r < A.nl && sbins[t] != NEG_ORD) atomicMax(&A.bins[r * A.p + (t % A.p)], sbins[t]);
+            for (int t = threadIdx.x; t < R * nbins; t += blockDim.x) {
+                const int64_t r = i0 + t / nbins;
+                if (r < A.nl && sbins[t] != NEG_ORD) atomicMax(&A.bins[r * nbins + (t % nbins)], sbins[t]);
                 sbins[t] = NEG_ORD;
             }
             __syncthreads();
+        } else {
+            // this unit's per-row lists -> the row's slot for column group g
+#pragma unroll
+            for (int a = 0; a < RPL; ++a) {
+                const int64_t r = rbase + a;
+                if (r >= A.nl) continue;
+                const int rl = rl0 + a;
+                const int32_t cnt = lcnt[rl];
+                const int64_t slot = r * A.ngroups + g;
+                A.scnt[slot] = cnt;
+                for (int e = 0; e < cnt; ++e) {
+                    A.skey[slot * A.p + e] = lkey[rl * A.p + e];
+                    A.sj[slot * A.p + e] = lj[rl * A.p + e];
+                }
+            }
         }
     }
 }
 
 template <typename T>
-size_t band_smem(bool bins_mode, int p)
+size_t band_smem(bool bins_mode, int p, int rpl)
 {
-    constexpr int RPL = BandGeo<T>::RPL, NW = BandGeo<T>::NW;
+    constexpr int NW = BAND_NW;
+    const int R = 32 * rpl * NW;
     size_t s = (size_t)NW * CH * sizeof(Col<T>) + (size_t)NW * 2 * CH * sizeof(T);
-    if (bins_mode) s += (size_t)32 * RPL * NW * p * sizeof(int);
+    if (bins_mode) s += (size_t)R * band_nbins(p) * sizeof(int);
+    else s += (size_t)R * p * (sizeof(T) + sizeof(int32_t)) + (size_t)R * sizeof(int32_t);
     return s;
 }
 
-template <typename T>
-static void *band_fn(bool bins)
+template <typename T, int RPL>
+static const void *band_fn_rpl(bool bins)
 {
-    constexpr int RPL = BandGeo<T>::RPL, NW = BandGeo<T>::NW;
-    return bins ? (void *)k_band<T, RPL, NW, true> : (void *)k_band<T, RPL, NW, false>;
+    return bins ? (const void *)k_band<T, RPL, BAND_NW, true> : (const void *)k_band<T, RPL, BAND_NW, false>;
 }
 
 template <typename T>
-int band_occupancy(bool bins_mode, int p)
+static const void *band_fn(bool bins, int rpl)
 {
-    constexpr int NW = BandGeo<T>::NW;
-    const void *fn = band_fn<T>(bins_mode);
-    const size_t sm = band_smem<T>(bins_mode, p);
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    switch (rpl) {
+    case 8: return band_fn_rpl<T, 8>(bins);
+    case 4: return band_fn_rpl<T, 4>(bins);
+    case 2: return band_fn_rpl<T, 2>(bins);
+    default: return band_fn_rpl<T, 1>(bins);
+    }
+}
+
+template <typename T>
+int band_occupancy(bool bins_mode, int p, int rpl)
+{
+    const void *fn = band_fn<T>(bins_mode, rpl);
+    const size_t sm = band_smem<T>(bins_mode, p, rpl);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return 0;
     int blocks = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, NW * 32, sm);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, BAND_NW * 32, sm) != cudaSuccess) return 0;
     return blocks;
 }
 
 template <typename T>
 void launch_band(const BandArgs<T> &a, bool bins_mode, int grid, cudaStream_t s)
 {
-    constexpr int RPL = BandGeo<T>::RPL, NW = BandGeo<T>::NW;
-    const size_t sm = band_smem<T>(bins_mode, a.p);
-    if (bins_mode) {
-        cudaFuncSetAttribute(k_band<T, RPL, NW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_band<T, RPL, NW, true><<<grid, NW * 32, sm, s>>>(a);
-    } else {
-        cudaFuncSetAttribute(k_band<T, RPL, NW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_band<T, RPL, NW, false><<<grid, NW * 32, sm, s>>>(a);
-    }
+    const int rpl = a.rpl;
+    const size_t sm = band_smem<T>(bins_mode, a.p, rpl);
+    const void *fn = band_fn<T>(bins_mode, rpl);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    void *args[] = {const_cast<BandArgs<T> *>(&a)};
+    cudaLaunchKernel(fn, dim3(grid), dim3(BAND_NW * 32), args, sm, s);
 }
 
 template void launch_band<float>(const BandArgs<float> &, bool, int, cudaStream_t);
 template void launch_band<double>(const BandArgs<double> &, bool, int, cudaStream_t);
-template int band_occupancy<float>(bool, int);
-template int band_occupancy<double>(bool, int);
-template size_t band_smem<float>(bool, int);
-template size_t band_smem<double>(bool, int);
+template int band_occupancy<float>(bool, int, int);
+template int band_occupancy<double>(bool, int, int);
+template size_t band_smem<float>(bool, int, int);
+template size_t band_smem<double>(bool, int, int);
 
 }  // namespace mad

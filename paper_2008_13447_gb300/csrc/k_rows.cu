@@ -57,6 +57,75 @@ __device__ double comoment(const double *x, int64_t i, int64_t j, int l, double 
     return s;
 }
 
+// Error of d = sqrt(2 l (1 - q)) caused by an error dq of q (d^2 moves by
+// 2 l dq at most).
+__device__ __forceinline__ double dist_err(double d, double dq, int l)
+{
+    const double t = 2.0 * l * dq;
+    return t / (d + sqrt(d * d + t));
+}
+__device__ __forceinline__ bool needs_refine(const ErrModel &em, double d, double dq, int l)
+{
+    if (!(dq > 0.0)) return false;
+    const double tol = em.rel_tol * d + em.abs_coef * sqrt((double)l);
+    return dist_err(d, dq, l) > 0.5 * tol;
+}
+__device__ __forceinline__ double dq_pair(const ErrModel &em, int64_t i, int64_t j)
+{
+    return em.dq0 * (double)em.kappa[i] * (double)em.kappa[j];
+}
+__device__ __forceinline__ double dq_row(const ErrModel &em, int64_t i)
+{
+    return em.dq0 * (double)em.kappa[i] * (double)(*em.kappa_max);
+}
+
+// A row's stored entries during one length: correlation q (estimated),
+// its error bound dq, partner j and storage slot e, kept sorted by
+// (q desc, j asc).
+struct Ent {
+    double q;
+    float dq;
+    int32_t j;
+    int32_t e;
+};
+
+__device__ __forceinline__ void ins_ent(Ent *v, int n, Ent x)
+{
+    int t = n;
+    while (t > 0 && (v[t - 1].q < x.q || (v[t - 1].q == x.q && v[t - 1].j > x.j))) {
+        v[t] = v[t - 1];
+        --t;
+    }
+    v[t] = x;
+}
+
+// Re-evaluate in FP64 every entry among the first m (in correlation order)
+// whose distance error could exceed half the tolerance; repeat until the
+// first m are all accurate (re-evaluation can reorder entries).
+__device__ void refine_reported(const double *x, int64_t i, int l, double mui, double m2i, const double *mu,
+                                const double *m2, const ErrModel &em, RowState st, int64_t n0, Ent *v, int cnt, int m,
+                                unsigned long long *stat_dq)
+{
+    double dqmax = 0.0;
+    for (int pass = 0; pass <= cnt; ++pass) {
+        int hit = -1;
+        for (int a = 0; a < m && a < cnt; ++a)
+            if (needs_refine(em, dist_from_q(v[a].q, l), v[a].dq, l)) { hit = a; break; }
+        if (hit < 0) break;
+        Ent t = v[hit];
+        const double c = comoment(x, i, t.j, l, mui, mu[t.j]);
+        const double q = clamp_q(c / sqrt(m2i * m2[t.j]));
+        dqmax = fmax(dqmax, fabs(q - t.q));
+        st.ent_c[(int64_t)t.e * n0 + i] = c;
+        st.ent_dq[(int64_t)t.e * n0 + i] = 0.0f;
+        t.q = q;
+        t.dq = 0.0f;
+        for (int a = hit; a + 1 < cnt; ++a) v[a] = v[a + 1];
+        ins_ent(v, cnt - 1, t);
+    }
+    if (dqmax > 0.0 && stat_dq) atomicMax(stat_dq, (unsigned long long)__double_as_longlong(dqmax));
+}
+
 // ------------------------------------------------------------ extension
 //
 // For one length l > lmin and every row i < n_l:
@@ -88,8 +157,7 @@ __device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i)
     const double xi = A.x[i + l - 1] - A.mu_prev[i];
     const double wgt = (l - 1.0) / l;
 
-    double qs[MAXP];
-    int32_t js[MAXP];
+    Ent v[MAXP];
     int cnt = 0;
     for (int e = 0; e < A.p; ++e) {
         const int32_t j = A.st.ent_j[e * n0 + i];
@@ -101,29 +169,45 @@ __device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i)
         const double c = fma(wgt * xi, A.x[j + l - 1] - A.mu_prev[j], A.st.ent_c[e * n0 + i]);
         A.st.ent_c[e * n0 + i] = c;
         const bool flat_j = A.run[j] >= l;
-        ins_qj(qs, js, cnt, corr(c, m2i, A.m2[j], false, flat_j), j);
+        Ent t{corr(c, m2i, A.m2[j], false, flat_j), flat_j ? 0.0f : A.st.ent_dq[e * n0 + i], j, e};
+        ins_ent(v, cnt, t);
         ++cnt;
     }
     const double sig = sqrt(m2i / l);
     const double B = A.st.bnum[i] / sig;
     const int m = A.m_max;
-    const bool ok = cnt >= m && dist_from_q(qs[m - 1] - A.dq_entry, l) < B;
+    // the m-th smallest true distance is at most the m-th smallest pessimistic one
+    bool ok = false;
+    if (cnt >= m) {
+        double dp[MAXP];
+        for (int a = 0; a < cnt; ++a) {
+            const double d = dist_from_q(v[a].q - v[a].dq, l);
+            int b = a;
+            while (b > 0 && dp[b - 1] > d) { dp[b] = dp[b - 1]; --b; }
+            dp[b] = d;
+        }
+        ok = dp[m - 1] < B;
+    }
     if (ok) {
+        refine_reported(A.x, i, l, A.mu[i], m2i, A.mu, A.m2, A.em, A.st, n0, v, cnt, m, &A.out.stats[3]);
         double ds[MAXP];
-        for (int e = 0; e < cnt; ++e) ds[e] = dist_from_q(qs[e], l);
-        // correlation order is distance order (ties: smaller offset)
+        int32_t js[MAXP];
+        for (int a = 0; a < cnt; ++a) {
+            ds[a] = dist_from_q(v[a].q, l);
+            js[a] = v[a].j;
+        }
         write_nn(A.out, n0, i, m, ds, js, cnt);
         valmp_update(A.vm, i, ds[0], js[0], l);
         A.st.flag[i] = ROW_DONE;
         A.thr[i] = T(pinf());
         return 1;
     }
-    // theta_q: p-th best among p distinct, exactly evaluated partners (the
-    // remaining entries, lowered by their error bound, then partners next
-    // to the exclusion zone evaluated directly in FP64)
+    // theta_q: p-th best among p distinct partners with known lower bounds
+    // on their correlation (the remaining entries lowered by their error
+    // bound, then partners next to the exclusion zone evaluated in FP64)
     double qlow[MAXP];
     int nlow = 0;
-    for (int e = 0; e < cnt; ++e) qlow[nlow++] = qs[e] - A.dq_entry;
+    for (int a = 0; a < cnt; ++a) qlow[nlow++] = v[a].q - v[a].dq;
     const int64_t ntc = nontrivial_count(i, A.nl, E);
     double theta = -pinf();
     if (ntc > A.p) {
@@ -133,7 +217,7 @@ __device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i)
                 const int64_t j = side == 0 ? i + E + t : i - E - t;
                 if (j < 0 || j >= A.nl) continue;
                 bool have = false;
-                for (int e = 0; e < cnt; ++e) have |= (js[e] == j);
+                for (int a = 0; a < cnt; ++a) have |= (v[a].j == j);
                 if (have) continue;
                 const bool flat_j = A.run[j] >= l;
                 const double c = flat_j ? 0.0 : comoment(A.x, i, j, l, mui, A.mu[j]);
@@ -142,12 +226,12 @@ __device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i)
         }
         if (nlow >= A.p) {
             for (int a = 1; a < nlow; ++a) {
-                const double v = qlow[a];
+                const double val = qlow[a];
                 int b = a;
-                while (b > 0 && qlow[b - 1] < v) { qlow[b] = qlow[b - 1]; --b; }
-                qlow[b] = v;
+                while (b > 0 && qlow[b - 1] < val) { qlow[b] = qlow[b - 1]; --b; }
+                qlow[b] = val;
             }
-            theta = qlow[A.p - 1] - A.dq_band;
+            theta = qlow[A.p - 1] - dq_row(A.em, i);
         }
     }
     A.st.flag[i] = ROW_RECOMPUTE;
@@ -196,15 +280,14 @@ template void launch_extend<double>(const ExtArgs<double> &, cudaStream_t);
 // ---------------------------------------------------------------- merge
 //
 // After the band kernel: for every row flagged for recompute, select the p
-// largest keys (ties: smaller offset) among its candidates. They are the
-// row's new stored entries at base length l (the p smallest Eq. LB values,
-// Algorithm 3 lines storing into listDP); the row's matrix profile value and
-// m-th best matches at l come from them; the bound numerator is
-// sqrt(l (1 - max(q_p + dq_band, 0)^2)) * sigma_i(l) (+inf when the row has
-// at most p non-trivial partners, all of them stored).
-// A candidate list that overflowed is replaced by a tighter threshold (the
-// p-th best key among the kept candidates, p distinct columns) and the row
-// stays flagged for another pass.
+// largest keys (ties: smaller offset) among the per-group lists the band
+// kernel kept. They are the row's new stored entries at base length l (the
+// p smallest Eq. LB values, Algorithm 3 filling listDP); the row's matrix
+// profile value and m-th best matches at l come from them; the bound
+// numerator is sqrt(l (1 - max(q_p + dq_band, 0)^2)) * sigma_i(l) (+inf when
+// the row has at most p non-trivial partners, all of them stored).
+// A row whose lists hold fewer than min(p, partners) keys had a threshold
+// above its p-th best key; it is flagged for another pass without one.
 template <typename T>
 __global__ void k_merge(MergeArgs<T> A)
 {
@@ -213,63 +296,39 @@ __global__ void k_merge(MergeArgs<T> A)
     if (A.st.flag[i] != ROW_RECOMPUTE) return;
     const int l = A.l;
     const int64_t n0 = A.n0, E = A.E;
-    const int cap = A.cap;
     const int p = A.p;
-    const int cnt = A.ccnt[i];
     const int64_t ntc = nontrivial_count(i, A.nl, E);
     const int need = (int)(ntc < p ? ntc : p);
-    const T *kk = A.ckey + i * cap;
-    const int32_t *jj = A.cj + i * cap;
 
-    if (cnt > cap || cnt < need) {
-        // refill: p-th best key among the kept candidates, or no threshold
-        T th = T(-pinf());
-        if (cnt > cap) {
-            T best[MAXP];
-            int nb = 0;
-            for (int c = 0; c < cap; ++c) {
-                const T v = kk[c];
-                if (nb < p) {
-                    int b = nb++;
-                    while (b > 0 && best[b - 1] < v) { best[b] = best[b - 1]; --b; }
-                    best[b] = v;
-                } else if (v > best[p - 1]) {
-                    int b = p - 1;
-                    while (b > 0 && best[b - 1] < v) { best[b] = best[b - 1]; --b; }
-                    best[b] = v;
-                }
-            }
-            // keys >= best[p-1] are wanted again: threshold one step below it
-            const T v = best[p - 1];
-            th = v - (v > T(0) ? v : -v) * T(1e-6) - T(1e-30);
-            if (!(th > A.thr[i])) th = A.thr[i];
-        }
-        A.thr[i] = th;
-        A.ccnt[i] = 0;
-        atomicAdd(A.overflow, 1u);
-        return;
-    }
-    // top-p by key desc, offset asc
+    // top-p by key desc, offset asc over all groups
     T bk[MAXP];
     int32_t bj[MAXP];
     int nb = 0;
-    for (int c = 0; c < cnt; ++c) {
-        const T v = kk[c];
-        const int32_t j = jj[c];
-        if (nb == p && !(v > bk[p - 1] || (v == bk[p - 1] && j < bj[p - 1]))) continue;
-        int b = nb < p ? nb++ : p - 1;
-        while (b > 0 && (bk[b - 1] < v || (bk[b - 1] == v && bj[b - 1] > j))) {
-            bk[b] = bk[b - 1];
-            bj[b] = bj[b - 1];
-            --b;
+    for (int g = 0; g < A.ngroups && (int64_t)g * A.group_w < A.nl; ++g) {
+        const int64_t slot = i * A.ngroups + g;
+        const int cnt = A.scnt[slot];
+        for (int c = 0; c < cnt; ++c) {
+            const T v = A.skey[slot * p + c];
+            const int32_t j = A.sj[slot * p + c];
+            if (nb == p && !(v > bk[p - 1] || (v == bk[p - 1] && j < bj[p - 1]))) continue;
+            int b = nb < p ? nb++ : p - 1;
+            while (b > 0 && (bk[b - 1] < v || (bk[b - 1] == v && bj[b - 1] > j))) {
+                bk[b] = bk[b - 1];
+                bj[b] = bj[b - 1];
+                --b;
+            }
+            bk[b] = v;
+            bj[b] = j;
         }
-        bk[b] = v;
-        bj[b] = j;
+    }
+    if (nb < need) {
+        A.thr[i] = T(-pinf());
+        atomicAdd(A.overflow, 1u);
+        return;
     }
     const double m2i = A.m2[i];
     const double sqm2i = sqrt(m2i);
-    double qs[MAXP];
-    int32_t js[MAXP];
+    Ent v[MAXP];
     int nq = 0;
     for (int e = 0; e < p; ++e) {
         if (e < nb) {
@@ -277,51 +336,26 @@ __global__ void k_merge(MergeArgs<T> A)
             const double inv = (double)A.col[j].inv;
             const bool flat_j = A.run[j] >= l;
             const double c = (flat_j || inv == 0.0) ? 0.0 : (double)bk[e] / inv;
+            const float dq = flat_j ? 0.0f : (float)dq_pair(A.em, i, j);
             A.st.ent_j[e * n0 + i] = j;
             A.st.ent_c[e * n0 + i] = c;
-            ins_qj(qs, js, nq, corr(c, m2i, A.m2[j], false, flat_j), j);
+            A.st.ent_dq[e * n0 + i] = dq;
+            Ent t{corr(c, m2i, A.m2[j], false, flat_j), dq, j, e};
+            ins_ent(v, nq, t);
             ++nq;
         } else {
             A.st.ent_j[e * n0 + i] = -1;
             A.st.ent_c[e * n0 + i] = 0.0;
+            A.st.ent_dq[e * n0 + i] = 0.0f;
         }
     }
-    // Entries at a small distance are re-evaluated directly in FP64: near
-    // d = 0 the distance amplifies any error of q (d^2 = 2 l (1 - q)).
-    if (A.d_refine > 0.0) {
-        const double mui = A.mu[i];
-        double dqmax = 0.0;
-        bool changed = false;
-        for (int e = 0; e < nq; ++e) {
-            if (!(dist_from_q(qs[e], l) < A.d_refine)) continue;
-            const int32_t j = js[e];
-            if (A.run[j] >= l) continue;
-            const double c = comoment(A.x, i, j, l, mui, A.mu[j]);
-            const double q = corr(c, m2i, A.m2[j], false, false);
-            dqmax = fmax(dqmax, fabs(q - qs[e]));
-            qs[e] = q;
-            changed = true;
-            for (int f = 0; f < p; ++f)
-                if (A.st.ent_j[f * n0 + i] == j) A.st.ent_c[f * n0 + i] = c;
-        }
-        if (changed) {
-            for (int a = 1; a < nq; ++a) {   // restore (q desc, j asc) order
-                const double q = qs[a];
-                const int32_t j = js[a];
-                int b = a;
-                while (b > 0 && (qs[b - 1] < q || (qs[b - 1] == q && js[b - 1] > j))) {
-                    qs[b] = qs[b - 1];
-                    js[b] = js[b - 1];
-                    --b;
-                }
-                qs[b] = q;
-                js[b] = j;
-            }
-            atomicMax(&A.out.stats[3], (unsigned long long)__double_as_longlong(dqmax));
-        }
-    }
+    refine_reported(A.x, i, l, A.mu[i], m2i, A.mu, A.m2, A.em, A.st, n0, v, nq, A.m_max, &A.out.stats[3]);
     double ds[MAXP];
-    for (int e = 0; e < nq; ++e) ds[e] = dist_from_q(qs[e], l);
+    int32_t js[MAXP];
+    for (int e = 0; e < nq; ++e) {
+        ds[e] = dist_from_q(v[e].q, l);
+        js[e] = v[e].j;
+    }
     write_nn(A.out, n0, i, A.m_max, ds, js, nq);
     if (nq > 0) valmp_update(A.vm, i, ds[0], js[0], l);
     A.st.base[i] = l;
@@ -329,13 +363,13 @@ __global__ void k_merge(MergeArgs<T> A)
     if (ntc <= p) {
         A.st.bnum[i] = pinf();
     } else {
-        double qp = (double)bk[p - 1] / sqm2i + A.dq_band;
+        // unstored partners have band keys <= the p-th kept key
+        double qp = (double)bk[p - 1] / sqm2i + dq_row(A.em, i);
         qp = qp > 1.0 ? 1.0 : (qp < 0.0 ? 0.0 : qp);
         A.st.bnum[i] = sqrt((double)l * (1.0 - qp * qp)) * sig;
     }
     A.st.flag[i] = ROW_DONE;
     A.thr[i] = T(pinf());
-    A.ccnt[i] = 0;
 }
 
 template <typename T>
@@ -347,34 +381,44 @@ void launch_merge(const MergeArgs<T> &a, cudaStream_t s)
 template void launch_merge<float>(const MergeArgs<float> &, cudaStream_t);
 template void launch_merge<double>(const MergeArgs<double> &, cudaStream_t);
 
-// First threshold at lmin from the interleaved maxima: the smallest of the
-// p bin maxima (p distinct columns) lower-bounds the p-th best key; rows
-// with an empty bin get no threshold.
+// First threshold at lmin from the interleaved maxima: bin b holds the
+// largest key over the column chunks of index = b (mod nbins); the p-th
+// largest of those maxima comes from p distinct columns, so it lower-bounds
+// the row's p-th best key. Rows with fewer than p non-empty bins get none.
 template <typename T>
-__global__ void k_theta_bins(const int *bins, int64_t nl, int p, const double *m2, double dq_band, T *thr)
+__global__ void k_theta_bins(const int *bins, int nbins, int64_t nl, int p, const double *m2, ErrModel em, T *thr)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= nl) return;
-    float mn = __int_as_float(0x7f800000);
-    for (int b = 0; b < p; ++b) mn = fminf(mn, ord2f(bins[i * p + b]));
-    double th = (double)mn;
-    if (mn == -__int_as_float(0x7f800000) || mn != mn) {
+    float top[2 * MAXP];
+    int nt = 0;
+    for (int b = 0; b < nbins; ++b) {
+        const float v = ord2f(bins[i * nbins + b]);
+        if (!(v > -__int_as_float(0x7f800000))) continue;
+        int t = nt++;
+        while (t > 0 && top[t - 1] < v) { top[t] = top[t - 1]; --t; }
+        top[t] = v;
+    }
+    if (nt < p) {
         thr[i] = T(-pinf());
         return;
     }
+    double th = (double)top[p - 1];
     // bins hold keys rounded down; widen by the key error and one FP32 step
-    th -= dq_band * sqrt(m2[i]) + fabs(th) * 1e-6;
+    th -= dq_row(em, i) * sqrt(m2[i]) + fabs(th) * 1e-6;
     thr[i] = T(th);
 }
 
 template <typename T>
-void launch_theta_bins(const int *bins, int64_t nl, int p, const double *m2, double dq_band, T *thr, cudaStream_t s)
+void launch_theta_bins(const int *bins, int nbins, int64_t nl, int p, const double *m2, ErrModel em, T *thr,
+                       cudaStream_t s)
 {
     const int B = 256;
-    k_theta_bins<T><<<(unsigned)((nl + B - 1) / B), B, 0, s>>>(bins, nl, p, m2, dq_band, thr);
+    k_theta_bins<T><<<(unsigned)((nl + B - 1) / B), B, 0, s>>>(bins, nbins, nl, p, m2, em, thr);
 }
-template void launch_theta_bins<float>(const int *, int64_t, int, const double *, double, float *, cudaStream_t);
-template void launch_theta_bins<double>(const int *, int64_t, int, const double *, double, double *, cudaStream_t);
+template void launch_theta_bins<float>(const int *, int, int64_t, int, const double *, ErrModel, float *, cudaStream_t);
+template void launch_theta_bins<double>(const int *, int, int64_t, int, const double *, ErrModel, double *,
+                                        cudaStream_t);
 
 // ----------------------------------------------------------- flat rows
 //
@@ -414,6 +458,7 @@ __global__ void k_flat_rows(FlatArgs A)
     for (int e = 0; e < p; ++e) {
         A.st.ent_j[e * n0 + i] = e < nf ? js[e] : -1;
         A.st.ent_c[e * n0 + i] = 0.0;
+        A.st.ent_dq[e * n0 + i] = 0.0f;
     }
     for (int e = 0; e < nf; ++e) ds[e] = dist_from_q(qs[e], l);
     write_nn(A.out, n0, i, A.m_max, ds, js, nf);

@@ -99,6 +99,53 @@ template void launch_coldata<float>(const double *, int64_t, int64_t, int, const
 template void launch_coldata<double>(const double *, int64_t, int64_t, int, const double *, const double *,
                                      const int32_t *, Col<double> *, cudaStream_t);
 
+// Contrast factor kappa_i (see ErrModel): block maxima of M2 over 256
+// windows, then for each window the maximum over the blocks that cover the R
+// windows ending at it (a superset of them, so kappa is not underestimated).
+__global__ void k_m2_blockmax(const double *__restrict__ m2, int64_t nl, double *__restrict__ blkmax)
+{
+    __shared__ double sh[32];
+    const int64_t i = blockIdx.x * (int64_t)256 + threadIdx.x;
+    double v = i < nl ? m2[i] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < 8 ? sh[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (threadIdx.x == 0) blkmax[blockIdx.x] = v;
+    }
+}
+
+__global__ void k_kappa(const double *__restrict__ m2, const int32_t *__restrict__ run, int64_t nl, int l, int R,
+                        const double *__restrict__ blkmax, float *__restrict__ kappa, float *__restrict__ kappa_max)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    float k = 1.0f;
+    if (i < nl) {
+        const double mi = m2[i];
+        if (run[i] < l && mi > 0.0) {
+            const int64_t lo = i - R + 1 < 0 ? 0 : i - R + 1;
+            double mx = mi;
+            for (int64_t b = lo / 256; b <= i / 256; ++b) mx = fmax(mx, blkmax[b]);
+            k = (float)sqrt(mx / mi) * 1.0001f;
+            if (!(k >= 1.0f)) k = 1.0f;
+        }
+        kappa[i] = k;
+    }
+    for (int o = 16; o > 0; o >>= 1) k = fmaxf(k, __shfl_xor_sync(0xffffffffu, k, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(kappa_max), __float_as_int(k));
+}
+
+void launch_kappa(const double *m2, const int32_t *run, int64_t nl, int l, int R, double *blkmax, float *kappa,
+                  float *kappa_max, cudaStream_t s)
+{
+    const unsigned nb = (unsigned)((nl + 255) / 256);
+    k_m2_blockmax<<<nb, 256, 0, s>>>(m2, nl, blkmax);
+    cudaMemsetAsync(kappa_max, 0, sizeof(float), s);
+    k_kappa<<<nb, 256, 0, s>>>(m2, run, nl, l, R, blkmax, kappa, kappa_max);
+}
+
 __global__ void k_widen_f32(const float *__restrict__ in, int64_t n, double *__restrict__ out)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)

@@ -47,20 +47,39 @@ template <typename T> struct BandArgs {
     int64_t nl;
     int l;
     int64_t E;
-    int64_t group_w;        // columns per work unit (multiple of the band height)
+    int rpl;                // rows per lane (band height R = 32 * rpl * BAND_NW)
+    int64_t group_w;        // columns per work unit (multiple of R)
     int ngroups;
-    // candidate lists (append mode)
-    T *ckey;
-    int32_t *cj;
-    int32_t *ccnt;
-    int cap;
-    // per-row interleaved maxima (bins mode)
-    int *bins;
     int p;
+    // top-p mode: per row and column group, up to p (key, offset) pairs
+    T *skey;                // [row][group][p]
+    int32_t *sj;            // [row][group][p]
+    int32_t *scnt;          // [row][group]
+    // bins mode: per row, the maximum key of each class of column chunks
+    int *bins;              // [row][nbins] order-preserving ints
+    int nbins;
 };
 template <typename T> void launch_band(const BandArgs<T> &a, bool bins_mode, int grid, cudaStream_t s);
-template <typename T> int band_occupancy(bool bins_mode, int p);
-template <typename T> size_t band_smem(bool bins_mode, int p);
+template <typename T> int band_occupancy(bool bins_mode, int p, int rpl);
+template <typename T> size_t band_smem(bool bins_mode, int p, int rpl);
+
+// ------------------------------------------------------------- error model
+// Rounding of the band kernel's recurrence accumulates along a diagonal; its
+// size relative to a cell's normaliser sqrt(M2_i M2_j) grows with the
+// variance met earlier on the chain. kappa_i = sqrt(max M2 over the R windows
+// ending at i / M2_i) (>= 1) measures that contrast, and the correlation of a
+// band key for cell (i, j) is trusted to dq0 * kappa_i * kappa_j. A distance
+// whose resulting error could exceed half its tolerance is re-evaluated
+// directly in FP64.
+struct ErrModel {
+    const float *kappa;     // per window
+    const float *kappa_max; // max over windows at this length (device scalar)
+    double dq0;
+    double rel_tol;         // distance tolerance = rel_tol * d + abs_coef * sqrt(l)
+    double abs_coef;
+};
+void launch_kappa(const double *m2, const int32_t *run, int64_t nl, int l, int R, double *blkmax, float *kappa,
+                  float *kappa_max, cudaStream_t s);
 
 // ----------------------------------------------------------------- k_rows.cu
 // Per-row state kept across lengths (structure of arrays, n0 = n - lmin + 1):
@@ -73,6 +92,7 @@ template <typename T> size_t band_smem(bool bins_mode, int p);
 struct RowState {
     int32_t *ent_j;
     double *ent_c;
+    float *ent_dq;          // correlation error bound of each entry (0 once re-evaluated in FP64)
     int32_t *base;
     double *bnum;
     int32_t *flag;
@@ -106,8 +126,7 @@ template <typename T> struct ExtArgs {
     Valmp vm;
     LenOut out;
     T *thr;
-    double dq_entry;        // correlation error bound of stored entries
-    double dq_band;         // correlation error bound of the band kernel's keys
+    ErrModel em;
 };
 template <typename T> void launch_extend(const ExtArgs<T> &a, cudaStream_t s);
 
@@ -116,26 +135,27 @@ template <typename T> struct MergeArgs {
     int64_t n0, nl;
     int l;
     int64_t E;
-    int p, m_max, cap;
+    int p, m_max;
     const double *mu;
     const double *m2;
     const int32_t *run;
     const Col<T> *col;
-    const T *ckey;
-    const int32_t *cj;
-    int32_t *ccnt;
+    const T *skey;
+    const int32_t *sj;
+    const int32_t *scnt;
+    int ngroups;
+    int64_t group_w;        // columns per group; groups starting at or past n_l are empty
     T *thr;
     RowState st;
     Valmp vm;
     LenOut out;
-    double dq_band;
-    double d_refine;        // entries closer than this are re-evaluated directly in FP64
+    ErrModel em;
     unsigned int *overflow;
 };
 template <typename T> void launch_merge(const MergeArgs<T> &a, cudaStream_t s);
 
 template <typename T>
-void launch_theta_bins(const int *bins, int64_t nl, int p, const double *m2, double dq_band, T *thr,
+void launch_theta_bins(const int *bins, int nbins, int64_t nl, int p, const double *m2, ErrModel em, T *thr,
                        cudaStream_t s);
 
 struct FlatArgs {

@@ -137,21 +137,21 @@ void init_ctx(mad_ctx *ctx, const mad_options *opt)
 
 // ------------------------------------------------------------- profile
 
+// Error model of the band kernel's keys (see ErrModel): base correlation
+// error dq0 (scaled per cell by the contrast factors) and the distance
+// tolerance that decides which reported entries are re-evaluated in FP64.
 template <typename T>
 struct Precision;
 template <>
 struct Precision<double> {
-    // Correlation error bounds used by the bound tests and thresholds: FP64
-    // recurrences over at most one band of rows from FP64 seeds.
-    static constexpr double dq_entry = 1e-10, dq_band = 1e-10;
+    // FP64 recurrence over at most one band from FP64 seeds: ~1e-14 observed.
+    static constexpr double dq0 = 5e-14, rel_tol = 1e-9, abs_coef = 0.0;
 };
 template <>
 struct Precision<float> {
-    // FP32 recurrence over at most one band (2048 rows) from FP32 seeds.
-    // Observed errors are ~1e-7 on smooth data and reach ~5e-5 where a
-    // diagonal crosses a strong variance contrast (flat segments); the
-    // margin covers the latter.
-    static constexpr double dq_entry = 1e-4, dq_band = 1e-4;
+    // FP32 recurrence over at most one band from FP32 seeds: ~1e-6 observed
+    // on smooth data (epsilon_32 * sqrt(R) ~ 2.7e-6 for R = 2048).
+    static constexpr double dq0 = 3e-6, rel_tol = 0.0, abs_coef = 1e-4;
 };
 
 template <typename T>
@@ -179,11 +179,12 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     s.n0 = n0;
     const int m_max = o.m_max, k_max = o.k_max;
     const int nL = lmax - lmin + 1;
-    constexpr int R = band_rows<T>();
+    const int rpl = band_rpl<T>(p);
+    const int R = 32 * rpl * BAND_NW;
+    const int nbins = band_nbins(p);
     const int64_t K = (n0 + R - 1) / R;
     const int64_t npad = round_up(n0, R) + R + CH;
     const int64_t spitch = round_up(n0, R) + R + CH;
-    const int cap = p * 8 > 32 ? p * 8 : 32;
 
     // ---- buffers
     int32_t *run = dalloc<int32_t>(ctx, s, n);
@@ -193,13 +194,15 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     T *seed = dalloc<T>(ctx, s, K * spitch);
     T *thr = dalloc<T>(ctx, s, npad);
     RowState rs{dalloc<int32_t>(ctx, s, (size_t)p * n0), dalloc<double>(ctx, s, (size_t)p * n0),
-                dalloc<int32_t>(ctx, s, n0), dalloc<double>(ctx, s, n0), dalloc<int32_t>(ctx, s, n0)};
+                dalloc<float>(ctx, s, (size_t)p * n0), dalloc<int32_t>(ctx, s, n0), dalloc<double>(ctx, s, n0),
+                dalloc<int32_t>(ctx, s, n0)};
+    float *kappa = dalloc<float>(ctx, s, n0);
+    float *kappa_max = dalloc<float>(ctx, s, 1);
+    double *m2blk = dalloc<double>(ctx, s, (n0 + 255) / 256);
+    const ErrModel em{kappa, kappa_max, Precision<T>::dq0, Precision<T>::rel_tol, Precision<T>::abs_coef};
     Valmp vm{dalloc<double>(ctx, s, n0), dalloc<double>(ctx, s, n0), dalloc<int32_t>(ctx, s, n0),
              dalloc<int32_t>(ctx, s, n0)};
-    T *ckey = dalloc<T>(ctx, s, (size_t)n0 * cap);
-    int32_t *cj = dalloc<int32_t>(ctx, s, (size_t)n0 * cap);
-    int32_t *ccnt = dalloc<int32_t>(ctx, s, n0);
-    int *bins = dalloc<int>(ctx, s, (size_t)n0 * p);
+    int *bins = dalloc<int>(ctx, s, (size_t)n0 * nbins);
     int32_t *bands = dalloc<int32_t>(ctx, s, K);
     int32_t *counters = dalloc<int32_t>(ctx, s, 4);   // nbands, unit counter, overflow
     int32_t *krows = dalloc<int32_t>(ctx, s, K);
@@ -228,16 +231,16 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     CK(cudaMemsetAsync(dstats, 0, (size_t)nL * 5 * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(vm.len, 0, n0 * sizeof(int32_t), st));
     CK(cudaMemsetAsync(tab.len, 0, (size_t)k_max * m_max * sizeof(int32_t), st));
-    CK(cudaMemsetAsync(ccnt, 0, n0 * sizeof(int32_t), st));
     CK(cudaMemsetAsync(rs.ent_j, 0xff, (size_t)p * n0 * sizeof(int32_t), st));
     CK(cudaMemsetAsync(rs.ent_c, 0, (size_t)p * n0 * sizeof(double), st));
+    CK(cudaMemsetAsync(rs.ent_dq, 0, (size_t)p * n0 * sizeof(float), st));
     launch_fill<T>(thr, npad, T(INFINITY), st);
     k_flat_runs<<<1024, 256, 0, st>>>(s.x, n, lmax, run);
     k_stats_init<<<(unsigned)((n0 + 255) / 256), 256, 0, st>>>(s.x, n0, lmin, mu[0], m2[0]);
     CK(cudaGetLastError());
 
-    const int occ_band = band_occupancy<T>(false, p);
-    const int occ_bins = band_occupancy<T>(true, p);
+    const int occ_band = band_occupancy<T>(false, p, rpl);
+    const int occ_bins = band_occupancy<T>(true, p, rpl);
     REQUIRE(occ_band > 0 && occ_bins > 0, "band kernel does not fit on this device");
     const int grid_band = ctx->num_sms * occ_band;
     const int grid_bins = ctx->num_sms * occ_bins;
@@ -246,6 +249,10 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     if (G < 1) G = 1;
     if (G > K) G = K;
     const int64_t group_w = G * R;
+    const int ngroups_max = (int)((n0 + group_w - 1) / group_w);
+    T *skey = dalloc<T>(ctx, s, (size_t)n0 * ngroups_max * p);
+    int32_t *sj = dalloc<int32_t>(ctx, s, (size_t)n0 * ngroups_max * p);
+    int32_t *scnt = dalloc<int32_t>(ctx, s, (size_t)n0 * ngroups_max);
 
     BandArgs<T> ba{};
     ba.col = col;
@@ -255,13 +262,14 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     ba.bands = bands;
     ba.nbands = nbands_d;
     ba.unit_ctr = unit_ctr;
+    ba.rpl = rpl;
     ba.group_w = group_w;
-    ba.ckey = ckey;
-    ba.cj = cj;
-    ba.ccnt = ccnt;
-    ba.cap = cap;
-    ba.bins = bins;
     ba.p = p;
+    ba.skey = skey;
+    ba.sj = sj;
+    ba.scnt = scnt;
+    ba.bins = bins;
+    ba.nbins = nbins;
 
     int cur = 0;
     s.stats.assign(nL, mad_length_stats{});
@@ -296,7 +304,8 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
             cur ^= 1;
         }
         launch_coldata<T>(s.x, nl, npad, l, mu[cur], m2[cur], run, col, st);
-        ++nlaunch;
+        launch_kappa(m2[cur], run, nl, l, R, m2blk, kappa, kappa_max, st);
+        nlaunch += 3;
         CK(cudaGetLastError());
 
         if (l == lmin) {
@@ -321,8 +330,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
             ea.vm = vm;
             ea.out = lo;
             ea.thr = thr;
-            ea.dq_entry = Precision<T>::dq_entry;
-            ea.dq_band = Precision<T>::dq_band;
+            ea.em = em;
             launch_extend<T>(ea, st);
             ++nlaunch;
         }
@@ -341,10 +349,11 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
             ba.nl = nl;
             ba.l = l;
             ba.E = E;
-            ba.ngroups = (int)((nl + group_w - 1) / group_w);
+            // the slot layout keeps the lmin group count for every length
+            ba.ngroups = ngroups_max;
             if (l == lmin) {
                 // first thresholds from interleaved maxima
-                launch_fill<int32_t>(bins, (int64_t)n0 * p, (int32_t)0x807fffff, st);  // ord(-inf)
+                launch_fill<int32_t>(bins, (int64_t)n0 * nbins, (int32_t)0x807fffff, st);  // ord(-inf)
                 CK(cudaMemsetAsync(unit_ctr, 0, sizeof(int32_t), st));
                 {
                     const size_t e = ev_pair(li);
@@ -353,7 +362,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
                     CK(cudaEventRecord(evs[e].b, st));
                 }
                 host_cells[li] += (unsigned long long)nb_active * R * nl;
-                launch_theta_bins<T>(bins, nl, p, m2[cur], Precision<T>::dq_band, thr, st);
+                launch_theta_bins<T>(bins, nbins, nl, p, m2[cur], em, thr, st);
                 launch_mask_thr<T>(rs.flag, n0, thr, st);
                 nlaunch += 4;
                 CK(cudaGetLastError());
@@ -361,26 +370,25 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
             MergeArgs<T> ma{};
             ma.x = s.x;
             ma.mu = mu[cur];
-            // FP32 keys: entries closer than 0.05 sqrt(l) are re-evaluated in FP64
-            ma.d_refine = sizeof(T) == 4 ? 0.05 * std::sqrt((double)l) : 0.0;
             ma.n0 = n0;
             ma.nl = nl;
             ma.l = l;
             ma.E = E;
             ma.p = p;
             ma.m_max = m_max;
-            ma.cap = cap;
             ma.m2 = m2[cur];
             ma.run = run;
             ma.col = col;
-            ma.ckey = ckey;
-            ma.cj = cj;
-            ma.ccnt = ccnt;
+            ma.skey = skey;
+            ma.sj = sj;
+            ma.scnt = scnt;
+            ma.ngroups = ngroups_max;
+            ma.group_w = group_w;
             ma.thr = thr;
             ma.st = rs;
             ma.vm = vm;
             ma.out = lo;
-            ma.dq_band = Precision<T>::dq_band;
+            ma.em = em;
             ma.overflow = overflow;
             int passes = 0;
             for (;;) {

@@ -18,14 +18,22 @@ constexpr int CH = 32;              // columns per wavefront chunk (one per lane
 constexpr int MAXP = 64;            // largest p (entries kept per row)
 constexpr int KMAX = 64;            // largest discord-table rank count
 
-// Rows per lane / warps per CTA of the diagonal band kernel. A band holds
-// R = 32 * RPL * NW consecutive rows, which is also the re-seed period of
-// every diagonal (each diagonal is restarted from a direct dot product at
-// the top or left edge of every R x R tile).
-template <typename T> struct BandGeo;
-template <> struct BandGeo<float> { static constexpr int RPL = 8, NW = 8; };   // R = 2048
-template <> struct BandGeo<double> { static constexpr int RPL = 4, NW = 8; };  // R = 1024
-template <typename T> constexpr int band_rows() { return 32 * BandGeo<T>::RPL * BandGeo<T>::NW; }
+// Geometry of the diagonal band kernel: BAND_NW warps per CTA, RPL rows per
+// lane, so a band holds R = 32 * RPL * BAND_NW consecutive rows; R is also
+// the re-seed period of every diagonal (each diagonal restarts from a direct
+// dot product at the top or left edge of every R x R tile). RPL is chosen per
+// precision and p so that the per-row top-p lists fit in shared memory.
+constexpr int BAND_NW = 8;
+__host__ __device__ __forceinline__ int band_nbins(int p) { return 2 * p; }
+template <typename T> inline int band_rpl(int p)
+{
+    // shared bytes per row for the top-p list: p * (sizeof(T) + 4) + 4
+    const int budget = 96 * 1024;
+    const int max_rpl = sizeof(T) == 4 ? 8 : 4;
+    for (int rpl = max_rpl; rpl > 1; rpl /= 2)
+        if (32 * rpl * BAND_NW * (p * (int)(sizeof(T) + 4) + 4) <= budget) return rpl;
+    return 1;
+}
 
 // Per-window data the band kernel reads for column j (and for row j):
 //   df = df_{j-1} = (x_{j-1+l} - x_{j-1}) / 2
