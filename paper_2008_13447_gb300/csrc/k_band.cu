@@ -238,14 +238,54 @@ __device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *c
     }
 }
 
+// Pairwise synchronisation of the warp wavefront: warp w (producer) hands
+// the last row of its rows to warp w+1 (consumer) one chunk of CH columns at
+// a time through a ring of NSLOT buffers guarded by shared-memory mbarriers:
+// full[w+1][slot] (producer arrives after writing) and empty[w+1][slot]
+// (consumer arrives after reading). Chunks are counted across the CTA's work
+// units so slot and phase parity stay consistent. Every wait is bounded: when
+// the bound runs out the kernel records an error (reported as MAD_ETIMEOUT)
+// and carries on without blocking.
+constexpr int NSLOT = 4;
+constexpr int WAIT_LIMIT = 1 << 20;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *b, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(b))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(b)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void mbar_wait(uint64_t *b, unsigned parity, int *err)
+{
+    for (int it = 0; it < WAIT_LIMIT; ++it)
+        if (mbar_try_wait(b, parity)) return;
+    atomicExch(err, 1);
+}
+
 template <typename T, int RPL, int NW, bool BINS>
 __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
 {
     constexpr int R = 32 * RPL * NW;
     extern __shared__ __align__(32) unsigned char smem_raw[];
-    Col<T> *colbuf = reinterpret_cast<Col<T> *>(smem_raw);        // [NW][CH]
-    T *bbuf = reinterpret_cast<T *>(colbuf + NW * CH);             // [NW][2][CH]
-    unsigned char *tail = reinterpret_cast<unsigned char *>(bbuf + NW * 2 * CH);
+    uint64_t *mfull = reinterpret_cast<uint64_t *>(smem_raw);       // [NW][NSLOT]
+    uint64_t *mempty = mfull + NW * NSLOT;                         // [NW][NSLOT]
+    Col<T> *colbuf = reinterpret_cast<Col<T> *>(mempty + NW * NSLOT);  // [NW][CH]
+    T *bbuf = reinterpret_cast<T *>(colbuf + NW * CH);             // [NW][NSLOT][CH]
+    unsigned char *tail = reinterpret_cast<unsigned char *>(bbuf + NW * NSLOT * CH);
     // bins mode: int [R][nbins];  top-p mode: T [R][p], int32 [R][p], int32 [R]
     int *sbins = reinterpret_cast<int *>(tail);
     T *lkey = reinterpret_cast<T *>(tail);
@@ -261,6 +301,12 @@ __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
 
     if (BINS)
         for (int t = threadIdx.x; t < R * nbins; t += blockDim.x) sbins[t] = NEG_ORD;
+    if (threadIdx.x < NW * NSLOT) {
+        mbar_init(&mfull[threadIdx.x], 1);
+        mbar_init(&mempty[threadIdx.x], 1);
+    }
+    __syncthreads();
+    unsigned qg = 0;    // chunks processed by this CTA so far (same for every warp)
 
     for (;;) {
         if (threadIdx.x == 0) s_unit = atomicAdd(A.unit_ctr, 1);
@@ -295,44 +341,48 @@ __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
         }
         T carry = sleft[rfirst];
 
-        for (int s = 0; s < nchunk + NW - 1; ++s) {
-            const int q = s - w;
-            if (q >= 0 && q < nchunk) {
-                const int64_t cs = c0 + (int64_t)q * CH;
-                Col<T> *cbuf = colbuf + w * CH;
-                cbuf[lane] = A.col[cs + lane];
-                T tp;
-                if (w == 0) {
-                    tp = stop[cs + lane];
-                } else {
-                    const T *bb = bbuf + (w * 2 + (q & 1)) * CH;
-                    const T prev = bb[lane == 0 ? 0 : lane - 1];
-                    tp = lane == 0 ? carry : prev;
-                    carry = bb[CH - 1];
-                }
+        for (int q = 0; q < nchunk; ++q, ++qg) {
+            const int slot = (int)(qg % NSLOT);
+            const unsigned par = (qg / NSLOT) & 1u;
+            const int64_t cs = c0 + (int64_t)q * CH;
+            Col<T> *cbuf = colbuf + w * CH;
+            cbuf[lane] = A.col[cs + lane];
+            T tp;
+            if (w == 0) {
+                tp = stop[cs + lane];
+            } else {
+                mbar_wait(&mfull[w * NSLOT + slot], par, A.err);        // chunk q from warp w-1
+                const T *bb = bbuf + (w * NSLOT + slot) * CH;
+                const T prev = bb[lane == 0 ? 0 : lane - 1];
+                tp = lane == 0 ? carry : prev;
+                carry = bb[CH - 1];
                 __syncwarp();
-                T *bout = bbuf + ((w + 1 < NW ? w + 1 : 0) * 2 + (q & 1)) * CH;
-                // does this warp's row range meet the exclusion zone in this chunk?
-                const int64_t rlo = rfirst, rhi = rfirst + 32 * RPL - 1;
-                const bool diag = (cs <= rhi + A.E) && (cs + CH - 1 >= rlo - A.E);
-                if (diag)
-                    band_chunk<T, RPL, NW, BINS, true>(A, cbuf, tp, bout, lane, w, cs, rbase, rl0, C, dfr, dgr, th,
-                                                       runmax, lkey, lj, lcnt);
-                else
-                    band_chunk<T, RPL, NW, BINS, false>(A, cbuf, tp, bout, lane, w, cs, rbase, rl0, C, dfr, dgr, th,
-                                                        runmax, lkey, lj, lcnt);
-                if (BINS) {
-                    const int bin = (int)((cs / CH) % nbins);
-#pragma unroll
-                    for (int a = 0; a < RPL; ++a) {
-                        atomicMax(&sbins[(rl0 + a) * nbins + bin], f2ord(to_float_rd(runmax[a])));
-                        runmax[a] = neg_inf<T>();
-                    }
-                }
-                __syncwarp();
+                if (lane == 0) mbar_arrive(&mempty[w * NSLOT + slot]);   // slot free again
             }
-            __syncthreads();
+            if (w < NW - 1) mbar_wait(&mempty[(w + 1) * NSLOT + slot], par ^ 1u, A.err);  // slot free
+            __syncwarp();
+            T *bout = bbuf + ((w + 1 < NW ? w + 1 : 0) * NSLOT + slot) * CH;
+            // does this warp's row range meet the exclusion zone in this chunk?
+            const int64_t rlo = rfirst, rhi = rfirst + 32 * RPL - 1;
+            const bool diag = (cs <= rhi + A.E) && (cs + CH - 1 >= rlo - A.E);
+            if (diag)
+                band_chunk<T, RPL, NW, BINS, true>(A, cbuf, tp, bout, lane, w, cs, rbase, rl0, C, dfr, dgr, th,
+                                                   runmax, lkey, lj, lcnt);
+            else
+                band_chunk<T, RPL, NW, BINS, false>(A, cbuf, tp, bout, lane, w, cs, rbase, rl0, C, dfr, dgr, th,
+                                                    runmax, lkey, lj, lcnt);
+            if (w < NW - 1 && lane == 31) mbar_arrive(&mfull[(w + 1) * NSLOT + slot]);   // chunk q written
+            if (BINS) {
+                const int bin = (int)((cs / CH) % nbins);
+#pragma unroll
+                for (int a = 0; a < RPL; ++a) {
+                    atomicMax(&sbins[(rl0 + a) * nbins + bin], f2ord(to_float_rd(runmax[a])));
+                    runmax[a] = neg_inf<T>();
+                }
+            }
+            __syncwarp();
         }
+        __syncthreads();
         if (BINS) {
             for (int t = threadIdx.x; t < R * nbins; t += blockDim.x) {
                 const int64_t r = i0 + t / nbins;
@@ -364,7 +414,8 @@ size_t band_smem(bool bins_mode, int p, int rpl)
 {
     constexpr int NW = BAND_NW;
     const int R = 32 * rpl * NW;
-    size_t s = (size_t)NW * CH * sizeof(Col<T>) + (size_t)NW * 2 * CH * sizeof(T);
+    size_t s = (size_t)2 * NW * NSLOT * sizeof(uint64_t) + (size_t)NW * CH * sizeof(Col<T>) +
+               (size_t)NW * NSLOT * CH * sizeof(T);
     if (bins_mode) s += (size_t)R * band_nbins(p) * sizeof(int);
     else s += (size_t)R * p * (sizeof(T) + sizeof(int32_t)) + (size_t)R * sizeof(int32_t);
     return s;

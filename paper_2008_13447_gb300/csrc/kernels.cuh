@@ -58,6 +58,7 @@ template <typename T> struct BandArgs {
     // bins mode: per row, the maximum key of each class of column chunks
     int *bins;              // [row][nbins] order-preserving ints
     int nbins;
+    int *err;               // set to 1 if a bounded wait ran out
 };
 template <typename T> void launch_band(const BandArgs<T> &a, bool bins_mode, int grid, cudaStream_t s);
 template <typename T> int band_occupancy(bool bins_mode, int p, int rpl);

@@ -221,6 +221,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     }
     int32_t *nbands_d = counters, *unit_ctr = counters + 1;
     unsigned int *overflow = reinterpret_cast<unsigned int *>(counters + 2);
+    int32_t *wait_err = counters + 3;
 
     // ---- one-off initialisation
     {
@@ -229,6 +230,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         CK(cudaMemcpyAsync(krows, kr.data(), K * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     }
     CK(cudaMemsetAsync(dstats, 0, (size_t)nL * 5 * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(counters, 0, 4 * sizeof(int32_t), st));
     CK(cudaMemsetAsync(vm.len, 0, n0 * sizeof(int32_t), st));
     CK(cudaMemsetAsync(tab.len, 0, (size_t)k_max * m_max * sizeof(int32_t), st));
     CK(cudaMemsetAsync(rs.ent_j, 0xff, (size_t)p * n0 * sizeof(int32_t), st));
@@ -270,6 +272,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     ba.scnt = scnt;
     ba.bins = bins;
     ba.nbins = nbins;
+    ba.err = wait_err;
 
     int cur = 0;
     s.stats.assign(nL, mad_length_stats{});
@@ -406,10 +409,14 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
                 CK(cudaGetLastError());
                 ++passes;
                 host_tiles[li] += (unsigned long long)nb_active * ba.ngroups;
-                unsigned int ovf = 0;
-                CK(cudaMemcpyAsync(&ovf, overflow, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+                unsigned int flags[2] = {0, 0};   // overflow count, bounded-wait error
+                CK(cudaMemcpyAsync(flags, overflow, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
                 CK(cudaStreamSynchronize(st));
-                if (ovf == 0) break;
+                if (flags[1] != 0) {
+                    set_err(ctx, "a bounded wait in the band kernel ran out");
+                    throw Fail{MAD_ETIMEOUT};
+                }
+                if (flags[0] == 0) break;
                 if (passes >= 64) {
                     set_err(ctx, "candidate lists kept overflowing");
                     throw Fail{MAD_EINTERNAL};
