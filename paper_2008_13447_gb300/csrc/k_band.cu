@@ -190,6 +190,24 @@ __device__ __forceinline__ void topp_insert(T *K, int32_t *J, int32_t &cnt, int 
     th = mn > th ? mn : th;
 }
 
+template <int RPL>
+__device__ __forceinline__ bool any_positive(const float (&C)[RPL], float inv, const float (&th)[RPL])
+{
+    unsigned acc = 0xffffffffu;
+#pragma unroll
+    for (int a = 0; a < RPL; ++a) acc &= __float_as_uint(fmaf(C[a], inv, -th[a]));
+    return (int)acc >= 0;
+}
+
+template <int RPL>
+__device__ __forceinline__ bool any_positive(const double (&C)[RPL], double inv, const double (&th)[RPL])
+{
+    unsigned acc = 0xffffffffu;
+#pragma unroll
+    for (int a = 0; a < RPL; ++a) acc &= (unsigned)(__double_as_longlong(fma(C[a], inv, -th[a])) >> 32);
+    return (int)acc >= 0;
+}
+
 template <typename T, int RPL, int NW, bool BINS, bool DIAG>
 __device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *cbuf, T tp, T *bout, int lane, int w,
                                            int64_t cs, int64_t rbase, int rl0, T (&C)[RPL], const T (&dfr)[RPL],
@@ -208,11 +226,14 @@ __device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *c
         if (w < NW - 1 && lane == 31) bout[c] = C[RPL - 1];
         if (!BINS) {
             bool hit = false;
+            if (DIAG) {
 #pragma unroll
-            for (int a = 0; a < RPL; ++a) {
-                bool h = C[a] * cd.inv > th[a];
-                if (DIAG) h = h && nontrivial(rbase + a, cs + c, A.E);
-                hit |= h;
+                for (int a = 0; a < RPL; ++a)
+                    hit |= (C[a] * cd.inv > th[a]) && nontrivial(rbase + a, cs + c, A.E);
+            } else {
+                // any key - th > 0 ? (AND of the sign bits of key - th over the
+                // rows; +0 and NaN count as hits and are re-tested below)
+                hit = any_positive(C, cd.inv, th);
             }
             if (hit) {
                 const int32_t j = (int32_t)(cs + c);
@@ -291,8 +312,6 @@ __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
     T *lkey = reinterpret_cast<T *>(tail);
     int32_t *lj = reinterpret_cast<int32_t *>(lkey + R * A.p);
     int32_t *lcnt = lj + R * A.p;
-    __shared__ int s_unit;
-
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nb = *A.nbands;
     const int64_t total = (int64_t)nb * A.ngroups;
@@ -308,12 +327,10 @@ __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
     __syncthreads();
     unsigned qg = 0;    // chunks processed by this CTA so far (same for every warp)
 
-    for (;;) {
-        if (threadIdx.x == 0) s_unit = atomicAdd(A.unit_ctr, 1);
-        __syncthreads();
-        const int64_t u = s_unit;
-        __syncthreads();
-        if (u >= total) break;
+    // Static schedule: every warp walks the same unit sequence, so warps flow
+    // from one unit into the next without a CTA-wide barrier (the ring of
+    // mbarriers keeps them in order).
+    for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
         const int g = (int)(u / nb);
         const int band = A.bands[u % nb];
         const int64_t i0 = (int64_t)band * R;
@@ -324,8 +341,8 @@ __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
         const int64_t rfirst = i0 + (int64_t)w * 32 * RPL;
         const int64_t rbase = rfirst + lane * RPL;
         const int rl0 = w * 32 * RPL + lane * RPL;
-        const T *sleft = A.seed + (c0 / R) * A.spitch;
-        const T *stop = A.seed + (int64_t)band * A.spitch;
+        const T *sleft = A.seed + (c0 / A.sp) * A.spitch;
+        const T *stop = A.seed + (i0 / A.sp) * A.spitch;
 
         T C[RPL], dfr[RPL], dgr[RPL], th[RPL], runmax[RPL];
 #pragma unroll
@@ -340,16 +357,21 @@ __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
             if (!BINS) lcnt[rl0 + a] = 0;
         }
         T carry = sleft[rfirst];
+        // prefetched column data / top edge of the next chunk
+        Col<T> ncol = A.col[c0 + lane];
+        T ntop = w == 0 ? stop[c0 + lane] : T(0);
 
         for (int q = 0; q < nchunk; ++q, ++qg) {
             const int slot = (int)(qg % NSLOT);
             const unsigned par = (qg / NSLOT) & 1u;
             const int64_t cs = c0 + (int64_t)q * CH;
             Col<T> *cbuf = colbuf + w * CH;
-            cbuf[lane] = A.col[cs + lane];
+            cbuf[lane] = ncol;
             T tp;
+            if (q + 1 < nchunk) ncol = A.col[cs + CH + lane];
             if (w == 0) {
-                tp = stop[cs + lane];
+                tp = ntop;
+                if (q + 1 < nchunk) ntop = stop[cs + CH + lane];
             } else {
                 mbar_wait(&mfull[w * NSLOT + slot], par, A.err);        // chunk q from warp w-1
                 const T *bb = bbuf + (w * NSLOT + slot) * CH;
@@ -382,8 +404,8 @@ __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
             }
             __syncwarp();
         }
-        __syncthreads();
         if (BINS) {
+            __syncthreads();
             for (int t = threadIdx.x; t < R * nbins; t += blockDim.x) {
                 const int64_t r = i0 + t / nbins;
                 if (r < A.nl && sbins[t] != NEG_ORD) atomicMax(&A.bins[r * nbins + (t % nbins)], sbins[t]);

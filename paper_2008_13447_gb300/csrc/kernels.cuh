@@ -15,20 +15,22 @@ void launch_coldata(const double *x, int64_t nl, int64_t npad, int l, const doub
 __global__ void k_widen_f32(const float *in, int64_t n, double *out);
 
 // ----------------------------------------------------------------- k_band.cu
-// Seed rows of the diagonal recurrence. Seed row k (band start kR) holds,
-// for every column j, the value that precedes cell (kR, j) on its diagonal:
-//   S_k[j] = C(kR - 1, j - 1)            for k >= 1, j >= 1
-//   S_k[j] = C(kR, j)                    for k == 0 or j == 0
+// Seed rows of the diagonal recurrence. Seed row k (row kS, S the seed
+// spacing) holds, for every column j, the value that precedes cell (kS, j)
+// on its diagonal:
+//   S_k[j] = C(kS - 1, j - 1)            for k >= 1, j >= 1
+//   S_k[j] = C(kS, j)                    for k == 0 or j == 0
 // (the second line makes the recurrence start exactly at the first row /
 // column, whose virtual predecessors carry df = dg = 0). By symmetry of C,
-// S_k[r] is also the value preceding cell (r, kR), the left edge of column
-// block k. Entries whose column is past the last window are 0.
+// S_k[r] is also the value preceding cell (r, kS): the left edge of a column
+// group starting at kS. Bands start at multiples of R = 2S. Entries whose
+// column is past the last window are 0.
 template <typename T> struct SeedArgs {
     const double *x;
     const double *mu;       // window means at l
     int64_t nl;
     int l;
-    int R;
+    int R;                  // seed spacing S
     const int32_t *krows;   // seed rows to compute
     int nk;
     int64_t spitch;         // elements per seed row
@@ -43,12 +45,12 @@ template <typename T> struct BandArgs {
     const T *thr;           // per-row key threshold (+inf: row not wanted)
     const int32_t *bands;   // active band ids
     const int32_t *nbands;  // number of active bands (device)
-    int32_t *unit_ctr;      // work counter, zero before launch
     int64_t nl;
     int l;
     int64_t E;
     int rpl;                // rows per lane (band height R = 32 * rpl * BAND_NW)
-    int64_t group_w;        // columns per work unit (multiple of R)
+    int64_t sp;             // seed-row spacing (R / 2): seed row k sits at row k * sp
+    int64_t group_w;        // columns per work unit (multiple of sp)
     int ngroups;
     int p;
     // top-p mode: per row and column group, up to p (key, offset) pairs

@@ -182,7 +182,9 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     const int rpl = band_rpl<T>(p);
     const int R = 32 * rpl * BAND_NW;
     const int nbins = band_nbins(p);
-    const int64_t K = (n0 + R - 1) / R;
+    const int SP = R / 2;                       // seed-row spacing
+    const int64_t K = (n0 + SP - 1) / SP;       // seed rows
+    const int64_t KB = (n0 + R - 1) / R;        // bands
     const int64_t npad = round_up(n0, R) + R + CH;
     const int64_t spitch = round_up(n0, R) + R + CH;
 
@@ -203,7 +205,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     Valmp vm{dalloc<double>(ctx, s, n0), dalloc<double>(ctx, s, n0), dalloc<int32_t>(ctx, s, n0),
              dalloc<int32_t>(ctx, s, n0)};
     int *bins = dalloc<int>(ctx, s, (size_t)n0 * nbins);
-    int32_t *bands = dalloc<int32_t>(ctx, s, K);
+    int32_t *bands = dalloc<int32_t>(ctx, s, KB);
     int32_t *counters = dalloc<int32_t>(ctx, s, 4);   // nbands, unit counter, overflow
     int32_t *krows = dalloc<int32_t>(ctx, s, K);
     double *nnd = dalloc<double>(ctx, s, (size_t)m_max * n0);
@@ -246,11 +248,12 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     REQUIRE(occ_band > 0 && occ_bins > 0, "band kernel does not fit on this device");
     const int grid_band = ctx->num_sms * occ_band;
     const int grid_bins = ctx->num_sms * occ_bins;
-    // columns per work unit: a multiple of R, ~8 units per resident CTA when possible
-    int64_t G = (K * K) / (8 * (int64_t)grid_band);
+    // columns per work unit: a multiple of the seed spacing, ~8 units per
+    // resident CTA when possible
+    int64_t G = (KB * K) / (8 * (int64_t)grid_band);
     if (G < 1) G = 1;
     if (G > K) G = K;
-    const int64_t group_w = G * R;
+    const int64_t group_w = G * SP;
     const int ngroups_max = (int)((n0 + group_w - 1) / group_w);
     T *skey = dalloc<T>(ctx, s, (size_t)n0 * ngroups_max * p);
     int32_t *sj = dalloc<int32_t>(ctx, s, (size_t)n0 * ngroups_max * p);
@@ -263,8 +266,8 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     ba.thr = thr;
     ba.bands = bands;
     ba.nbands = nbands_d;
-    ba.unit_ctr = unit_ctr;
     ba.rpl = rpl;
+    ba.sp = SP;
     ba.group_w = group_w;
     ba.p = p;
     ba.skey = skey;
@@ -346,7 +349,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         CK(cudaStreamSynchronize(st));
 
         if (nb_active > 0) {
-            SeedArgs<T> sa{s.x, mu[cur], nl, l, R, krows, (int)K, spitch, seed};
+            SeedArgs<T> sa{s.x, mu[cur], nl, l, SP, krows, (int)K, spitch, seed};
             launch_seed<T>(sa, st);
             ++nlaunch;
             ba.nl = nl;
@@ -357,7 +360,6 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
             if (l == lmin) {
                 // first thresholds from interleaved maxima
                 launch_fill<int32_t>(bins, (int64_t)n0 * nbins, (int32_t)0x807fffff, st);  // ord(-inf)
-                CK(cudaMemsetAsync(unit_ctr, 0, sizeof(int32_t), st));
                 {
                     const size_t e = ev_pair(li);
                     CK(cudaEventRecord(evs[e].a, st));
@@ -395,7 +397,6 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
             ma.overflow = overflow;
             int passes = 0;
             for (;;) {
-                CK(cudaMemsetAsync(unit_ctr, 0, sizeof(int32_t), st));
                 CK(cudaMemsetAsync(overflow, 0, sizeof(unsigned int), st));
                 {
                     const size_t e = ev_pair(li);
