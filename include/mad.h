@@ -121,6 +121,8 @@ typedef struct {
     int64_t band_cells;     /* cells the matrix-profile (band) kernel evaluated at this length:
                                rows of its active bands x columns, summed over passes */
     int64_t launches;       /* GPU kernel launches issued for this length */
+    int64_t inserts;        /* insertions into the band kernel's per-row top-p lists (cells that
+                               beat their row's running p-th best key) */
     double band_ms;         /* device time of those band-kernel launches (CUDA events recorded
                                on the context's stream around each launch) */
     double fp32_dq_max;     /* MAD_FP32: largest |q_FP32 - q_FP64| among stored entries that were

@@ -212,7 +212,7 @@ template <typename T, int RPL, int NW, bool BINS, bool DIAG>
 __device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *cbuf, T tp, T *bout, int lane, int w,
                                            int64_t cs, int64_t rbase, int rl0, T (&C)[RPL], const T (&dfr)[RPL],
                                            const T (&dgr)[RPL], T (&th)[RPL], T (&runmax)[RPL], T *lkey,
-                                           int32_t *lj, int32_t *lcnt)
+                                           int32_t *lj, int32_t *lcnt, unsigned &ninsert)
 {
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
@@ -245,6 +245,7 @@ __device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *c
                         int32_t cnt = lcnt[rl];
                         topp_insert<T>(lkey + rl * A.p, lj + rl * A.p, cnt, A.p, key, j, th[a]);
                         lcnt[rl] = cnt;
+                        ++ninsert;
                     }
                 }
             }
@@ -320,17 +321,40 @@ __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
 
     if (BINS)
         for (int t = threadIdx.x; t < R * nbins; t += blockDim.x) sbins[t] = NEG_ORD;
+    // unit queue: warp 0 takes the next work unit from the global counter and
+    // hands its index to every warp through uq[] (full: 1 arrival from warp
+    // 0; empty: one arrival per warp), so warps flow from one unit into the
+    // next without a CTA-wide barrier and units are balanced dynamically.
+    __shared__ int uq[NSLOT];
+    __shared__ __align__(8) uint64_t ufull[NSLOT], uempty[NSLOT];
     if (threadIdx.x < NW * NSLOT) {
         mbar_init(&mfull[threadIdx.x], 1);
         mbar_init(&mempty[threadIdx.x], 1);
     }
+    if (threadIdx.x < NSLOT) {
+        mbar_init(&ufull[threadIdx.x], 1);
+        mbar_init(&uempty[threadIdx.x], NW);
+    }
     __syncthreads();
     unsigned qg = 0;    // chunks processed by this CTA so far (same for every warp)
+    unsigned ninsert = 0;
 
-    // Static schedule: every warp walks the same unit sequence, so warps flow
-    // from one unit into the next without a CTA-wide barrier (the ring of
-    // mbarriers keeps them in order).
-    for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
+    for (unsigned useq = 0;; ++useq) {
+        const int us = (int)(useq % NSLOT);
+        const unsigned upar = (useq / NSLOT) & 1u;
+        if (w == 0) {
+            mbar_wait(&uempty[us], upar ^ 1u, A.err);
+            if (lane == 0) {
+                uq[us] = atomicAdd(A.unit_ctr, 1);
+                mbar_arrive(&ufull[us]);
+            }
+        }
+        mbar_wait(&ufull[us], upar, A.err);
+        const int64_t u = uq[us];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&uempty[us]);
+        if (u >= total) break;
+        {
         const int g = (int)(u / nb);
         const int band = A.bands[u % nb];
         const int64_t i0 = (int64_t)band * R;
@@ -389,10 +413,10 @@ __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
             const bool diag = (cs <= rhi + A.E) && (cs + CH - 1 >= rlo - A.E);
             if (diag)
                 band_chunk<T, RPL, NW, BINS, true>(A, cbuf, tp, bout, lane, w, cs, rbase, rl0, C, dfr, dgr, th,
-                                                   runmax, lkey, lj, lcnt);
+                                                   runmax, lkey, lj, lcnt, ninsert);
             else
                 band_chunk<T, RPL, NW, BINS, false>(A, cbuf, tp, bout, lane, w, cs, rbase, rl0, C, dfr, dgr, th,
-                                                    runmax, lkey, lj, lcnt);
+                                                    runmax, lkey, lj, lcnt, ninsert);
             if (w < NW - 1 && lane == 31) mbar_arrive(&mfull[(w + 1) * NSLOT + slot]);   // chunk q written
             if (BINS) {
                 const int bin = (int)((cs / CH) % nbins);
@@ -428,6 +452,11 @@ __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
                 }
             }
         }
+        }
+    }
+    if (!BINS) {
+        for (int o = 16; o > 0; o >>= 1) ninsert += __shfl_xor_sync(0xffffffffu, ninsert, o);
+        if (lane == 0 && ninsert) atomicAdd(A.ninsert, (unsigned long long)ninsert);
     }
 }
 

@@ -45,6 +45,7 @@ template <typename T> struct BandArgs {
     const T *thr;           // per-row key threshold (+inf: row not wanted)
     const int32_t *bands;   // active band ids
     const int32_t *nbands;  // number of active bands (device)
+    int32_t *unit_ctr;      // work counter, zero before launch
     int64_t nl;
     int l;
     int64_t E;
@@ -61,6 +62,7 @@ template <typename T> struct BandArgs {
     int *bins;              // [row][nbins] order-preserving ints
     int nbins;
     int *err;               // set to 1 if a bounded wait ran out
+    unsigned long long *ninsert;  // top-p list insertions (diagnostic counter)
 };
 template <typename T> void launch_band(const BandArgs<T> &a, bool bins_mode, int grid, cudaStream_t s);
 template <typename T> int band_occupancy(bool bins_mode, int p, int rpl);

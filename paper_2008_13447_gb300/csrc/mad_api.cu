@@ -266,6 +266,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     ba.thr = thr;
     ba.bands = bands;
     ba.nbands = nbands_d;
+    ba.unit_ctr = unit_ctr;
     ba.rpl = rpl;
     ba.sp = SP;
     ba.group_w = group_w;
@@ -360,6 +361,8 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
             if (l == lmin) {
                 // first thresholds from interleaved maxima
                 launch_fill<int32_t>(bins, (int64_t)n0 * nbins, (int32_t)0x807fffff, st);  // ord(-inf)
+                CK(cudaMemsetAsync(unit_ctr, 0, sizeof(int32_t), st));
+                ba.ninsert = lo.stats + 4;
                 {
                     const size_t e = ev_pair(li);
                     CK(cudaEventRecord(evs[e].a, st));
@@ -398,6 +401,8 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
             int passes = 0;
             for (;;) {
                 CK(cudaMemsetAsync(overflow, 0, sizeof(unsigned int), st));
+                CK(cudaMemsetAsync(unit_ctr, 0, sizeof(int32_t), st));
+                ba.ninsert = lo.stats + 4;
                 {
                     const size_t e = ev_pair(li);
                     CK(cudaEventRecord(evs[e].a, st));
@@ -458,6 +463,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         unsigned long long bits = hs[li * 5 + 3];
         std::memcpy(&q.fp32_dq_max, &bits, sizeof(double));
         q.band_cells = (int64_t)host_cells[li];
+        q.inserts = (int64_t)hs[li * 5 + 4];
         q.launches = (int64_t)host_launch[li];
         q.band_ms = 0.0;
     }
