@@ -42,6 +42,7 @@ __global__ void k_seed(SeedArgs<T> A);
 template <>
 __global__ void k_seed<double>(SeedArgs<double> A)
 {
+    if (A.nbands && *A.nbands == 0) return;
     extern __shared__ double sh_d[];
     const int l = A.l;
     double *arow = sh_d;                  // centred row window (l)
@@ -77,6 +78,7 @@ __global__ void k_seed<double>(SeedArgs<double> A)
 template <>
 __global__ void k_seed<float>(SeedArgs<float> A)
 {
+    if (A.nbands && *A.nbands == 0) return;
     extern __shared__ float sh_f[];
     const int l = A.l;
     const int B = blockDim.x;
@@ -316,6 +318,10 @@ __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nb = *A.nbands;
     const int64_t total = (int64_t)nb * A.ngroups;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && nb > 0 && A.stats) {
+        atomicAdd(&A.stats[5], (unsigned long long)total);
+        atomicAdd(&A.stats[6], (unsigned long long)nb * R * (unsigned long long)A.nl);
+    }
     const int NEG_ORD = f2ord(-__int_as_float(0x7f800000));
     const int nbins = A.nbins;
 

@@ -274,14 +274,19 @@ void launch_recheck_pairs(const double *x, int64_t n, const int32_t *pairs, int 
 }
 
 // m-th best-match distance of window `off` at length L from a full FP64
-// distance profile (two-pass statistics for every window), one block per
-// cell. Each thread keeps its own m smallest (distance, offset) pairs; the
-// block then extracts the overall m smallest one at a time.
-__global__ void k_recheck_discords(const double *x, int64_t n, const int32_t *cells, int num, int den, double *out)
+// distance profile (two-pass statistics for every window). Each cell's
+// columns are split over RSLICES blocks; each block keeps its m smallest
+// (distance, offset) pairs (per thread, then extracted block-wide one at a
+// time); a second kernel merges the slices of a cell.
+constexpr int RSLICES = 64;
+
+__global__ void k_recheck_slices(const double *x, int64_t n, const int32_t *cells, int num, int den, double *sd,
+                                 int32_t *sj, int mcap)
 {
-    const int64_t off = cells[3 * blockIdx.x];
-    const int L = cells[3 * blockIdx.x + 1];
-    const int m = cells[3 * blockIdx.x + 2];
+    const int cell = blockIdx.x / RSLICES, slice = blockIdx.x % RSLICES;
+    const int64_t off = cells[3 * cell];
+    const int L = cells[3 * cell + 1];
+    const int m = cells[3 * cell + 2];
     const int64_t nl = n - L + 1;
     const int64_t E = excl_zone(L, num, den);
     const bool fo = window_flat(x, off, L);
@@ -291,10 +296,12 @@ __global__ void k_recheck_discords(const double *x, int64_t n, const int32_t *ce
     double vo = 0.0;
     for (int t = threadIdx.x; t < L; t += blockDim.x) { const double d = x[off + t] - mo; vo = fma(d, d, vo); }
     vo = block_sum(vo);
+    const int64_t per = (nl + RSLICES - 1) / RSLICES;
+    const int64_t j0 = (int64_t)slice * per, j1 = j0 + per < nl ? j0 + per : nl;
     double best[MAXP];
     int32_t bj[MAXP];
     int nb = 0;
-    for (int64_t j = threadIdx.x; j < nl; j += blockDim.x) {
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
         const int64_t dd = j - off;
         if (!(dd > E || -dd > E)) continue;
         double s = 0.0;
@@ -315,29 +322,65 @@ __global__ void k_recheck_discords(const double *x, int64_t n, const int32_t *ce
             q = q > 1.0 ? 1.0 : (q < -1.0 ? -1.0 : q);
             d = sqrt(2.0 * L * (1.0 - q));
         }
-        if (nb < m || d < best[m - 1]) {
+        if (nb < m || d < best[m - 1] || (d == best[m - 1] && (int32_t)j < bj[m - 1])) {
             int b = nb < m ? nb++ : m - 1;
-            while (b > 0 && best[b - 1] > d) { best[b] = best[b - 1]; bj[b] = bj[b - 1]; --b; }
+            while (b > 0 && (best[b - 1] > d || (best[b - 1] == d && bj[b - 1] > (int32_t)j))) {
+                best[b] = best[b - 1];
+                bj[b] = bj[b - 1];
+                --b;
+            }
             best[b] = d;
             bj[b] = (int32_t)j;
         }
     }
     int head = 0;
-    double res = dinf();
     for (int r = 0; r < m; ++r) {
         double v = head < nb ? best[head] : dinf();
         int32_t ix = head < nb ? bj[head] : -1;
         block_best<false>(v, ix);
         if (head < nb && bj[head] == ix && ix >= 0) ++head;
+        if (threadIdx.x == 0) {
+            sd[((int64_t)cell * RSLICES + slice) * mcap + r] = v;
+            sj[((int64_t)cell * RSLICES + slice) * mcap + r] = ix;
+        }
+    }
+}
+
+__global__ void k_recheck_merge(const int32_t *cells, const double *sd, const int32_t *sj, int mcap, double *out)
+{
+    const int cell = blockIdx.x;
+    const int m = cells[3 * cell + 2];
+    // m rounds of block-wide minimum over the slices' sorted lists
+    __shared__ int head[RSLICES];
+    if (threadIdx.x < RSLICES) head[threadIdx.x] = 0;
+    __syncthreads();
+    double res = dinf();
+    for (int r = 0; r < m; ++r) {
+        double v = dinf();
+        int32_t ix = -1;
+        if (threadIdx.x < RSLICES && head[threadIdx.x] < m) {
+            const int64_t k = ((int64_t)cell * RSLICES + threadIdx.x) * mcap + head[threadIdx.x];
+            v = sd[k];
+            ix = sj[k];
+        }
+        block_best<false>(v, ix);
+        if (threadIdx.x < RSLICES && head[threadIdx.x] < m && ix >= 0 &&
+            sj[((int64_t)cell * RSLICES + threadIdx.x) * mcap + head[threadIdx.x]] == ix)
+            ++head[threadIdx.x];
+        __syncthreads();
         res = v;
     }
-    if (threadIdx.x == 0) out[blockIdx.x] = res;
+    if (threadIdx.x == 0) out[cell] = res;
 }
 
 void launch_recheck_discords(const double *x, int64_t n, const int32_t *cells, int ncells, int num, int den,
-                             double *out, cudaStream_t s)
+                             double *out, double *sd, int32_t *sj, int mcap, cudaStream_t s)
 {
-    if (ncells > 0) k_recheck_discords<<<ncells, 256, 0, s>>>(x, n, cells, num, den, out);
+    if (ncells <= 0) return;
+    k_recheck_slices<<<ncells * RSLICES, 256, 0, s>>>(x, n, cells, num, den, sd, sj, mcap);
+    k_recheck_merge<<<ncells, 64, 0, s>>>(cells, sd, sj, mcap, out);
 }
+
+size_t recheck_scratch(int ncells, int mcap) { return (size_t)ncells * RSLICES * mcap; }
 
 }  // namespace mad

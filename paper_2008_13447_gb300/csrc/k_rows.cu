@@ -323,7 +323,7 @@ __global__ void k_merge(MergeArgs<T> A)
     }
     if (nb < need) {
         A.thr[i] = T(-pinf());
-        atomicAdd(A.overflow, 1u);
+        atomicAdd(A.overflow, 1ull);
         return;
     }
     const double m2i = A.m2[i];

@@ -35,6 +35,7 @@ template <typename T> struct SeedArgs {
     int nk;
     int64_t spitch;         // elements per seed row
     T *seed;
+    const int32_t *nbands;  // nothing to do when the device count is 0
 };
 template <typename T> void launch_seed(const SeedArgs<T> &a, cudaStream_t s);
 
@@ -63,6 +64,7 @@ template <typename T> struct BandArgs {
     int nbins;
     int *err;               // set to 1 if a bounded wait ran out
     unsigned long long *ninsert;  // top-p list insertions (diagnostic counter)
+    unsigned long long *stats;    // this length's counters ([5] units, [6] cells)
 };
 template <typename T> void launch_band(const BandArgs<T> &a, bool bins_mode, int grid, cudaStream_t s);
 template <typename T> int band_occupancy(bool bins_mode, int p, int rpl);
@@ -155,7 +157,7 @@ template <typename T> struct MergeArgs {
     Valmp vm;
     LenOut out;
     ErrModel em;
-    unsigned int *overflow;
+    unsigned long long *overflow;   // rows that need a second pass
 };
 template <typename T> void launch_merge(const MergeArgs<T> &a, cudaStream_t s);
 
@@ -201,6 +203,7 @@ void launch_motif_round(const Valmp &vm, int64_t n0, int num, int den, int32_t *
 void launch_recheck_pairs(const double *x, int64_t n, const int32_t *pairs /* a,b,len */, int npairs,
                           double *out, cudaStream_t s);
 void launch_recheck_discords(const double *x, int64_t n, const int32_t *cells /* off,len,m */, int ncells,
-                             int num, int den, double *out, cudaStream_t s);
+                             int num, int den, double *out, double *sd, int32_t *sj, int mcap, cudaStream_t s);
+size_t recheck_scratch(int ncells, int mcap);   // entries of sd / sj
 
 }  // namespace mad

@@ -213,7 +213,11 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     const int64_t nblk = (n0 + 255) / 256;
     double *bval = dalloc<double>(ctx, s, (size_t)m_max * nblk);
     int32_t *bidx = dalloc<int32_t>(ctx, s, (size_t)m_max * nblk);
-    unsigned long long *dstats = dalloc<unsigned long long>(ctx, s, (size_t)nL * 5);
+    // per-length device counters: [0] rows left for a second pass, [1] certified,
+    // [2] recomputed, [3] largest FP32-vs-FP64 correlation gap (bits),
+    // [4] top-p insertions, [5] band units, [6] band cells
+    constexpr int NSTAT = 8;
+    unsigned long long *dstats = dalloc<unsigned long long>(ctx, s, (size_t)nL * NSTAT);
     DiscTable tab{dalloc<double>(ctx, s, (size_t)k_max * m_max), dalloc<double>(ctx, s, (size_t)k_max * m_max),
                   dalloc<int32_t>(ctx, s, (size_t)k_max * m_max), dalloc<int32_t>(ctx, s, (size_t)k_max * m_max),
                   dalloc<int32_t>(ctx, s, (size_t)k_max * m_max)};
@@ -222,7 +226,6 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         s.keep_nnj = dalloc<int32_t>(ctx, s, (size_t)nL * m_max * n0);
     }
     int32_t *nbands_d = counters, *unit_ctr = counters + 1;
-    unsigned int *overflow = reinterpret_cast<unsigned int *>(counters + 2);
     int32_t *wait_err = counters + 3;
 
     // ---- one-off initialisation
@@ -231,7 +234,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         for (int64_t k = 0; k < K; ++k) kr[k] = (int32_t)k;
         CK(cudaMemcpyAsync(krows, kr.data(), K * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     }
-    CK(cudaMemsetAsync(dstats, 0, (size_t)nL * 5 * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(dstats, 0, (size_t)nL * NSTAT * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(counters, 0, 4 * sizeof(int32_t), st));
     CK(cudaMemsetAsync(vm.len, 0, n0 * sizeof(int32_t), st));
     CK(cudaMemsetAsync(tab.len, 0, (size_t)k_max * m_max * sizeof(int32_t), st));
@@ -280,7 +283,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
 
     int cur = 0;
     s.stats.assign(nL, mad_length_stats{});
-    std::vector<unsigned long long> host_tiles(nL, 0), host_passes(nL, 0), host_cells(nL, 0), host_launch(nL, 0);
+    std::vector<unsigned long long> host_launch(nL, 0);
     // CUDA events around every band-kernel launch (device time of the
     // dominant kernel, per length)
     struct Ev { int li; cudaEvent_t a, b; };
@@ -303,7 +306,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         const int li = l - lmin;
         const int64_t nl = n - l + 1;
         const int64_t E = excl_zone(l, num, den);
-        LenOut lo{nnd, nnj, dstats + (size_t)li * 5};
+        LenOut lo{nnd, nnj, dstats + (size_t)li * NSTAT};
         if (l > lmin) {
             ++nlaunch;
             k_stats_step<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(s.x, nl, l, mu[cur], m2[cur], mu[cur ^ 1],
@@ -343,97 +346,75 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         }
         CK(cudaGetLastError());
 
+        // Rows to recompute -> bands -> seeds -> band kernel -> merge, with no
+        // host round trip: the kernels read the band count on the device
+        // (and do nothing when it is 0). A second pass picks up rows whose
+        // threshold turned out too high (none by construction; it runs
+        // without threshold, so it cannot fall short again).
         launch_compact_bands(rs.flag, nl, R, bands, nbands_d, st);
         ++nlaunch;
-        int32_t nb_active = 0;
-        CK(cudaMemcpyAsync(&nb_active, nbands_d, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-
-        if (nb_active > 0) {
-            SeedArgs<T> sa{s.x, mu[cur], nl, l, SP, krows, (int)K, spitch, seed};
-            launch_seed<T>(sa, st);
-            ++nlaunch;
-            ba.nl = nl;
-            ba.l = l;
-            ba.E = E;
-            // the slot layout keeps the lmin group count for every length
-            ba.ngroups = ngroups_max;
-            if (l == lmin) {
-                // first thresholds from interleaved maxima
-                launch_fill<int32_t>(bins, (int64_t)n0 * nbins, (int32_t)0x807fffff, st);  // ord(-inf)
-                CK(cudaMemsetAsync(unit_ctr, 0, sizeof(int32_t), st));
-                ba.ninsert = lo.stats + 4;
-                {
-                    const size_t e = ev_pair(li);
-                    CK(cudaEventRecord(evs[e].a, st));
-                    launch_band<T>(ba, true, grid_bins, st);
-                    CK(cudaEventRecord(evs[e].b, st));
-                }
-                host_cells[li] += (unsigned long long)nb_active * R * nl;
-                launch_theta_bins<T>(bins, nbins, nl, p, m2[cur], em, thr, st);
-                launch_mask_thr<T>(rs.flag, n0, thr, st);
-                nlaunch += 4;
-                CK(cudaGetLastError());
+        SeedArgs<T> sa{s.x, mu[cur], nl, l, SP, krows, (int)K, spitch, seed, nbands_d};
+        launch_seed<T>(sa, st);
+        ++nlaunch;
+        ba.nl = nl;
+        ba.l = l;
+        ba.E = E;
+        ba.ngroups = ngroups_max;   // the slot layout keeps the lmin group count
+        ba.stats = lo.stats;
+        ba.ninsert = lo.stats + 4;
+        if (l == lmin) {
+            // first thresholds from interleaved maxima
+            launch_fill<int32_t>(bins, (int64_t)n0 * nbins, (int32_t)0x807fffff, st);  // ord(-inf)
+            CK(cudaMemsetAsync(unit_ctr, 0, sizeof(int32_t), st));
+            {
+                const size_t e = ev_pair(li);
+                CK(cudaEventRecord(evs[e].a, st));
+                launch_band<T>(ba, true, grid_bins, st);
+                CK(cudaEventRecord(evs[e].b, st));
             }
-            MergeArgs<T> ma{};
-            ma.x = s.x;
-            ma.mu = mu[cur];
-            ma.n0 = n0;
-            ma.nl = nl;
-            ma.l = l;
-            ma.E = E;
-            ma.p = p;
-            ma.m_max = m_max;
-            ma.m2 = m2[cur];
-            ma.run = run;
-            ma.col = col;
-            ma.skey = skey;
-            ma.sj = sj;
-            ma.scnt = scnt;
-            ma.ngroups = ngroups_max;
-            ma.group_w = group_w;
-            ma.thr = thr;
-            ma.st = rs;
-            ma.vm = vm;
-            ma.out = lo;
-            ma.em = em;
-            ma.overflow = overflow;
-            int passes = 0;
-            for (;;) {
-                CK(cudaMemsetAsync(overflow, 0, sizeof(unsigned int), st));
-                CK(cudaMemsetAsync(unit_ctr, 0, sizeof(int32_t), st));
-                ba.ninsert = lo.stats + 4;
-                {
-                    const size_t e = ev_pair(li);
-                    CK(cudaEventRecord(evs[e].a, st));
-                    launch_band<T>(ba, false, grid_band, st);
-                    CK(cudaEventRecord(evs[e].b, st));
-                }
-                launch_merge<T>(ma, st);
-                nlaunch += 2;
-                host_cells[li] += (unsigned long long)nb_active * R * nl;
-                CK(cudaGetLastError());
-                ++passes;
-                host_tiles[li] += (unsigned long long)nb_active * ba.ngroups;
-                unsigned int flags[2] = {0, 0};   // overflow count, bounded-wait error
-                CK(cudaMemcpyAsync(flags, overflow, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
-                CK(cudaStreamSynchronize(st));
-                if (flags[1] != 0) {
-                    set_err(ctx, "a bounded wait in the band kernel ran out");
-                    throw Fail{MAD_ETIMEOUT};
-                }
-                if (flags[0] == 0) break;
-                if (passes >= 64) {
-                    set_err(ctx, "candidate lists kept overflowing");
-                    throw Fail{MAD_EINTERNAL};
-                }
+            launch_theta_bins<T>(bins, nbins, nl, p, m2[cur], em, thr, st);
+            launch_mask_thr<T>(rs.flag, n0, thr, st);
+            nlaunch += 4;
+            CK(cudaGetLastError());
+        }
+        MergeArgs<T> ma{};
+        ma.x = s.x;
+        ma.mu = mu[cur];
+        ma.n0 = n0;
+        ma.nl = nl;
+        ma.l = l;
+        ma.E = E;
+        ma.p = p;
+        ma.m_max = m_max;
+        ma.m2 = m2[cur];
+        ma.run = run;
+        ma.col = col;
+        ma.skey = skey;
+        ma.sj = sj;
+        ma.scnt = scnt;
+        ma.ngroups = ngroups_max;
+        ma.group_w = group_w;
+        ma.thr = thr;
+        ma.st = rs;
+        ma.vm = vm;
+        ma.out = lo;
+        ma.em = em;
+        ma.overflow = lo.stats + 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 1) {
                 launch_compact_bands(rs.flag, nl, R, bands, nbands_d, st);
                 ++nlaunch;
-                CK(cudaMemcpyAsync(&nb_active, nbands_d, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-                CK(cudaStreamSynchronize(st));
-                if (nb_active == 0) break;
             }
-            host_passes[li] = passes;
+            CK(cudaMemsetAsync(unit_ctr, 0, sizeof(int32_t), st));
+            {
+                const size_t e = ev_pair(li);
+                CK(cudaEventRecord(evs[e].a, st));
+                launch_band<T>(ba, false, grid_band, st);
+                CK(cudaEventRecord(evs[e].b, st));
+            }
+            launch_merge<T>(ma, st);
+            nlaunch += 2;
+            CK(cudaGetLastError());
         }
         FlatArgs fa{n0, nl, l, E, p, m_max, run, rs, vm, lo};
         launch_flat_rows(fa, st);
@@ -449,21 +430,28 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         host_launch[li] = nlaunch;
         nlaunch = 0;
     }
-    std::vector<unsigned long long> hs((size_t)nL * 5);
+    int32_t herr = 0;
+    CK(cudaMemcpyAsync(&herr, wait_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    std::vector<unsigned long long> hs((size_t)nL * NSTAT);
     CK(cudaMemcpyAsync(hs.data(), dstats, hs.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (herr != 0) {
+        set_err(ctx, "a bounded wait in the band kernel ran out");
+        throw Fail{MAD_ETIMEOUT};
+    }
     for (int li = 0; li < nL; ++li) {
         mad_length_stats &q = s.stats[li];
+        const unsigned long long *h = &hs[(size_t)li * NSTAT];
         q.len = lmin + li;
         q.rows = n - (lmin + li) + 1;
-        q.certified = (int64_t)hs[li * 5 + 1];
-        q.recomputed = (int64_t)hs[li * 5 + 2];
-        q.tiles = (int64_t)host_tiles[li];
-        q.passes = (int64_t)host_passes[li];
-        unsigned long long bits = hs[li * 5 + 3];
+        q.certified = (int64_t)h[1];
+        q.recomputed = (int64_t)h[2];
+        q.tiles = (int64_t)h[5];
+        q.passes = q.recomputed > 0 ? (h[0] > 0 ? 2 : 1) : 0;
+        unsigned long long bits = h[3];
         std::memcpy(&q.fp32_dq_max, &bits, sizeof(double));
-        q.band_cells = (int64_t)host_cells[li];
-        q.inserts = (int64_t)hs[li * 5 + 4];
+        q.band_cells = (int64_t)h[6];
+        q.inserts = (int64_t)h[4];
         q.launches = (int64_t)host_launch[li];
         q.band_ms = 0.0;
     }
@@ -727,18 +715,25 @@ MAD_API mad_status mad_discords(mad_ctx *ctx, int32_t series, int32_t k, int32_t
             }
         std::vector<double> rec(where.size(), NAN);
         if (!where.empty()) {
-            void *dreq = nullptr, *dout = nullptr;
-            CK(cudaMalloc(&dreq, req.size() * sizeof(int32_t)));
-            cudaError_t e2 = cudaMalloc(&dout, where.size() * sizeof(double));
-            if (e2 != cudaSuccess) { cudaFree(dreq); CK(e2); }
-            cudaMemcpyAsync(dreq, req.data(), req.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
-            launch_recheck_discords(s.x, s.n, (const int32_t *)dreq, (int)where.size(), ctx->opt.excl_num,
-                                    ctx->opt.excl_den, (double *)dout, st);
-            cudaError_t e3 = cudaMemcpyAsync(rec.data(), dout, where.size() * sizeof(double),
-                                             cudaMemcpyDeviceToHost, st);
-            cudaError_t e4 = cudaStreamSynchronize(st);
+            const int nc = (int)where.size();
+            const size_t ns = recheck_scratch(nc, m);
+            void *dreq = nullptr, *dout = nullptr, *dsd = nullptr, *dsj = nullptr;
+            cudaError_t e1 = cudaMalloc(&dreq, req.size() * sizeof(int32_t));
+            if (e1 == cudaSuccess) e1 = cudaMalloc(&dout, nc * sizeof(double));
+            if (e1 == cudaSuccess) e1 = cudaMalloc(&dsd, ns * sizeof(double));
+            if (e1 == cudaSuccess) e1 = cudaMalloc(&dsj, ns * sizeof(int32_t));
+            cudaError_t e3 = e1, e4 = cudaSuccess;
+            if (e1 == cudaSuccess) {
+                cudaMemcpyAsync(dreq, req.data(), req.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+                launch_recheck_discords(s.x, s.n, (const int32_t *)dreq, nc, ctx->opt.excl_num, ctx->opt.excl_den,
+                                        (double *)dout, (double *)dsd, (int32_t *)dsj, m, st);
+                e3 = cudaMemcpyAsync(rec.data(), dout, nc * sizeof(double), cudaMemcpyDeviceToHost, st);
+                e4 = cudaStreamSynchronize(st);
+            }
             cudaFree(dreq);
             cudaFree(dout);
+            cudaFree(dsd);
+            cudaFree(dsj);
             CK(e3);
             CK(e4);
             CK(cudaGetLastError());
