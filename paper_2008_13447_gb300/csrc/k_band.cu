@@ -210,11 +210,44 @@ __device__ __forceinline__ bool any_positive(const double (&C)[RPL], double inv,
     return (int)acc >= 0;
 }
 
-template <typename T, int RPL, int NW, bool BINS, bool DIAG>
+template <int RPL>
+__device__ __forceinline__ bool any_positive2(const float (&C)[RPL], float inv, const float (&th)[RPL],
+                                              const float (&invr)[RPL], float thc)
+{
+    unsigned acc = 0xffffffffu;
+#pragma unroll
+    for (int a = 0; a < RPL; ++a)
+        acc &= __float_as_uint(fmaf(C[a], inv, -th[a])) & __float_as_uint(fmaf(C[a], invr[a], -thc));
+    return (int)acc >= 0;
+}
+
+template <int RPL>
+__device__ __forceinline__ bool any_positive2(const double (&C)[RPL], double inv, const double (&th)[RPL],
+                                              const double (&invr)[RPL], double thc)
+{
+    unsigned acc = 0xffffffffu;
+#pragma unroll
+    for (int a = 0; a < RPL; ++a)
+        acc &= (unsigned)(__double_as_longlong(fma(C[a], inv, -th[a])) >> 32) &
+               (unsigned)(__double_as_longlong(fma(C[a], invr[a], -thc)) >> 32);
+    return (int)acc >= 0;
+}
+
+enum { MODE_TOPP = 0, MODE_BINS = 1, MODE_SYM = 2 };
+
+// One chunk of CH columns for the lane's RPL rows.
+//  MODE_TOPP: every column; row keys against the row thresholds.
+//  MODE_BINS: every column; running maxima of the row keys.
+//  MODE_SYM : cells above the exclusion zone only (j - r > E); each cell is
+//             tested for its row (key C / sqrt(M2_j) against th_r, into the
+//             row's list) and for its column (key C / sqrt(M2_r) against the
+//             column's threshold, staged in cd.pad, appended to row j's
+//             candidate list in global memory).
+template <typename T, int RPL, int NW, int MODE, bool DIAG>
 __device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *cbuf, T tp, T *bout, int lane, int w,
                                            int64_t cs, int64_t rbase, int rl0, T (&C)[RPL], const T (&dfr)[RPL],
-                                           const T (&dgr)[RPL], T (&th)[RPL], T (&runmax)[RPL], T *lkey,
-                                           int32_t *lj, int32_t *lcnt, unsigned &ninsert)
+                                           const T (&dgr)[RPL], T (&th)[RPL], const T (&invr)[RPL],
+                                           T (&runmax)[RPL], T *lkey, int32_t *lj, int32_t *lcnt, unsigned &ninsert)
 {
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
@@ -226,8 +259,17 @@ __device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *c
         for (int a = RPL - 1; a >= 1; --a) C[a] = fma(dfr[a], cd.dg, fma(cd.df, dgr[a], C[a - 1]));
         C[0] = fma(dfr[0], cd.dg, fma(cd.df, dgr[0], v));
         if (w < NW - 1 && lane == 31) bout[c] = C[RPL - 1];
-        if (!BINS) {
-            bool hit = false;
+        if (MODE == MODE_BINS) {
+#pragma unroll
+            for (int a = 0; a < RPL; ++a) {
+                T key = C[a] * cd.inv;
+                if (DIAG && !nontrivial(rbase + a, cs + c, A.E)) key = neg_inf<T>();
+                runmax[a] = fmax_t(runmax[a], key);   // NaN keys (padding) are ignored
+            }
+            continue;
+        }
+        bool hit = false;
+        if (MODE == MODE_TOPP) {
             if (DIAG) {
 #pragma unroll
                 for (int a = 0; a < RPL; ++a)
@@ -237,26 +279,41 @@ __device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *c
                 // rows; +0 and NaN count as hits and are re-tested below)
                 hit = any_positive(C, cd.inv, th);
             }
-            if (hit) {
-                const int32_t j = (int32_t)(cs + c);
+        } else {
+            if (DIAG) {
 #pragma unroll
-                for (int a = 0; a < RPL; ++a) {
-                    const T key = C[a] * cd.inv;
-                    if (key > th[a] && nontrivial(rbase + a, j, A.E)) {
-                        const int rl = rl0 + a;
-                        int32_t cnt = lcnt[rl];
-                        topp_insert<T>(lkey + rl * A.p, lj + rl * A.p, cnt, A.p, key, j, th[a]);
-                        lcnt[rl] = cnt;
+                for (int a = 0; a < RPL; ++a)
+                    hit |= ((cs + c) - (rbase + a) > A.E) && ((C[a] * cd.inv > th[a]) || (C[a] * invr[a] > cd.pad));
+            } else {
+                hit = any_positive2(C, cd.inv, th, invr, cd.pad);
+            }
+        }
+        if (hit) {
+            const int32_t j = (int32_t)(cs + c);
+#pragma unroll
+            for (int a = 0; a < RPL; ++a) {
+                const int64_t r = rbase + a;
+                const bool valid = MODE == MODE_SYM ? (j - r > A.E) : nontrivial(r, j, A.E);
+                if (!valid) continue;
+                const T key = C[a] * cd.inv;
+                if (key > th[a]) {
+                    const int rl = rl0 + a;
+                    int32_t cnt = lcnt[rl];
+                    topp_insert<T>(lkey + rl * A.p, lj + rl * A.p, cnt, A.p, key, j, th[a]);
+                    lcnt[rl] = cnt;
+                    ++ninsert;
+                }
+                if (MODE == MODE_SYM) {
+                    const T kc = C[a] * invr[a];
+                    if (kc > cd.pad) {
+                        const int slot = atomicAdd(&A.ccnt[j], 1);
+                        if (slot < A.cap) {
+                            A.ckey[(int64_t)j * A.cap + slot] = kc;
+                            A.cj[(int64_t)j * A.cap + slot] = (int32_t)r;
+                        }
                         ++ninsert;
                     }
                 }
-            }
-        } else {
-#pragma unroll
-            for (int a = 0; a < RPL; ++a) {
-                T key = C[a] * cd.inv;
-                if (DIAG && !nontrivial(rbase + a, cs + c, A.E)) key = neg_inf<T>();
-                runmax[a] = fmax_t(runmax[a], key);   // NaN keys (padding) are ignored
             }
         }
     }
@@ -300,9 +357,11 @@ __device__ __forceinline__ void mbar_wait(uint64_t *b, unsigned parity, int *err
     atomicExch(err, 1);
 }
 
-template <typename T, int RPL, int NW, bool BINS>
-__global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
+template <typename T, int RPL, int NW, int MODE>
+__global__ void __launch_bounds__(NW * 32, 2) k_band(const BandArgs<T> A)
 {
+    constexpr bool BINS = MODE == MODE_BINS;
+    constexpr bool SYM = MODE == MODE_SYM;
     constexpr int R = 32 * RPL * NW;
     extern __shared__ __align__(32) unsigned char smem_raw[];
     uint64_t *mfull = reinterpret_cast<uint64_t *>(smem_raw);       // [NW][NSLOT]
@@ -316,12 +375,14 @@ __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
     int32_t *lj = reinterpret_cast<int32_t *>(lkey + R * A.p);
     int32_t *lcnt = lj + R * A.p;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int nb = *A.nbands;
+    const int nb_active = *A.nbands;
+    // The symmetric form walks all bands and only the upper triangle; it is
+    // used when at least half of the bands hold rows to recompute.
+    const bool sym_on = A.allow_sym && 2 * nb_active >= A.kb_total;
+    if (MODE == MODE_SYM && !sym_on) return;
+    if (MODE == MODE_TOPP && sym_on) return;
+    const int nb = SYM ? A.kb_total : nb_active;
     const int64_t total = (int64_t)nb * A.ngroups;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && nb > 0 && A.stats) {
-        atomicAdd(&A.stats[5], (unsigned long long)total);
-        atomicAdd(&A.stats[6], (unsigned long long)nb * R * (unsigned long long)A.nl);
-    }
     const int NEG_ORD = f2ord(-__int_as_float(0x7f800000));
     const int nbins = A.nbins;
 
@@ -362,11 +423,16 @@ __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
         if (u >= total) break;
         {
         const int g = (int)(u / nb);
-        const int band = A.bands[u % nb];
+        const int band = SYM ? (int)(u % nb) : A.bands[u % nb];
         const int64_t i0 = (int64_t)band * R;
         const int64_t c0 = (int64_t)g * A.group_w;
         if (c0 >= A.nl) continue;
+        if (SYM && c0 + A.group_w <= i0) continue;   // entirely below the diagonal
         const int64_t c1 = c0 + A.group_w < A.nl ? c0 + A.group_w : A.nl;
+        if (threadIdx.x == 0 && A.stats) {
+            atomicAdd(&A.stats[5], 1ull);
+            atomicAdd(&A.stats[6], (unsigned long long)R * (unsigned long long)(c1 - c0));
+        }
         const int nchunk = (int)((c1 - c0 + CH - 1) / CH);
         const int64_t rfirst = i0 + (int64_t)w * 32 * RPL;
         const int64_t rbase = rfirst + lane * RPL;
@@ -374,21 +440,24 @@ __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
         const T *sleft = A.seed + (c0 / A.sp) * A.spitch;
         const T *stop = A.seed + (i0 / A.sp) * A.spitch;
 
-        T C[RPL], dfr[RPL], dgr[RPL], th[RPL], runmax[RPL];
+        T C[RPL], dfr[RPL], dgr[RPL], th[RPL], runmax[RPL], invr[RPL];
 #pragma unroll
         for (int a = 0; a < RPL; ++a) {
             const int64_t r = rbase + a;
             const Col<T> cr = A.col[r];
             dfr[a] = cr.df;
             dgr[a] = cr.dg;
+            invr[a] = cr.inv;
             th[a] = A.thr[r];
             C[a] = sleft[r + 1];
             runmax[a] = neg_inf<T>();
             if (!BINS) lcnt[rl0 + a] = 0;
         }
         T carry = sleft[rfirst];
-        // prefetched column data / top edge of the next chunk
+        // prefetched column data / top edge of the next chunk (the symmetric
+        // form carries the column's threshold in the spare field)
         Col<T> ncol = A.col[c0 + lane];
+        if (SYM) ncol.pad = A.thr[c0 + lane];
         T ntop = w == 0 ? stop[c0 + lane] : T(0);
 
         for (int q = 0; q < nchunk; ++q, ++qg) {
@@ -398,7 +467,10 @@ __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
             Col<T> *cbuf = colbuf + w * CH;
             cbuf[lane] = ncol;
             T tp;
-            if (q + 1 < nchunk) ncol = A.col[cs + CH + lane];
+            if (q + 1 < nchunk) {
+                ncol = A.col[cs + CH + lane];
+                if (SYM) ncol.pad = A.thr[cs + CH + lane];
+            }
             if (w == 0) {
                 tp = ntop;
                 if (q + 1 < nchunk) ntop = stop[cs + CH + lane];
@@ -416,13 +488,14 @@ __global__ void __launch_bounds__(NW * 32) k_band(const BandArgs<T> A)
             T *bout = bbuf + ((w + 1 < NW ? w + 1 : 0) * NSLOT + slot) * CH;
             // does this warp's row range meet the exclusion zone in this chunk?
             const int64_t rlo = rfirst, rhi = rfirst + 32 * RPL - 1;
-            const bool diag = (cs <= rhi + A.E) && (cs + CH - 1 >= rlo - A.E);
+            // (symmetric form: everything not wholly above the zone is tested cell by cell)
+            const bool diag = SYM ? !(cs > rhi + A.E) : (cs <= rhi + A.E) && (cs + CH - 1 >= rlo - A.E);
             if (diag)
-                band_chunk<T, RPL, NW, BINS, true>(A, cbuf, tp, bout, lane, w, cs, rbase, rl0, C, dfr, dgr, th,
-                                                   runmax, lkey, lj, lcnt, ninsert);
+                band_chunk<T, RPL, NW, MODE, true>(A, cbuf, tp, bout, lane, w, cs, rbase, rl0, C, dfr, dgr, th,
+                                                   invr, runmax, lkey, lj, lcnt, ninsert);
             else
-                band_chunk<T, RPL, NW, BINS, false>(A, cbuf, tp, bout, lane, w, cs, rbase, rl0, C, dfr, dgr, th,
-                                                    runmax, lkey, lj, lcnt, ninsert);
+                band_chunk<T, RPL, NW, MODE, false>(A, cbuf, tp, bout, lane, w, cs, rbase, rl0, C, dfr, dgr, th,
+                                                    invr, runmax, lkey, lj, lcnt, ninsert);
             if (w < NW - 1 && lane == 31) mbar_arrive(&mfull[(w + 1) * NSLOT + slot]);   // chunk q written
             if (BINS) {
                 const int bin = (int)((cs / CH) % nbins);
@@ -479,42 +552,63 @@ size_t band_smem(bool bins_mode, int p, int rpl)
 }
 
 template <typename T, int RPL>
-static const void *band_fn_rpl(bool bins)
+static const void *band_fn_rpl(int mode)
 {
-    return bins ? (const void *)k_band<T, RPL, BAND_NW, true> : (const void *)k_band<T, RPL, BAND_NW, false>;
+    switch (mode) {
+    case MODE_BINS: return (const void *)k_band<T, RPL, BAND_NW, MODE_BINS>;
+    case MODE_SYM: return (const void *)k_band<T, RPL, BAND_NW, MODE_SYM>;
+    default: return (const void *)k_band<T, RPL, BAND_NW, MODE_TOPP>;
+    }
 }
 
 template <typename T>
-static const void *band_fn(bool bins, int rpl)
+static const void *band_fn(int mode, int rpl)
 {
     switch (rpl) {
-    case 8: return band_fn_rpl<T, 8>(bins);
-    case 4: return band_fn_rpl<T, 4>(bins);
-    case 2: return band_fn_rpl<T, 2>(bins);
-    default: return band_fn_rpl<T, 1>(bins);
+    case 8: return band_fn_rpl<T, 8>(mode);
+    case 4: return band_fn_rpl<T, 4>(mode);
+    case 2: return band_fn_rpl<T, 2>(mode);
+    default: return band_fn_rpl<T, 1>(mode);
     }
 }
 
 template <typename T>
 int band_occupancy(bool bins_mode, int p, int rpl)
 {
-    const void *fn = band_fn<T>(bins_mode, rpl);
-    const size_t sm = band_smem<T>(bins_mode, p, rpl);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return 0;
-    int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, BAND_NW * 32, sm) != cudaSuccess) return 0;
-    return blocks;
+    int worst = 1 << 30;
+    for (int mode : {bins_mode ? (int)MODE_BINS : (int)MODE_TOPP, bins_mode ? (int)MODE_BINS : (int)MODE_SYM}) {
+        const void *fn = band_fn<T>(mode, rpl);
+        const size_t sm = band_smem<T>(bins_mode, p, rpl);
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return 0;
+        int blocks = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, BAND_NW * 32, sm) != cudaSuccess) return 0;
+        worst = blocks < worst ? blocks : worst;
+    }
+    return worst;
 }
 
 template <typename T>
-void launch_band(const BandArgs<T> &a, bool bins_mode, int grid, cudaStream_t s)
+static void launch_mode(const BandArgs<T> &a, int mode, bool bins_mode, int grid, cudaStream_t s)
 {
-    const int rpl = a.rpl;
-    const size_t sm = band_smem<T>(bins_mode, a.p, rpl);
-    const void *fn = band_fn<T>(bins_mode, rpl);
+    const size_t sm = band_smem<T>(bins_mode, a.p, a.rpl);
+    const void *fn = band_fn<T>(mode, a.rpl);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     void *args[] = {const_cast<BandArgs<T> *>(&a)};
     cudaLaunchKernel(fn, dim3(grid), dim3(BAND_NW * 32), args, sm, s);
+}
+
+// bins mode: one launch. Otherwise two launches, of which exactly one works:
+// the symmetric form when at least half of the bands are active (and
+// allowed), the full-square form on the active bands otherwise.
+template <typename T>
+void launch_band(const BandArgs<T> &a, bool bins_mode, int grid, cudaStream_t s)
+{
+    if (bins_mode) {
+        launch_mode<T>(a, MODE_BINS, true, grid, s);
+        return;
+    }
+    launch_mode<T>(a, MODE_TOPP, false, grid, s);
+    if (a.allow_sym) launch_mode<T>(a, MODE_SYM, false, grid, s);
 }
 
 template void launch_band<float>(const BandArgs<float> &, bool, int, cudaStream_t);

@@ -300,26 +300,41 @@ __global__ void k_merge(MergeArgs<T> A)
     const int64_t ntc = nontrivial_count(i, A.nl, E);
     const int need = (int)(ntc < p ? ntc : p);
 
-    // top-p by key desc, offset asc over all groups
+    // top-p by key desc, offset asc over the row's lists. The symmetric form
+    // wrote row-side lists for the column groups from the row's band
+    // diagonal on, and appended the column-side candidates (cells (i', i),
+    // i' < i) to the row's candidate list.
+    const bool sym_on = A.allow_sym && 2 * (*A.nbands) >= A.kb_total;
     T bk[MAXP];
     int32_t bj[MAXP];
     int nb = 0;
-    for (int g = 0; g < A.ngroups && (int64_t)g * A.group_w < A.nl; ++g) {
+    auto offer = [&](T v, int32_t j) {
+        if (nb == p && !(v > bk[p - 1] || (v == bk[p - 1] && j < bj[p - 1]))) return;
+        int b = nb < p ? nb++ : p - 1;
+        while (b > 0 && (bk[b - 1] < v || (bk[b - 1] == v && bj[b - 1] > j))) {
+            bk[b] = bk[b - 1];
+            bj[b] = bj[b - 1];
+            --b;
+        }
+        bk[b] = v;
+        bj[b] = j;
+    };
+    const int g0 = sym_on ? (int)(((i / A.R) * (int64_t)A.R) / A.group_w) : 0;
+    for (int g = g0; g < A.ngroups && (int64_t)g * A.group_w < A.nl; ++g) {
         const int64_t slot = i * A.ngroups + g;
         const int cnt = A.scnt[slot];
-        for (int c = 0; c < cnt; ++c) {
-            const T v = A.skey[slot * p + c];
-            const int32_t j = A.sj[slot * p + c];
-            if (nb == p && !(v > bk[p - 1] || (v == bk[p - 1] && j < bj[p - 1]))) continue;
-            int b = nb < p ? nb++ : p - 1;
-            while (b > 0 && (bk[b - 1] < v || (bk[b - 1] == v && bj[b - 1] > j))) {
-                bk[b] = bk[b - 1];
-                bj[b] = bj[b - 1];
-                --b;
-            }
-            bk[b] = v;
-            bj[b] = j;
+        for (int c = 0; c < cnt; ++c) offer(A.skey[slot * p + c], A.sj[slot * p + c]);
+    }
+    if (sym_on) {
+        const int cc = A.ccnt[i];
+        A.ccnt[i] = 0;
+        if (cc > A.cap) {
+            // more column-side candidates than kept: redo the row in full
+            // (its threshold stays valid)
+            atomicAdd(A.overflow, 1ull);
+            return;
         }
+        for (int c = 0; c < cc; ++c) offer(A.ckey[i * A.cap + c], A.cj[i * A.cap + c]);
     }
     if (nb < need) {
         A.thr[i] = T(-pinf());

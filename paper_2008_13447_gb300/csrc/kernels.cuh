@@ -65,6 +65,13 @@ template <typename T> struct BandArgs {
     int *err;               // set to 1 if a bounded wait ran out
     unsigned long long *ninsert;  // top-p list insertions (diagnostic counter)
     unsigned long long *stats;    // this length's counters ([5] units, [6] cells)
+    // symmetric form
+    int kb_total;           // number of bands covering n_l rows
+    int allow_sym;
+    T *ckey;                // [row][cap] column-side candidates (key, partner)
+    int32_t *cj;
+    int32_t *ccnt;          // [row]
+    int cap;
 };
 template <typename T> void launch_band(const BandArgs<T> &a, bool bins_mode, int grid, cudaStream_t s);
 template <typename T> int band_occupancy(bool bins_mode, int p, int rpl);
@@ -158,6 +165,15 @@ template <typename T> struct MergeArgs {
     LenOut out;
     ErrModel em;
     unsigned long long *overflow;   // rows that need a second pass
+    // symmetric form (same rule as the band kernel)
+    const int32_t *nbands;
+    int kb_total;
+    int allow_sym;
+    int R;
+    const T *ckey;
+    const int32_t *cj;
+    int32_t *ccnt;
+    int cap;
 };
 template <typename T> void launch_merge(const MergeArgs<T> &a, cudaStream_t s);
 

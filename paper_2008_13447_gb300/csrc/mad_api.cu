@@ -258,6 +258,11 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     if (G > K) G = K;
     const int64_t group_w = G * SP;
     const int ngroups_max = (int)((n0 + group_w - 1) / group_w);
+    const int ccap = p * 8 > 32 ? p * 8 : 32;
+    T *ckey = dalloc<T>(ctx, s, (size_t)n0 * ccap);
+    int32_t *cjj = dalloc<int32_t>(ctx, s, (size_t)n0 * ccap);
+    int32_t *ccnt = dalloc<int32_t>(ctx, s, n0);
+    CK(cudaMemsetAsync(ccnt, 0, n0 * sizeof(int32_t), st));
     T *skey = dalloc<T>(ctx, s, (size_t)n0 * ngroups_max * p);
     int32_t *sj = dalloc<int32_t>(ctx, s, (size_t)n0 * ngroups_max * p);
     int32_t *scnt = dalloc<int32_t>(ctx, s, (size_t)n0 * ngroups_max);
@@ -280,8 +285,14 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     ba.bins = bins;
     ba.nbins = nbins;
     ba.err = wait_err;
+    ba.ckey = ckey;
+    ba.cj = cjj;
+    ba.ccnt = ccnt;
+    ba.cap = ccap;
 
     int cur = 0;
+    // the symmetric band form (upper triangle, both sides of each cell)
+    const int use_sym = 1;
     s.stats.assign(nL, mad_length_stats{});
     std::vector<unsigned long long> host_launch(nL, 0);
     // CUDA events around every band-kernel launch (device time of the
@@ -362,6 +373,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         ba.ngroups = ngroups_max;   // the slot layout keeps the lmin group count
         ba.stats = lo.stats;
         ba.ninsert = lo.stats + 4;
+        ba.kb_total = (int)((nl + R - 1) / R);
         if (l == lmin) {
             // first thresholds from interleaved maxima
             launch_fill<int32_t>(bins, (int64_t)n0 * nbins, (int32_t)0x807fffff, st);  // ord(-inf)
@@ -400,7 +412,18 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         ma.out = lo;
         ma.em = em;
         ma.overflow = lo.stats + 0;
+        ma.nbands = nbands_d;
+        ma.kb_total = ba.kb_total;
+        ma.R = R;
+        ma.ckey = ckey;
+        ma.cj = cjj;
+        ma.ccnt = ccnt;
+        ma.cap = ccap;
         for (int pass = 0; pass < 2; ++pass) {
+            // pass 0 may use the symmetric form; pass 1 (rows whose lists
+            // fell short) always runs the full-square form
+            ba.allow_sym = pass == 0 ? use_sym : 0;
+            ma.allow_sym = ba.allow_sym;
             if (pass == 1) {
                 launch_compact_bands(rs.flag, nl, R, bands, nbands_d, st);
                 ++nlaunch;
@@ -413,7 +436,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
                 CK(cudaEventRecord(evs[e].b, st));
             }
             launch_merge<T>(ma, st);
-            nlaunch += 2;
+            nlaunch += ba.allow_sym ? 3 : 2;
             CK(cudaGetLastError());
         }
         FlatArgs fa{n0, nl, l, E, p, m_max, run, rs, vm, lo};
