@@ -123,6 +123,9 @@ typedef struct {
     int64_t launches;       /* GPU kernel launches issued for this length */
     int64_t inserts;        /* insertions into the band kernel's per-row top-p lists (cells that
                                beat their row's running p-th best key) */
+    int64_t col_appends;    /* symmetric band form: cells appended to their column row's
+                               candidate list */
+    int64_t second_pass_rows; /* rows whose lists fell short and were redone in full */
     double band_ms;         /* device time of those band-kernel launches (CUDA events recorded
                                on the context's stream around each launch) */
     double fp32_dq_max;     /* MAD_FP32: largest |q_FP32 - q_FP64| among stored entries that were

@@ -311,7 +311,7 @@ __device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *c
                             A.ckey[(int64_t)j * A.cap + slot] = kc;
                             A.cj[(int64_t)j * A.cap + slot] = (int32_t)r;
                         }
-                        ++ninsert;
+                        ninsert += 1u << 16;
                     }
                 }
             }
@@ -534,8 +534,14 @@ __global__ void __launch_bounds__(NW * 32, 2) k_band(const BandArgs<T> A)
         }
     }
     if (!BINS) {
-        for (int o = 16; o > 0; o >>= 1) ninsert += __shfl_xor_sync(0xffffffffu, ninsert, o);
-        if (lane == 0 && ninsert) atomicAdd(A.ninsert, (unsigned long long)ninsert);
+        // low 16 bits: row-list insertions, high 16 bits: column-side appends
+        unsigned long long rowi = ninsert & 0xffffu, coli = ninsert >> 16;
+        for (int o = 16; o > 0; o >>= 1) {
+            rowi += __shfl_xor_sync(0xffffffffu, rowi, o);
+            coli += __shfl_xor_sync(0xffffffffu, coli, o);
+        }
+        if (lane == 0 && rowi) atomicAdd(A.ninsert, rowi);
+        if (lane == 0 && coli && A.stats) atomicAdd(&A.stats[7], coli);
     }
 }
 

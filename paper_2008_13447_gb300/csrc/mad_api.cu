@@ -258,7 +258,9 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     if (G > K) G = K;
     const int64_t group_w = G * SP;
     const int ngroups_max = (int)((n0 + group_w - 1) / group_w);
-    const int ccap = p * 8 > 32 ? p * 8 : 32;
+    // column-side candidates per row (symmetric form): runs of adjacent
+    // partners can clear a row's threshold together, so keep many
+    const int ccap = p * 32 > 256 ? p * 32 : 256;
     T *ckey = dalloc<T>(ctx, s, (size_t)n0 * ccap);
     int32_t *cjj = dalloc<int32_t>(ctx, s, (size_t)n0 * ccap);
     int32_t *ccnt = dalloc<int32_t>(ctx, s, n0);
@@ -475,6 +477,8 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         std::memcpy(&q.fp32_dq_max, &bits, sizeof(double));
         q.band_cells = (int64_t)h[6];
         q.inserts = (int64_t)h[4];
+        q.col_appends = (int64_t)h[7];
+        q.second_pass_rows = (int64_t)h[0];
         q.launches = (int64_t)host_launch[li];
         q.band_ms = 0.0;
     }
