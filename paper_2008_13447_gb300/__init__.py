@@ -36,7 +36,7 @@ ABI_FUNCTIONS = ("mad_create", "mad_create_device", "mad_create_batch", "mad_pro
 class mad_options(C.Structure):
     _fields_ = [("excl_num", C.c_int32), ("excl_den", C.c_int32), ("precision", C.c_int32),
                 ("k_max", C.c_int32), ("m_max", C.c_int32), ("keep_profiles", C.c_int32),
-                ("mode", C.c_int32), ("reserved", C.c_int32), ("stream", C.c_void_p)]
+                ("mode", C.c_int32), ("band_form", C.c_int32), ("stream", C.c_void_p)]
 
 
 class mad_motif(C.Structure):
@@ -104,7 +104,7 @@ def _check(status, ctx):
         raise MadError(status, library().mad_last_error(ctx).decode())
 
 
-def _options(precision=MAD_FP64, excl=(1, 4), k_max=10, m_max=1, keep_profiles=False, stream=None):
+def _options(precision=MAD_FP64, excl=(1, 4), k_max=10, m_max=1, keep_profiles=False, stream=None, band_form=0):
     o = mad_options()
     o.excl_num, o.excl_den = excl
     o.precision = precision
@@ -112,7 +112,7 @@ def _options(precision=MAD_FP64, excl=(1, 4), k_max=10, m_max=1, keep_profiles=F
     o.m_max = m_max
     o.keep_profiles = 1 if keep_profiles else 0
     o.mode = 0
-    o.reserved = 0
+    o.band_form = band_form
     if stream is not None:
         o.stream = stream if isinstance(stream, int) else stream.cuda_stream
     return o

@@ -339,6 +339,7 @@ __global__ void k_merge(MergeArgs<T> A)
     if (nb < need) {
         A.thr[i] = T(-pinf());
         atomicAdd(A.overflow, 1ull);
+        atomicAdd(A.overflow + 8, 1ull);
         return;
     }
     const double m2i = A.m2[i];

@@ -123,7 +123,7 @@ void check_options(mad_ctx *ctx, const mad_options &o)
     REQUIRE(o.k_max >= 1 && o.k_max <= KMAX, "k_max must be in [1, 64]");
     REQUIRE(o.m_max >= 1 && o.m_max <= MAXP, "m_max must be in [1, 64]");
     REQUIRE(o.mode == 0, "mode must be 0");
-    REQUIRE(o.reserved == 0, "reserved option field must be 0");
+    REQUIRE(o.band_form == 0 || o.band_form == 1, "band_form must be 0 or 1");
 }
 
 void init_ctx(mad_ctx *ctx, const mad_options *opt)
@@ -216,7 +216,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     // per-length device counters: [0] rows left for a second pass, [1] certified,
     // [2] recomputed, [3] largest FP32-vs-FP64 correlation gap (bits),
     // [4] top-p insertions, [5] band units, [6] band cells
-    constexpr int NSTAT = 8;
+    constexpr int NSTAT = 10;
     unsigned long long *dstats = dalloc<unsigned long long>(ctx, s, (size_t)nL * NSTAT);
     DiscTable tab{dalloc<double>(ctx, s, (size_t)k_max * m_max), dalloc<double>(ctx, s, (size_t)k_max * m_max),
                   dalloc<int32_t>(ctx, s, (size_t)k_max * m_max), dalloc<int32_t>(ctx, s, (size_t)k_max * m_max),
@@ -294,7 +294,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
 
     int cur = 0;
     // the symmetric band form (upper triangle, both sides of each cell)
-    const int use_sym = 1;
+    const int use_sym = o.band_form == 0 ? 1 : 0;
     s.stats.assign(nL, mad_length_stats{});
     std::vector<unsigned long long> host_launch(nL, 0);
     // CUDA events around every band-kernel launch (device time of the
