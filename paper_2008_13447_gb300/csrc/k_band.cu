@@ -235,45 +235,6 @@ __device__ __forceinline__ bool any_positive2(const double (&C)[RPL], double inv
 
 enum { MODE_TOPP = 0, MODE_BINS = 1, MODE_SYM = 2 };
 
-template <typename T, int RPL> struct Vec { T v[RPL]; };
-
-// Cells of one column that passed the cheap test (rare): test each of the
-// lane's rows exactly and insert into the row's list / append to the column
-// row's candidate list. Out of line so that the per-column loop stays small
-// enough to unroll; the row values arrive by value.
-template <typename T, int RPL, int MODE>
-__device__ __noinline__ Vec<T, RPL> hit_rows(Vec<T, RPL> c, Vec<T, RPL> th, Vec<T, RPL> invr, T inv_j, T thc_j,
-                                            int32_t j, int64_t rbase, int rl0, int64_t E, int p, T *lkey,
-                                            int32_t *lj, int32_t *lcnt, int32_t *ccnt, T *ckey, int32_t *cj, int cap,
-                                            unsigned *nins)
-{
-    for (int a = 0; a < RPL; ++a) {
-        const int64_t r = rbase + a;
-        const bool valid = MODE == MODE_SYM ? (j - r > E) : nontrivial(r, j, E);
-        if (!valid) continue;
-        const T key = c.v[a] * inv_j;
-        if (key > th.v[a]) {
-            const int rl = rl0 + a;
-            int32_t cnt = lcnt[rl];
-            topp_insert<T>(lkey + rl * p, lj + rl * p, cnt, p, key, j, th.v[a]);
-            lcnt[rl] = cnt;
-            *nins += 1u;
-        }
-        if (MODE == MODE_SYM) {
-            const T kc = c.v[a] * invr.v[a];
-            if (kc > thc_j) {
-                const int slot = atomicAdd(&ccnt[j], 1);
-                if (slot < cap) {
-                    ckey[(int64_t)j * cap + slot] = kc;
-                    cj[(int64_t)j * cap + slot] = (int32_t)r;
-                }
-                *nins += 1u << 16;
-            }
-        }
-    }
-    return th;
-}
-
 // One chunk of CH columns for the lane's RPL rows.
 //  MODE_TOPP: every column; row keys against the row thresholds.
 //  MODE_BINS: every column; running maxima of the row keys.
@@ -288,7 +249,6 @@ __device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *c
                                            const T (&dgr)[RPL], T (&th)[RPL], const T (&invr)[RPL],
                                            T (&runmax)[RPL], T *lkey, int32_t *lj, int32_t *lcnt, unsigned &ninsert)
 {
-    const bool writer = (w < NW - 1) && (lane == 31);
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
         const Col<T> cd = cbuf[c];
@@ -298,7 +258,7 @@ __device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *c
 #pragma unroll
         for (int a = RPL - 1; a >= 1; --a) C[a] = fma(dfr[a], cd.dg, fma(cd.df, dgr[a], C[a - 1]));
         C[0] = fma(dfr[0], cd.dg, fma(cd.df, dgr[0], v));
-        if (writer) bout[c] = C[RPL - 1];
+        if (w < NW - 1 && lane == 31) bout[c] = C[RPL - 1];
         if (MODE == MODE_BINS) {
 #pragma unroll
             for (int a = 0; a < RPL; ++a) {
@@ -316,7 +276,7 @@ __device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *c
                     hit |= (C[a] * cd.inv > th[a]) && nontrivial(rbase + a, cs + c, A.E);
             } else {
                 // any key - th > 0 ? (AND of the sign bits of key - th over the
-                // rows; +0 and NaN count as hits and are re-tested exactly)
+                // rows; +0 and NaN count as hits and are re-tested below)
                 hit = any_positive(C, cd.inv, th);
             }
         } else {
@@ -329,18 +289,32 @@ __device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *c
             }
         }
         if (hit) {
-            Vec<T, RPL> vc, vth, vinv;
+            const int32_t j = (int32_t)(cs + c);
 #pragma unroll
             for (int a = 0; a < RPL; ++a) {
-                vc.v[a] = C[a];
-                vth.v[a] = th[a];
-                vinv.v[a] = invr[a];
+                const int64_t r = rbase + a;
+                const bool valid = MODE == MODE_SYM ? (j - r > A.E) : nontrivial(r, j, A.E);
+                if (!valid) continue;
+                const T key = C[a] * cd.inv;
+                if (key > th[a]) {
+                    const int rl = rl0 + a;
+                    int32_t cnt = lcnt[rl];
+                    topp_insert<T>(lkey + rl * A.p, lj + rl * A.p, cnt, A.p, key, j, th[a]);
+                    lcnt[rl] = cnt;
+                    ++ninsert;
+                }
+                if (MODE == MODE_SYM) {
+                    const T kc = C[a] * invr[a];
+                    if (kc > cd.pad) {
+                        const int slot = atomicAdd(&A.ccnt[j], 1);
+                        if (slot < A.cap) {
+                            A.ckey[(int64_t)j * A.cap + slot] = kc;
+                            A.cj[(int64_t)j * A.cap + slot] = (int32_t)r;
+                        }
+                        ninsert += 1u << 16;
+                    }
+                }
             }
-            const Vec<T, RPL> nt = hit_rows<T, RPL, MODE>(vc, vth, vinv, cd.inv, cd.pad, (int32_t)(cs + c), rbase, rl0,
-                                                          A.E, A.p, lkey, lj, lcnt, A.ccnt, A.ckey, A.cj, A.cap,
-                                                          &ninsert);
-#pragma unroll
-            for (int a = 0; a < RPL; ++a) th[a] = nt.v[a];
         }
     }
 }
