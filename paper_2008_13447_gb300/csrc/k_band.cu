@@ -377,8 +377,8 @@ __global__ void __launch_bounds__(NW * 32, 2) k_band(const BandArgs<T> A)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nb_active = *A.nbands;
     // The symmetric form walks all bands and only the upper triangle; it is
-    // used when at least half of the bands hold rows to recompute.
-    const bool sym_on = A.allow_sym && 2 * nb_active >= A.kb_total;
+    // used when at least half of the rows need recomputing.
+    const bool sym_on = sym_rule(A.allow_sym, *A.nflagged, A.nl);
     if (MODE == MODE_SYM && !sym_on) return;
     if (MODE == MODE_TOPP && sym_on) return;
     const int nb = SYM ? A.kb_total : nb_active;

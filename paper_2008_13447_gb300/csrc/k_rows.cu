@@ -11,6 +11,7 @@
 namespace mad {
 
 __device__ __forceinline__ double pinf() { return __longlong_as_double(0x7ff0000000000000LL); }
+__device__ __forceinline__ int direct_cols_per_block_dev() { return 4096; }   // k_direct.cu: DCOLS
 
 // Insert (q, j) into arrays sorted by q descending, j ascending; n entries.
 __device__ __forceinline__ void ins_qj(double *qs, int32_t *js, int n, double q, int32_t j)
@@ -293,7 +294,8 @@ __global__ void k_merge(MergeArgs<T> A)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= A.nl) return;
-    if (A.st.flag[i] != ROW_RECOMPUTE) return;
+    const int32_t fl = A.st.flag[i];
+    if (fl != ROW_RECOMPUTE && fl != ROW_DIRECT) return;
     const int l = A.l;
     const int64_t n0 = A.n0, E = A.E;
     const int p = A.p;
@@ -304,7 +306,7 @@ __global__ void k_merge(MergeArgs<T> A)
     // wrote row-side lists for the column groups from the row's band
     // diagonal on, and appended the column-side candidates (cells (i', i),
     // i' < i) to the row's candidate list.
-    const bool sym_on = A.allow_sym && 2 * (*A.nbands) >= A.kb_total;
+    const bool sym_on = sym_rule(A.allow_sym, *A.nflagged, A.nl) && fl == ROW_RECOMPUTE;
     T bk[MAXP];
     int32_t bj[MAXP];
     int nb = 0;
@@ -319,18 +321,30 @@ __global__ void k_merge(MergeArgs<T> A)
         bk[b] = v;
         bj[b] = j;
     };
-    const int g0 = sym_on ? (int)(((i / A.R) * (int64_t)A.R) / A.group_w) : 0;
-    for (int g = g0; g < A.ngroups && (int64_t)g * A.group_w < A.nl; ++g) {
-        const int64_t slot = i * A.ngroups + g;
-        const int cnt = A.scnt[slot];
-        for (int c = 0; c < cnt; ++c) offer(A.skey[slot * p + c], A.sj[slot * p + c]);
+    if (fl == ROW_DIRECT) {
+        const int64_t d = A.dindex[i];
+        for (int g = 0; g < A.dnblk; ++g) {
+            const int64_t slot = d * A.dnblk + g;
+            if ((int64_t)g * direct_cols_per_block_dev() >= A.nl) break;
+            const int cnt = A.dcnt[slot];
+            for (int c = 0; c < cnt; ++c) offer(A.dkey[slot * p + c], A.dj[slot * p + c]);
+        }
+    } else {
+        const int g0 = sym_on ? (int)(((i / A.R) * (int64_t)A.R) / A.group_w) : 0;
+        for (int g = g0; g < A.ngroups && (int64_t)g * A.group_w < A.nl; ++g) {
+            const int64_t slot = i * A.ngroups + g;
+            const int cnt = A.scnt[slot];
+            for (int c = 0; c < cnt; ++c) offer(A.skey[slot * p + c], A.sj[slot * p + c]);
+        }
     }
+    if (A.allow_sym && fl == ROW_DIRECT) A.ccnt[i] = 0;
     if (sym_on) {
         const int cc = A.ccnt[i];
         A.ccnt[i] = 0;
         if (cc > A.cap) {
             // more column-side candidates than kept: redo the row in full
             // (its threshold stays valid)
+            A.st.flag[i] = ROW_RECOMPUTE;
             atomicAdd(A.overflow, 1ull);
             return;
         }
@@ -338,6 +352,7 @@ __global__ void k_merge(MergeArgs<T> A)
     }
     if (nb < need) {
         A.thr[i] = T(-pinf());
+        A.st.flag[i] = ROW_RECOMPUTE;
         atomicAdd(A.overflow, 1ull);
         atomicAdd(A.overflow + 8, 1ull);
         return;
@@ -447,7 +462,9 @@ __global__ void k_flat_rows(FlatArgs A)
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= A.nl) return;
-    if (A.st.flag[i] != ROW_FLAT) return;
+    const int32_t fl = A.st.flag[i];
+    if ((fl == ROW_RECOMPUTE || fl == ROW_DIRECT) && lane == 0) atomicExch(A.left_over, 1);
+    if (fl != ROW_FLAT) return;
     const int l = A.l;
     const int64_t n0 = A.n0, E = A.E;
     const int p = A.p;
@@ -536,6 +553,76 @@ void launch_compact_bands(const int32_t *flag, int64_t nl, int R, int32_t *bands
     const int64_t nb = (nl + R - 1) / R;
     cudaMemsetAsync(nbands, 0, sizeof(int32_t), s);
     k_compact_bands<<<(unsigned)nb, 256, 0, s>>>(flag, nl, R, bands, nbands);
+}
+
+// One block per band: count the band's rows to recompute; route them to the
+// direct path (few rows, room left in the list, symmetric form off) or list
+// the band for the band kernel.
+__global__ void k_split(SplitArgs A)
+{
+    const int64_t b = blockIdx.x;
+    const int64_t r0 = b * A.R;
+    int cnt = 0;
+    for (int64_t r = r0 + threadIdx.x; r < r0 + A.R && r < A.nl; r += blockDim.x) cnt += (A.flag[r] == ROW_RECOMPUTE);
+    cnt = __syncthreads_count(cnt);
+    if (cnt == 0) return;
+    const bool sym_on = sym_rule(A.allow_sym, *A.nflagged, A.nl);
+    __shared__ int base;
+    bool direct = A.force_direct || (!sym_on && cnt <= A.lim);
+    if (direct) {
+        if (threadIdx.x == 0) {
+            base = atomicAdd(A.ndirect, cnt);
+            if (base + cnt > A.max_direct) {
+                atomicSub(A.ndirect, cnt);
+                base = -1;
+            }
+        }
+        __syncthreads();
+        direct = base >= 0;
+    }
+    if (!direct) {
+        if (threadIdx.x == 0) {
+            const int slot = atomicAdd(A.nbands, 1);
+            A.bands[slot] = (int32_t)b;
+        }
+        return;
+    }
+    // positions within the list: block-wide ballot prefix per pass of rows
+    __shared__ int run;
+    __shared__ int wsum[32];
+    if (threadIdx.x == 0) run = base;
+    __syncthreads();
+    for (int64_t r0w = r0; r0w < r0 + A.R && r0w < A.nl; r0w += blockDim.x) {
+        const int64_t r = r0w + threadIdx.x;
+        const bool f = r < r0 + A.R && r < A.nl && A.flag[r] == ROW_RECOMPUTE;
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) wsum[wid] = __popc(bal);
+        __syncthreads();
+        int before = 0;
+        for (int q = 0; q < wid; ++q) before += wsum[q];
+        if (f) {
+            const int pos = run + before + __popc(bal & ((1u << lane) - 1u));
+            A.drows[pos] = (int32_t)r;
+            A.dindex[r] = pos;
+            A.flag[r] = ROW_DIRECT;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += wsum[q];
+            run += tot;
+        }
+        __syncthreads();
+    }
+}
+
+void launch_split(const SplitArgs &a, cudaStream_t s)
+{
+    const int64_t nb = (a.nl + a.R - 1) / a.R;
+    cudaMemsetAsync(a.nbands, 0, sizeof(int32_t), s);
+    cudaMemsetAsync(a.ndirect, 0, sizeof(int32_t), s);
+    k_split<<<(unsigned)nb, 256, 0, s>>>(a);
 }
 
 template <typename T>

@@ -68,6 +68,7 @@ template <typename T> struct BandArgs {
     // symmetric form
     int kb_total;           // number of bands covering n_l rows
     int allow_sym;
+    const unsigned long long *nflagged;   // rows to recompute at this length
     T *ckey;                // [row][cap] column-side candidates (key, partner)
     int32_t *cj;
     int32_t *ccnt;          // [row]
@@ -166,10 +167,15 @@ template <typename T> struct MergeArgs {
     ErrModel em;
     unsigned long long *overflow;   // rows that need a second pass
     // symmetric form (same rule as the band kernel)
-    const int32_t *nbands;
-    int kb_total;
+    const unsigned long long *nflagged;
     int allow_sym;
     int R;
+    // direct path
+    const int32_t *dindex;
+    const T *dkey;
+    const int32_t *dj;
+    const int32_t *dcnt;
+    int dnblk;
     const T *ckey;
     const int32_t *cj;
     int32_t *ccnt;
@@ -190,6 +196,7 @@ struct FlatArgs {
     RowState st;
     Valmp vm;
     LenOut out;
+    int *left_over;         // set when a row is still waiting for a recompute
 };
 void launch_flat_rows(const FlatArgs &a, cudaStream_t s);
 
@@ -198,6 +205,53 @@ template <typename T> void launch_mask_thr(const int32_t *flag, int64_t n0, T *t
 
 void launch_compact_bands(const int32_t *flag, int64_t nl, int R, int32_t *bands, int32_t *nbands,
                           cudaStream_t s);
+
+// Rows to recompute, split between the band kernel and the direct path: a
+// band whose rows to recompute number at most `lim` hands them to the direct
+// path (flag ROW_DIRECT, listed in drows with dindex[row] = position, while
+// the list has room), other bands go to the band list. When the symmetric
+// band form is on (at least half of the rows to recompute, read from
+// *nflagged) nothing goes direct unless force_direct.
+struct SplitArgs {
+    int32_t *flag;
+    int64_t nl;
+    int R;
+    int lim;
+    int force_direct;
+    int allow_sym;
+    const unsigned long long *nflagged;
+    int32_t *bands;
+    int32_t *nbands;
+    int32_t *drows;
+    int32_t *ndirect;
+    int32_t *dindex;
+    int max_direct;
+};
+void launch_split(const SplitArgs &a, cudaStream_t s);
+__host__ __device__ __forceinline__ bool sym_rule(int allow_sym, unsigned long long nflagged, int64_t nl)
+{
+    return allow_sym && 2 * (int64_t)nflagged >= nl;
+}
+
+// Direct recompute of listed rows (k_direct.cu).
+template <typename T> struct DirectArgs {
+    const double *x;
+    const double *mu;
+    const Col<T> *col;
+    int64_t nl;
+    int l;
+    int64_t E;
+    int p;
+    const int32_t *rows;
+    const int32_t *nrows;
+    const T *thr;
+    T *okey;                // [list position][nblk][p]
+    int32_t *oj;
+    int32_t *ocnt;          // [list position][nblk]
+    int nblk;
+};
+template <typename T> void launch_direct(const DirectArgs<T> &a, int grid, cudaStream_t s);
+int direct_cols_per_block();
 
 template <typename T>
 void launch_fill(T *p, int64_t n, T v, cudaStream_t s);

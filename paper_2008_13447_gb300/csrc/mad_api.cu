@@ -227,6 +227,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     }
     int32_t *nbands_d = counters, *unit_ctr = counters + 1;
     int32_t *wait_err = counters + 3;
+    int32_t *ndirect = dalloc<int32_t>(ctx, s, 1);
 
     // ---- one-off initialisation
     {
@@ -250,6 +251,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     const int occ_bins = band_occupancy<T>(true, p, rpl);
     REQUIRE(occ_band > 0 && occ_bins > 0, "band kernel does not fit on this device");
     const int grid_band = ctx->num_sms * occ_band;
+    const int grid_direct = ctx->num_sms * 4;
     const int grid_bins = ctx->num_sms * occ_bins;
     // columns per work unit: a multiple of the seed spacing, ~8 units per
     // resident CTA when possible
@@ -265,6 +267,14 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     int32_t *cjj = dalloc<int32_t>(ctx, s, (size_t)n0 * ccap);
     int32_t *ccnt = dalloc<int32_t>(ctx, s, n0);
     CK(cudaMemsetAsync(ccnt, 0, n0 * sizeof(int32_t), st));
+    // direct path: row list, list positions, per (row, column block) top-p
+    const int max_direct = (int)(n0 < (1 << 16) ? n0 : (1 << 16));
+    const int dnblk = (int)((n0 + direct_cols_per_block() - 1) / direct_cols_per_block());
+    int32_t *drows = dalloc<int32_t>(ctx, s, max_direct);
+    int32_t *dindex = dalloc<int32_t>(ctx, s, n0);
+    T *dkey = dalloc<T>(ctx, s, (size_t)max_direct * dnblk * p);
+    int32_t *djj = dalloc<int32_t>(ctx, s, (size_t)max_direct * dnblk * p);
+    int32_t *dcnt = dalloc<int32_t>(ctx, s, (size_t)max_direct * dnblk);
     T *skey = dalloc<T>(ctx, s, (size_t)n0 * ngroups_max * p);
     int32_t *sj = dalloc<int32_t>(ctx, s, (size_t)n0 * ngroups_max * p);
     int32_t *scnt = dalloc<int32_t>(ctx, s, (size_t)n0 * ngroups_max);
@@ -359,12 +369,26 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         }
         CK(cudaGetLastError());
 
-        // Rows to recompute -> bands -> seeds -> band kernel -> merge, with no
-        // host round trip: the kernels read the band count on the device
-        // (and do nothing when it is 0). A second pass picks up rows whose
-        // threshold turned out too high (none by construction; it runs
-        // without threshold, so it cannot fall short again).
-        launch_compact_bands(rs.flag, nl, R, bands, nbands_d, st);
+        // Rows to recompute -> (bands | direct rows) -> seeds -> band kernel
+        // -> direct kernel -> merge, with no host round trip: kernels read
+        // their counts on the device (and do nothing when they are 0). A
+        // second pass recomputes directly the rows whose lists fell short
+        // (column-side list overflow in the symmetric form).
+        SplitArgs sp{};
+        sp.flag = rs.flag;
+        sp.nl = nl;
+        sp.R = R;
+        sp.lim = (4 * R) / l > 1 ? (4 * R) / l : 1;
+        sp.force_direct = 0;
+        sp.allow_sym = use_sym;
+        sp.nflagged = lo.stats + 2;
+        sp.bands = bands;
+        sp.nbands = nbands_d;
+        sp.drows = drows;
+        sp.ndirect = ndirect;
+        sp.dindex = dindex;
+        sp.max_direct = max_direct;
+        launch_split(sp, st);
         ++nlaunch;
         SeedArgs<T> sa{s.x, mu[cur], nl, l, SP, krows, (int)K, spitch, seed, nbands_d};
         launch_seed<T>(sa, st);
@@ -376,6 +400,8 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         ba.stats = lo.stats;
         ba.ninsert = lo.stats + 4;
         ba.kb_total = (int)((nl + R - 1) / R);
+        ba.nflagged = lo.stats + 2;
+        ba.allow_sym = use_sym;
         if (l == lmin) {
             // first thresholds from interleaved maxima
             launch_fill<int32_t>(bins, (int64_t)n0 * nbins, (int32_t)0x807fffff, st);  // ord(-inf)
@@ -391,6 +417,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
             nlaunch += 4;
             CK(cudaGetLastError());
         }
+        DirectArgs<T> da{s.x, mu[cur], col, nl, l, E, p, drows, ndirect, thr, dkey, djj, dcnt, dnblk};
         MergeArgs<T> ma{};
         ma.x = s.x;
         ma.mu = mu[cur];
@@ -414,34 +441,38 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         ma.out = lo;
         ma.em = em;
         ma.overflow = lo.stats + 0;
-        ma.nbands = nbands_d;
-        ma.kb_total = ba.kb_total;
+        ma.nflagged = lo.stats + 2;
         ma.R = R;
         ma.ckey = ckey;
         ma.cj = cjj;
         ma.ccnt = ccnt;
         ma.cap = ccap;
+        ma.dindex = dindex;
+        ma.dkey = dkey;
+        ma.dj = djj;
+        ma.dcnt = dcnt;
+        ma.dnblk = dnblk;
         for (int pass = 0; pass < 2; ++pass) {
-            // pass 0 may use the symmetric form; pass 1 (rows whose lists
-            // fell short) always runs the full-square form
-            ba.allow_sym = pass == 0 ? use_sym : 0;
-            ma.allow_sym = ba.allow_sym;
-            if (pass == 1) {
-                launch_compact_bands(rs.flag, nl, R, bands, nbands_d, st);
-                ++nlaunch;
-            }
-            CK(cudaMemsetAsync(unit_ctr, 0, sizeof(int32_t), st));
-            {
+            ma.allow_sym = pass == 0 ? use_sym : 0;
+            if (pass == 0) {
+                CK(cudaMemsetAsync(unit_ctr, 0, sizeof(int32_t), st));
                 const size_t e = ev_pair(li);
                 CK(cudaEventRecord(evs[e].a, st));
                 launch_band<T>(ba, false, grid_band, st);
                 CK(cudaEventRecord(evs[e].b, st));
+                nlaunch += use_sym ? 2 : 1;
+            } else {
+                sp.force_direct = 1;
+                sp.allow_sym = 0;
+                launch_split(sp, st);
+                ++nlaunch;
             }
+            launch_direct<T>(da, grid_direct, st);
             launch_merge<T>(ma, st);
-            nlaunch += ba.allow_sym ? 3 : 2;
+            nlaunch += 2;
             CK(cudaGetLastError());
         }
-        FlatArgs fa{n0, nl, l, E, p, m_max, run, rs, vm, lo};
+        FlatArgs fa{n0, nl, l, E, p, m_max, run, rs, vm, lo, wait_err + 0 /* same error word */};
         launch_flat_rows(fa, st);
         launch_discords_length(nnd, nnj, n0, nl, l, E, k_max, m_max, bval, bidx, tab, st);
         nlaunch += 3;
@@ -461,7 +492,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     CK(cudaMemcpyAsync(hs.data(), dstats, hs.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (herr != 0) {
-        set_err(ctx, "a bounded wait in the band kernel ran out");
+        set_err(ctx, "a bounded wait in the band kernel ran out, or a row was left without its recompute");
         throw Fail{MAD_ETIMEOUT};
     }
     for (int li = 0; li < nL; ++li) {
