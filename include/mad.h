@@ -128,6 +128,7 @@ typedef struct {
     int64_t col_appends;    /* symmetric band form: cells appended to their column row's
                                candidate list */
     int64_t second_pass_rows; /* rows whose lists fell short and were redone in full */
+    int64_t direct_rows;    /* rows recomputed by direct dot products instead of the band kernel */
     double band_ms;         /* device time of those band-kernel launches (CUDA events recorded
                                on the context's stream around each launch) */
     double fp32_dq_max;     /* MAD_FP32: largest |q_FP32 - q_FP64| among stored entries that were

@@ -54,7 +54,8 @@ class mad_length_stats(C.Structure):
     _fields_ = [("len", C.c_int32), ("reserved", C.c_int32), ("rows", C.c_int64), ("certified", C.c_int64),
                 ("recomputed", C.c_int64), ("tiles", C.c_int64), ("passes", C.c_int64),
                 ("band_cells", C.c_int64), ("launches", C.c_int64), ("inserts", C.c_int64),
-                ("col_appends", C.c_int64), ("second_pass_rows", C.c_int64), ("band_ms", C.c_double),
+                ("col_appends", C.c_int64), ("second_pass_rows", C.c_int64), ("direct_rows", C.c_int64),
+                ("band_ms", C.c_double),
                 ("fp32_dq_max", C.c_double)]
 
 
@@ -207,7 +208,7 @@ def mad_stats(ctx, series, cap=1 << 16):
     _check(library().mad_stats(ctx, series, out, cap, C.byref(n)), ctx)
     return [dict(len=s.len, rows=s.rows, certified=s.certified, recomputed=s.recomputed, tiles=s.tiles,
                  passes=s.passes, band_cells=s.band_cells, launches=s.launches, inserts=s.inserts,
-                 col_appends=s.col_appends, second_pass_rows=s.second_pass_rows,
+                 col_appends=s.col_appends, second_pass_rows=s.second_pass_rows, direct_rows=s.direct_rows,
                  band_ms=s.band_ms,
                  fp32_dq_max=s.fp32_dq_max) for s in out[:min(n.value, cap)]]
 

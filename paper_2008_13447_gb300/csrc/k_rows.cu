@@ -575,6 +575,8 @@ __global__ void k_split(SplitArgs A)
             if (base + cnt > A.max_direct) {
                 atomicSub(A.ndirect, cnt);
                 base = -1;
+            } else if (A.stat_direct) {
+                atomicAdd(A.stat_direct, (unsigned long long)cnt);
             }
         }
         __syncthreads();

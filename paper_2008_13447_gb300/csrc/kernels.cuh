@@ -226,6 +226,7 @@ struct SplitArgs {
     int32_t *ndirect;
     int32_t *dindex;
     int max_direct;
+    unsigned long long *stat_direct;   // rows routed to the direct path (counter)
 };
 void launch_split(const SplitArgs &a, cudaStream_t s);
 __host__ __device__ __forceinline__ bool sym_rule(int allow_sym, unsigned long long nflagged, int64_t nl)

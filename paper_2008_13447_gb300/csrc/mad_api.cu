@@ -388,6 +388,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         sp.ndirect = ndirect;
         sp.dindex = dindex;
         sp.max_direct = max_direct;
+        sp.stat_direct = lo.stats + 9;
         launch_split(sp, st);
         ++nlaunch;
         SeedArgs<T> sa{s.x, mu[cur], nl, l, SP, krows, (int)K, spitch, seed, nbands_d};
@@ -510,6 +511,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         q.inserts = (int64_t)h[4];
         q.col_appends = (int64_t)h[7];
         q.second_pass_rows = (int64_t)h[0];
+        q.direct_rows = (int64_t)h[9];
         q.launches = (int64_t)host_launch[li];
         q.band_ms = 0.0;
     }
