@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="planted65k")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--band-form", type=int, default=0, choices=[0, 1],
+                    help="0: symmetric band form when most bands are active, else full rows; 1: full rows")
     ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the plain FP64 GPU path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
@@ -228,7 +230,8 @@ def main():
     n, lmin, lmax, p, k, m = len(x), w.lmin[0], w.lmax[0], w.p, w.k, w.m
     prec = mad.MAD_FP32 if args.precision == "fp32" else mad.MAD_FP64
     xt = torch.tensor(x, device=dev, dtype=torch.float64)
-    ctx = mad.mad_create_device(xt, precision=prec, k_max=k, m_max=m, stream=stream)
+    ctx = mad.mad_create_device(xt, precision=prec, k_max=k, m_max=m, stream=stream,
+                                band_form=args.band_form)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
     def step():
@@ -292,14 +295,15 @@ def main():
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32" if prec == mad.MAD_FP32 else "f64", "data": "synthetic",
            "config": {"workload": args.workload, "n": n, "lmin": lmin, "lmax": lmax, "p": p, "k": k, "m": m,
-                      "exclusion": "ceil(l/4)", "precision": args.precision, "cells_per_step": cells,
+                      "exclusion": "ceil(l/4)", "precision": args.precision, "band_form": args.band_form, "cells_per_step": cells,
                       "l2": "flushed between timed steps (512 MB write)", "parallelism": "replicas"},
            "roofline": roof, "gpu_launches": int(round(launches_per_step * args.steps)),
            "clocks": clk}
 
     # plain FP64 GPU path, one step, for the comparison the metric names
     if rank == 0 and not args.no_fp64_path and prec == mad.MAD_FP32:
-        c64 = mad.mad_create_device(xt, precision=mad.MAD_FP64, k_max=k, m_max=m, stream=stream)
+        c64 = mad.mad_create_device(xt, precision=mad.MAD_FP64, k_max=k, m_max=m, stream=stream,
+                                    band_form=args.band_form)
         try:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             flush.fill_(7)
@@ -324,7 +328,7 @@ def main():
     for _ in range(2):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        c2 = mad.mad_create(xh, precision=prec, k_max=k, m_max=m, stream=stream)
+        c2 = mad.mad_create(xh, precision=prec, k_max=k, m_max=m, stream=stream, band_form=args.band_form)
         try:
             mad.mad_profile(c2, lmin, lmax, p)
             mot = mad.mad_motifs(c2, 0, k)

@@ -562,12 +562,18 @@ __global__ void k_split(SplitArgs A)
 {
     const int64_t b = blockIdx.x;
     const int64_t r0 = b * A.R;
-    int cnt = 0;
-    for (int64_t r = r0 + threadIdx.x; r < r0 + A.R && r < A.nl; r += blockDim.x) cnt += (A.flag[r] == ROW_RECOMPUTE);
-    cnt = __syncthreads_count(cnt);
+    __shared__ int total;
+    __shared__ int base;
+    if (threadIdx.x == 0) total = 0;
+    __syncthreads();
+    int mine = 0;
+    for (int64_t r = r0 + threadIdx.x; r < r0 + A.R && r < A.nl; r += blockDim.x) mine += (A.flag[r] == ROW_RECOMPUTE);
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&total, mine);
+    __syncthreads();
+    const int cnt = total;
     if (cnt == 0) return;
     const bool sym_on = sym_rule(A.allow_sym, *A.nflagged, A.nl);
-    __shared__ int base;
     bool direct = A.force_direct || (!sym_on && cnt <= A.lim);
     if (direct) {
         if (threadIdx.x == 0) {

@@ -34,8 +34,9 @@ def check_index_choice(x, l, i, j_gpu, d_ref, tol, num, den):
     assert abs(d - d_ref) <= tol + 1e-12, (l, i, j_gpu, d, d_ref)
 
 
-def run_gpu(x, lmin, lmax, p, prec, m_max=1, k_max=5, excl=(1, 4)):
-    ctx = mad.mad_create(x, precision=prec, k_max=k_max, m_max=m_max, excl=excl, keep_profiles=True)
+def run_gpu(x, lmin, lmax, p, prec, m_max=1, k_max=5, excl=(1, 4), band_form=0):
+    ctx = mad.mad_create(x, precision=prec, k_max=k_max, m_max=m_max, excl=excl, keep_profiles=True,
+                         band_form=band_form)
     try:
         mad.mad_profile(ctx, lmin, lmax, p)
         n = len(x)
@@ -49,10 +50,10 @@ def run_gpu(x, lmin, lmax, p, prec, m_max=1, k_max=5, excl=(1, 4)):
     return prof, vm, mot, dis, st
 
 
-def compare_all(x, lmin, lmax, p, prec, m_max=1, k_max=5, excl=(1, 4)):
+def compare_all(x, lmin, lmax, p, prec, m_max=1, k_max=5, excl=(1, 4), band_form=0):
     num, den = excl
     ref = oracle.valmp_plain(x, lmin, lmax, m_max=m_max, num=num, den=den, keep_nn=True)
-    prof, vm, mot, dis, st = run_gpu(x, lmin, lmax, p, prec, m_max, k_max, excl)
+    prof, vm, mot, dis, st = run_gpu(x, lmin, lmax, p, prec, m_max, k_max, excl, band_form)
     n = len(x)
     n0 = n - lmin + 1
     worst = 0.0

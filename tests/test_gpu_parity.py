@@ -43,12 +43,21 @@ def test_ar2_mth_neighbours_half_zone(prec):
     compare_all(x, 30, 36, 6, prec, m_max=3, k_max=4, excl=(1, 2))
 
 
+@pytest.mark.parametrize("band_form", [0, 1], ids=["auto", "full_rows"])
 @pytest.mark.parametrize("prec", PRECS)
-def test_ecg_pruned_regime(prec):
+def test_ecg_pruned_regime(prec, band_form):
     x = workloads.ecg_like(4500, 103, period=60.0)
-    r = compare_all(x, 60, 72, 8, prec, m_max=2, k_max=3)
+    r = compare_all(x, 60, 72, 8, prec, m_max=2, k_max=3, band_form=band_form)
     st = r["stats"]
     assert sum(s["certified"] for s in st[1:]) > 0.5 * sum(s["rows"] for s in st[1:])
+    # few uncertified rows per band: they take the direct path
+    assert sum(s["direct_rows"] for s in st[1:]) > 0
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_random_walk_full_rows_form(prec):
+    x = workloads.random_walk(5000, 101)
+    compare_all(x, 40, 48, 5, prec, band_form=1)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -66,6 +75,15 @@ def test_ragged_band_edges(prec):
     R = 1024 if prec == mad.MAD_FP64 else 2048
     x = workloads.random_walk(R + 16, 105)
     compare_all(x, 16, 20, 3, prec, k_max=2)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_long_windows_shared_memory_line(prec):
+    # FP64 at l = 409 puts the direct kernel's dynamic shared memory just
+    # under 48 KB and its static + dynamic total just over; long windows with
+    # a short series also give a sparse band for the direct path
+    x = workloads.random_walk(2400, 108)
+    compare_all(x, 406, 412, 3, prec, k_max=2)
 
 
 @pytest.mark.parametrize("prec", PRECS)
