@@ -195,8 +195,45 @@ MAD_API mad_status mad_matrix_profile(mad_ctx *ctx, int32_t series, int32_t len,
 MAD_API mad_status mad_stats(mad_ctx *ctx, int32_t series, mad_length_stats *out, int32_t cap,
                              int32_t *n_out);
 
+/* Largest ncells * m_max of one mad_mth_nn_dist_noalloc call: the number of
+ * (cell, rank) slots in its fixed scratch (1024 slots, about 0.8 MB of
+ * device memory per device, linked into the library). */
+#define MAD_NOALLOC_MAX_SLOTS 1024
+
+/* The m-th best-match distance of listed windows, recomputed directly in
+ * FP64 from a full distance profile (Eq. DIST with two-pass window
+ * statistics; the m-th best match of Definition 6), i.e. the computation
+ * behind mad_discords' dist_recheck, without allocating any memory. The
+ * paper has no counterpart of this function: it serves callers that cannot
+ * allocate device memory during the call (memory held in a caching
+ * allocator's pools, latency-bound code that cannot afford cudaFree's
+ * device-wide wait, or a fixed footprint known up front).
+ *   x      device, n doubles: the series (current device's memory).
+ *   cells  host, ncells x 3 int32, row-major (off, len, m): window
+ *          [off, off + len) and the rank m of the best match wanted.
+ *   m_max  the largest m among the cells, in [1, 64]; ncells * m_max must
+ *          not exceed MAD_NOALLOC_MAX_SLOTS (else MAD_EINVAL, nothing run).
+ *   excl_num / excl_den  exclusion zone E(len) = ceil(len * num / den).
+ *   out    device, ncells doubles: the distances (+inf when the window has
+ *          fewer than m non-trivial partners).
+ *   stream the CUDA stream to use (NULL: legacy default stream).
+ * Errors: MAD_EINVAL for a bad argument or cell (checked on the host before
+ * any GPU work, or x / out not device memory of the current device),
+ * MAD_ECUDA for a failed CUDA call; mad_last_error(NULL) gives the text.
+ * The call makes no cudaMalloc / cudaFree or other allocating call. Its
+ * scratch is one statically sized device array per device; the first call
+ * on each device (with that device current) looks up the array's address,
+ * which is set-up work: make that first call before any stream capture
+ * begins. The scratch needs no zero initialisation. All calls on a device
+ * share the one scratch, so calls that overlap in time (other streams or
+ * host threads) race: order them. Synchronous with respect to the host. */
+MAD_API mad_status mad_mth_nn_dist_noalloc(const double *x, int64_t n, const int32_t *cells,
+                                           int32_t ncells, int32_t m_max, int32_t excl_num,
+                                           int32_t excl_den, double *out, void *stream);
+
 /* Human-readable description of the last error on ctx (or of the calling
- * thread's last mad_create* error when ctx is NULL). Never NULL. */
+ * thread's last mad_create* or mad_mth_nn_dist_noalloc error when ctx is
+ * NULL). Never NULL. */
 MAD_API const char *mad_last_error(const mad_ctx *ctx);
 
 /* Release the context and its device memory. NULL-safe. */

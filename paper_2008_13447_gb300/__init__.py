@@ -26,11 +26,12 @@ LIB_PATH = os.path.join(HERE, "_build", "libmad.so")
 
 MAD_OK, MAD_EINVAL, MAD_ENOMEM, MAD_ECUDA, MAD_ESTATE, MAD_ETIMEOUT, MAD_EINTERNAL = range(7)
 MAD_FP64, MAD_FP32 = 0, 1
+MAD_NOALLOC_MAX_SLOTS = 1024
 STATUS_NAMES = {0: "MAD_OK", 1: "MAD_EINVAL", 2: "MAD_ENOMEM", 3: "MAD_ECUDA", 4: "MAD_ESTATE",
                 5: "MAD_ETIMEOUT", 6: "MAD_EINTERNAL"}
 ABI_FUNCTIONS = ("mad_create", "mad_create_device", "mad_create_batch", "mad_profile", "mad_profile_batch",
                  "mad_motifs", "mad_discords", "mad_valmp", "mad_matrix_profile", "mad_stats",
-                 "mad_last_error", "mad_destroy")
+                 "mad_mth_nn_dist_noalloc", "mad_last_error", "mad_destroy")
 
 
 class mad_options(C.Structure):
@@ -87,6 +88,7 @@ def library() -> C.CDLL:
             "mad_valmp": [P, i32, P, P, P, P],
             "mad_matrix_profile": [P, i32, i32, P, P, P, P],
             "mad_stats": [P, i32, C.POINTER(mad_length_stats), i32, C.POINTER(i32)],
+            "mad_mth_nn_dist_noalloc": [P, i64, P, i32, i32, i32, i32, P, P],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -211,6 +213,17 @@ def mad_stats(ctx, series, cap=1 << 16):
                  col_appends=s.col_appends, second_pass_rows=s.second_pass_rows, direct_rows=s.direct_rows,
                  band_ms=s.band_ms,
                  fp32_dq_max=s.fp32_dq_max) for s in out[:min(n.value, cap)]]
+
+
+def mad_mth_nn_dist_noalloc(x_ptr, n, cells, m_max, out_ptr, excl=(1, 4), stream=None):
+    """m-th best-match distances of the windows in ``cells`` (rows of
+    (off, len, m)), recomputed in FP64, written to ``out_ptr``. ``x_ptr`` and
+    ``out_ptr`` are device addresses (ints, e.g. ``tensor.data_ptr()``) of n
+    and len(cells) doubles; the call allocates no device memory."""
+    c = np.ascontiguousarray(cells, dtype=np.int32).reshape(-1, 3)
+    st = None if stream is None else C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(library().mad_mth_nn_dist_noalloc(C.c_void_p(x_ptr), n, _p(c), len(c), m_max, excl[0], excl[1],
+                                             C.c_void_p(out_ptr), st), None)
 
 
 def mad_last_error(ctx=None):

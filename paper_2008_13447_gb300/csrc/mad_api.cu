@@ -565,6 +565,11 @@ mad_status run_guarded(mad_ctx *ctx, F &&f)
 
 // ---------------------------------------------------------------- the ABI
 
+namespace mad {
+// Error text of context-free calls, returned by mad_last_error(NULL).
+void set_thread_error(const std::string &msg) { g_create_err = msg; }
+}  // namespace mad
+
 extern "C" {
 
 MAD_API mad_status mad_create(const double *host_series, int64_t n, const mad_options *opt, mad_ctx **out)
