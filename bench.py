@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--workload", default="planted65k")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--band-form", type=int, default=0, choices=[0, 1],
-                    help="0: symmetric band form when most bands are active, else full rows; 1: full rows")
+                    help="0: full rows; 1: symmetric band form when most bands are active")
     ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the plain FP64 GPU path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
@@ -125,7 +125,7 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("k_band.cu", "kernels.cuh", "mad_internal.cuh"):
+    for f in ("k_band.cuh", "k_band_f32.cu", "kernels.cuh", "mad_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2008_13447_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -80,9 +80,10 @@ typedef struct mad_options {
                                doubles and offsets; meant for small inputs) */
     int32_t mode;           /* 0 (only mode): every row the bound cannot certify is recomputed,
                                so every per-length result is exact for every offset */
-    int32_t band_form;      /* matrix-profile kernel form: 0 = automatic (the symmetric form, which
-                               computes each pair once and feeds both windows, when at least half of
-                               the row bands need recomputing; otherwise full rows), 1 = full rows only */
+    int32_t band_form;      /* matrix-profile kernel form: 0 = full rows (each row band walks every
+                               column; the faster form on GB300), 1 = symmetric (upper triangle only,
+                               each pair computed once and fed to both windows, used for the lengths
+                               where at least half of the row bands need recomputing) */
     void *stream;           /* cudaStream_t to issue work on; NULL = the legacy default stream */
 } mad_options;
 

@@ -1,4 +1,4 @@
-// k_band.cu -- the matrix-profile kernel: diagonal (QT) recurrence over R x R
+// k_band.cuh -- the matrix-profile kernel: diagonal (QT) recurrence over R x R
 // tiles, wavefront across warps, per-row candidate selection.
 //
 // What it computes (Algorithm 3 ComputeMatrixProfile, restricted to the rows
@@ -29,6 +29,7 @@
 // chunk of CH columns behind (a wavefront over the warps, one barrier per
 // chunk). Per-column data (df, dg, inv) is staged per chunk in shared memory
 // and read as broadcasts.
+#pragma once
 #include "kernels.cuh"
 
 namespace mad {
@@ -38,107 +39,6 @@ namespace mad {
 template <typename T>
 __global__ void k_seed(SeedArgs<T> A);
 
-// FP64 seeds: the centred dot product evaluated directly in FP64.
-template <>
-__global__ void k_seed<double>(SeedArgs<double> A)
-{
-    if (A.nbands && *A.nbands == 0) return;
-    extern __shared__ double sh_d[];
-    const int l = A.l;
-    double *arow = sh_d;                  // centred row window (l)
-    const int k = A.krows[blockIdx.y];
-    const int64_t kr = (int64_t)k * A.R;
-    const int64_t a = (k == 0) ? 0 : kr - 1;
-    const double mua = A.mu[a];
-    for (int t = threadIdx.x; t < l; t += blockDim.x) arow[t] = A.x[a + t] - mua;
-    __syncthreads();
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= A.spitch) return;
-    int64_t ra, c;
-    if (k == 0) { ra = 0; c = j; }
-    else if (j == 0) { ra = kr; c = 0; }
-    else { ra = kr - 1; c = j - 1; }
-    double s = 0.0;
-    if (c < A.nl && ra < A.nl) {
-        const double muc = A.mu[c];
-        if (ra == a) {
-            for (int t = 0; t < l; ++t) s = fma(arow[t], A.x[c + t] - muc, s);
-        } else {
-            const double mur = A.mu[ra];
-            for (int t = 0; t < l; ++t) s = fma(A.x[ra + t] - mur, A.x[c + t] - muc, s);
-        }
-    }
-    A.seed[(int64_t)k * A.spitch + j] = s;
-}
-
-// FP32 seeds: the row window is centred in FP64 and rounded; the column
-// windows are shifted by one constant per block of columns (close to their
-// means) and rounded; the dot product runs in FP32 and the shift is removed
-// exactly to first order with the FP32 sum of the rounded row window.
-template <>
-__global__ void k_seed<float>(SeedArgs<float> A)
-{
-    if (A.nbands && *A.nbands == 0) return;
-    extern __shared__ float sh_f[];
-    const int l = A.l;
-    const int B = blockDim.x;
-    float *arow = sh_f;                   // l
-    float *ycol = sh_f + l;               // B + l
-    __shared__ float s_asum;
-    const int k = A.krows[blockIdx.y];
-    const int64_t kr = (int64_t)k * A.R;
-    const int64_t a = (k == 0) ? 0 : kr - 1;
-    const int64_t jb = (int64_t)blockIdx.x * B;
-    // first column window of this block and its shift
-    const int64_t cb = (k == 0) ? jb : (jb > 0 ? jb - 1 : 0);
-    const int64_t cshift = cb < A.nl ? cb : A.nl - 1;
-    const double shift = A.mu[cshift];
-    const double mua = A.mu[a];
-    for (int t = threadIdx.x; t < l; t += B) arow[t] = (float)(A.x[a + t] - mua);
-    for (int u = threadIdx.x; u < B + l; u += B) {
-        const int64_t idx = cb + u;
-        ycol[u] = idx < A.nl + l - 1 ? (float)(A.x[idx] - shift) : 0.0f;
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        float s = 0.0f;
-        for (int t = threadIdx.x; t < l; t += 32) s += arow[t];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (threadIdx.x == 0) s_asum = s;
-    }
-    __syncthreads();
-    const int64_t j = jb + threadIdx.x;
-    if (j >= A.spitch) return;
-    int64_t ra, c;
-    if (k == 0) { ra = 0; c = j; }
-    else if (j == 0) { ra = kr; c = 0; }
-    else { ra = kr - 1; c = j - 1; }
-    float out = 0.0f;
-    if (c < A.nl && ra < A.nl) {
-        if (ra == a) {
-            const float *y = ycol + (c - cb);
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-            int t = 0;
-            for (; t + 3 < l; t += 4) {
-                s0 = fmaf(arow[t], y[t], s0);
-                s1 = fmaf(arow[t + 1], y[t + 1], s1);
-                s2 = fmaf(arow[t + 2], y[t + 2], s2);
-                s3 = fmaf(arow[t + 3], y[t + 3], s3);
-            }
-            for (; t < l; ++t) s0 = fmaf(arow[t], y[t], s0);
-            const double corr = (double)s_asum * (A.mu[c] - shift);
-            out = (float)(((double)s0 + (double)s1) + ((double)s2 + (double)s3) - corr);
-        } else {
-            // the single (kR, 0) entry: direct FP64
-            const double mur = A.mu[ra], muc = A.mu[c];
-            double s = 0.0;
-            for (int t = 0; t < l; ++t) s = fma(A.x[ra + t] - mur, A.x[c + t] - muc, s);
-            out = (float)s;
-        }
-    }
-    A.seed[(int64_t)k * A.spitch + j] = out;
-}
-
 template <typename T>
 void launch_seed(const SeedArgs<T> &a, cudaStream_t s)
 {
@@ -147,8 +47,6 @@ void launch_seed(const SeedArgs<T> &a, cudaStream_t s)
     size_t sm = sizeof(T) == 8 ? sizeof(double) * a.l : sizeof(float) * (2 * a.l + B);
     k_seed<T><<<grid, B, sm, s>>>(a);
 }
-template void launch_seed<float>(const SeedArgs<float> &, cudaStream_t);
-template void launch_seed<double>(const SeedArgs<double> &, cudaStream_t);
 
 // ------------------------------------------------------------- band kernel
 
@@ -234,6 +132,7 @@ __device__ __forceinline__ bool any_positive2(const double (&C)[RPL], double inv
 }
 
 enum { MODE_TOPP = 0, MODE_BINS = 1, MODE_SYM = 2 };
+constexpr bool BAND_PAIR = true;   // two columns per hit test in the common case
 
 // One chunk of CH columns for the lane's RPL rows.
 //  MODE_TOPP: every column; row keys against the row thresholds.
@@ -288,7 +187,9 @@ __device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *c
                 hit = any_positive2(C, cd.inv, th, invr, cd.pad);
             }
         }
-        if (hit) {
+        // warp-uniform branch: the common no-hit path costs one vote and
+        // no reconvergence bookkeeping; lanes without a hit idle inside
+        if (__any_sync(0xffffffffu, hit) && hit) {
             const int32_t j = (int32_t)(cs + c);
 #pragma unroll
             for (int a = 0; a < RPL; ++a) {
@@ -315,6 +216,68 @@ __device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *c
                     }
                 }
             }
+        }
+    }
+}
+
+// The common case of the full-rows form (MODE_TOPP away from the exclusion
+// zone) two columns at a time: both columns' co-moments are formed first and
+// one warp vote covers both threshold tests, which halves the branches and
+// gives the scheduler two columns of independent arithmetic per block.
+// Column c's co-moments stay in C0 until its hits are handled; a hit in
+// column c may raise th before column c+1 is handled, which the per-row test
+// inside the insert re-checks.
+template <typename T, int RPL>
+__device__ __forceinline__ void topp_hits(const BandArgs<T> &A, const T (&Cc)[RPL], T inv, int32_t j, int64_t rbase,
+                                          int rl0, T (&th)[RPL], T *lkey, int32_t *lj, int32_t *lcnt,
+                                          unsigned &ninsert)
+{
+#pragma unroll
+    for (int a = 0; a < RPL; ++a) {
+        const T key = Cc[a] * inv;
+        if (key > th[a] && nontrivial(rbase + a, j, A.E)) {
+            const int rl = rl0 + a;
+            int32_t cnt = lcnt[rl];
+            topp_insert<T>(lkey + rl * A.p, lj + rl * A.p, cnt, A.p, key, j, th[a]);
+            lcnt[rl] = cnt;
+            ++ninsert;
+        }
+    }
+}
+
+template <typename T, int RPL, int NW>
+__device__ __forceinline__ void band_chunk_pair(const BandArgs<T> &A, const Col<T> *cbuf, T tp, T *bout, int lane,
+                                                int w, int64_t cs, int64_t rbase, int rl0, T (&C)[RPL],
+                                                const T (&dfr)[RPL], const T (&dgr)[RPL], T (&th)[RPL], T *lkey,
+                                                int32_t *lj, int32_t *lcnt, unsigned &ninsert)
+{
+    const bool send = w < NW - 1 && lane == 31;
+#pragma unroll
+    for (int c = 0; c < CH; c += 2) {
+        const Col<T> cd0 = cbuf[c];
+        const Col<T> cd1 = cbuf[c + 1];
+        T C0[RPL];
+        T v = __shfl_up_sync(0xffffffffu, C[RPL - 1], 1);
+        T vt = __shfl_sync(0xffffffffu, tp, c);
+        if (lane == 0) v = vt;
+#pragma unroll
+        for (int a = RPL - 1; a >= 1; --a) C0[a] = fma(dfr[a], cd0.dg, fma(cd0.df, dgr[a], C[a - 1]));
+        C0[0] = fma(dfr[0], cd0.dg, fma(cd0.df, dgr[0], v));
+        v = __shfl_up_sync(0xffffffffu, C0[RPL - 1], 1);
+        vt = __shfl_sync(0xffffffffu, tp, c + 1);
+        if (lane == 0) v = vt;
+#pragma unroll
+        for (int a = RPL - 1; a >= 1; --a) C[a] = fma(dfr[a], cd1.dg, fma(cd1.df, dgr[a], C0[a - 1]));
+        C[0] = fma(dfr[0], cd1.dg, fma(cd1.df, dgr[0], v));
+        if (send) {
+            bout[c] = C0[RPL - 1];
+            bout[c + 1] = C[RPL - 1];
+        }
+        const bool h0 = any_positive(C0, cd0.inv, th);
+        const bool h1 = any_positive(C, cd1.inv, th);
+        if (__any_sync(0xffffffffu, h0 || h1)) {
+            if (h0) topp_hits<T, RPL>(A, C0, cd0.inv, (int32_t)(cs + c), rbase, rl0, th, lkey, lj, lcnt, ninsert);
+            if (h1) topp_hits<T, RPL>(A, C, cd1.inv, (int32_t)(cs + c + 1), rbase, rl0, th, lkey, lj, lcnt, ninsert);
         }
     }
 }
@@ -357,8 +320,12 @@ __device__ __forceinline__ void mbar_wait(uint64_t *b, unsigned parity, int *err
     atomicExch(err, 1);
 }
 
+// FP32 with up to four rows per lane fits three CTAs per SM (80 registers);
+// otherwise two.
+template <typename T, int RPL> constexpr int band_min_blocks() { return (sizeof(T) == 4 && RPL <= 4) ? 3 : 2; }
+
 template <typename T, int RPL, int NW, int MODE>
-__global__ void __launch_bounds__(NW * 32, 2) k_band(const BandArgs<T> A)
+__global__ void __launch_bounds__(NW * 32, band_min_blocks<T, RPL>()) k_band(const BandArgs<T> A)
 {
     constexpr bool BINS = MODE == MODE_BINS;
     constexpr bool SYM = MODE == MODE_SYM;
@@ -493,6 +460,9 @@ __global__ void __launch_bounds__(NW * 32, 2) k_band(const BandArgs<T> A)
             if (diag)
                 band_chunk<T, RPL, NW, MODE, true>(A, cbuf, tp, bout, lane, w, cs, rbase, rl0, C, dfr, dgr, th,
                                                    invr, runmax, lkey, lj, lcnt, ninsert);
+            else if (MODE == MODE_TOPP && BAND_PAIR)
+                band_chunk_pair<T, RPL, NW>(A, cbuf, tp, bout, lane, w, cs, rbase, rl0, C, dfr, dgr, th, lkey, lj,
+                                            lcnt, ninsert);
             else
                 band_chunk<T, RPL, NW, MODE, false>(A, cbuf, tp, bout, lane, w, cs, rbase, rl0, C, dfr, dgr, th,
                                                     invr, runmax, lkey, lj, lcnt, ninsert);
@@ -571,7 +541,6 @@ template <typename T>
 static const void *band_fn(int mode, int rpl)
 {
     switch (rpl) {
-    case 8: return band_fn_rpl<T, 8>(mode);
     case 4: return band_fn_rpl<T, 4>(mode);
     case 2: return band_fn_rpl<T, 2>(mode);
     default: return band_fn_rpl<T, 1>(mode);
@@ -617,11 +586,5 @@ void launch_band(const BandArgs<T> &a, bool bins_mode, int grid, cudaStream_t s)
     if (a.allow_sym) launch_mode<T>(a, MODE_SYM, false, grid, s);
 }
 
-template void launch_band<float>(const BandArgs<float> &, bool, int, cudaStream_t);
-template void launch_band<double>(const BandArgs<double> &, bool, int, cudaStream_t);
-template int band_occupancy<float>(bool, int, int);
-template int band_occupancy<double>(bool, int, int);
-template size_t band_smem<float>(bool, int, int);
-template size_t band_smem<double>(bool, int, int);
 
 }  // namespace mad

@@ -14,7 +14,7 @@ void launch_coldata(const double *x, int64_t nl, int64_t npad, int l, const doub
                     const int32_t *run, Col<T> *col, cudaStream_t s);
 __global__ void k_widen_f32(const float *in, int64_t n, double *out);
 
-// ----------------------------------------------------------------- k_band.cu
+// ------------------------------------------- k_band.cuh (k_band_f32.cu, k_band_f64.cu)
 // Seed rows of the diagonal recurrence. Seed row k (row kS, S the seed
 // spacing) holds, for every column j, the value that precedes cell (kS, j)
 // on its diagonal:
@@ -51,7 +51,7 @@ template <typename T> struct BandArgs {
     int l;
     int64_t E;
     int rpl;                // rows per lane (band height R = 32 * rpl * BAND_NW)
-    int64_t sp;             // seed-row spacing (R / 2): seed row k sits at row k * sp
+    int64_t sp;             // seed-row spacing (divides R): seed row k sits at row k * sp
     int64_t group_w;        // columns per work unit (multiple of sp)
     int ngroups;
     int p;

@@ -21,7 +21,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/mad.h"
+#include "mad.h"
 #include "kernels.cuh"
 
 using namespace mad;
@@ -150,7 +150,7 @@ struct Precision<double> {
 template <>
 struct Precision<float> {
     // FP32 recurrence over at most one band from FP32 seeds: ~1e-6 observed
-    // on smooth data (epsilon_32 * sqrt(R) ~ 2.7e-6 for R = 2048).
+    // on smooth data (epsilon_32 * sqrt(R) ~ 1.9e-6 for R = 1024).
     static constexpr double dq0 = 3e-6, rel_tol = 0.0, abs_coef = 1e-4;
 };
 
@@ -182,7 +182,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     const int rpl = band_rpl<T>(p);
     const int R = 32 * rpl * BAND_NW;
     const int nbins = band_nbins(p);
-    const int SP = R / 2;                       // seed-row spacing
+    const int SP = R < 1024 ? R : 1024;         // seed-row spacing (every band start)
     const int64_t K = (n0 + SP - 1) / SP;       // seed rows
     const int64_t KB = (n0 + R - 1) / R;        // bands
     const int64_t npad = round_up(n0, R) + R + CH;
@@ -304,7 +304,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
 
     int cur = 0;
     // the symmetric band form (upper triangle, both sides of each cell)
-    const int use_sym = o.band_form == 0 ? 1 : 0;
+    const int use_sym = o.band_form == 1 ? 1 : 0;
     s.stats.assign(nL, mad_length_stats{});
     std::vector<unsigned long long> host_launch(nL, 0);
     // CUDA events around every band-kernel launch (device time of the

@@ -21,15 +21,18 @@ constexpr int KMAX = 64;            // largest discord-table rank count
 // Geometry of the diagonal band kernel: BAND_NW warps per CTA, RPL rows per
 // lane, so a band holds R = 32 * RPL * BAND_NW consecutive rows; R is also
 // the re-seed period of every diagonal (each diagonal restarts from a direct
-// dot product at the top or left edge of every R x R tile). RPL is chosen per
-// precision and p so that the per-row top-p lists fit in shared memory.
+// dot product at the top or left edge of every work unit). RPL is at most 4:
+// four rows per lane keep the FP32 kernel within 80 registers, so three CTAs
+// (24 warps) share an SM, which hides the recurrence's latency better than
+// eight rows per lane at two CTAs. Smaller RPL when the per-row top-p lists
+// would not fit in shared memory.
 constexpr int BAND_NW = 8;
 __host__ __device__ __forceinline__ int band_nbins(int p) { return 2 * p; }
 template <typename T> inline int band_rpl(int p)
 {
     // shared bytes per row for the top-p list: p * (sizeof(T) + 4) + 4
     const int budget = 96 * 1024;
-    const int max_rpl = sizeof(T) == 4 ? 8 : 4;
+    const int max_rpl = 4;
     for (int rpl = max_rpl; rpl > 1; rpl /= 2)
         if (32 * rpl * BAND_NW * (p * (int)(sizeof(T) + 4) + 4) <= budget) return rpl;
     return 1;

@@ -17,7 +17,7 @@
 #include <string>
 
 #include "kernels.cuh"
-#include "../../include/mad.h"
+#include "mad.h"
 
 namespace mad {
 

@@ -1,6 +1,6 @@
 """CUDA path vs the CPU oracle, element by element, through the C ABI.
 
-Sizes span several R x R tiles (R = 1024 rows in FP64, 2048 in FP32) and a
+Sizes span several R x R tiles (R = 1024 rows) and a
 ragged last band; the rw4096 case is the small configuration of the
 benchmark suite in full."""
 import math
@@ -43,7 +43,7 @@ def test_ar2_mth_neighbours_half_zone(prec):
     compare_all(x, 30, 36, 6, prec, m_max=3, k_max=4, excl=(1, 2))
 
 
-@pytest.mark.parametrize("band_form", [0, 1], ids=["auto", "full_rows"])
+@pytest.mark.parametrize("band_form", [0, 1], ids=["full_rows", "symmetric"])
 @pytest.mark.parametrize("prec", PRECS)
 def test_ecg_pruned_regime(prec, band_form):
     x = workloads.ecg_like(4500, 103, period=60.0)
@@ -55,7 +55,7 @@ def test_ecg_pruned_regime(prec, band_form):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_random_walk_full_rows_form(prec):
+def test_random_walk_symmetric_form(prec):
     x = workloads.random_walk(5000, 101)
     compare_all(x, 40, 48, 5, prec, band_form=1)
 
@@ -72,7 +72,7 @@ def test_flat_segments(prec):
 @pytest.mark.parametrize("prec", PRECS)
 def test_ragged_band_edges(prec):
     # n_lmin = R + 1 : the last band holds one row
-    R = 1024 if prec == mad.MAD_FP64 else 2048
+    R = 1024
     x = workloads.random_walk(R + 16, 105)
     compare_all(x, 16, 20, 3, prec, k_max=2)
 
