@@ -39,15 +39,6 @@ namespace mad {
 template <typename T>
 __global__ void k_seed(SeedArgs<T> A);
 
-template <typename T>
-void launch_seed(const SeedArgs<T> &a, cudaStream_t s)
-{
-    const int B = 256;
-    dim3 grid((unsigned)((a.spitch + B - 1) / B), (unsigned)a.nk);
-    size_t sm = sizeof(T) == 8 ? sizeof(double) * a.l : sizeof(float) * (2 * a.l + B);
-    k_seed<T><<<grid, B, sm, s>>>(a);
-}
-
 // ------------------------------------------------------------- band kernel
 
 template <typename T> __device__ __forceinline__ T neg_inf();

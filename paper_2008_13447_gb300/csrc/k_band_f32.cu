@@ -5,74 +5,146 @@
 namespace mad {
 
 // FP32 seeds: the row window is centred in FP64 and rounded; the column
-// windows are shifted by one constant per block of columns (close to their
-// means) and rounded; the dot product runs in FP32 and the shift is removed
-// exactly to first order with the FP32 sum of the rounded row window.
-template <>
-__global__ void k_seed<float>(SeedArgs<float> A)
+// windows are shifted by one constant per tile of columns (close to their
+// means) and rounded; the dot product runs in FP32 (four partial sums, by
+// the index t mod 4, added in FP64) and the shift is removed exactly to first
+// order with the FP32 sum of the rounded row window.
+//
+// Seed row k holds, for j >= 1, C(a_k, j - 1) with a_k = kS - 1 (the
+// predecessor of cell (kS, j) on its diagonal), and C(kS, 0) at j = 0; row 0
+// holds C(0, j). Register blocking: a block takes SEED_ROWS seed rows and
+// SEED_THREADS * SEED_COLS columns; each thread keeps SEED_ROWS x SEED_COLS
+// dot products, reading the rows' values at one t as one float4 (layout
+// [t][row]) and its columns' shifted values as float4 runs, so shared-memory
+// reads stay a small fraction of the FMAs.
+constexpr int SEED_ROWS = 4;
+constexpr int SEED_COLS = 4;
+constexpr int SEED_THREADS = 128;
+constexpr int SEED_TILE = SEED_THREADS * SEED_COLS;
+
+__host__ __device__ inline int seed_l4(int l) { return (l + 3) & ~3; }
+
+__global__ void __launch_bounds__(SEED_THREADS) k_seed_f32(SeedArgs<float> A)
 {
     if (A.nbands && *A.nbands == 0) return;
-    extern __shared__ float sh_f[];
+    extern __shared__ __align__(16) float sh_f[];
     const int l = A.l;
-    const int B = blockDim.x;
-    float *arow = sh_f;                   // l
-    float *ycol = sh_f + l;               // B + l
-    __shared__ float s_asum;
-    const int k = A.krows[blockIdx.y];
-    const int64_t kr = (int64_t)k * A.R;
-    const int64_t a = (k == 0) ? 0 : kr - 1;
-    const int64_t jb = (int64_t)blockIdx.x * B;
-    // first column window of this block and its shift
-    const int64_t cb = (k == 0) ? jb : (jb > 0 ? jb - 1 : 0);
+    const int l4 = seed_l4(l);
+    float4 *arow = reinterpret_cast<float4 *>(sh_f);      // [l4] (one value per seed row)
+    float *ycol = sh_f + 4 * l4;                          // [SEED_TILE + l4 + 4]
+    __shared__ float s_asum[SEED_ROWS];
+    __shared__ int64_t s_a[SEED_ROWS];
+    __shared__ int s_k[SEED_ROWS];
+    const int64_t cb = (int64_t)blockIdx.x * SEED_TILE;
+    if (threadIdx.x < SEED_ROWS) {
+        const int q = blockIdx.y * SEED_ROWS + threadIdx.x;
+        const int k = q < A.nk ? A.krows[q] : -1;
+        int64_t a = k < 0 ? -1 : (k == 0 ? 0 : (int64_t)k * A.R - 1);
+        if (a >= A.nl) a = -1;
+        s_k[threadIdx.x] = k;
+        s_a[threadIdx.x] = a;
+    }
+    __syncthreads();
     const int64_t cshift = cb < A.nl ? cb : A.nl - 1;
     const double shift = A.mu[cshift];
-    const double mua = A.mu[a];
-    for (int t = threadIdx.x; t < l; t += B) arow[t] = (float)(A.x[a + t] - mua);
-    for (int u = threadIdx.x; u < B + l; u += B) {
+    for (int t = threadIdx.x; t < l4; t += SEED_THREADS) {
+        float v[SEED_ROWS];
+#pragma unroll
+        for (int r = 0; r < SEED_ROWS; ++r) {
+            const int64_t a = s_a[r];
+            v[r] = (a >= 0 && t < l) ? (float)(A.x[a + t] - A.mu[a]) : 0.0f;
+        }
+        arow[t] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    for (int u = threadIdx.x; u < SEED_TILE + l4 + 4; u += SEED_THREADS) {
         const int64_t idx = cb + u;
         ycol[u] = idx < A.nl + l - 1 ? (float)(A.x[idx] - shift) : 0.0f;
     }
     __syncthreads();
     if (threadIdx.x < 32) {
-        float s = 0.0f;
-        for (int t = threadIdx.x; t < l; t += 32) s += arow[t];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (threadIdx.x == 0) s_asum = s;
-    }
-    __syncthreads();
-    const int64_t j = jb + threadIdx.x;
-    if (j >= A.spitch) return;
-    int64_t ra, c;
-    if (k == 0) { ra = 0; c = j; }
-    else if (j == 0) { ra = kr; c = 0; }
-    else { ra = kr - 1; c = j - 1; }
-    float out = 0.0f;
-    if (c < A.nl && ra < A.nl) {
-        if (ra == a) {
-            const float *y = ycol + (c - cb);
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-            int t = 0;
-            for (; t + 3 < l; t += 4) {
-                s0 = fmaf(arow[t], y[t], s0);
-                s1 = fmaf(arow[t + 1], y[t + 1], s1);
-                s2 = fmaf(arow[t + 2], y[t + 2], s2);
-                s3 = fmaf(arow[t + 3], y[t + 3], s3);
-            }
-            for (; t < l; ++t) s0 = fmaf(arow[t], y[t], s0);
-            const double corr = (double)s_asum * (A.mu[c] - shift);
-            out = (float)(((double)s0 + (double)s1) + ((double)s2 + (double)s3) - corr);
-        } else {
-            // the single (kR, 0) entry: direct FP64
-            const double mur = A.mu[ra], muc = A.mu[c];
-            double s = 0.0;
-            for (int t = 0; t < l; ++t) s = fma(A.x[ra + t] - mur, A.x[c + t] - muc, s);
-            out = (float)s;
+        float sr[SEED_ROWS] = {0.f, 0.f, 0.f, 0.f};
+        for (int t = threadIdx.x; t < l; t += 32) {
+            const float4 v = arow[t];
+            sr[0] += v.x;
+            sr[1] += v.y;
+            sr[2] += v.z;
+            sr[3] += v.w;
+        }
+#pragma unroll
+        for (int r = 0; r < SEED_ROWS; ++r) {
+            for (int o = 16; o > 0; o >>= 1) sr[r] += __shfl_xor_sync(0xffffffffu, sr[r], o);
+            if (threadIdx.x == 0) s_asum[r] = sr[r];
         }
     }
-    A.seed[(int64_t)k * A.spitch + j] = out;
+    __syncthreads();
+
+    const int c0 = threadIdx.x * SEED_COLS;
+    float acc[4][SEED_ROWS][SEED_COLS];
+#pragma unroll
+    for (int h = 0; h < 4; ++h)
+#pragma unroll
+        for (int r = 0; r < SEED_ROWS; ++r)
+#pragma unroll
+            for (int c = 0; c < SEED_COLS; ++c) acc[h][r][c] = 0.0f;
+    for (int t0 = 0; t0 < l4; t0 += 4) {
+        const float4 y0 = *reinterpret_cast<const float4 *>(ycol + c0 + t0);
+        const float4 y1 = *reinterpret_cast<const float4 *>(ycol + c0 + t0 + 4);
+        const float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const float4 av = arow[t0 + h];
+            const float a4[SEED_ROWS] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+            for (int r = 0; r < SEED_ROWS; ++r)
+#pragma unroll
+                for (int c = 0; c < SEED_COLS; ++c) acc[h][r][c] = fmaf(a4[r], yv[c + h], acc[h][r][c]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < SEED_ROWS; ++r) {
+        const int k = s_k[r];
+        if (k < 0) continue;
+        const int64_t a = s_a[r];
+        const int64_t o = k == 0 ? 0 : 1;   // output index j = c + o
+#pragma unroll
+        for (int c = 0; c < SEED_COLS; ++c) {
+            const int64_t col = cb + c0 + c;
+            const int64_t j = col + o;
+            if (j >= A.spitch) continue;
+            float out = 0.0f;
+            if (a >= 0 && col < A.nl) {
+                const double corr = (double)s_asum[r] * (A.mu[col] - shift);
+                out = (float)(((double)acc[0][r][c] + (double)acc[1][r][c]) +
+                              ((double)acc[2][r][c] + (double)acc[3][r][c]) - corr);
+            }
+            A.seed[(int64_t)k * A.spitch + j] = out;
+        }
+    }
+    // the single (kS, 0) entry of rows k >= 1: direct FP64
+    if (blockIdx.x == 0 && threadIdx.x < SEED_ROWS) {
+        const int k = s_k[threadIdx.x];
+        if (k >= 1) {
+            const int64_t ra = (int64_t)k * A.R;
+            double sum = 0.0;
+            if (ra < A.nl) {
+                const double mur = A.mu[ra], muc = A.mu[0];
+                for (int t = 0; t < l; ++t) sum = fma(A.x[ra + t] - mur, A.x[t] - muc, sum);
+            }
+            A.seed[(int64_t)k * A.spitch] = (float)sum;
+        }
+    }
 }
 
-template void launch_seed<float>(const SeedArgs<float> &, cudaStream_t);
+template <>
+void launch_seed<float>(const SeedArgs<float> &a, cudaStream_t s)
+{
+    dim3 grid((unsigned)((a.spitch + SEED_TILE - 1) / SEED_TILE), (unsigned)((a.nk + SEED_ROWS - 1) / SEED_ROWS));
+    const int l4 = seed_l4(a.l);
+    const size_t sm = sizeof(float) * (4 * (size_t)l4 + SEED_TILE + l4 + 4);
+    cudaFuncSetAttribute(k_seed_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_seed_f32<<<grid, SEED_THREADS, sm, s>>>(a);
+}
+
 template void launch_band<float>(const BandArgs<float> &, bool, int, cudaStream_t);
 template int band_occupancy<float>(bool, int, int);
 template size_t band_smem<float>(bool, int, int);

@@ -37,7 +37,15 @@ __global__ void k_seed<double>(SeedArgs<double> A)
     A.seed[(int64_t)k * A.spitch + j] = s;
 }
 
-template void launch_seed<double>(const SeedArgs<double> &, cudaStream_t);
+template <>
+void launch_seed<double>(const SeedArgs<double> &a, cudaStream_t s)
+{
+    const int B = 256;
+    dim3 grid((unsigned)((a.spitch + B - 1) / B), (unsigned)a.nk);
+    const size_t sm = sizeof(double) * a.l;
+    cudaFuncSetAttribute(k_seed<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_seed<double><<<grid, B, sm, s>>>(a);
+}
 template void launch_band<double>(const BandArgs<double> &, bool, int, cudaStream_t);
 template int band_occupancy<double>(bool, int, int);
 template size_t band_smem<double>(bool, int, int);

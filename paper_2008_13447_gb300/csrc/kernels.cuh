@@ -38,6 +38,8 @@ template <typename T> struct SeedArgs {
     const int32_t *nbands;  // nothing to do when the device count is 0
 };
 template <typename T> void launch_seed(const SeedArgs<T> &a, cudaStream_t s);
+template <> void launch_seed<float>(const SeedArgs<float> &a, cudaStream_t s);
+template <> void launch_seed<double>(const SeedArgs<double> &a, cudaStream_t s);
 
 template <typename T> struct BandArgs {
     const Col<T> *col;      // per-window recurrence data, rows and columns
