@@ -236,6 +236,17 @@ __device__ __forceinline__ void topp_hits(const BandArgs<T> &A, const T (&Cc)[RP
     }
 }
 
+// Two consecutive boundary values in one 8- or 16-byte store (c is even and
+// the ring slots are 16-byte aligned).
+__device__ __forceinline__ void store_pair(float *p, float a, float b)
+{
+    *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+}
+__device__ __forceinline__ void store_pair(double *p, double a, double b)
+{
+    *reinterpret_cast<double2 *>(p) = make_double2(a, b);
+}
+
 template <typename T, int RPL, int NW>
 __device__ __forceinline__ void band_chunk_pair(const BandArgs<T> &A, const Col<T> *cbuf, T tp, T *bout, int lane,
                                                 int w, int64_t cs, int64_t rbase, int rl0, T (&C)[RPL],
@@ -260,10 +271,7 @@ __device__ __forceinline__ void band_chunk_pair(const BandArgs<T> &A, const Col<
 #pragma unroll
         for (int a = RPL - 1; a >= 1; --a) C[a] = fma(dfr[a], cd1.dg, fma(cd1.df, dgr[a], C0[a - 1]));
         C[0] = fma(dfr[0], cd1.dg, fma(cd1.df, dgr[0], v));
-        if (send) {
-            bout[c] = C0[RPL - 1];
-            bout[c + 1] = C[RPL - 1];
-        }
+        if (send) store_pair(bout + c, C0[RPL - 1], C[RPL - 1]);
         const bool h0 = any_positive(C0, cd0.inv, th);
         const bool h1 = any_positive(C, cd1.inv, th);
         if (__any_sync(0xffffffffu, h0 || h1)) {
