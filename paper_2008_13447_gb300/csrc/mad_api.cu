@@ -208,8 +208,11 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     int32_t *bands = dalloc<int32_t>(ctx, s, KB);
     int32_t *counters = dalloc<int32_t>(ctx, s, 4);   // nbands, unit counter, overflow
     int32_t *krows = dalloc<int32_t>(ctx, s, K);
-    double *nnd = dalloc<double>(ctx, s, (size_t)m_max * n0);
-    int32_t *nnj = dalloc<int32_t>(ctx, s, (size_t)m_max * n0);
+    // m-th best matches of the current length, double-buffered: the discord
+    // tables of length l read one buffer on a side stream while length l+1
+    // writes the other
+    double *nndbuf[2] = {dalloc<double>(ctx, s, (size_t)m_max * n0), dalloc<double>(ctx, s, (size_t)m_max * n0)};
+    int32_t *nnjbuf[2] = {dalloc<int32_t>(ctx, s, (size_t)m_max * n0), dalloc<int32_t>(ctx, s, (size_t)m_max * n0)};
     const int64_t nblk = (n0 + 255) / 256;
     double *bval = dalloc<double>(ctx, s, (size_t)m_max * nblk);
     int32_t *bidx = dalloc<int32_t>(ctx, s, (size_t)m_max * nblk);
@@ -325,10 +328,36 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     // launches issued for the current length, counted at each launch site
     unsigned long long nlaunch = 1 /* k_flat_runs */ + 1 /* k_stats_init */ + 1 /* fill thr */;
 
+    // Side streams: the seed rows of length l need only the window means, so
+    // they run beside the extension, the split and the column data; the
+    // discord tables of length l need only that length's m-th best matches,
+    // so they run while the next length proceeds. Events order them against
+    // the context's stream.
+    struct Side {
+        cudaStream_t seed = nullptr, disc = nullptr;
+        cudaEvent_t ev[8] = {};
+        ~Side()
+        {
+            if (seed) cudaStreamDestroy(seed);
+            if (disc) cudaStreamDestroy(disc);
+            for (cudaEvent_t e : ev)
+                if (e) cudaEventDestroy(e);
+        }
+    } side;
+    CK(cudaStreamCreateWithFlags(&side.seed, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&side.disc, cudaStreamNonBlocking));
+    for (cudaEvent_t &e : side.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaEvent_t ev_stats = side.ev[0], ev_seed = side.ev[1], ev_nnd = side.ev[2], ev_end = side.ev[3];
+    cudaEvent_t *ev_disc = side.ev + 4;   // [2], one per buffer
+
     for (int l = lmin; l <= lmax; ++l) {
         const int li = l - lmin;
         const int64_t nl = n - l + 1;
         const int64_t E = excl_zone(l, num, den);
+        double *nnd = nndbuf[li & 1];
+        int32_t *nnj = nnjbuf[li & 1];
+        // the discord tables of length l-2 have finished reading this buffer
+        if (li >= 2) CK(cudaStreamWaitEvent(st, ev_disc[li & 1], 0));
         LenOut lo{nnd, nnj, dstats + (size_t)li * NSTAT};
         if (l > lmin) {
             ++nlaunch;
@@ -340,6 +369,16 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         launch_kappa(m2[cur], run, nl, l, R, m2blk, kappa, kappa_max, st);
         nlaunch += 3;
         CK(cudaGetLastError());
+        // seed rows of this length (the previous band kernel, earlier on the
+        // context's stream, is done with the seed buffer)
+        CK(cudaEventRecord(ev_stats, st));
+        CK(cudaStreamWaitEvent(side.seed, ev_stats, 0));
+        {
+            SeedArgs<T> sa{s.x, mu[cur], nl, l, SP, krows, (int)K, spitch, seed, nullptr};
+            launch_seed<T>(sa, side.seed);
+            ++nlaunch;
+        }
+        CK(cudaEventRecord(ev_seed, side.seed));
 
         if (l == lmin) {
             // every row recomputed; flat rows apart
@@ -391,9 +430,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         sp.stat_direct = lo.stats + 9;
         launch_split(sp, st);
         ++nlaunch;
-        SeedArgs<T> sa{s.x, mu[cur], nl, l, SP, krows, (int)K, spitch, seed, nbands_d};
-        launch_seed<T>(sa, st);
-        ++nlaunch;
+        CK(cudaStreamWaitEvent(st, ev_seed, 0));
         ba.nl = nl;
         ba.l = l;
         ba.E = E;
@@ -475,18 +512,26 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         }
         FlatArgs fa{n0, nl, l, E, p, m_max, run, rs, vm, lo, wait_err + 0 /* same error word */};
         launch_flat_rows(fa, st);
-        launch_discords_length(nnd, nnj, n0, nl, l, E, k_max, m_max, bval, bidx, tab, st);
+        CK(cudaEventRecord(ev_nnd, st));
+        CK(cudaStreamWaitEvent(side.disc, ev_nnd, 0));
+        launch_discords_length(nnd, nnj, n0, nl, l, E, k_max, m_max, bval, bidx, tab, side.disc);
         nlaunch += 3;
         if (o.keep_profiles) {
             CK(cudaMemcpyAsync(s.keep_nnd + (size_t)li * m_max * n0, nnd, (size_t)m_max * n0 * sizeof(double),
-                               cudaMemcpyDeviceToDevice, st));
+                               cudaMemcpyDeviceToDevice, side.disc));
             CK(cudaMemcpyAsync(s.keep_nnj + (size_t)li * m_max * n0, nnj, (size_t)m_max * n0 * sizeof(int32_t),
-                               cudaMemcpyDeviceToDevice, st));
+                               cudaMemcpyDeviceToDevice, side.disc));
         }
+        CK(cudaEventRecord(ev_disc[li & 1], side.disc));
         CK(cudaGetLastError());
         host_launch[li] = nlaunch;
         nlaunch = 0;
     }
+    // the side streams' last work is done before the read-back
+    CK(cudaEventRecord(ev_end, side.disc));
+    CK(cudaStreamWaitEvent(st, ev_end, 0));
+    CK(cudaEventRecord(ev_end, side.seed));
+    CK(cudaStreamWaitEvent(st, ev_end, 0));
     int32_t herr = 0;
     CK(cudaMemcpyAsync(&herr, wait_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     std::vector<unsigned long long> hs((size_t)nL * NSTAT);
