@@ -6,9 +6,9 @@ namespace mad {
 
 // FP32 seeds: the row window is centred in FP64 and rounded; the column
 // windows are shifted by one constant per tile of columns (close to their
-// means) and rounded; the dot product runs in FP32 (four partial sums, by
-// the index t mod 4, added in FP64) and the shift is removed exactly to first
-// order with the FP32 sum of the rounded row window.
+// means) and rounded; the dot product runs in FP32 (two partial sums, by the
+// parity of t, added in FP64) and the shift is removed exactly to first order
+// with the FP32 sum of the rounded row window.
 //
 // Seed row k holds, for j >= 1, C(a_k, j - 1) with a_k = kS - 1 (the
 // predecessor of cell (kS, j) on its diagonal), and C(kS, 0) at j = 0; row 0
@@ -16,7 +16,9 @@ namespace mad {
 // SEED_THREADS * SEED_COLS columns; each thread keeps SEED_ROWS x SEED_COLS
 // dot products, reading the rows' values at one t as one float4 (layout
 // [t][row]) and its columns' shifted values as float4 runs, so shared-memory
-// reads stay a small fraction of the FMAs.
+// reads stay a small fraction of the FMAs; the next step's operands are
+// loaded before the current step's FMAs, and 88 registers let four blocks
+// share an SM.
 constexpr int SEED_ROWS = 4;
 constexpr int SEED_COLS = 4;
 constexpr int SEED_THREADS = 128;
@@ -24,7 +26,7 @@ constexpr int SEED_TILE = SEED_THREADS * SEED_COLS;
 
 __host__ __device__ inline int seed_l4(int l) { return (l + 3) & ~3; }
 
-__global__ void __launch_bounds__(SEED_THREADS) k_seed_f32(SeedArgs<float> A)
+__global__ void __launch_bounds__(SEED_THREADS, 4) k_seed_f32(SeedArgs<float> A)
 {
     if (A.nbands && *A.nbands == 0) return;
     extern __shared__ __align__(16) float sh_f[];
@@ -79,25 +81,33 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed_f32(SeedArgs<float> A)
     __syncthreads();
 
     const int c0 = threadIdx.x * SEED_COLS;
-    float acc[4][SEED_ROWS][SEED_COLS];
+    float acc[2][SEED_ROWS][SEED_COLS];
 #pragma unroll
-    for (int h = 0; h < 4; ++h)
+    for (int h = 0; h < 2; ++h)
 #pragma unroll
         for (int r = 0; r < SEED_ROWS; ++r)
 #pragma unroll
             for (int c = 0; c < SEED_COLS; ++c) acc[h][r][c] = 0.0f;
+    float4 y0n = *reinterpret_cast<const float4 *>(ycol + c0);
+    float4 y1n = *reinterpret_cast<const float4 *>(ycol + c0 + 4);
+    float4 an[4] = {arow[0], arow[1], arow[2], arow[3]};
     for (int t0 = 0; t0 < l4; t0 += 4) {
-        const float4 y0 = *reinterpret_cast<const float4 *>(ycol + c0 + t0);
-        const float4 y1 = *reinterpret_cast<const float4 *>(ycol + c0 + t0 + 4);
+        const float4 y0 = y0n, y1 = y1n;
+        const float4 ac[4] = {an[0], an[1], an[2], an[3]};
+        if (t0 + 4 < l4) {
+            y0n = *reinterpret_cast<const float4 *>(ycol + c0 + t0 + 4);
+            y1n = *reinterpret_cast<const float4 *>(ycol + c0 + t0 + 8);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) an[h] = arow[t0 + 4 + h];
+        }
         const float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
-            const float4 av = arow[t0 + h];
-            const float a4[SEED_ROWS] = {av.x, av.y, av.z, av.w};
+            const float a4[SEED_ROWS] = {ac[h].x, ac[h].y, ac[h].z, ac[h].w};
 #pragma unroll
             for (int r = 0; r < SEED_ROWS; ++r)
 #pragma unroll
-                for (int c = 0; c < SEED_COLS; ++c) acc[h][r][c] = fmaf(a4[r], yv[c + h], acc[h][r][c]);
+                for (int c = 0; c < SEED_COLS; ++c) acc[h & 1][r][c] = fmaf(a4[r], yv[c + h], acc[h & 1][r][c]);
         }
     }
 #pragma unroll
@@ -114,8 +124,7 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed_f32(SeedArgs<float> A)
             float out = 0.0f;
             if (a >= 0 && col < A.nl) {
                 const double corr = (double)s_asum[r] * (A.mu[col] - shift);
-                out = (float)(((double)acc[0][r][c] + (double)acc[1][r][c]) +
-                              ((double)acc[2][r][c] + (double)acc[3][r][c]) - corr);
+                out = (float)(((double)acc[0][r][c] + (double)acc[1][r][c]) - corr);
             }
             A.seed[(int64_t)k * A.spitch + j] = out;
         }

@@ -50,12 +50,56 @@ __device__ __forceinline__ void write_nn(const LenOut &o, int64_t n0, int64_t i,
 }
 
 
-// Exact FP64 centred co-moment of windows i and j at length l.
+// Exact FP64 centred co-moment of windows i and j at length l (four
+// partial sums, so consecutive products do not wait on each other).
 __device__ double comoment(const double *x, int64_t i, int64_t j, int l, double mui, double muj)
 {
-    double s = 0.0;
-    for (int t = 0; t < l; ++t) s = fma(x[i + t] - mui, x[j + t] - muj, s);
-    return s;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int t = 0;
+    for (; t + 3 < l; t += 4) {
+        s0 = fma(x[i + t] - mui, x[j + t] - muj, s0);
+        s1 = fma(x[i + t + 1] - mui, x[j + t + 1] - muj, s1);
+        s2 = fma(x[i + t + 2] - mui, x[j + t + 2] - muj, s2);
+        s3 = fma(x[i + t + 3] - mui, x[j + t + 3] - muj, s3);
+    }
+    for (; t < l; ++t) s0 = fma(x[i + t] - mui, x[j + t] - muj, s0);
+    return (s0 + s1) + (s2 + s3);
+}
+
+// The same co-moment from x split into FP32 pairs (x = xh + xl), in FP32
+// with error-free transformations: each centred value is formed as
+// (xh - muh) + (xl - mul) (relative error about 2u, u = 2^-24), each product
+// is split exactly into p + e by an FMA (TwoProd) and each partial sum into
+// s + e by TwoSum (Knuth), the errors accumulating separately. The result is
+// within about 4u sum_t |a_t b_t| <= 4u sqrt(M2_i M2_j) (Cauchy-Schwarz) of
+// the exact co-moment, i.e. its correlation within DQ_COMP.
+constexpr double DQ_COMP = 3e-7;
+
+__device__ double comoment_comp(const float *__restrict__ xh, const float *__restrict__ xl, int64_t i, int64_t j,
+                                int l, double mui, double muj)
+{
+    const float mih = (float)mui, mil = (float)(mui - (double)mih);
+    const float mjh = (float)muj, mjl = (float)(muj - (double)mjh);
+    float S = 0.0f, Er = 0.0f;
+    for (int t = 0; t < l; ++t) {
+        const float a = (xh[i + t] - mih) + (xl[i + t] - mil);
+        const float b = (xh[j + t] - mjh) + (xl[j + t] - mjl);
+        const float pr = a * b;
+        const float pe = fmaf(a, b, -pr);
+        const float sn = S + pr;
+        const float bv = sn - S;
+        const float se = (S - (sn - bv)) + (pr - bv);
+        S = sn;
+        Er += pe + se;
+    }
+    return (double)S + (double)Er;
+}
+
+// Correlation from the co-moment and the windows' 1 / sqrt(M2) (flat
+// partner: 0).
+__device__ __forceinline__ double corr_isd(double c, double isdi, double isdj, bool flat_j)
+{
+    return flat_j ? 0.0 : clamp_q(c * isdi * isdj);
 }
 
 // Error of d = sqrt(2 l (1 - q)) caused by an error dq of q (d^2 moves by
@@ -80,51 +124,121 @@ __device__ __forceinline__ double dq_row(const ErrModel &em, int64_t i)
     return em.dq0 * (double)em.kappa[i] * (double)(*em.kappa_max);
 }
 
-// A row's stored entries during one length: correlation q (estimated),
-// its error bound dq, partner j and storage slot e, kept sorted by
-// (q desc, j asc).
-struct Ent {
-    double q;
-    float dq;
-    int32_t j;
-    int32_t e;
+// A row's stored entries during one length, held in registers: PM is a
+// compile-time bound on p (8, 16 or 64) so that every loop over entries
+// unrolls with constant indices (for PM = 64 the loops stay rolled and the
+// arrays live in local memory). Entry e sits in index e (its storage slot);
+// j < 0 marks an empty one. Orders are taken by counting, not by moving
+// entries.
+template <int PM> struct RowEnts {
+    double q[PM];    // correlation (estimate)
+    float dq[PM];    // its error bound
+    int32_t j[PM];   // partner offset, -1 = empty
 };
 
-__device__ __forceinline__ void ins_ent(Ent *v, int n, Ent x)
+template <int PM, typename F>
+__device__ __forceinline__ void for_pm(F &&f)
 {
-    int t = n;
-    while (t > 0 && (v[t - 1].q < x.q || (v[t - 1].q == x.q && v[t - 1].j > x.j))) {
-        v[t] = v[t - 1];
-        --t;
+    if constexpr (PM <= 16) {
+#pragma unroll
+        for (int a = 0; a < PM; ++a) f(a);
+    } else {
+#pragma unroll 1
+        for (int a = 0; a < PM; ++a) f(a);
     }
-    v[t] = x;
 }
 
-// Re-evaluate in FP64 every entry among the first m (in correlation order)
-// whose distance error could exceed half the tolerance; repeat until the
-// first m are all accurate (re-evaluation can reorder entries).
-__device__ void refine_reported(const double *x, int64_t i, int l, double mui, double m2i, const double *mu,
-                                const double *m2, const ErrModel &em, RowState st, int64_t n0, Ent *v, int cnt, int m,
-                                unsigned long long *stat_dq)
+// (q desc, j asc): does (qa, ja) come before (qb, jb)?
+__device__ __forceinline__ bool q_before(double qa, int32_t ja, double qb, int32_t jb)
+{
+    return qa > qb || (qa == qb && ja < jb);
+}
+
+// Rank of every entry in (q desc, j asc) order (0 = best).
+template <int PM>
+__device__ __forceinline__ void corr_ranks(const RowEnts<PM> &r, int (&rk)[PM])
+{
+    for_pm<PM>([&](int a) {
+        int k = 0;
+        for_pm<PM>([&](int b) { k += (r.j[b] >= 0 && q_before(r.q[b], r.j[b], r.q[a], r.j[a])); });
+        rk[a] = k;
+    });
+}
+
+// Re-evaluate in FP64, one at a time, the best-ranked entry among the first
+// m (correlation order) whose distance error could exceed half the
+// tolerance, until none is left (a re-evaluation can reorder entries).
+// An entry is re-evaluated first by the compensated FP32 co-moment, which
+// it keeps (with error bound DQ_COMP) if that bound meets half the tolerance
+// (only with an absolute tolerance, i.e. the FP32 path), else in FP64.
+template <int PM>
+__device__ void refine_reported(const double *x, const float *xh, const float *xl, int64_t i, int l, double mui,
+                                double isdi, const double *mu, const double *isd, const ErrModel &em, RowState st,
+                                int64_t n0, RowEnts<PM> &r, int m, unsigned long long *stat_dq)
 {
     double dqmax = 0.0;
-    for (int pass = 0; pass <= cnt; ++pass) {
-        int hit = -1;
-        for (int a = 0; a < m && a < cnt; ++a)
-            if (needs_refine(em, dist_from_q(v[a].q, l), v[a].dq, l)) { hit = a; break; }
+    for (int pass = 0; pass <= PM; ++pass) {
+        int rk[PM];
+        corr_ranks(r, rk);
+        int hit = -1, hr = 1 << 30;
+        int32_t j = -1;
+        double qold = 0.0;
+        for_pm<PM>([&](int a) {
+            if (r.j[a] >= 0 && rk[a] < m && rk[a] < hr && needs_refine(em, dist_from_q(r.q[a], l), r.dq[a], l)) {
+                hit = a;
+                hr = rk[a];
+                j = r.j[a];
+                qold = r.q[a];
+            }
+        });
         if (hit < 0) break;
-        Ent t = v[hit];
-        const double c = comoment(x, i, t.j, l, mui, mu[t.j]);
-        const double q = clamp_q(c / sqrt(m2i * m2[t.j]));
-        dqmax = fmax(dqmax, fabs(q - t.q));
-        st.ent_c[(int64_t)t.e * n0 + i] = c;
-        st.ent_dq[(int64_t)t.e * n0 + i] = 0.0f;
-        t.q = q;
-        t.dq = 0.0f;
-        for (int a = hit; a + 1 < cnt; ++a) v[a] = v[a + 1];
-        ins_ent(v, cnt - 1, t);
+        double c = 0.0, q = 0.0;
+        float dqn = 0.0f;
+        bool done = false;
+        if (em.abs_coef > 0.0) {
+            c = comoment_comp(xh, xl, i, j, l, mui, mu[j]);
+            q = clamp_q(c * isdi * isd[j]);
+            dqn = (float)DQ_COMP;
+            done = !needs_refine(em, dist_from_q(q, l), DQ_COMP, l);
+        }
+        if (!done) {
+            c = comoment(x, i, j, l, mui, mu[j]);
+            q = clamp_q(c * isdi * isd[j]);
+            dqn = 0.0f;
+        }
+        dqmax = fmax(dqmax, fabs(q - qold));
+        st.ent_c[(int64_t)hit * n0 + i] = c;
+        st.ent_dq[(int64_t)hit * n0 + i] = dqn;
+        for_pm<PM>([&](int a) {
+            if (a == hit) {
+                r.q[a] = q;
+                r.dq[a] = dqn;
+            }
+        });
     }
     if (dqmax > 0.0 && stat_dq) atomicMax(stat_dq, (unsigned long long)__double_as_longlong(dqmax));
+}
+
+// The row's m-th best matches (first m entries in correlation order), +inf
+// past the last of its cnt entries, and VALMP from the best (Algorithm 2).
+template <int PM>
+__device__ void report_row(const LenOut &o, const Valmp &vm, int64_t n0, int64_t i, int l, const RowEnts<PM> &r,
+                           int cnt, int m)
+{
+    int rk[PM];
+    corr_ranks(r, rk);
+    for_pm<PM>([&](int a) {
+        if (r.j[a] >= 0 && rk[a] < m) {
+            const double d = dist_from_q(r.q[a], l);
+            o.nnd[(int64_t)rk[a] * n0 + i] = d;
+            o.nnj[(int64_t)rk[a] * n0 + i] = r.j[a];
+            if (rk[a] == 0) valmp_update(vm, i, d, r.j[a], l);
+        }
+    });
+    for (int t = cnt; t < m; ++t) {
+        o.nnd[(int64_t)t * n0 + i] = pinf();
+        o.nnj[(int64_t)t * n0 + i] = -1;
+    }
 }
 
 // ------------------------------------------------------------ extension
@@ -144,96 +258,106 @@ __device__ void refine_reported(const double *x, int64_t i, int l, double mui, d
 //    key > (theta_q - dq_band) sqrt(M2_i), theta_q being a proven lower bound
 //    on the row's p-th best correlation at l (the p-th best of p distinct
 //    exactly evaluated partners).
-template <typename T>
+// The row's loads are all issued before its stores.
+template <typename T, int PM>
 __device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i)
 {
     const int l = A.l;
     const int64_t n0 = A.n0, E = A.E;
+    const int p = A.p;
     if (A.run[i] >= l) {                 // flat at l: handled by k_flat_rows
         A.st.flag[i] = ROW_FLAT;
         A.thr[i] = T(pinf());
         return 2;
     }
     const double m2i = A.m2[i];
+    const double isdi = A.isd[i];
     const double xi = A.x[i + l - 1] - A.mu_prev[i];
     const double wgt = (l - 1.0) / l;
 
-    Ent v[MAXP];
-    int cnt = 0;
-    for (int e = 0; e < A.p; ++e) {
-        const int32_t j = A.st.ent_j[e * n0 + i];
-        if (j < 0) continue;
-        if (j >= A.nl || !nontrivial(i, j, E)) {
-            A.st.ent_j[e * n0 + i] = -1;
-            continue;
-        }
-        const double c = fma(wgt * xi, A.x[j + l - 1] - A.mu_prev[j], A.st.ent_c[e * n0 + i]);
-        A.st.ent_c[e * n0 + i] = c;
+    RowEnts<PM> r;
+    bool dropped[PM];
+    double cn[PM];
+    for_pm<PM>([&](int e) {
+        int32_t j = e < p ? A.st.ent_j[(int64_t)e * n0 + i] : -1;
+        dropped[e] = j >= 0 && (j >= A.nl || !nontrivial(i, j, E));
+        if (dropped[e]) j = -1;
+        r.j[e] = j;
+        r.q[e] = -pinf();
+        r.dq[e] = 0.0f;
+        cn[e] = 0.0;
+    });
+    for_pm<PM>([&](int e) {
+        const int32_t j = r.j[e];
+        if (j < 0) return;
+        const int64_t at = (int64_t)e * n0 + i;
+        cn[e] = fma(wgt * xi, A.x[j + l - 1] - A.mu_prev[j], A.st.ent_c[at]);
         const bool flat_j = A.run[j] >= l;
-        Ent t{corr(c, m2i, A.m2[j], false, flat_j), flat_j ? 0.0f : A.st.ent_dq[e * n0 + i], j, e};
-        ins_ent(v, cnt, t);
-        ++cnt;
-    }
+        r.q[e] = corr_isd(cn[e], isdi, A.isd[j], flat_j);
+        r.dq[e] = flat_j ? 0.0f : A.st.ent_dq[at];
+    });
+    int cnt = 0;
+    for_pm<PM>([&](int e) {
+        const int64_t at = (int64_t)e * n0 + i;
+        if (dropped[e]) A.st.ent_j[at] = -1;
+        if (r.j[e] >= 0) {
+            A.st.ent_c[at] = cn[e];
+            ++cnt;
+        }
+    });
     const double sig = sqrt(m2i / l);
     const double B = A.st.bnum[i] / sig;
     const int m = A.m_max;
-    // the m-th smallest true distance is at most the m-th smallest pessimistic one
+    // the m-th smallest true distance is at most the m-th smallest pessimistic
+    // one (compared as squared distances 2 l (1 - q))
     bool ok = false;
     if (cnt >= m) {
-        double dp[MAXP];
-        for (int a = 0; a < cnt; ++a) {
-            const double d = dist_from_q(v[a].q - v[a].dq, l);
-            int b = a;
-            while (b > 0 && dp[b - 1] > d) { dp[b] = dp[b - 1]; --b; }
-            dp[b] = d;
-        }
-        ok = dp[m - 1] < B;
+        double dp[PM];
+        for_pm<PM>([&](int a) { dp[a] = r.j[a] >= 0 ? 2.0 * l * (1.0 - clamp_q(r.q[a] - r.dq[a])) : pinf(); });
+        double dm = pinf();
+        for_pm<PM>([&](int a) {
+            int k = 0;
+            for_pm<PM>([&](int b) { k += (r.j[b] >= 0 && (dp[b] < dp[a] || (dp[b] == dp[a] && b < a))); });
+            if (r.j[a] >= 0 && k == m - 1) dm = dp[a];
+        });
+        ok = dm < B * B;
     }
     if (ok) {
-        refine_reported(A.x, i, l, A.mu[i], m2i, A.mu, A.m2, A.em, A.st, n0, v, cnt, m, &A.out.stats[3]);
-        double ds[MAXP];
-        int32_t js[MAXP];
-        for (int a = 0; a < cnt; ++a) {
-            ds[a] = dist_from_q(v[a].q, l);
-            js[a] = v[a].j;
-        }
-        write_nn(A.out, n0, i, m, ds, js, cnt);
-        valmp_update(A.vm, i, ds[0], js[0], l);
+        refine_reported<PM>(A.x, A.xh, A.xl, i, l, A.mu[i], isdi, A.mu, A.isd, A.em, A.st, n0, r, m,
+                            &A.out.stats[3]);
+        report_row<PM>(A.out, A.vm, n0, i, l, r, cnt, m);
         A.st.flag[i] = ROW_DONE;
         A.thr[i] = T(pinf());
         return 1;
     }
     // theta_q: p-th best among p distinct partners with known lower bounds
     // on their correlation (the remaining entries lowered by their error
-    // bound, then partners next to the exclusion zone evaluated in FP64)
-    double qlow[MAXP];
-    int nlow = 0;
-    for (int a = 0; a < cnt; ++a) qlow[nlow++] = v[a].q - v[a].dq;
+    // bound, then partners next to the exclusion zone evaluated in FP64).
+    // There are never more than p such values, so the p-th best is the
+    // smallest once there are p of them.
+    double qmin = pinf();
+    for_pm<PM>([&](int a) {
+        if (r.j[a] >= 0) qmin = fmin(qmin, r.q[a] - r.dq[a]);
+    });
+    int nlow = cnt;
     const int64_t ntc = nontrivial_count(i, A.nl, E);
     double theta = -pinf();
-    if (ntc > A.p) {
+    if (ntc > p) {
         const double mui = A.mu[i];
-        for (int64_t t = 1; nlow < A.p && t <= A.nl; ++t) {
-            for (int side = 0; side < 2 && nlow < A.p; ++side) {
+        for (int64_t t = 1; nlow < p && t <= A.nl; ++t) {
+            for (int side = 0; side < 2 && nlow < p; ++side) {
                 const int64_t j = side == 0 ? i + E + t : i - E - t;
                 if (j < 0 || j >= A.nl) continue;
                 bool have = false;
-                for (int a = 0; a < cnt; ++a) have |= (v[a].j == j);
+                for_pm<PM>([&](int a) { have |= (r.j[a] == j); });
                 if (have) continue;
                 const bool flat_j = A.run[j] >= l;
                 const double c = flat_j ? 0.0 : comoment(A.x, i, j, l, mui, A.mu[j]);
-                qlow[nlow++] = corr(c, m2i, A.m2[j], false, flat_j);
+                qmin = fmin(qmin, corr_isd(c, isdi, A.isd[j], flat_j));
+                ++nlow;
             }
         }
-        if (nlow >= A.p) {
-            for (int a = 1; a < nlow; ++a) {
-                const double val = qlow[a];
-                int b = a;
-                while (b > 0 && qlow[b - 1] < val) { qlow[b] = qlow[b - 1]; --b; }
-                qlow[b] = val;
-            }
-            theta = qlow[A.p - 1] - dq_row(A.em, i);
-        }
+        if (nlow >= p) theta = qmin - dq_row(A.em, i);
     }
     A.st.flag[i] = ROW_RECOMPUTE;
     if (theta == -pinf()) {
@@ -248,9 +372,12 @@ __device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i)
     return 2;
 }
 
-template <typename T>
+template <typename T, int PM>
 __global__ void k_extend(ExtArgs<T> A)
 {
+    __shared__ unsigned sc[2];
+    if (threadIdx.x < 2) sc[threadIdx.x] = 0;
+    __syncthreads();
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int cat = 0;
     if (i < A.n0) {
@@ -258,22 +385,35 @@ __global__ void k_extend(ExtArgs<T> A)
             A.st.flag[i] = ROW_DONE;
             A.thr[i] = T(pinf());
         } else {
-            cat = extend_row(A, i);
+            cat = extend_row<T, PM>(A, i);
         }
     }
-    const unsigned mask = __activemask();
-    const unsigned b1 = __ballot_sync(mask, cat == 1), b2 = __ballot_sync(mask, cat == 2);
-    if ((threadIdx.x & 31) == __ffs(mask) - 1) {
-        if (b1) atomicAdd(&A.out.stats[1], (unsigned long long)__popc(b1));
-        if (b2) atomicAdd(&A.out.stats[2], (unsigned long long)__popc(b2));
+    // certified / recomputed counts: one shared add per warp, one global per block
+    const unsigned b1 = __ballot_sync(0xffffffffu, cat == 1), b2 = __ballot_sync(0xffffffffu, cat == 2);
+    if ((threadIdx.x & 31) == 0) {
+        if (b1) atomicAdd(&sc[0], (unsigned)__popc(b1));
+        if (b2) atomicAdd(&sc[1], (unsigned)__popc(b2));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (sc[0]) atomicAdd(&A.out.stats[1], (unsigned long long)sc[0]);
+        if (sc[1]) atomicAdd(&A.out.stats[2], (unsigned long long)sc[1]);
     }
 }
+
+// Largest p the register-resident row code is instantiated for.
+inline int row_pm(int p) { return p <= 8 ? 8 : (p <= 16 ? 16 : 64); }
 
 template <typename T>
 void launch_extend(const ExtArgs<T> &a, cudaStream_t s)
 {
     const int B = 128;
-    k_extend<T><<<(unsigned)((a.n0 + B - 1) / B), B, 0, s>>>(a);
+    const unsigned g = (unsigned)((a.n0 + B - 1) / B);
+    switch (row_pm(a.p)) {
+    case 8: k_extend<T, 8><<<g, B, 0, s>>>(a); break;
+    case 16: k_extend<T, 16><<<g, B, 0, s>>>(a); break;
+    default: k_extend<T, 64><<<g, B, 0, s>>>(a); break;
+    }
 }
 template void launch_extend<float>(const ExtArgs<float> &, cudaStream_t);
 template void launch_extend<double>(const ExtArgs<double> &, cudaStream_t);
@@ -289,7 +429,16 @@ template void launch_extend<double>(const ExtArgs<double> &, cudaStream_t);
 // the row has at most p non-trivial partners, all of them stored).
 // A row whose lists hold fewer than min(p, partners) keys had a threshold
 // above its p-th best key; it is flagged for another pass without one.
+// The kept keys sit in registers, sorted, updated by one fixed-length
+// compare-and-swap pass per offered key; the group counts are read four at
+// a time (the group stride is a multiple of 4).
 template <typename T>
+__device__ __forceinline__ bool key_before(T ka, int32_t ja, T kb, int32_t jb)
+{
+    return ka > kb || (ka == kb && ja < jb);
+}
+
+template <typename T, int PM>
 __global__ void k_merge(MergeArgs<T> A)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -302,24 +451,38 @@ __global__ void k_merge(MergeArgs<T> A)
     const int64_t ntc = nontrivial_count(i, A.nl, E);
     const int need = (int)(ntc < p ? ntc : p);
 
-    // top-p by key desc, offset asc over the row's lists. The symmetric form
-    // wrote row-side lists for the column groups from the row's band
-    // diagonal on, and appended the column-side candidates (cells (i', i),
-    // i' < i) to the row's candidate list.
+    // The symmetric form wrote row-side lists for the column groups from the
+    // row's band diagonal on, and appended the column-side candidates (cells
+    // (i', i), i' < i) to the row's candidate list.
     const bool sym_on = sym_rule(A.allow_sym, *A.nflagged, A.nl) && fl == ROW_RECOMPUTE;
-    T bk[MAXP];
-    int32_t bj[MAXP];
-    int nb = 0;
+    T bk[PM];
+    int32_t bj[PM];
+    for_pm<PM>([&](int t) {
+        bk[t] = T(-pinf());
+        bj[t] = INT32_MAX;
+    });
+    T lastk = T(-pinf());       // the p-th kept key (a sentinel until p are kept)
+    int32_t lastj = INT32_MAX;
     auto offer = [&](T v, int32_t j) {
-        if (nb == p && !(v > bk[p - 1] || (v == bk[p - 1] && j < bj[p - 1]))) return;
-        int b = nb < p ? nb++ : p - 1;
-        while (b > 0 && (bk[b - 1] < v || (bk[b - 1] == v && bj[b - 1] > j))) {
-            bk[b] = bk[b - 1];
-            bj[b] = bj[b - 1];
-            --b;
-        }
-        bk[b] = v;
-        bj[b] = j;
+        if (!key_before(v, j, lastk, lastj)) return;
+        T cv = v;
+        int32_t cj = j;
+        for_pm<PM>([&](int t) {
+            if (t < p && key_before(cv, cj, bk[t], bj[t])) {
+                const T tk = bk[t];
+                const int32_t tj = bj[t];
+                bk[t] = cv;
+                bj[t] = cj;
+                cv = tk;
+                cj = tj;
+            }
+        });
+        for_pm<PM>([&](int t) {
+            if (t == p - 1) {
+                lastk = bk[t];
+                lastj = bj[t];
+            }
+        });
     };
     if (fl == ROW_DIRECT) {
         const int64_t d = A.dindex[i];
@@ -331,10 +494,24 @@ __global__ void k_merge(MergeArgs<T> A)
         }
     } else {
         const int g0 = sym_on ? (int)(((i / A.R) * (int64_t)A.R) / A.group_w) : 0;
-        for (int g = g0; g < A.ngroups && (int64_t)g * A.group_w < A.nl; ++g) {
-            const int64_t slot = i * A.ngroups + g;
-            const int cnt = A.scnt[slot];
-            for (int c = 0; c < cnt; ++c) offer(A.skey[slot * p + c], A.sj[slot * p + c]);
+        const int64_t gl = (A.nl + A.group_w - 1) / A.group_w;
+        const int gend = (int)(gl < A.ngroups ? gl : A.ngroups);
+        const int4 *c4 = reinterpret_cast<const int4 *>(A.scnt + i * A.ngroups);
+        for (int gq = g0 & ~3; gq < gend; gq += 16) {
+            int4 cv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) cv[u] = gq + 4 * u < gend ? c4[(gq >> 2) + u] : make_int4(0, 0, 0, 0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int cs[4] = {cv[u].x, cv[u].y, cv[u].z, cv[u].w};
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const int g = gq + 4 * u + w;
+                    if (g < g0 || g >= gend) continue;
+                    const int64_t slot = i * A.ngroups + g;
+                    for (int c = 0; c < cs[w]; ++c) offer(A.skey[slot * p + c], A.sj[slot * p + c]);
+                }
+            }
         }
     }
     if (A.allow_sym && fl == ROW_DIRECT) A.ccnt[i] = 0;
@@ -350,6 +527,8 @@ __global__ void k_merge(MergeArgs<T> A)
         }
         for (int c = 0; c < cc; ++c) offer(A.ckey[i * A.cap + c], A.cj[i * A.cap + c]);
     }
+    int nb = 0;
+    for_pm<PM>([&](int t) { nb += (t < p && bj[t] != INT32_MAX); });
     if (nb < need) {
         A.thr[i] = T(-pinf());
         A.st.flag[i] = ROW_RECOMPUTE;
@@ -357,45 +536,43 @@ __global__ void k_merge(MergeArgs<T> A)
         atomicAdd(A.overflow + 8, 1ull);
         return;
     }
-    const double m2i = A.m2[i];
-    const double sqm2i = sqrt(m2i);
-    Ent v[MAXP];
-    int nq = 0;
-    for (int e = 0; e < p; ++e) {
+    const double isdi = A.isd[i];
+    RowEnts<PM> r;
+    for_pm<PM>([&](int e) {
+        r.j[e] = -1;
+        r.q[e] = -pinf();
+        r.dq[e] = 0.0f;
+        if (e >= p) return;
+        const int64_t at = (int64_t)e * n0 + i;
         if (e < nb) {
             const int32_t j = bj[e];
             const double inv = (double)A.col[j].inv;
             const bool flat_j = A.run[j] >= l;
             const double c = (flat_j || inv == 0.0) ? 0.0 : (double)bk[e] / inv;
             const float dq = flat_j ? 0.0f : (float)dq_pair(A.em, i, j);
-            A.st.ent_j[e * n0 + i] = j;
-            A.st.ent_c[e * n0 + i] = c;
-            A.st.ent_dq[e * n0 + i] = dq;
-            Ent t{corr(c, m2i, A.m2[j], false, flat_j), dq, j, e};
-            ins_ent(v, nq, t);
-            ++nq;
+            A.st.ent_j[at] = j;
+            A.st.ent_c[at] = c;
+            A.st.ent_dq[at] = dq;
+            r.j[e] = j;
+            r.q[e] = corr_isd(c, isdi, A.isd[j], flat_j);
+            r.dq[e] = dq;
         } else {
-            A.st.ent_j[e * n0 + i] = -1;
-            A.st.ent_c[e * n0 + i] = 0.0;
-            A.st.ent_dq[e * n0 + i] = 0.0f;
+            A.st.ent_j[at] = -1;
+            A.st.ent_c[at] = 0.0;
+            A.st.ent_dq[at] = 0.0f;
         }
-    }
-    refine_reported(A.x, i, l, A.mu[i], m2i, A.mu, A.m2, A.em, A.st, n0, v, nq, A.m_max, &A.out.stats[3]);
-    double ds[MAXP];
-    int32_t js[MAXP];
-    for (int e = 0; e < nq; ++e) {
-        ds[e] = dist_from_q(v[e].q, l);
-        js[e] = v[e].j;
-    }
-    write_nn(A.out, n0, i, A.m_max, ds, js, nq);
-    if (nq > 0) valmp_update(A.vm, i, ds[0], js[0], l);
+    });
+    refine_reported<PM>(A.x, A.xh, A.xl, i, l, A.mu[i], isdi, A.mu, A.isd, A.em, A.st, n0, r, A.m_max,
+                        &A.out.stats[3]);
+    report_row<PM>(A.out, A.vm, n0, i, l, r, nb, A.m_max);
     A.st.base[i] = l;
+    const double sqm2i = sqrt(A.m2[i]);
     const double sig = sqm2i / sqrt((double)l);
     if (ntc <= p) {
         A.st.bnum[i] = pinf();
     } else {
         // unstored partners have band keys <= the p-th kept key
-        double qp = (double)bk[p - 1] / sqm2i + dq_row(A.em, i);
+        double qp = (double)lastk / sqm2i + dq_row(A.em, i);
         qp = qp > 1.0 ? 1.0 : (qp < 0.0 ? 0.0 : qp);
         A.st.bnum[i] = sqrt((double)l * (1.0 - qp * qp)) * sig;
     }
@@ -407,7 +584,12 @@ template <typename T>
 void launch_merge(const MergeArgs<T> &a, cudaStream_t s)
 {
     const int B = 128;
-    k_merge<T><<<(unsigned)((a.nl + B - 1) / B), B, 0, s>>>(a);
+    const unsigned g = (unsigned)((a.nl + B - 1) / B);
+    switch (row_pm(a.p)) {
+    case 8: k_merge<T, 8><<<g, B, 0, s>>>(a); break;
+    case 16: k_merge<T, 16><<<g, B, 0, s>>>(a); break;
+    default: k_merge<T, 64><<<g, B, 0, s>>>(a); break;
+    }
 }
 template void launch_merge<float>(const MergeArgs<float> &, cudaStream_t);
 template void launch_merge<double>(const MergeArgs<double> &, cudaStream_t);

@@ -64,7 +64,7 @@ __global__ void k_stats_step(const double *__restrict__ x, int64_t nl, int l, co
 template <typename T>
 __global__ void k_coldata(const double *__restrict__ x, int64_t nl, int64_t npad, int l,
                           const double *__restrict__ mu, const double *__restrict__ m2,
-                          const int32_t *__restrict__ run, Col<T> *__restrict__ col)
+                          const int32_t *__restrict__ run, Col<T> *__restrict__ col, double *__restrict__ isd)
 {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < npad; j += (int64_t)gridDim.x * blockDim.x) {
         Col<T> c;
@@ -78,7 +78,9 @@ __global__ void k_coldata(const double *__restrict__ x, int64_t nl, int64_t npad
                 c.df = T(0);
                 c.dg = T(0);
             }
-            c.inv = (run[j] >= l) ? T(0) : T(1.0 / sqrt(m2[j]));
+            const double iv = (run[j] >= l) ? 0.0 : 1.0 / sqrt(m2[j]);
+            c.inv = T(iv);
+            isd[j] = iv;
         } else {
             c.df = T(0);
             c.dg = T(0);
@@ -90,14 +92,30 @@ __global__ void k_coldata(const double *__restrict__ x, int64_t nl, int64_t npad
 
 template <typename T>
 void launch_coldata(const double *x, int64_t nl, int64_t npad, int l, const double *mu, const double *m2,
-                    const int32_t *run, Col<T> *col, cudaStream_t s)
+                    const int32_t *run, Col<T> *col, double *isd, cudaStream_t s)
 {
-    k_coldata<T><<<(unsigned)((npad + 255) / 256), 256, 0, s>>>(x, nl, npad, l, mu, m2, run, col);
+    k_coldata<T><<<(unsigned)((npad + 255) / 256), 256, 0, s>>>(x, nl, npad, l, mu, m2, run, col, isd);
 }
 template void launch_coldata<float>(const double *, int64_t, int64_t, int, const double *, const double *,
-                                    const int32_t *, Col<float> *, cudaStream_t);
+                                    const int32_t *, Col<float> *, double *, cudaStream_t);
 template void launch_coldata<double>(const double *, int64_t, int64_t, int, const double *, const double *,
-                                     const int32_t *, Col<double> *, cudaStream_t);
+                                     const int32_t *, Col<double> *, double *, cudaStream_t);
+
+__global__ void k_split_x(const double *__restrict__ x, int64_t n, float *__restrict__ xh, float *__restrict__ xl)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const float h = (float)x[k];
+        xh[k] = h;
+        xl[k] = (float)(x[k] - (double)h);
+    }
+}
+
+void launch_split_x(const double *x, int64_t n, float *xh, float *xl, cudaStream_t s)
+{
+    int64_t g = (n + 255) / 256;
+    if (g > 4096) g = 4096;
+    k_split_x<<<(unsigned)g, 256, 0, s>>>(x, n, xh, xl);
+}
 
 // Contrast factor kappa_i (see ErrModel): block maxima of M2 over 256
 // windows, then for each window the maximum over the blocks that cover the R

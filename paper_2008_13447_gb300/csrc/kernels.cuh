@@ -9,9 +9,13 @@ __global__ void k_flat_runs(const double *x, int64_t n, int cap, int32_t *run);
 __global__ void k_stats_init(const double *x, int64_t nl, int l, double *mu, double *m2);
 __global__ void k_stats_step(const double *x, int64_t nl, int l, const double *mu_o, const double *m2_o,
                              double *mu_n, double *m2_n);
+// Column data of the band kernel, and isd[j] = 1 / sqrt(M2_j) in FP64 (0 for
+// a flat window) for the per-row kernels.
 template <typename T>
 void launch_coldata(const double *x, int64_t nl, int64_t npad, int l, const double *mu, const double *m2,
-                    const int32_t *run, Col<T> *col, cudaStream_t s);
+                    const int32_t *run, Col<T> *col, double *isd, cudaStream_t s);
+// x split into FP32 pairs, x[k] = xh[k] + xl[k] to about 48 bits.
+void launch_split_x(const double *x, int64_t n, float *xh, float *xl, cudaStream_t s);
 __global__ void k_widen_f32(const float *in, int64_t n, double *out);
 
 // ------------------------------------------- k_band.cuh (k_band_f32.cu, k_band_f64.cu)
@@ -131,6 +135,8 @@ struct LenOut {
 
 template <typename T> struct ExtArgs {
     const double *x;
+    const float *xh, *xl;   // x as FP32 pairs (compensated re-evaluation)
+    const double *isd;      // 1 / sqrt(M2) at l (0: flat)
     int64_t n0, nl;
     int l;
     int64_t E;
@@ -149,6 +155,8 @@ template <typename T> void launch_extend(const ExtArgs<T> &a, cudaStream_t s);
 
 template <typename T> struct MergeArgs {
     const double *x;
+    const float *xh, *xl;
+    const double *isd;
     int64_t n0, nl;
     int l;
     int64_t E;

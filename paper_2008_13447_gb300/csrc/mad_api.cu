@@ -201,6 +201,8 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     float *kappa = dalloc<float>(ctx, s, n0);
     float *kappa_max = dalloc<float>(ctx, s, 1);
     double *m2blk = dalloc<double>(ctx, s, (n0 + 255) / 256);
+    double *isd = dalloc<double>(ctx, s, n0);
+    float *xh = dalloc<float>(ctx, s, n), *xl = dalloc<float>(ctx, s, n);
     const ErrModel em{kappa, kappa_max, Precision<T>::dq0, Precision<T>::rel_tol, Precision<T>::abs_coef};
     Valmp vm{dalloc<double>(ctx, s, n0), dalloc<double>(ctx, s, n0), dalloc<int32_t>(ctx, s, n0),
              dalloc<int32_t>(ctx, s, n0)};
@@ -248,6 +250,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     launch_fill<T>(thr, npad, T(INFINITY), st);
     k_flat_runs<<<1024, 256, 0, st>>>(s.x, n, lmax, run);
     k_stats_init<<<(unsigned)((n0 + 255) / 256), 256, 0, st>>>(s.x, n0, lmin, mu[0], m2[0]);
+    launch_split_x(s.x, n, xh, xl, st);
     CK(cudaGetLastError());
 
     const int occ_band = band_occupancy<T>(false, p, rpl);
@@ -262,7 +265,10 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     if (G < 1) G = 1;
     if (G > K) G = K;
     const int64_t group_w = G * SP;
-    const int ngroups_max = (int)((n0 + group_w - 1) / group_w);
+    // column groups at lmin, the per-row slot stride rounded up to a multiple
+    // of 4 (the merge reads the per-group counts four at a time; groups past
+    // the last column are never written nor read as groups)
+    const int ngroups_max = (int)(((n0 + group_w - 1) / group_w + 3) / 4 * 4);
     // column-side candidates per row (symmetric form): runs of adjacent
     // partners can clear a row's threshold together, so keep many
     const int ccap = p * 32 > 256 ? p * 32 : 256;
@@ -326,7 +332,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         ~EvGuard() { for (Ev &e : v) { if (e.a) cudaEventDestroy(e.a); if (e.b) cudaEventDestroy(e.b); } }
     } ev_guard{evs};
     // launches issued for the current length, counted at each launch site
-    unsigned long long nlaunch = 1 /* k_flat_runs */ + 1 /* k_stats_init */ + 1 /* fill thr */;
+    unsigned long long nlaunch = 1 /* k_flat_runs */ + 1 /* k_stats_init */ + 1 /* k_split_x */ + 1 /* fill thr */;
 
     // Side streams: the seed rows of length l need only the window means, so
     // they run beside the extension, the split and the column data; the
@@ -365,7 +371,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
                                                                       m2[cur ^ 1]);
             cur ^= 1;
         }
-        launch_coldata<T>(s.x, nl, npad, l, mu[cur], m2[cur], run, col, st);
+        launch_coldata<T>(s.x, nl, npad, l, mu[cur], m2[cur], run, col, isd, st);
         launch_kappa(m2[cur], run, nl, l, R, m2blk, kappa, kappa_max, st);
         nlaunch += 3;
         CK(cudaGetLastError());
@@ -387,6 +393,9 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
             k_init_flags<<<(unsigned)((n0 + 255) / 256), 256, 0, st>>>(run, n0, l, rs.flag, lo.stats);
         } else {
             ExtArgs<T> ea{};
+            ea.xh = xh;
+            ea.xl = xl;
+            ea.isd = isd;
             ea.x = s.x;
             ea.n0 = n0;
             ea.nl = nl;
@@ -478,6 +487,9 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         ma.vm = vm;
         ma.out = lo;
         ma.em = em;
+        ma.xh = xh;
+        ma.xl = xl;
+        ma.isd = isd;
         ma.overflow = lo.stats + 0;
         ma.nflagged = lo.stats + 2;
         ma.R = R;
