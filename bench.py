@@ -54,7 +54,28 @@ def parse():
     ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the plain FP64 GPU path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
+    ap.add_argument("--ncu-case", default=None, metavar="LMIN:LMAX",
+                    help="profile the workload once over [LMIN, LMAX] and exit (a small case for ncu captures)")
     return ap.parse_args()
+
+
+def run_ncu_case(args):
+    """One mad_profile of the workload over a short length range, for
+    profiler captures (the first length runs the threshold pass and the
+    first recompute; later lengths are the steady state)."""
+    import paper_2008_13447_gb300 as mad
+    import workloads
+    w = workloads.make(args.workload)
+    a, b = (int(v) for v in args.ncu_case.split(":"))
+    prec = mad.MAD_FP32 if args.precision == "fp32" else mad.MAD_FP64
+    ctx = mad.mad_create(w.series[0], precision=prec, k_max=w.k, m_max=w.m, band_form=args.band_form)
+    try:
+        mad.mad_profile(ctx, a, b, w.p)
+        for s in mad.mad_stats(ctx, 0):
+            print(json.dumps({k: s[k] for k in ("len", "rows", "certified", "recomputed", "band_cells", "band_ms")}))
+    finally:
+        mad.mad_destroy(ctx)
+    return 0
 
 
 def dist_env():
@@ -210,6 +231,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.ncu_case:
+        return run_ncu_case(args)
     import numpy as np
     import torch
     import paper_2008_13447_gb300 as mad
