@@ -388,8 +388,14 @@ __global__ void __launch_bounds__(NW * 32, band_min_blocks<T, RPL>()) k_band(con
         if (lane == 0) mbar_arrive(&uempty[us]);
         if (u >= total) break;
         {
-        const int g = (int)(u / nb);
         const int band = SYM ? (int)(u % nb) : A.bands[u % nb];
+        int g = (int)(u / nb);
+        if (!SYM) {
+            // each band's diagonal group first, then to the right (wrapping)
+            const int gd = (int)(((int64_t)band * R) / A.group_w);
+            g += gd;
+            if (g >= A.ngroups) g -= A.ngroups;
+        }
         const int64_t i0 = (int64_t)band * R;
         const int64_t c0 = (int64_t)g * A.group_w;
         if (c0 >= A.nl) continue;
