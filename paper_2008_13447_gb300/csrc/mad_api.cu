@@ -192,18 +192,22 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     int32_t *run = dalloc<int32_t>(ctx, s, n);
     double *mu[2] = {dalloc<double>(ctx, s, n0), dalloc<double>(ctx, s, n0)};
     double *m2[2] = {dalloc<double>(ctx, s, n0), dalloc<double>(ctx, s, n0)};
-    Col<T> *col = dalloc<Col<T>>(ctx, s, npad);
-    T *seed = dalloc<T>(ctx, s, K * spitch);
+    // per-length inputs of the band kernel and the per-row kernels, double
+    // buffered by length parity: length l+1's are prepared on a side stream
+    // while length l's band kernel runs
+    Col<T> *colb[2] = {dalloc<Col<T>>(ctx, s, npad), dalloc<Col<T>>(ctx, s, npad)};
+    T *seedb[2] = {dalloc<T>(ctx, s, K * spitch), dalloc<T>(ctx, s, K * spitch)};
     T *thr = dalloc<T>(ctx, s, npad);
     RowState rs{dalloc<int32_t>(ctx, s, (size_t)p * n0), dalloc<double>(ctx, s, (size_t)p * n0),
                 dalloc<float>(ctx, s, (size_t)p * n0), dalloc<int32_t>(ctx, s, n0), dalloc<double>(ctx, s, n0),
                 dalloc<int32_t>(ctx, s, n0)};
-    float *kappa = dalloc<float>(ctx, s, n0);
-    float *kappa_max = dalloc<float>(ctx, s, 1);
+    float *kappab[2] = {dalloc<float>(ctx, s, n0), dalloc<float>(ctx, s, n0)};
+    float *kmaxb[2] = {dalloc<float>(ctx, s, 1), dalloc<float>(ctx, s, 1)};
     double *m2blk = dalloc<double>(ctx, s, (n0 + 255) / 256);
-    double *isd = dalloc<double>(ctx, s, n0);
+    double *isdb[2] = {dalloc<double>(ctx, s, n0), dalloc<double>(ctx, s, n0)};
     float *xh = dalloc<float>(ctx, s, n), *xl = dalloc<float>(ctx, s, n);
-    const ErrModel em{kappa, kappa_max, Precision<T>::dq0, Precision<T>::rel_tol, Precision<T>::abs_coef};
+    const ErrModel emb[2] = {{kappab[0], kmaxb[0], Precision<T>::dq0, Precision<T>::rel_tol, Precision<T>::abs_coef},
+                             {kappab[1], kmaxb[1], Precision<T>::dq0, Precision<T>::rel_tol, Precision<T>::abs_coef}};
     Valmp vm{dalloc<double>(ctx, s, n0), dalloc<double>(ctx, s, n0), dalloc<int32_t>(ctx, s, n0),
              dalloc<int32_t>(ctx, s, n0)};
     int *bins = dalloc<int>(ctx, s, (size_t)n0 * nbins);
@@ -289,8 +293,6 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     int32_t *scnt = dalloc<int32_t>(ctx, s, (size_t)n0 * ngroups_max);
 
     BandArgs<T> ba{};
-    ba.col = col;
-    ba.seed = seed;
     ba.spitch = spitch;
     ba.thr = thr;
     ba.bands = bands;
@@ -311,7 +313,6 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     ba.ccnt = ccnt;
     ba.cap = ccap;
 
-    int cur = 0;
     // the symmetric band form (upper triangle, both sides of each cell)
     const int use_sym = o.band_form == 1 ? 1 : 0;
     s.stats.assign(nL, mad_length_stats{});
@@ -340,21 +341,45 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     // so they run while the next length proceeds. Events order them against
     // the context's stream.
     struct Side {
-        cudaStream_t seed = nullptr, disc = nullptr;
-        cudaEvent_t ev[8] = {};
+        cudaStream_t prep = nullptr, disc = nullptr;
+        cudaEvent_t ev[10] = {};
         ~Side()
         {
-            if (seed) cudaStreamDestroy(seed);
+            if (prep) cudaStreamDestroy(prep);
             if (disc) cudaStreamDestroy(disc);
             for (cudaEvent_t e : ev)
                 if (e) cudaEventDestroy(e);
         }
     } side;
-    CK(cudaStreamCreateWithFlags(&side.seed, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&side.prep, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&side.disc, cudaStreamNonBlocking));
     for (cudaEvent_t &e : side.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    cudaEvent_t ev_stats = side.ev[0], ev_seed = side.ev[1], ev_nnd = side.ev[2], ev_end = side.ev[3];
-    cudaEvent_t *ev_disc = side.ev + 4;   // [2], one per buffer
+    cudaEvent_t ev_nnd = side.ev[2], ev_end = side.ev[3];
+    cudaEvent_t *ev_disc = side.ev + 4;   // [2], one per m-th NN buffer
+    cudaEvent_t *ev_prep = side.ev + 6;   // [2], length prepared (by parity)
+    cudaEvent_t *ev_ext = side.ev + 8;    // [2], extension done (by parity)
+    // Preparation of length l on the side stream: window statistics (one
+    // Welford step), column data and 1/sqrt(M2), contrast factors, seed rows.
+    // Its buffers (parity of l) held length l-2, whose last readers (band,
+    // direct and merge kernels of l-2, extension of l-1 for the means) are
+    // done once the extension of l-1 is.
+    auto prep = [&](int l) {
+        const int li = l - lmin, b = li & 1;
+        const int64_t nl = n - l + 1;
+        CK(cudaStreamWaitEvent(side.prep, ev_ext[b ^ 1], 0));
+        if (l > lmin)
+            k_stats_step<<<(unsigned)((nl + 255) / 256), 256, 0, side.prep>>>(s.x, nl, l, mu[b ^ 1], m2[b ^ 1],
+                                                                             mu[b], m2[b]);
+        launch_coldata<T>(s.x, nl, npad, l, mu[b], m2[b], run, colb[b], isdb[b], side.prep);
+        launch_kappa(m2[b], run, nl, l, R, m2blk, kappab[b], kmaxb[b], side.prep);
+        SeedArgs<T> sa{s.x, mu[b], nl, l, SP, krows, (int)K, spitch, seedb[b], nullptr};
+        launch_seed<T>(sa, side.prep);
+        CK(cudaEventRecord(ev_prep[b], side.prep));
+        CK(cudaGetLastError());
+    };
+    // length lmin: after the one-off initialisation on the context's stream
+    CK(cudaEventRecord(ev_ext[1], st));
+    prep(lmin);
 
     for (int l = lmin; l <= lmax; ++l) {
         const int li = l - lmin;
@@ -365,26 +390,10 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         // the discord tables of length l-2 have finished reading this buffer
         if (li >= 2) CK(cudaStreamWaitEvent(st, ev_disc[li & 1], 0));
         LenOut lo{nnd, nnj, dstats + (size_t)li * NSTAT};
-        if (l > lmin) {
-            ++nlaunch;
-            k_stats_step<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(s.x, nl, l, mu[cur], m2[cur], mu[cur ^ 1],
-                                                                      m2[cur ^ 1]);
-            cur ^= 1;
-        }
-        launch_coldata<T>(s.x, nl, npad, l, mu[cur], m2[cur], run, col, isd, st);
-        launch_kappa(m2[cur], run, nl, l, R, m2blk, kappa, kappa_max, st);
-        nlaunch += 3;
-        CK(cudaGetLastError());
-        // seed rows of this length (the previous band kernel, earlier on the
-        // context's stream, is done with the seed buffer)
-        CK(cudaEventRecord(ev_stats, st));
-        CK(cudaStreamWaitEvent(side.seed, ev_stats, 0));
-        {
-            SeedArgs<T> sa{s.x, mu[cur], nl, l, SP, krows, (int)K, spitch, seed, nullptr};
-            launch_seed<T>(sa, side.seed);
-            ++nlaunch;
-        }
-        CK(cudaEventRecord(ev_seed, side.seed));
+        const int b = li & 1;
+        const ErrModel &em = emb[b];
+        CK(cudaStreamWaitEvent(st, ev_prep[b], 0));
+        nlaunch += (l > lmin ? 1 : 0) + 4;   // stats step, column data, kappa (2), seeds
 
         if (l == lmin) {
             // every row recomputed; flat rows apart
@@ -395,7 +404,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
             ExtArgs<T> ea{};
             ea.xh = xh;
             ea.xl = xl;
-            ea.isd = isd;
+            ea.isd = isdb[b];
             ea.x = s.x;
             ea.n0 = n0;
             ea.nl = nl;
@@ -403,9 +412,9 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
             ea.E = E;
             ea.p = p;
             ea.m_max = m_max;
-            ea.mu_prev = mu[cur ^ 1];
-            ea.mu = mu[cur];
-            ea.m2 = m2[cur];
+            ea.mu_prev = mu[b ^ 1];
+            ea.mu = mu[b];
+            ea.m2 = m2[b];
             ea.run = run;
             ea.st = rs;
             ea.vm = vm;
@@ -416,6 +425,10 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
             ++nlaunch;
         }
         CK(cudaGetLastError());
+        // the next length's preparation may start (it overlaps this length's
+        // band kernel and fills the SMs its tail leaves idle)
+        CK(cudaEventRecord(ev_ext[b], st));
+        if (l < lmax) prep(l + 1);
 
         // Rows to recompute -> (bands | direct rows) -> seeds -> band kernel
         // -> direct kernel -> merge, with no host round trip: kernels read
@@ -439,7 +452,8 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         sp.stat_direct = lo.stats + 9;
         launch_split(sp, st);
         ++nlaunch;
-        CK(cudaStreamWaitEvent(st, ev_seed, 0));
+        ba.col = colb[b];
+        ba.seed = seedb[b];
         ba.nl = nl;
         ba.l = l;
         ba.E = E;
@@ -459,24 +473,24 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
                 launch_band<T>(ba, true, grid_bins, st);
                 CK(cudaEventRecord(evs[e].b, st));
             }
-            launch_theta_bins<T>(bins, nbins, nl, p, m2[cur], em, thr, st);
+            launch_theta_bins<T>(bins, nbins, nl, p, m2[b], em, thr, st);
             launch_mask_thr<T>(rs.flag, n0, thr, st);
             nlaunch += 4;
             CK(cudaGetLastError());
         }
-        DirectArgs<T> da{s.x, mu[cur], col, nl, l, E, p, drows, ndirect, thr, dkey, djj, dcnt, dnblk};
+        DirectArgs<T> da{s.x, mu[b], colb[b], nl, l, E, p, drows, ndirect, thr, dkey, djj, dcnt, dnblk};
         MergeArgs<T> ma{};
         ma.x = s.x;
-        ma.mu = mu[cur];
+        ma.mu = mu[b];
         ma.n0 = n0;
         ma.nl = nl;
         ma.l = l;
         ma.E = E;
         ma.p = p;
         ma.m_max = m_max;
-        ma.m2 = m2[cur];
+        ma.m2 = m2[b];
         ma.run = run;
-        ma.col = col;
+        ma.col = colb[b];
         ma.skey = skey;
         ma.sj = sj;
         ma.scnt = scnt;
@@ -489,7 +503,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         ma.em = em;
         ma.xh = xh;
         ma.xl = xl;
-        ma.isd = isd;
+        ma.isd = isdb[b];
         ma.overflow = lo.stats + 0;
         ma.nflagged = lo.stats + 2;
         ma.R = R;
@@ -542,7 +556,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     // the side streams' last work is done before the read-back
     CK(cudaEventRecord(ev_end, side.disc));
     CK(cudaStreamWaitEvent(st, ev_end, 0));
-    CK(cudaEventRecord(ev_end, side.seed));
+    CK(cudaEventRecord(ev_end, side.prep));
     CK(cudaStreamWaitEvent(st, ev_end, 0));
     int32_t herr = 0;
     CK(cudaMemcpyAsync(&herr, wait_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
