@@ -275,11 +275,16 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     const int ngroups_max = (int)(((n0 + group_w - 1) / group_w + 3) / 4 * 4);
     // column-side candidates per row (symmetric form): runs of adjacent
     // partners can clear a row's threshold together, so keep many
+    // (allocated only for the symmetric form, the only one that touches them)
     const int ccap = p * 32 > 256 ? p * 32 : 256;
-    T *ckey = dalloc<T>(ctx, s, (size_t)n0 * ccap);
-    int32_t *cjj = dalloc<int32_t>(ctx, s, (size_t)n0 * ccap);
-    int32_t *ccnt = dalloc<int32_t>(ctx, s, n0);
-    CK(cudaMemsetAsync(ccnt, 0, n0 * sizeof(int32_t), st));
+    T *ckey = nullptr;
+    int32_t *cjj = nullptr, *ccnt = nullptr;
+    if (o.band_form == 1) {
+        ckey = dalloc<T>(ctx, s, (size_t)n0 * ccap);
+        cjj = dalloc<int32_t>(ctx, s, (size_t)n0 * ccap);
+        ccnt = dalloc<int32_t>(ctx, s, n0);
+        CK(cudaMemsetAsync(ccnt, 0, n0 * sizeof(int32_t), st));
+    }
     // direct path: row list, list positions, per (row, column block) top-p
     const int max_direct = (int)(n0 < (1 << 16) ? n0 : (1 << 16));
     const int dnblk = (int)((n0 + direct_cols_per_block() - 1) / direct_cols_per_block());
