@@ -66,6 +66,8 @@ def _L():
                                        P, P, P, P, P, P]),
             "orc_valmod_pruned": (None, [P, i64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                          P, P, P, P, P, P, P]),
+            "orc_valmod_motif": (None, [P, i64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                        P, P, P, P, P, P]),
             "orc_topk_motifs": (C.c_int, [i64, P, P, P, P, C.c_int, C.c_int, C.c_int, P, P, P, P, P]),
             "orc_discords_one_length": (C.c_int, [i64, P, P, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P]),
             "orc_discords": (None, [i64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P, P,
@@ -208,6 +210,24 @@ def valmod_pruned(x, lmin, lmax, p, m_max=1, num=1, den=4, keep_nn=False):
     if keep_nn:
         out.update(nnd=nnd, nnj=nnj)
     return out
+
+
+def valmod_motif(x, lmin, lmax, p, num=1, den=4):
+    """The paper-literal pruned iteration (motif of every length guaranteed,
+    not every row). Returns VALMP as valmp_plain does, plus ``submp``
+    (|L|, n_lmin) with NaN where a row's value at that length is undefined,
+    and ``stats`` (|L|, 5): rows, valid, non-valid, recomputed, full."""
+    if not (1 <= p <= 64):
+        raise ValueError("need 1 <= p <= 64")
+    x = _f64(x)
+    n0 = len(x) - lmin + 1
+    dist_, norm_, len_, nn_ = _valmp_out(n0)
+    nL = lmax - lmin + 1
+    submp = np.empty((nL, n0))
+    stats = np.empty((nL, 5), np.int64)
+    _L().orc_valmod_motif(_p(x), len(x), lmin, lmax, num, den, p, _p(dist_), _p(norm_), _p(len_), _p(nn_),
+                          _p(submp), _p(stats))
+    return dict(dist=dist_, norm=norm_, len=len_, nn=nn_, submp=submp, stats=stats)
 
 
 def topk_motifs(valmp, k, num=1, den=4):

@@ -480,6 +480,157 @@ void orc_valmod_pruned(const double *x, i64 n, int lmin, int lmax, int num, int 
     free(nnj);
 }
 
+/* The paper-literal pruned iteration (Algorithm 1 with ComputeSubMP,
+ * Algorithm 4), whose guarantee is the motif of every length, not every
+ * row: at lmin the full matrix profile (Algorithm 3); at every longer length
+ *  - each row's stored entries are re-evaluated (trivial / out-of-range ones
+ *    skipped); a row is valid iff its smallest stored distance is strictly
+ *    below its bound B = bound_base * sigma_b / sigma_l (Eq. LB with rank
+ *    preservation); valid rows give SubMP[i] exactly and minDistAbs is the
+ *    smallest of them; the others are non-valid with lbMax = B (a flat row
+ *    has no usable bound: non-valid with lbMax = 0);
+ *  - bBestM = minDistAbs < min over non-valid rows of lbMax;
+ *  - if not, and fewer than n log(p) / log(n) rows are non-valid (n = |T|,
+ *    natural logarithms; the ratio does not depend on the base), every
+ *    non-valid row with lbMax < minDistAbs is recomputed in full (its
+ *    profile minimum, new stored entries and bound), and bBestM holds;
+ *  - if bBestM still fails, the full matrix profile at l is computed
+ *    (Algorithm 1's ComputeMatrixProfile branch: every row recomputed);
+ *  - VALMP is updated with the defined SubMP values only.
+ * Rows that stay undefined keep their (extended) stored entries. Outputs:
+ * VALMP (len[] zero-initialised by the caller); optionally SubMP per length
+ * submp_all[(l-lmin)*n_lmin + i] (NaN where undefined) and stats
+ * [(l-lmin)*5 + {0..4}] = rows, valid, non-valid, recomputed, full (0/1). */
+void orc_valmod_motif(const double *x, i64 n, int lmin, int lmax, int num, int den, int p,
+                      double *dist, double *norm, int32_t *len, i64 *nn, double *submp_all, i64 *stats)
+{
+    i64 n0 = n - lmin + 1;
+    row_state *st = (row_state *)calloc((size_t)n0, sizeof(row_state));
+    i64 *jstore = (i64 *)malloc(sizeof(i64) * (size_t)(n0 * p));
+    for (i64 i = 0; i < n0; ++i) st[i].j = jstore + i * p;
+    double *mp = (double *)malloc(sizeof(double) * (size_t)n0);
+    i64 *ip = (i64 *)malloc(sizeof(i64) * (size_t)n0);
+    double *nnd = (double *)malloc(sizeof(double) * (size_t)n0);
+    i64 *nnj = (i64 *)malloc(sizeof(i64) * (size_t)n0);
+    double *lbmax = (double *)malloc(sizeof(double) * (size_t)n0);
+    signed char *state = (signed char *)malloc((size_t)n0);   /* 1 valid, 0 non-valid */
+    const double limit = (double)n * log((double)p) / log((double)n);
+
+    for (int l = lmin; l <= lmax; ++l) {
+        i64 nl = n - l + 1, E = orc_excl(l, num, den);
+        i64 nvalid = 0, nnon = 0, nrecomp = 0;
+        int full = (l == lmin);
+        double min_dist_abs = INFINITY, min_lb_abs = INFINITY;
+        if (!full) {
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : nvalid, nnon) reduction(min : min_dist_abs, min_lb_abs)
+            for (i64 i = 0; i < nl; ++i) {
+                mp[i] = INFINITY;
+                ip[i] = -1;
+                if (orc_is_flat(x, n, l, i)) {
+                    state[i] = 0;
+                    lbmax[i] = 0.0;
+                    ++nnon;
+                    min_lb_abs = fmin(min_lb_abs, 0.0);
+                    continue;
+                }
+                double best = INFINITY;
+                i64 bj = -1;
+                for (int e = 0; e < st[i].cnt; ++e) {
+                    i64 j = st[i].j[e];
+                    i64 dd = i > j ? i - j : j - i;
+                    if (j >= nl || dd <= E) continue;
+                    double d = orc_dist(x, n, l, i, j);
+                    if (d < best || (d == best && j < bj)) { best = d; bj = j; }
+                }
+                double mu, sig;
+                orc_window_stats(x, n, l, i, &mu, &sig);
+                double B = st[i].bound_base * st[i].sig_b / sig;
+                if (bj >= 0 && best < B) {
+                    state[i] = 1;
+                    mp[i] = best;
+                    ip[i] = bj;
+                    ++nvalid;
+                    min_dist_abs = fmin(min_dist_abs, best);
+                } else {
+                    state[i] = 0;
+                    lbmax[i] = B;
+                    ++nnon;
+                    min_lb_abs = fmin(min_lb_abs, B);
+                }
+            }
+            int best_m = min_dist_abs < min_lb_abs;
+            if (!best_m && (double)nnon < limit) {
+#pragma omp parallel reduction(+ : nrecomp)
+                {
+                    double *prof = (double *)malloc(sizeof(double) * (size_t)n0);
+                    dj_t *dbuf = (dj_t *)malloc(sizeof(dj_t) * (size_t)n0);
+                    qj_t *qbuf = (qj_t *)malloc(sizeof(qj_t) * (size_t)n0);
+#pragma omp for schedule(dynamic, 1)
+                    for (i64 i = 0; i < nl; ++i) {
+                        if (state[i] != 0 || !(lbmax[i] < min_dist_abs)) continue;
+                        recompute_row(x, n, l, num, den, p, 1, i, &st[i], mp, ip, nnd, nnj, prof, dbuf, qbuf);
+                        ++nrecomp;
+                    }
+                    free(prof);
+                    free(dbuf);
+                    free(qbuf);
+                }
+                best_m = 1;
+            }
+            if (!best_m) full = 1;
+        }
+        if (full) {
+            nrecomp = 0;
+#pragma omp parallel reduction(+ : nrecomp)
+            {
+                double *prof = (double *)malloc(sizeof(double) * (size_t)n0);
+                dj_t *dbuf = (dj_t *)malloc(sizeof(dj_t) * (size_t)n0);
+                qj_t *qbuf = (qj_t *)malloc(sizeof(qj_t) * (size_t)n0);
+#pragma omp for schedule(dynamic, 8)
+                for (i64 i = 0; i < nl; ++i) {
+                    recompute_row(x, n, l, num, den, p, 1, i, &st[i], mp, ip, nnd, nnj, prof, dbuf, qbuf);
+                    ++nrecomp;
+                }
+                free(prof);
+                free(dbuf);
+                free(qbuf);
+            }
+        }
+        /* VALMP with the defined values only */
+        double f = sqrt(1.0 / l);
+        for (i64 i = 0; i < nl; ++i) {
+            if (!isfinite(mp[i]) || ip[i] < 0) continue;
+            double nd = mp[i] * f;
+            if (len[i] == 0 || nd < norm[i]) {
+                dist[i] = mp[i];
+                norm[i] = nd;
+                len[i] = l;
+                nn[i] = ip[i];
+            }
+        }
+        if (submp_all) {
+            double *o = submp_all + (i64)(l - lmin) * n0;
+            for (i64 i = 0; i < n0; ++i) o[i] = (i < nl && ip[i] >= 0) ? mp[i] : NAN;
+        }
+        if (stats) {
+            i64 *s5 = stats + (i64)(l - lmin) * 5;
+            s5[0] = nl;
+            s5[1] = full && l == lmin ? 0 : nvalid;
+            s5[2] = full && l == lmin ? nl : nnon;
+            s5[3] = nrecomp;
+            s5[4] = full;
+        }
+    }
+    free(st);
+    free(jstore);
+    free(mp);
+    free(ip);
+    free(nnd);
+    free(nnj);
+    free(lbmax);
+    free(state);
+}
+
 /* ------------------------------------------------------------ read-outs */
 
 typedef struct { double key; i64 i; } ki_t;

@@ -313,6 +313,52 @@ def test_pruned_prunes_on_periodic_data():
     assert st[1:, 2].sum() < 0.2 * st[1:, 0].sum()
 
 
+@pytest.mark.parametrize("gen,n,lmin,lmax,p", [
+    ("rw", 500, 20, 34, 5),
+    ("rw", 300, 12, 20, 2),       # n log p / log n = 36 rows: full-profile fallbacks
+    ("ar2", 450, 18, 30, 5),
+    ("ecg", 900, 40, 60, 4),
+    ("planted", 1200, 30, 44, 5),
+])
+def test_motif_mode_finds_every_lengths_motif(gen, n, lmin, lmax, p):
+    # Algorithm 4's guarantee: at every length the smallest SubMP value is the
+    # exact motif distance, and every value it defines is the exact matrix
+    # profile; checked against independent per-length profiles.
+    if gen == "rw":
+        x = workloads.random_walk(n, 41)
+    elif gen == "ar2":
+        x = workloads.ar2(n, 42)
+    elif gen == "ecg":
+        x = workloads.ecg_like(n, 43, period=40.0)
+    else:
+        x, _ = workloads.planted_walk(n, 34, motif_lengths=(30, 36), lmax=60)
+    mo = oracle.valmod_motif(x, lmin, lmax, p)
+    pl = oracle.valmp_plain(x, lmin, lmax, m_max=1, keep_nn=True)
+    st = mo["stats"]
+    for li, l in enumerate(range(lmin, lmax + 1)):
+        nl = n - l + 1
+        exact = pl["nnd"][li, :nl, 0]
+        sub = mo["submp"][li, :nl]
+        d = np.isfinite(sub)
+        np.testing.assert_array_equal(sub[d], exact[d])
+        assert sub[d].min() == exact.min()
+        assert st[li, 0] == nl and st[li, 1] + st[li, 2] == nl
+        if st[li, 4]:
+            assert d.all()                             # full profile: every row defined
+        else:
+            assert d.sum() == st[li, 1] + st[li, 3]   # valid + recomputed rows
+    assert st[0, 4] == 1                               # lmin: the full profile
+    # the variable-length motif (best normalised VALMP entry) is exact
+    assert mo["norm"].min() == pl["norm"].min()
+    i = int(np.argmin(mo["norm"]))
+    assert mo["dist"][i] == pl["dist"][i] and mo["len"][i] == pl["len"][i]
+    if (gen, p) == ("rw", 2):
+        assert st[1:, 4].sum() > 0                     # the fallback ran
+    if gen == "ecg":
+        computed = np.where(st[1:, 4] == 1, st[1:, 0], st[1:, 3]).sum()
+        assert computed < 0.5 * st[1:, 0].sum()       # it pruned (full profiles included)
+
+
 # ---------------------------------------------------------------- read-outs
 
 def test_topk_motif_planted_pair():
