@@ -78,8 +78,16 @@ typedef struct mad_options {
     int32_t keep_profiles;  /* nonzero: keep every per-length matrix profile and m-th best
                                match table for mad_matrix_profile (|L| * n_lmin * (1 + m_max)
                                doubles and offsets; meant for small inputs) */
-    int32_t mode;           /* 0 (only mode): every row the bound cannot certify is recomputed,
-                               so every per-length result is exact for every offset */
+    int32_t mode;           /* 0 (exact rows): every row the bound cannot certify is recomputed,
+                               so every per-length result is exact for every offset;
+                               1 (motif mode, Algorithm 1 with ComputeSubMP, Algorithm 4): per
+                               length only the motif is guaranteed. Rows whose bound is not
+                               below the best certified distance are left undefined (NaN in the
+                               kept profiles, no VALMP update); when that test fails and too many
+                               rows are non-valid (n log p / log n or more) the full profile is
+                               computed. The best length-normalised VALMP entry (the top-1
+                               variable-length motif) is exact. Needs m_max = 1; no discord
+                               table (mad_discords returns MAD_ESTATE). */
     int32_t band_form;      /* matrix-profile kernel form: 0 = full rows (each row band walks every
                                column; the faster form on GB300), 1 = symmetric (upper triangle only,
                                each pair computed once and fed to both windows, used for the lengths
@@ -134,6 +142,9 @@ typedef struct {
                                on the context's stream around each launch) */
     double fp32_dq_max;     /* MAD_FP32: largest |q_FP32 - q_FP64| among stored entries that were
                                re-evaluated in FP64 at this length (0 when none / MAD_FP64) */
+    int64_t skipped;        /* motif mode: non-valid rows left undefined at this length */
+    int32_t full_profile;   /* motif mode: 1 if the full profile was computed at this length */
+    int32_t reserved2;
 } mad_length_stats;
 
 /* Create a context for one series copied from host memory (FP64, n values).

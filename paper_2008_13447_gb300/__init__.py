@@ -57,7 +57,8 @@ class mad_length_stats(C.Structure):
                 ("band_cells", C.c_int64), ("launches", C.c_int64), ("inserts", C.c_int64),
                 ("col_appends", C.c_int64), ("second_pass_rows", C.c_int64), ("direct_rows", C.c_int64),
                 ("band_ms", C.c_double),
-                ("fp32_dq_max", C.c_double)]
+                ("fp32_dq_max", C.c_double), ("skipped", C.c_int64), ("full_profile", C.c_int32),
+                ("reserved2", C.c_int32)]
 
 
 class MadError(RuntimeError):
@@ -107,15 +108,16 @@ def _check(status, ctx):
         raise MadError(status, library().mad_last_error(ctx).decode())
 
 
-def _options(precision=MAD_FP64, excl=(1, 4), k_max=10, m_max=1, keep_profiles=False, stream=None, band_form=0):
+def _options(precision=MAD_FP64, excl=(1, 4), k_max=10, m_max=1, keep_profiles=False, stream=None, band_form=0,
+             mode=0):
     o = mad_options()
     o.excl_num, o.excl_den = excl
     o.precision = precision
     o.k_max = k_max
     o.m_max = m_max
     o.keep_profiles = 1 if keep_profiles else 0
-    o.mode = 0
     o.band_form = band_form
+    o.mode = mode
     if stream is not None:
         o.stream = stream if isinstance(stream, int) else stream.cuda_stream
     return o
@@ -211,8 +213,8 @@ def mad_stats(ctx, series, cap=1 << 16):
     return [dict(len=s.len, rows=s.rows, certified=s.certified, recomputed=s.recomputed, tiles=s.tiles,
                  passes=s.passes, band_cells=s.band_cells, launches=s.launches, inserts=s.inserts,
                  col_appends=s.col_appends, second_pass_rows=s.second_pass_rows, direct_rows=s.direct_rows,
-                 band_ms=s.band_ms,
-                 fp32_dq_max=s.fp32_dq_max) for s in out[:min(n.value, cap)]]
+                 band_ms=s.band_ms, fp32_dq_max=s.fp32_dq_max, skipped=s.skipped,
+                 full_profile=s.full_profile) for s in out[:min(n.value, cap)]]
 
 
 def mad_mth_nn_dist_noalloc(x_ptr, n, cells, m_max, out_ptr, excl=(1, 4), stream=None):

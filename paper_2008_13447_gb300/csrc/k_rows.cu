@@ -222,23 +222,28 @@ __device__ void refine_reported(const double *x, const float *xh, const float *x
 // The row's m-th best matches (first m entries in correlation order), +inf
 // past the last of its cnt entries, and VALMP from the best (Algorithm 2).
 template <int PM>
-__device__ void report_row(const LenOut &o, const Valmp &vm, int64_t n0, int64_t i, int l, const RowEnts<PM> &r,
-                           int cnt, int m)
+__device__ double report_row(const LenOut &o, const Valmp &vm, int64_t n0, int64_t i, int l, const RowEnts<PM> &r,
+                             int cnt, int m)
 {
     int rk[PM];
     corr_ranks(r, rk);
+    double best = pinf();
     for_pm<PM>([&](int a) {
         if (r.j[a] >= 0 && rk[a] < m) {
             const double d = dist_from_q(r.q[a], l);
             o.nnd[(int64_t)rk[a] * n0 + i] = d;
             o.nnj[(int64_t)rk[a] * n0 + i] = r.j[a];
-            if (rk[a] == 0) valmp_update(vm, i, d, r.j[a], l);
+            if (rk[a] == 0) {
+                valmp_update(vm, i, d, r.j[a], l);
+                best = d;
+            }
         }
     });
     for (int t = cnt; t < m; ++t) {
         o.nnd[(int64_t)t * n0 + i] = pinf();
         o.nnj[(int64_t)t * n0 + i] = -1;
     }
+    return best;
 }
 
 // ------------------------------------------------------------ extension
@@ -259,8 +264,10 @@ __device__ void report_row(const LenOut &o, const Valmp &vm, int64_t n0, int64_t
 //    on the row's p-th best correlation at l (the p-th best of p distinct
 //    exactly evaluated partners).
 // The row's loads are all issued before its stores.
+// Motif mode: dbest / lb receive the row's certified distance or its bound
+// (a flat row has no usable bound: 0).
 template <typename T, int PM>
-__device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i)
+__device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i, double &dbest, double &lb)
 {
     const int l = A.l;
     const int64_t n0 = A.n0, E = A.E;
@@ -268,6 +275,10 @@ __device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i)
     if (A.run[i] >= l) {                 // flat at l: handled by k_flat_rows
         A.st.flag[i] = ROW_FLAT;
         A.thr[i] = T(pinf());
+        if (A.lbmax) {
+            A.lbmax[i] = 0.0;
+            lb = 0.0;
+        }
         return 2;
     }
     const double m2i = A.m2[i];
@@ -325,10 +336,14 @@ __device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i)
     if (ok) {
         refine_reported<PM>(A.x, A.xh, A.xl, i, l, A.mu[i], isdi, A.mu, A.isd, A.em, A.st, n0, r, m,
                             &A.out.stats[3]);
-        report_row<PM>(A.out, A.vm, n0, i, l, r, cnt, m);
+        dbest = report_row<PM>(A.out, A.vm, n0, i, l, r, cnt, m);
         A.st.flag[i] = ROW_DONE;
         A.thr[i] = T(pinf());
         return 1;
+    }
+    if (A.lbmax) {
+        A.lbmax[i] = B;
+        lb = B;
     }
     // theta_q: p-th best among p distinct partners with known lower bounds
     // on their correlation (the remaining entries lowered by their error
@@ -376,16 +391,34 @@ template <typename T, int PM>
 __global__ void k_extend(ExtArgs<T> A)
 {
     __shared__ unsigned sc[2];
-    if (threadIdx.x < 2) sc[threadIdx.x] = 0;
+    __shared__ unsigned long long smin[2];
+    if (threadIdx.x < 2) {
+        sc[threadIdx.x] = 0;
+        smin[threadIdx.x] = (unsigned long long)__double_as_longlong(pinf());
+    }
     __syncthreads();
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int cat = 0;
+    double dbest = pinf(), lb = pinf();
     if (i < A.n0) {
         if (i >= A.nl) {
             A.st.flag[i] = ROW_DONE;
             A.thr[i] = T(pinf());
         } else {
-            cat = extend_row<T, PM>(A, i);
+            cat = extend_row<T, PM>(A, i, dbest, lb);
+        }
+    }
+    if (A.min_dist_abs) {
+        // smallest certified distance and smallest non-valid bound: warp,
+        // block, then one global atomic each (non-negative doubles order
+        // like their bit patterns)
+        for (int o = 16; o > 0; o >>= 1) {
+            dbest = fmin(dbest, __shfl_xor_sync(0xffffffffu, dbest, o));
+            lb = fmin(lb, __shfl_xor_sync(0xffffffffu, lb, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&smin[0], (unsigned long long)__double_as_longlong(dbest));
+            atomicMin(&smin[1], (unsigned long long)__double_as_longlong(lb));
         }
     }
     // certified / recomputed counts: one shared add per warp, one global per block
@@ -398,6 +431,10 @@ __global__ void k_extend(ExtArgs<T> A)
     if (threadIdx.x == 0) {
         if (sc[0]) atomicAdd(&A.out.stats[1], (unsigned long long)sc[0]);
         if (sc[1]) atomicAdd(&A.out.stats[2], (unsigned long long)sc[1]);
+        if (A.min_dist_abs) {
+            atomicMin(A.min_dist_abs, smin[0]);
+            atomicMin(A.min_lb_abs, smin[1]);
+        }
     }
 }
 
@@ -593,6 +630,45 @@ void launch_merge(const MergeArgs<T> &a, cudaStream_t s)
 }
 template void launch_merge<float>(const MergeArgs<float> &, cudaStream_t);
 template void launch_merge<double>(const MergeArgs<double> &, cudaStream_t);
+
+template <typename T>
+__global__ void k_submp_mark(SubmpArgs<T> A)
+{
+    const double md = __longlong_as_double((long long)*A.min_dist_abs);
+    const double ml = __longlong_as_double((long long)*A.min_lb_abs);
+    const int decision = md < ml ? 0 : ((double)*A.nonvalid < A.limit ? 1 : 2);
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool skip = false;
+    if (i < A.nl) {
+        const int32_t f = A.flag[i];
+        if (decision == 2) {
+            if (f == ROW_DONE) {                // the full profile recomputes certified rows too
+                A.flag[i] = ROW_RECOMPUTE;
+                A.thr[i] = T(-pinf());
+            }
+        } else if (f == ROW_RECOMPUTE || f == ROW_FLAT) {
+            skip = !(decision == 1 && A.lbmax[i] < md);
+            if (skip) {
+                A.flag[i] = ROW_SKIP;
+                A.thr[i] = T(pinf());
+                A.nnd[i] = __longlong_as_double(0x7ff8000000000000LL);
+                A.nnj[i] = -1;
+            }
+        }
+    }
+    const int c = __syncthreads_count(skip);
+    if (threadIdx.x == 0 && c) atomicAdd(&A.stats[10], (unsigned long long)c);
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.stats[11] = decision == 2 ? 1ull : 0ull;
+}
+
+template <typename T>
+void launch_submp_mark(const SubmpArgs<T> &a, cudaStream_t s)
+{
+    const int B = 256;
+    k_submp_mark<T><<<(unsigned)((a.nl + B - 1) / B), B, 0, s>>>(a);
+}
+template void launch_submp_mark<float>(const SubmpArgs<float> &, cudaStream_t);
+template void launch_submp_mark<double>(const SubmpArgs<double> &, cudaStream_t);
 
 // First threshold at lmin from the interleaved maxima: bin b holds the
 // largest key over the column chunks of index = b (mod nbins); the p-th

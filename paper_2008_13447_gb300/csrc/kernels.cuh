@@ -135,6 +135,11 @@ struct LenOut {
 
 template <typename T> struct ExtArgs {
     const double *x;
+    // motif mode (NULL otherwise): per-row bound of non-valid rows, and the
+    // smallest certified distance / non-valid bound (bits of non-negative
+    // doubles, reduced with atomicMin)
+    double *lbmax;
+    unsigned long long *min_dist_abs, *min_lb_abs;
     const float *xh, *xl;   // x as FP32 pairs (compensated re-evaluation)
     const double *isd;      // 1 / sqrt(M2) at l (0: flat)
     int64_t n0, nl;
@@ -152,6 +157,25 @@ template <typename T> struct ExtArgs {
     ErrModel em;
 };
 template <typename T> void launch_extend(const ExtArgs<T> &a, cudaStream_t s);
+
+// Motif mode, after the extension of a length (Algorithm 4's decision):
+// bBestM = minDistAbs < minLbAbs -> every non-valid row left undefined;
+// else with fewer than `limit` non-valid rows -> those with lbMax <
+// minDistAbs recomputed, the others undefined; else the full profile (every
+// row recomputed). Undefined rows get ROW_SKIP and NaN / -1 as their value.
+template <typename T> struct SubmpArgs {
+    int64_t nl;
+    int32_t *flag;
+    T *thr;
+    const double *lbmax;
+    const unsigned long long *min_dist_abs, *min_lb_abs;
+    const unsigned long long *nonvalid;   // rows flagged by the extension
+    double limit;                         // n log(p) / log(n)
+    double *nnd;                          // m = 1 row of the current length
+    int32_t *nnj;
+    unsigned long long *stats;            // [10] undefined rows, [11] full profile
+};
+template <typename T> void launch_submp_mark(const SubmpArgs<T> &a, cudaStream_t s);
 
 template <typename T> struct MergeArgs {
     const double *x;

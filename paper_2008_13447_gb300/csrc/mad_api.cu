@@ -122,7 +122,8 @@ void check_options(mad_ctx *ctx, const mad_options &o)
     REQUIRE(o.precision == MAD_FP64 || o.precision == MAD_FP32, "precision must be MAD_FP64 or MAD_FP32");
     REQUIRE(o.k_max >= 1 && o.k_max <= KMAX, "k_max must be in [1, 64]");
     REQUIRE(o.m_max >= 1 && o.m_max <= MAXP, "m_max must be in [1, 64]");
-    REQUIRE(o.mode == 0, "mode must be 0");
+    REQUIRE(o.mode == 0 || o.mode == 1, "mode must be 0 (exact rows) or 1 (motif mode)");
+    REQUIRE(o.mode == 0 || o.m_max == 1, "motif mode reports the motif of each length only: m_max must be 1");
     REQUIRE(o.band_form == 0 || o.band_form == 1, "band_form must be 0 or 1");
 }
 
@@ -225,8 +226,15 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
     // per-length device counters: [0] rows left for a second pass, [1] certified,
     // [2] recomputed, [3] largest FP32-vs-FP64 correlation gap (bits),
     // [4] top-p insertions, [5] band units, [6] band cells
-    constexpr int NSTAT = 10;
+    // [10] motif mode: rows left undefined, [11] motif mode: full profile
+    constexpr int NSTAT = 12;
     unsigned long long *dstats = dalloc<unsigned long long>(ctx, s, (size_t)nL * NSTAT);
+    // motif mode: per-row bound of non-valid rows; per length the smallest
+    // certified distance and non-valid bound (+inf until reduced)
+    const bool motif_mode = o.mode == 1;
+    double *lbmax = motif_mode ? dalloc<double>(ctx, s, n0) : nullptr;
+    double *mm = motif_mode ? dalloc<double>(ctx, s, (size_t)2 * nL) : nullptr;
+    const double motif_limit = (double)n * std::log((double)p) / std::log((double)n);
     DiscTable tab{dalloc<double>(ctx, s, (size_t)k_max * m_max), dalloc<double>(ctx, s, (size_t)k_max * m_max),
                   dalloc<int32_t>(ctx, s, (size_t)k_max * m_max), dalloc<int32_t>(ctx, s, (size_t)k_max * m_max),
                   dalloc<int32_t>(ctx, s, (size_t)k_max * m_max)};
@@ -245,6 +253,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         CK(cudaMemcpyAsync(krows, kr.data(), K * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     }
     CK(cudaMemsetAsync(dstats, 0, (size_t)nL * NSTAT * sizeof(unsigned long long), st));
+    if (motif_mode) launch_fill<double>(mm, (int64_t)2 * nL, INFINITY, st);
     CK(cudaMemsetAsync(counters, 0, 4 * sizeof(int32_t), st));
     CK(cudaMemsetAsync(vm.len, 0, n0 * sizeof(int32_t), st));
     CK(cudaMemsetAsync(tab.len, 0, (size_t)k_max * m_max * sizeof(int32_t), st));
@@ -426,7 +435,18 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
             ea.out = lo;
             ea.thr = thr;
             ea.em = em;
+            if (motif_mode) {
+                ea.lbmax = lbmax;
+                ea.min_dist_abs = reinterpret_cast<unsigned long long *>(mm + 2 * li);
+                ea.min_lb_abs = reinterpret_cast<unsigned long long *>(mm + 2 * li + 1);
+            }
             launch_extend<T>(ea, st);
+            if (motif_mode) {
+                SubmpArgs<T> sm{nl, rs.flag, thr, lbmax, ea.min_dist_abs, ea.min_lb_abs, lo.stats + 2, motif_limit,
+                                nnd, nnj, lo.stats};
+                launch_submp_mark<T>(sm, st);
+                ++nlaunch;
+            }
             ++nlaunch;
         }
         CK(cudaGetLastError());
@@ -545,7 +565,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         launch_flat_rows(fa, st);
         CK(cudaEventRecord(ev_nnd, st));
         CK(cudaStreamWaitEvent(side.disc, ev_nnd, 0));
-        launch_discords_length(nnd, nnj, n0, nl, l, E, k_max, m_max, bval, bidx, tab, side.disc);
+        if (!motif_mode) launch_discords_length(nnd, nnj, n0, nl, l, E, k_max, m_max, bval, bidx, tab, side.disc);
         nlaunch += 3;
         if (o.keep_profiles) {
             CK(cudaMemcpyAsync(s.keep_nnd + (size_t)li * m_max * n0, nnd, (size_t)m_max * n0 * sizeof(double),
@@ -579,6 +599,9 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
         q.rows = n - (lmin + li) + 1;
         q.certified = (int64_t)h[1];
         q.recomputed = (int64_t)h[2];
+        q.skipped = (int64_t)h[10];
+        q.full_profile = (int32_t)h[11];
+        if (motif_mode && li > 0) q.recomputed = q.full_profile ? q.rows : (int64_t)(h[2] - h[10]);
         q.tiles = (int64_t)h[5];
         q.passes = q.recomputed > 0 ? (h[0] > 0 ? 2 : 1) : 0;
         unsigned long long bits = h[3];
@@ -832,6 +855,10 @@ MAD_API mad_status mad_discords(mad_ctx *ctx, int32_t series, int32_t k, int32_t
         }
         REQUIRE(k >= 1 && k <= s.k_max, "k must be in [1, k_max]");
         REQUIRE(m >= 1 && m <= s.m_max, "m must be in [1, m_max]");
+        if (ctx->opt.mode == 1) {
+            set_err(ctx, "the discord table needs mode 0 (exact rows); motif mode keeps no discord table");
+            throw Fail{MAD_ESTATE};
+        }
         cudaStream_t st = ctx->stream;
         const size_t cells = (size_t)s.k_max * s.m_max;
         std::vector<double> nd(cells), dd(cells);

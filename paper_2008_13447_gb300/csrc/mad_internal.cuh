@@ -48,7 +48,8 @@ template <typename T> inline int band_rpl(int p)
 template <typename T> struct __align__(4 * sizeof(T)) Col { T df, dg, inv, pad; };
 
 // Row flags of the per-length pipeline.
-enum : int32_t { ROW_DONE = 0, ROW_RECOMPUTE = 1, ROW_FLAT = 2, ROW_DIRECT = 3 };
+// ROW_SKIP: motif mode, a non-valid row left undefined at this length.
+enum : int32_t { ROW_DONE = 0, ROW_RECOMPUTE = 1, ROW_FLAT = 2, ROW_DIRECT = 3, ROW_SKIP = 4 };
 
 // Order-preserving maps from floating point to signed integers (for
 // atomicMax on shared or global memory).
