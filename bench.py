@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--band-form", type=int, default=0, choices=[0, 1],
                     help="0: full rows; 1: symmetric band form when most bands are active")
     ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the plain FP64 GPU path")
+    ap.add_argument("--no-motif-path", action="store_true", help="skip timing the motif mode (mode 1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
     ap.add_argument("--ncu-case", default=None, metavar="LMIN:LMAX",
@@ -342,6 +343,32 @@ def main():
                                 "speedup_of_fp32": (cells / (ms_per_step / 1e3)) / (cells / (ms64 / 1e3))}
         finally:
             mad.mad_destroy(c64)
+
+    # motif mode (Algorithm 1 with ComputeSubMP): the same workload, only the
+    # motif of each length guaranteed; one warm-up step, one timed step
+    if rank == 0 and not args.no_motif_path and m == 1:
+        cm = mad.mad_create_device(xt, precision=prec, k_max=k, m_max=1, stream=stream, mode=1)
+        try:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for rep in range(2):
+                flush.fill_(7)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                mad.mad_profile(cm, lmin, lmax, p)
+                mot1 = mad.mad_motifs(cm, 0, k)
+                e1.record(stream)
+                torch.cuda.synchronize()
+            ms1 = e0.elapsed_time(e1)
+            st1 = mad.mad_stats(cm, 0)
+            rows = sum(s["rows"] for s in st1)
+            comp = sum(s["rows"] if (i == 0 or s["full_profile"]) else s["recomputed"] for i, s in enumerate(st1))
+            out["motif_mode_path"] = {
+                "value": cells / (ms1 / 1e3), "ms_per_step": ms1,
+                "rows_computed_frac": comp / rows,
+                "full_profile_lengths": int(sum(s["full_profile"] for s in st1[1:])),
+                "top_motif": {kk: mot1[0][kk] for kk in ("a", "b", "len", "dist", "dist_recheck")} if mot1 else None}
+        finally:
+            mad.mad_destroy(cm)
 
     # end to end through the public API with host buffers (pinned input)
     pinned = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
