@@ -132,9 +132,19 @@ __device__ __forceinline__ double dq_row(const ErrModel &em, int64_t i)
 // entries.
 template <int PM> struct RowEnts {
     double q[PM];    // correlation (estimate)
+    long long qk[PM];  // q as an order-preserving integer (ranking on the integer pipe)
     float dq[PM];    // its error bound
     int32_t j[PM];   // partner offset, -1 = empty
 };
+
+// Order-preserving map of a double (not NaN) to a signed 64-bit integer:
+// comparisons of the images order like the doubles, on the integer pipe
+// instead of GB300's 1/64-rate FP64 pipe.
+__device__ __forceinline__ long long ord64(double v)
+{
+    const long long b = __double_as_longlong(v);
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
 
 template <int PM, typename F>
 __device__ __forceinline__ void for_pm(F &&f)
@@ -148,10 +158,10 @@ __device__ __forceinline__ void for_pm(F &&f)
     }
 }
 
-// (q desc, j asc): does (qa, ja) come before (qb, jb)?
-__device__ __forceinline__ bool q_before(double qa, int32_t ja, double qb, int32_t jb)
+// (key desc, j asc) on the integer images of q.
+__device__ __forceinline__ bool qk_before(long long ka, int32_t ja, long long kb, int32_t jb)
 {
-    return qa > qb || (qa == qb && ja < jb);
+    return ka > kb || (ka == kb && ja < jb);
 }
 
 // Rank of every entry in (q desc, j asc) order (0 = best).
@@ -160,7 +170,7 @@ __device__ __forceinline__ void corr_ranks(const RowEnts<PM> &r, int (&rk)[PM])
 {
     for_pm<PM>([&](int a) {
         int k = 0;
-        for_pm<PM>([&](int b) { k += (r.j[b] >= 0 && q_before(r.q[b], r.j[b], r.q[a], r.j[a])); });
+        for_pm<PM>([&](int b) { k += (r.j[b] >= 0 && qk_before(r.qk[b], r.j[b], r.qk[a], r.j[a])); });
         rk[a] = k;
     });
 }
@@ -212,6 +222,7 @@ __device__ void refine_reported(const double *x, const float *xh, const float *x
         for_pm<PM>([&](int a) {
             if (a == hit) {
                 r.q[a] = q;
+                r.qk[a] = ord64(q);
                 r.dq[a] = dqn;
             }
         });
@@ -295,6 +306,7 @@ __device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i, double
         if (dropped[e]) j = -1;
         r.j[e] = j;
         r.q[e] = -pinf();
+        r.qk[e] = ord64(-pinf());
         r.dq[e] = 0.0f;
         cn[e] = 0.0;
     });
@@ -305,6 +317,7 @@ __device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i, double
         cn[e] = fma(wgt * xi, A.x[j + l - 1] - A.mu_prev[j], A.st.ent_c[at]);
         const bool flat_j = A.run[j] >= l;
         r.q[e] = corr_isd(cn[e], isdi, A.isd[j], flat_j);
+        r.qk[e] = ord64(r.q[e]);
         r.dq[e] = flat_j ? 0.0f : A.st.ent_dq[at];
     });
     int cnt = 0;
@@ -324,11 +337,15 @@ __device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i, double
     bool ok = false;
     if (cnt >= m) {
         double dp[PM];
-        for_pm<PM>([&](int a) { dp[a] = r.j[a] >= 0 ? 2.0 * l * (1.0 - clamp_q(r.q[a] - r.dq[a])) : pinf(); });
+        long long dk[PM];
+        for_pm<PM>([&](int a) {
+            dp[a] = r.j[a] >= 0 ? 2.0 * l * (1.0 - clamp_q(r.q[a] - r.dq[a])) : pinf();
+            dk[a] = ord64(dp[a]);
+        });
         double dm = pinf();
         for_pm<PM>([&](int a) {
             int k = 0;
-            for_pm<PM>([&](int b) { k += (r.j[b] >= 0 && (dp[b] < dp[a] || (dp[b] == dp[a] && b < a))); });
+            for_pm<PM>([&](int b) { k += (r.j[b] >= 0 && (dk[b] < dk[a] || (dk[b] == dk[a] && b < a))); });
             if (r.j[a] >= 0 && k == m - 1) dm = dp[a];
         });
         ok = dm < B * B;
@@ -578,6 +595,7 @@ __global__ void k_merge(MergeArgs<T> A)
     for_pm<PM>([&](int e) {
         r.j[e] = -1;
         r.q[e] = -pinf();
+        r.qk[e] = ord64(-pinf());
         r.dq[e] = 0.0f;
         if (e >= p) return;
         const int64_t at = (int64_t)e * n0 + i;
@@ -592,6 +610,7 @@ __global__ void k_merge(MergeArgs<T> A)
             A.st.ent_dq[at] = dq;
             r.j[e] = j;
             r.q[e] = corr_isd(c, isdi, A.isd[j], flat_j);
+            r.qk[e] = ord64(r.q[e]);
             r.dq[e] = dq;
         } else {
             A.st.ent_j[at] = -1;
