@@ -59,7 +59,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp%d" % os.getpid()
-        run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+        run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -552,6 +552,15 @@ static const void *band_fn(int mode, int rpl)
     }
 }
 
+// Shared-memory opt-in of each band kernel variant, once per device.
+template <typename T>
+static void band_optin(int mode, int rpl)
+{
+    static std::once_flag once[3][3][64];
+    const int ri = rpl == 4 ? 0 : (rpl == 2 ? 1 : 2);
+    smem_optin_max(band_fn<T>(mode, rpl), once[mode][ri]);
+}
+
 template <typename T>
 int band_occupancy(bool bins_mode, int p, int rpl)
 {
@@ -559,7 +568,7 @@ int band_occupancy(bool bins_mode, int p, int rpl)
     for (int mode : {bins_mode ? (int)MODE_BINS : (int)MODE_TOPP, bins_mode ? (int)MODE_BINS : (int)MODE_SYM}) {
         const void *fn = band_fn<T>(mode, rpl);
         const size_t sm = band_smem<T>(bins_mode, p, rpl);
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return 0;
+        band_optin<T>(mode, rpl);
         int blocks = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, BAND_NW * 32, sm) != cudaSuccess) return 0;
         worst = blocks < worst ? blocks : worst;
@@ -572,7 +581,7 @@ static void launch_mode(const BandArgs<T> &a, int mode, bool bins_mode, int grid
 {
     const size_t sm = band_smem<T>(bins_mode, a.p, a.rpl);
     const void *fn = band_fn<T>(mode, a.rpl);
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    band_optin<T>(mode, a.rpl);
     void *args[] = {const_cast<BandArgs<T> *>(&a)};
     cudaLaunchKernel(fn, dim3(grid), dim3(BAND_NW * 32), args, sm, s);
 }

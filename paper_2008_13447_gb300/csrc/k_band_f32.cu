@@ -150,7 +150,8 @@ void launch_seed<float>(const SeedArgs<float> &a, cudaStream_t s)
     dim3 grid((unsigned)((a.spitch + SEED_TILE - 1) / SEED_TILE), (unsigned)((a.nk + SEED_ROWS - 1) / SEED_ROWS));
     const int l4 = seed_l4(a.l);
     const size_t sm = sizeof(float) * (4 * (size_t)l4 + SEED_TILE + l4 + 4);
-    cudaFuncSetAttribute(k_seed_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static std::once_flag once[64];
+    smem_optin_max((const void *)k_seed_f32, once);
     k_seed_f32<<<grid, SEED_THREADS, sm, s>>>(a);
 }
 

@@ -43,7 +43,8 @@ void launch_seed<double>(const SeedArgs<double> &a, cudaStream_t s)
     const int B = 256;
     dim3 grid((unsigned)((a.spitch + B - 1) / B), (unsigned)a.nk);
     const size_t sm = sizeof(double) * a.l;
-    cudaFuncSetAttribute(k_seed<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static std::once_flag once[64];
+    smem_optin_max((const void *)k_seed<double>, once);
     k_seed<double><<<grid, B, sm, s>>>(a);
 }
 template void launch_band<double>(const BandArgs<double> &, bool, int, cudaStream_t);

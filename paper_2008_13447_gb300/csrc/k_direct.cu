@@ -155,11 +155,10 @@ __global__ void __launch_bounds__(DTHREADS) k_direct(DirectArgs<T> A)
 template <typename T>
 void launch_direct(const DirectArgs<T> &a, int grid, cudaStream_t s)
 {
-    // the opt-in covers dynamic plus static shared memory above 48 KB, so it
-    // is set for every launch rather than only when the dynamic part alone
-    // crosses that line
+    // (the opt-in covers dynamic plus static shared memory above 48 KB)
     const size_t sm = sizeof(T) * ((size_t)a.l * DR + DCOLS + a.l);
-    cudaFuncSetAttribute(k_direct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static std::once_flag once[64];
+    smem_optin_max((const void *)k_direct<T>, once);
     k_direct<T><<<grid, DTHREADS, sm, s>>>(a);
 }
 template void launch_direct<float>(const DirectArgs<float> &, int, cudaStream_t);

@@ -145,8 +145,8 @@ void launch_discords_length(const double *nnd, const int32_t *nnj, int64_t n0, i
     const int nblk = (int)((nl + DBLK - 1) / DBLK);
     k_disc_blockmax<<<dim3(nblk, m_max), DBLK, 0, s>>>(nnd, n0, nl, nblk, bval, bidx);
     const size_t sm = (size_t)nblk * (sizeof(double) + sizeof(int32_t));
-    // set on every launch: the 48 KB line counts static shared memory too
-    cudaFuncSetAttribute(k_disc_greedy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static std::once_flag once[64];
+    smem_optin_max((const void *)k_disc_greedy, once);
     k_disc_greedy<<<m_max, 1024, sm, s>>>(nnd, nnj, n0, nl, l, E, k_max, m_max, bval, bidx, nblk, tab);
 }
 

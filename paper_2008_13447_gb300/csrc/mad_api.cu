@@ -17,8 +17,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "mad.h"
@@ -63,10 +65,17 @@ struct Fail {
     mad_status st;
 };
 
+// (the batch path profiles series from several host threads)
+std::mutex g_err_mu;
+
 void set_err(mad_ctx *c, const std::string &m)
 {
-    if (c) c->err = m;
-    else g_create_err = m;
+    if (c) {
+        std::lock_guard<std::mutex> lock(g_err_mu);
+        c->err = m;
+    } else {
+        g_create_err = m;
+    }
 }
 
 #define CK(call)                                                                                   \
@@ -156,10 +165,9 @@ struct Precision<float> {
 };
 
 template <typename T>
-void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
+void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStream_t st)
 {
     const mad_options &o = ctx->opt;
-    cudaStream_t st = ctx->stream;
     const int num = o.excl_num, den = o.excl_den;
     const int64_t n = s.n;
     REQUIRE(lmin >= 2 && lmin <= lmax, "need 2 <= lmin <= lmax");
@@ -633,10 +641,10 @@ Series &get_series(mad_ctx *ctx, int32_t idx)
     return ctx->series[idx];
 }
 
-void profile_one(mad_ctx *ctx, Series &s, int lmin, int lmax, int p)
+void profile_one(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStream_t st)
 {
-    if (ctx->opt.precision == MAD_FP32) profile_series<float>(ctx, s, lmin, lmax, p);
-    else profile_series<double>(ctx, s, lmin, lmax, p);
+    if (ctx->opt.precision == MAD_FP32) profile_series<float>(ctx, s, lmin, lmax, p, st);
+    else profile_series<double>(ctx, s, lmin, lmax, p, st);
 }
 
 template <typename F>
@@ -769,7 +777,7 @@ MAD_API mad_status mad_profile(mad_ctx *ctx, int32_t lmin, int32_t lmax, int32_t
     if (!ctx) { g_create_err = "ctx is NULL"; return MAD_EINVAL; }
     return run_guarded(ctx, [&] {
         REQUIRE(ctx->series.size() == 1, "context holds several series: use mad_profile_batch");
-        profile_one(ctx, ctx->series[0], lmin, lmax, p);
+        profile_one(ctx, ctx->series[0], lmin, lmax, p, ctx->stream);
     });
 }
 
@@ -778,7 +786,51 @@ MAD_API mad_status mad_profile_batch(mad_ctx *ctx, const int32_t *lmin, const in
     if (!ctx) { g_create_err = "ctx is NULL"; return MAD_EINVAL; }
     return run_guarded(ctx, [&] {
         REQUIRE(lmin != nullptr && lmax != nullptr, "lmin / lmax arrays are NULL");
-        for (size_t s = 0; s < ctx->series.size(); ++s) profile_one(ctx, ctx->series[s], lmin[s], lmax[s], p);
+        // Series are independent: a few host threads, each with its own
+        // stream, profile them concurrently (small series, whose per-length
+        // pipelines are latency-bound, overlap one another). Every stream
+        // first waits for the context's stream (where the inputs were
+        // written); each profile synchronises its own stream before it
+        // returns, so all work is done when the threads are joined.
+        const int count = (int)ctx->series.size();
+        const int nw = count < 8 ? count : 8;
+        std::vector<cudaStream_t> ws(nw, nullptr);
+        cudaEvent_t ready = nullptr;
+        struct Guard {
+            std::vector<cudaStream_t> &ws;
+            cudaEvent_t &ev;
+            ~Guard()
+            {
+                for (cudaStream_t q : ws)
+                    if (q) cudaStreamDestroy(q);
+                if (ev) cudaEventDestroy(ev);
+            }
+        } guard{ws, ready};
+        CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+        CK(cudaEventRecord(ready, ctx->stream));
+        for (cudaStream_t &q : ws) {
+            CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+            CK(cudaStreamWaitEvent(q, ready, 0));
+        }
+        std::vector<mad_status> res(nw, MAD_OK);
+        std::vector<std::thread> th;
+        for (int t = 0; t < nw; ++t)
+            th.emplace_back([&, t] {
+                cudaSetDevice(ctx->device);
+                for (int k = t; k < count && res[t] == MAD_OK; k += nw) {
+                    try {
+                        profile_one(ctx, ctx->series[k], lmin[k], lmax[k], p, ws[t]);
+                    } catch (const Fail &e) {
+                        res[t] = e.st;
+                    } catch (...) {
+                        set_err(ctx, "internal error");
+                        res[t] = MAD_EINTERNAL;
+                    }
+                }
+            });
+        for (std::thread &x : th) x.join();
+        for (mad_status r : res)
+            if (r != MAD_OK) throw Fail{r};
     });
 }
 

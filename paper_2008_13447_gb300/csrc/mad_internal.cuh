@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 namespace mad {
 
 constexpr int CH = 32;              // columns per wavefront chunk (one per lane)
@@ -46,6 +48,25 @@ template <typename T> inline int band_rpl(int p)
 // The centred co-moment then obeys, along every diagonal,
 //   C(i, j) = C(i-1, j-1) + df_{i-1} dg_{j-1} + df_{j-1} dg_{i-1}.
 template <typename T> struct __align__(4 * sizeof(T)) Col { T df, dg, inv, pad; };
+
+// Dynamic shared-memory opt-in of kernel `fn` raised, once per device, to the
+// largest the device allows next to the kernel's static shared memory. Set
+// per launch instead, a smaller value set by one host thread could meet
+// another thread's larger launch (the batch path profiles series from
+// several threads).
+inline void smem_optin_max(const void *fn, std::once_flag (&once)[64])
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::call_once(once[dev], [fn, dev] {
+        int mx = 0;
+        cudaFuncAttributes fa{};
+        if (cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, fn) != cudaSuccess)
+            return;
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes);
+    });
+}
 
 // Row flags of the per-length pipeline.
 // ROW_SKIP: motif mode, a non-valid row left undefined at this length.
