@@ -69,6 +69,7 @@ def _L():
             "orc_valmod_motif": (None, [P, i64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                         P, P, P, P, P, P]),
             "orc_topk_motifs": (C.c_int, [i64, P, P, P, P, C.c_int, C.c_int, C.c_int, P, P, P, P, P]),
+            "orc_motif_sets": (None, [P, i64, C.c_int, P, P, P, P, d, C.c_int, C.c_int, C.c_int, P, P]),
             "orc_discords_one_length": (C.c_int, [i64, P, P, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P]),
             "orc_discords": (None, [i64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P, P,
                                     P, P, P, P, P]),
@@ -240,6 +241,21 @@ def topk_motifs(valmp, k, num=1, den=4):
     got = _L().orc_topk_motifs(len(d), _p(d), _p(nd), _p(ln), _p(nn), num, den, k,
                                _p(a), _p(b), _p(L), _p(od), _p(ond))
     return [(int(a[r]), int(b[r]), int(L[r]), float(od[r]), float(ond[r])) for r in range(got)]
+
+
+def motif_sets(x, pairs, D, cap, num=1, den=4):
+    """Motif sets grown from motif pairs [(a, b, len, dist), ...] with radius
+    D * dist: list of member offset lists (a, b first)."""
+    x = _f64(x)
+    k = len(pairs)
+    a = np.array([p[0] for p in pairs], np.int64)
+    b = np.array([p[1] for p in pairs], np.int64)
+    L = np.array([p[2] for p in pairs], np.int32)
+    d = np.array([p[3] for p in pairs], np.float64)
+    mem = np.zeros((k, cap), np.int64)
+    cnt = np.zeros(k, np.int32)
+    _L().orc_motif_sets(_p(x), len(x), k, _p(a), _p(b), _p(L), _p(d), float(D), num, den, cap, _p(mem), _p(cnt))
+    return [list(mem[s, :cnt[s]]) for s in range(k)]
 
 
 def discords_one_length(score, l, k, nbr=None, num=1, den=4):

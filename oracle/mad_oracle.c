@@ -480,6 +480,8 @@ void orc_valmod_pruned(const double *x, i64 n, int lmin, int lmax, int num, int 
     free(nnj);
 }
 
+static i64 iabs64(i64 v) { return v < 0 ? -v : v; }
+
 /* The paper-literal pruned iteration (Algorithm 1 with ComputeSubMP,
  * Algorithm 4), whose guarantee is the motif of every length, not every
  * row: at lmin the full matrix profile (Algorithm 3); at every longer length
@@ -631,6 +633,66 @@ void orc_valmod_motif(const double *x, i64 n, int lmin, int lmax, int num, int d
     free(state);
 }
 
+/* Variable-length motif sets (Sec. "Finding Motif Sets", Algorithm 6): for
+ * each motif pair s (offsets a_s, b_s at length l_s with distance d_s, in
+ * the order given) and radius r_s = D * d_s, the set is grown from the pair:
+ *  - candidates: windows j at l_s with min(d(a_s, j), d(b_s, j)) <= r_s that
+ *    are not trivial matches of a_s or b_s (|j - a_s|, |j - b_s| > E(l_s)),
+ *    and do not lie within max(E(l_s), E(l_t)) of a member of an earlier set
+ *    t (the used subsequences leave the search space, so sets never meet);
+ *  - a_s and b_s are members first; then candidates by (min distance,
+ *    offset) ascending, each accepted unless within E(l_s) of an accepted
+ *    member (the merge that removes trivial matches), until cap members.
+ * Writes members[s * cap + 0..counts[s]) (a_s, b_s, then in acceptance
+ * order). Distances are the FP64 distance profiles by definition. */
+void orc_motif_sets(const double *x, i64 n, int k, const i64 *a, const i64 *b, const int32_t *len,
+                    const double *dist, double D, int num, int den, int cap, i64 *members, int32_t *counts)
+{
+    i64 nmax = n;
+    double *pa = (double *)malloc(sizeof(double) * (size_t)nmax);
+    double *pb = (double *)malloc(sizeof(double) * (size_t)nmax);
+    dj_t *cand = (dj_t *)malloc(sizeof(dj_t) * (size_t)nmax);
+    for (int s = 0; s < k; ++s) {
+        int l = len[s];
+        i64 nl = n - l + 1, E = orc_excl(l, num, den);
+        double r = D * dist[s];
+        orc_distance_profile(x, n, l, num, den, a[s], pa);
+        orc_distance_profile(x, n, l, num, den, b[s], pb);
+        i64 c = 0;
+        for (i64 j = 0; j < nl; ++j) {
+            if (iabs64(j - a[s]) <= E || iabs64(j - b[s]) <= E) continue;
+            double d = fmin(pa[j], pb[j]);
+            if (!(d <= r)) continue;
+            int used = 0;
+            for (int t = 0; t < s && !used; ++t) {
+                i64 Et = orc_excl(len[t], num, den);
+                i64 Em = E > Et ? E : Et;
+                for (int u = 0; u < counts[t] && !used; ++u)
+                    if (iabs64(j - members[(i64)t * cap + u]) <= Em) used = 1;
+            }
+            if (used) continue;
+            cand[c].d = d;
+            cand[c].j = j;
+            ++c;
+        }
+        qsort(cand, (size_t)c, sizeof(dj_t), cmp_dj);
+        i64 *m = members + (i64)s * cap;
+        int cnt = 0;
+        if (cnt < cap) m[cnt++] = a[s];
+        if (cnt < cap) m[cnt++] = b[s];
+        for (i64 t = 0; t < c && cnt < cap; ++t) {
+            int ok = 1;
+            for (int u = 0; u < cnt && ok; ++u)
+                if (iabs64(cand[t].j - m[u]) <= E) ok = 0;
+            if (ok) m[cnt++] = cand[t].j;
+        }
+        counts[s] = cnt;
+    }
+    free(pa);
+    free(pb);
+    free(cand);
+}
+
 /* ------------------------------------------------------------ read-outs */
 
 typedef struct { double key; i64 i; } ki_t;
@@ -651,7 +713,6 @@ static int cmp_key_desc(const void *a, const void *b)
     return (u->i < v->i) ? -1 : (u->i > v->i);
 }
 
-static i64 iabs64(i64 v) { return v < 0 ? -v : v; }
 
 /* Top-k length-normalised motif pairs from VALMP (the ranking kept by
  * Algorithm 5's heap of best pairs, with the trivial-match removal of the

@@ -359,6 +359,86 @@ def test_motif_mode_finds_every_lengths_motif(gen, n, lmin, lmax, p):
         assert computed < 0.5 * st[1:, 0].sum()       # it pruned (full profiles included)
 
 
+def _znorm_dist(x, l, i, j):
+    a, b = x[i:i + l], x[j:j + l]
+    za, zb = (a - a.mean()) / a.std(), (b - b.mean()) / b.std()
+    return float(np.sqrt(((za - zb) ** 2).sum()))
+
+
+def test_motif_set_contains_planted_copies():
+    # four noisy copies of one pattern in a random walk: the set grown from
+    # the best pair holds all four (Sec. "Finding Motif Sets")
+    rng = np.random.default_rng(61)
+    n, L = 3000, 40
+    x = np.cumsum(rng.standard_normal(n))
+    pat = 3.0 * np.sin(np.linspace(0, 4 * np.pi, L)) * np.hanning(L)
+    offs = [300, 1000, 1700, 2400]
+    for o in offs:
+        seg = x[o:o + L]
+        x[o:o + L] = seg.mean() + pat * seg.std() + 0.05 * seg.std() * rng.standard_normal(L)
+    pl = oracle.valmp_plain(x, L, L)
+    top = oracle.topk_motifs(pl, 1)[0]
+    sets = oracle.motif_sets(x, [(top[0], top[1], top[2], top[3])], D=4.0, cap=16)
+    got = sets[0]
+    for o in offs:
+        assert any(abs(m - o) <= oracle.excl(L) for m in got), (o, got)
+
+
+def test_motif_sets_brute_force_tiny():
+    # the same growth rule restated with numpy distances on a tiny series
+    x = workloads.random_walk(260, 62)
+    l, num, den = 12, 1, 4
+    E = int(np.ceil(l * num / den))
+    nl = len(x) - l + 1
+    pl = oracle.valmp_plain(x, l, l + 3)
+    pairs = [(a, b, L, d) for a, b, L, d, _ in oracle.topk_motifs(pl, 3)]
+    got = oracle.motif_sets(x, pairs, D=1.6, cap=10)
+    used = []                           # (offset, length) of earlier members
+    for (a, b, L, d), g in zip(pairs, got):
+        EL = int(np.ceil(L * num / den))
+        nL = len(x) - L + 1
+        r = 1.6 * d
+        cand = []
+        for j in range(nL):
+            if abs(j - a) <= EL or abs(j - b) <= EL:
+                continue
+            dj = min(_znorm_dist(x, L, a, j), _znorm_dist(x, L, b, j))
+            if dj > r + 1e-9:
+                continue
+            if any(abs(j - m) <= max(EL, int(np.ceil(Lm * num / den))) for m, Lm in used):
+                continue
+            cand.append((dj, j))
+        cand.sort()
+        mem = [a, b]
+        for dj, j in cand:
+            if len(mem) >= 10:
+                break
+            if all(abs(j - m) > EL for m in mem):
+                mem.append(j)
+        assert [int(v) for v in g] == mem
+        used += [(m, L) for m in mem]
+
+
+def test_motif_set_properties():
+    x = workloads.ar2(2000, 63)
+    lmin, lmax = 24, 32
+    pl = oracle.valmp_plain(x, lmin, lmax)
+    pairs = [(a, b, L, d) for a, b, L, d, _ in oracle.topk_motifs(pl, 4)]
+    sets = oracle.motif_sets(x, pairs, D=2.0, cap=12)
+    seen = []
+    for (a, b, L, d), mem in zip(pairs, sets):
+        E = oracle.excl(L)
+        assert mem[0] == a and mem[1] == b and len(mem) <= 12
+        for i, m in enumerate(mem[2:]):
+            assert min(oracle.dist(x, L, a, m), oracle.dist(x, L, b, m)) <= 2.0 * d + 1e-9
+        for i in range(len(mem)):
+            for j in range(i + 1, len(mem)):
+                assert abs(mem[i] - mem[j]) > E
+        for m in mem[2:]:
+            assert all(abs(m - u) > max(E, oracle.excl(Lu)) for u, Lu in seen)
+        seen += [(m, L) for m in mem]
+
+
 # ---------------------------------------------------------------- read-outs
 
 def test_topk_motif_planted_pair():
