@@ -182,6 +182,28 @@ MAD_API mad_status mad_profile_batch(mad_ctx *ctx, const int32_t *lmin, const in
 MAD_API mad_status mad_motifs(mad_ctx *ctx, int32_t series, int32_t k, mad_motif *out,
                               int32_t *n_out);
 
+/* Variable-length motif sets (Sec. "Finding Motif Sets", Algorithm 6) grown
+ * from the top-k motif pairs of mad_motifs: set s starts from pair s
+ * (offsets a < b at length len) with radius = D * the pair's FP64 distance;
+ * it adds, by (distance, offset) ascending, windows j at len whose FP64
+ * distance to a or to b is at most the radius, that are not trivial matches
+ * of a, b or an accepted member (|j - m| <= E(len)), and that do not lie
+ * within max(E(len), E(len')) of a member of an earlier set (sets never
+ * meet), up to cap members (a and b first).
+ *   sets     host, k entries; sets[s].count members written
+ *   members  host, k x cap offsets, row s for set s
+ *   *n_out   the number of sets (the number of motif pairs found, <= k).
+ * Requires 2 <= cap <= 256, D >= 0, k in [1, 64]. */
+typedef struct {
+    int64_t a, b;           /* the motif pair */
+    int32_t len;            /* its length */
+    int32_t count;          /* members written */
+    double radius;          /* D times the pair's FP64 distance */
+} mad_motif_set;
+
+MAD_API mad_status mad_motif_sets(mad_ctx *ctx, int32_t series, int32_t k, double D, int32_t cap,
+                                  mad_motif_set *sets, int64_t *members, int32_t *n_out);
+
 /* The k x m block (ranks 1..k, columns 1..m) of dkm_{lmin,lmax}: per length
  * and column, offsets ranked by m-th best-match distance descending (ties:
  * smaller offset) with pairwise non-trivial picks; across lengths each cell

@@ -31,7 +31,7 @@ STATUS_NAMES = {0: "MAD_OK", 1: "MAD_EINVAL", 2: "MAD_ENOMEM", 3: "MAD_ECUDA", 4
                 5: "MAD_ETIMEOUT", 6: "MAD_EINTERNAL"}
 ABI_FUNCTIONS = ("mad_create", "mad_create_device", "mad_create_batch", "mad_profile", "mad_profile_batch",
                  "mad_motifs", "mad_discords", "mad_valmp", "mad_matrix_profile", "mad_stats",
-                 "mad_mth_nn_dist_noalloc", "mad_last_error", "mad_destroy")
+                 "mad_mth_nn_dist_noalloc", "mad_motif_sets", "mad_last_error", "mad_destroy")
 
 
 class mad_options(C.Structure):
@@ -59,6 +59,11 @@ class mad_length_stats(C.Structure):
                 ("band_ms", C.c_double),
                 ("fp32_dq_max", C.c_double), ("skipped", C.c_int64), ("full_profile", C.c_int32),
                 ("reserved2", C.c_int32)]
+
+
+class mad_motif_set(C.Structure):
+    _fields_ = [("a", C.c_int64), ("b", C.c_int64), ("len", C.c_int32), ("count", C.c_int32),
+                ("radius", C.c_double)]
 
 
 class MadError(RuntimeError):
@@ -90,6 +95,7 @@ def library() -> C.CDLL:
             "mad_matrix_profile": [P, i32, i32, P, P, P, P],
             "mad_stats": [P, i32, C.POINTER(mad_length_stats), i32, C.POINTER(i32)],
             "mad_mth_nn_dist_noalloc": [P, i64, P, i32, i32, i32, i32, P, P],
+            "mad_motif_sets": [P, i32, i32, C.c_double, i32, C.POINTER(mad_motif_set), P, C.POINTER(i32)],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -177,6 +183,17 @@ def mad_motifs(ctx, series, k):
     _check(library().mad_motifs(ctx, series, k, out, C.byref(n)), ctx)
     return [dict(a=m.a, b=m.b, len=m.len, dist=m.dist, norm_dist=m.norm_dist, dist_recheck=m.dist_recheck)
             for m in out[:n.value]]
+
+
+def mad_motif_sets(ctx, series, k, D, cap):
+    """Motif sets grown from the top-k motif pairs: list of dicts
+    (a, b, len, radius, members)."""
+    sets = (mad_motif_set * k)()
+    mem = np.zeros((k, cap), np.int64)
+    n = C.c_int32()
+    _check(library().mad_motif_sets(ctx, series, k, float(D), cap, sets, _p(mem), C.byref(n)), ctx)
+    return [dict(a=s.a, b=s.b, len=s.len, radius=s.radius, members=list(mem[i, :s.count]))
+            for i, s in enumerate(sets[:n.value])]
 
 
 def mad_discords(ctx, series, k, m):

@@ -177,6 +177,25 @@ template <typename T> struct SubmpArgs {
 };
 template <typename T> void launch_submp_mark(const SubmpArgs<T> &a, cudaStream_t s);
 
+// ----------------------------------------------------------------- k_sets.cu
+// One motif set grown from the pair (a, b) at length l with radius r.
+struct SetArgs {
+    const double *x;
+    int64_t n;
+    int l;
+    int64_t E;                 // E(l)
+    int64_t a, b;
+    double r;
+    const int64_t *prev_off;   // members of earlier sets ...
+    const int64_t *prev_E;     // ... and E of their lengths
+    int nprev;
+    double *ckey;              // candidate list (distance, offset), capacity capc
+    int32_t *cj;
+    int32_t *ccount;
+    int64_t capc;
+};
+void launch_motif_set(const SetArgs &a, int cap, int64_t *members, int32_t *mcount, cudaStream_t s);
+
 template <typename T> struct MergeArgs {
     const double *x;
     const float *xh, *xl;

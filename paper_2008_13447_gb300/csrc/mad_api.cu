@@ -87,6 +87,14 @@ void set_err(mad_ctx *c, const std::string &m)
         }                                                                                          \
     } while (0)
 
+#define REQUIRE_RET(cond, msg)                                                                     \
+    do {                                                                                           \
+        if (!(cond)) {                                                                             \
+            set_err(ctx, msg);                                                                     \
+            return MAD_EINVAL;                                                                     \
+        }                                                                                          \
+    } while (0)
+
 #define REQUIRE(cond, msg)                                                                         \
     do {                                                                                           \
         if (!(cond)) {                                                                             \
@@ -884,6 +892,91 @@ MAD_API mad_status mad_motifs(mad_ctx *ctx, int32_t series, int32_t k, mad_motif
                 m.dist = hd[hp[r]];
                 m.norm_dist = hn[hp[r]];
                 m.dist_recheck = hr[r];
+            }
+            *n_out = got;
+        } catch (...) {
+            for (void *p : tmp) cudaFree(p);
+            throw;
+        }
+        for (void *p : tmp) cudaFree(p);
+    });
+}
+
+MAD_API mad_status mad_motif_sets(mad_ctx *ctx, int32_t series, int32_t k, double D, int32_t cap,
+                                  mad_motif_set *sets, int64_t *members, int32_t *n_out)
+{
+    if (!ctx) { g_create_err = "ctx is NULL"; return MAD_EINVAL; }
+    // the motif pairs first (a call of its own, which validates the series
+    // and its state)
+    REQUIRE_RET(sets != nullptr && members != nullptr && n_out != nullptr, "output pointers are NULL");
+    REQUIRE_RET(k >= 1 && k <= 64, "k must be in [1, 64]");
+    REQUIRE_RET(cap >= 2 && cap <= 256, "cap must be in [2, 256]");
+    REQUIRE_RET(D >= 0.0 && D <= 1e300, "D must be a finite number >= 0");
+    std::vector<mad_motif> mot(k);
+    int32_t got = 0;
+    const mad_status ms = mad_motifs(ctx, series, k, mot.data(), &got);
+    if (ms != MAD_OK) return ms;
+    return run_guarded(ctx, [&] {
+        Series &s = get_series(ctx, series);
+        cudaStream_t st = ctx->stream;
+        const int num = ctx->opt.excl_num, den = ctx->opt.excl_den;
+        std::vector<void *> tmp;
+        auto talloc = [&](size_t bytes) {
+            void *p = nullptr;
+            CK(cudaMalloc(&p, bytes > 0 ? bytes : 1));
+            tmp.push_back(p);
+            return p;
+        };
+        try {
+            const int64_t capc = s.n0;
+            double *ckey = (double *)talloc(sizeof(double) * capc);
+            int32_t *cj = (int32_t *)talloc(sizeof(int32_t) * capc);
+            int32_t *ccount = (int32_t *)talloc(sizeof(int32_t));
+            int64_t *dmem = (int64_t *)talloc(sizeof(int64_t) * cap);
+            int32_t *dcnt = (int32_t *)talloc(sizeof(int32_t));
+            int64_t *poff = (int64_t *)talloc(sizeof(int64_t) * (size_t)k * cap);
+            int64_t *pE = (int64_t *)talloc(sizeof(int64_t) * (size_t)k * cap);
+            std::vector<int64_t> hoff, hE;
+            for (int si = 0; si < got; ++si) {
+                const mad_motif &m = mot[si];
+                const int l = m.len;
+                SetArgs a{};
+                a.x = s.x;
+                a.n = s.n;
+                a.l = l;
+                a.E = excl_zone(l, num, den);
+                a.a = m.a;
+                a.b = m.b;
+                a.r = D * m.dist_recheck;
+                a.nprev = (int)hoff.size();
+                if (a.nprev > 0) {
+                    CK(cudaMemcpyAsync(poff, hoff.data(), sizeof(int64_t) * hoff.size(), cudaMemcpyHostToDevice, st));
+                    CK(cudaMemcpyAsync(pE, hE.data(), sizeof(int64_t) * hE.size(), cudaMemcpyHostToDevice, st));
+                }
+                a.prev_off = poff;
+                a.prev_E = pE;
+                a.ckey = ckey;
+                a.cj = cj;
+                a.ccount = ccount;
+                a.capc = capc;
+                CK(cudaMemsetAsync(ccount, 0, sizeof(int32_t), st));
+                launch_motif_set(a, cap, dmem, dcnt, st);
+                CK(cudaGetLastError());
+                int32_t hc = 0;
+                CK(cudaMemcpyAsync(&hc, dcnt, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                CK(cudaMemcpyAsync(members + (size_t)si * cap, dmem, sizeof(int64_t) * hc, cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                mad_motif_set &o = sets[si];
+                o.a = m.a;
+                o.b = m.b;
+                o.len = l;
+                o.count = hc;
+                o.radius = a.r;
+                for (int t = 0; t < hc; ++t) {
+                    hoff.push_back(members[(size_t)si * cap + t]);
+                    hE.push_back(a.E);
+                }
             }
             *n_out = got;
         } catch (...) {
