@@ -65,7 +65,7 @@ def _L():
             "orc_valmp_plain": (None, [P, i64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                        P, P, P, P, P, P]),
             "orc_valmod_pruned": (None, [P, i64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
-                                         P, P, P, P, P, P, P]),
+                                         P, P, P, P, P, P, P, C.c_int, P, P]),
             "orc_valmod_motif": (None, [P, i64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                         P, P, P, P, P, P]),
             "orc_topk_motifs": (C.c_int, [i64, P, P, P, P, C.c_int, C.c_int, C.c_int, P, P, P, P, P]),
@@ -189,10 +189,11 @@ def valmp_plain(x, lmin, lmax, m_max=1, num=1, den=4, keep_nn=False):
     return out
 
 
-def valmod_pruned(x, lmin, lmax, p, m_max=1, num=1, den=4, keep_nn=False):
+def valmod_pruned(x, lmin, lmax, p, m_max=1, num=1, den=4, keep_nn=False, observe_len=0):
     """Pruned VALMOD (exact-rows reading). Returns the same dict as
     valmp_plain plus ``stats`` of shape (|L|, 3): rows alive, valid rows,
-    recomputed rows per length."""
+    recomputed rows per length; with observe_len (> lmin) also ``gap``
+    (maxLB - minED) and ``tlb`` (mean LB / ED) per row at that length."""
     if not (1 <= m_max <= p <= 64):
         raise ValueError("need 1 <= m_max <= p <= 64")
     x = _f64(x)
@@ -204,10 +205,17 @@ def valmod_pruned(x, lmin, lmax, p, m_max=1, num=1, den=4, keep_nn=False):
     if keep_nn:
         nnd = np.empty((nL, n0, m_max))
         nnj = np.empty((nL, n0, m_max), np.int64)
+    gap = tlb = None
+    if observe_len:
+        gap, tlb = np.full(n0, np.nan), np.full(n0, np.nan)
     _L().orc_valmod_pruned(_p(x), len(x), lmin, lmax, num, den, p, m_max, _p(dist_), _p(norm_),
                            _p(len_), _p(nn_), _p(nnd) if keep_nn else None,
-                           _p(nnj) if keep_nn else None, _p(stats))
+                           _p(nnj) if keep_nn else None, _p(stats), observe_len,
+                           _p(gap) if observe_len else None, _p(tlb) if observe_len else None)
     out = dict(dist=dist_, norm=norm_, len=len_, nn=nn_, stats=stats)
+    if observe_len:
+        nl = len(x) - observe_len + 1
+        out.update(gap=gap[:nl], tlb=tlb[:nl])
     if keep_nn:
         out.update(nnd=nnd, nnj=nnj)
     return out

@@ -392,9 +392,17 @@ static void recompute_row(const double *x, i64 n, int l, int num, int den, int p
     }
 }
 
+/* Observation at one length obs_len (> lmin, optional; the paper's
+ * pruning diagnostics, Sec. 6.3): for every row with stored entries, before
+ * its recompute decision, obs_gap[i] = maxLB - minED = B - (smallest stored
+ * distance) (> 0 exactly when the row is certified for its motif) and
+ * obs_tlb[i] = mean over its stored entries of LB / ED, the tightness of
+ * the lower bound, LB from Eq. LB with the entry's correlation at the row's
+ * base length; NaN for flat rows and rows without entries. */
 void orc_valmod_pruned(const double *x, i64 n, int lmin, int lmax, int num, int den, int p, int m_max,
                        double *dist, double *norm, int32_t *len, i64 *nn,
-                       double *nnd_all, i64 *nnj_all, i64 *stats)
+                       double *nnd_all, i64 *nnj_all, i64 *stats,
+                       int obs_len, double *obs_gap, double *obs_tlb)
 {
     i64 n0 = n - lmin + 1;
     row_state *st = (row_state *)calloc((size_t)n0, sizeof(row_state));
@@ -416,6 +424,10 @@ void orc_valmod_pruned(const double *x, i64 n, int lmin, int lmax, int num, int 
 #pragma omp for schedule(dynamic, 8)
             for (i64 i = 0; i < nl; ++i) {
                 int valid = 0;
+                if (l == obs_len && obs_gap) {
+                    obs_gap[i] = NAN;
+                    obs_tlb[i] = NAN;
+                }
                 if (l > lmin && !orc_is_flat(x, n, l, i)) {
                     /* Algorithm 4 / 10 row loop: re-evaluate stored entries */
                     dj_t cand[64];
@@ -434,6 +446,18 @@ void orc_valmod_pruned(const double *x, i64 n, int lmin, int lmax, int num, int 
                     double B = st[i].bound_base * st[i].sig_b / sig;
                     double dsort[64];
                     for (int e = 0; e < c; ++e) dsort[e] = cand[e].d;
+                    if (l == obs_len && obs_gap && c > 0) {
+                        obs_gap[i] = B - cand[0].d;
+                        double tsum = 0.0;
+                        int tc = 0;
+                        for (int e = 0; e < c; ++e) {
+                            if (!(cand[e].d > 0.0)) continue;
+                            double qb = orc_pearson(x, n, st[i].base, i, cand[e].j);
+                            tsum += orc_lower_bound(st[i].base, qb, st[i].sig_b, sig) / cand[e].d;
+                            ++tc;
+                        }
+                        obs_tlb[i] = tc > 0 ? tsum / tc : NAN;
+                    }
                     if (orc_row_valid(dsort, c, m_max, B)) {
                         valid = 1;
                         mp[i] = cand[0].d;

@@ -439,6 +439,22 @@ def test_motif_set_properties():
         seen += [(m, L) for m in mem]
 
 
+@pytest.mark.parametrize("gen", ["rw", "ecg"])
+def test_observation_gap_and_tlb(gen):
+    # maxLB - minED > 0 exactly for the rows the bound certifies, and the
+    # tightness LB / ED lies in (0, 1] (Eq. LB lower-bounds the distance)
+    x = workloads.random_walk(700, 81) if gen == "rw" else workloads.ecg_like(900, 82, period=40.0)
+    lmin, L = 30, 36
+    pr = oracle.valmod_pruned(x, lmin, L, 5, observe_len=L)
+    gap, tlb = pr["gap"], pr["tlb"]
+    ok = np.isfinite(gap)
+    assert ok.sum() > 0.9 * len(gap)
+    # certified rows at L are those with a positive gap
+    assert int((gap[ok] > 0).sum()) == pr["stats"][-1, 1]
+    t = tlb[np.isfinite(tlb)]
+    assert np.all(t > 0) and np.all(t <= 1 + 1e-12)
+
+
 # ---------------------------------------------------------------- read-outs
 
 def test_topk_motif_planted_pair():
