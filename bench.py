@@ -55,9 +55,41 @@ def parse():
     ap.add_argument("--no-motif-path", action="store_true", help="skip timing the motif mode (mode 1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
+    ap.add_argument("--p-sweep", default=None, metavar="LMIN:LMAX",
+                    help="pruning versus p: profile the workload over [LMIN, LMAX] for p in 5..64 and print one "
+                         "JSON line (certified / recomputed fractions, time)")
     ap.add_argument("--ncu-case", default=None, metavar="LMIN:LMAX",
                     help="profile the workload once over [LMIN, LMAX] and exit (a small case for ncu captures)")
     return ap.parse_args()
+
+
+def run_p_sweep(args):
+    """Pruning versus the number p of stored entries per row (Sec. 6.3): the
+    fractions of rows certified and recomputed after lmin, and the time."""
+    import time
+    import paper_2008_13447_gb300 as mad
+    import workloads
+    w = workloads.make(args.workload)
+    a, b = (int(v) for v in args.p_sweep.split(":"))
+    prec = mad.MAD_FP32 if args.precision == "fp32" else mad.MAD_FP64
+    x = w.series[0]
+    res = []
+    for p in (5, 10, 20, 40, 64):
+        ctx = mad.mad_create(x, precision=prec, k_max=w.k, m_max=1, band_form=args.band_form)
+        try:
+            mad.mad_profile(ctx, a, b, p)          # warm-up
+            t = time.perf_counter()
+            mad.mad_profile(ctx, a, b, p)
+            dt = time.perf_counter() - t
+            st = mad.mad_stats(ctx, 0)[1:]
+        finally:
+            mad.mad_destroy(ctx)
+        rows = sum(s["rows"] for s in st)
+        res.append({"p": p, "certified_frac": sum(s["certified"] for s in st) / rows,
+                    "recomputed_frac": sum(s["recomputed"] for s in st) / rows,
+                    "direct_rows": sum(s["direct_rows"] for s in st), "ms": dt * 1e3})
+    print(json.dumps({"p_sweep": res, "workload": args.workload, "lengths": [a, b], "precision": args.precision}))
+    return 0
 
 
 def run_ncu_case(args):
@@ -234,6 +266,8 @@ def main():
         return run_reference(args)
     if args.ncu_case:
         return run_ncu_case(args)
+    if args.p_sweep:
+        return run_p_sweep(args)
     import numpy as np
     import torch
     import paper_2008_13447_gb300 as mad

@@ -92,6 +92,9 @@ typedef struct mad_options {
                                column; the faster form on GB300), 1 = symmetric (upper triangle only,
                                each pair computed once and fed to both windows, used for the lengths
                                where at least half of the row bands need recomputing) */
+    int32_t observe_len;    /* 0 = off; else a length in (lmin, lmax] at which mad_profile records,
+                               per row, maxLB - minED and the mean tightness of the lower bound
+                               (read with mad_observe) */
     void *stream;           /* cudaStream_t to issue work on; NULL = the legacy default stream */
 } mad_options;
 
@@ -264,6 +267,19 @@ MAD_API mad_status mad_stats(mad_ctx *ctx, int32_t series, mad_length_stats *out
 MAD_API mad_status mad_mth_nn_dist_noalloc(const double *x, int64_t n, const int32_t *cells,
                                            int32_t ncells, int32_t m_max, int32_t excl_num,
                                            int32_t excl_den, double *out, void *stream);
+
+/* Pruning observation at options.observe_len (Sec. 6.3 diagnostics), for
+ * the n - observe_len + 1 rows at that length, host arrays:
+ *   gap[i] = maxLB - minED: the row's bound (Eq. LB from its p-th stored
+ *            entry) minus its smallest stored distance; > 0 exactly when
+ *            the stored entries certify the row's nearest neighbour;
+ *   tlb[i] = mean over its stored entries of LB / ED (Eq. LB with the
+ *            entry's correlation at the row's base length over the entry's
+ *            distance at observe_len), the tightness of the lower bound;
+ * NaN for flat rows and rows without stored entries. Needs a profile whose
+ * range contains observe_len with lmin < observe_len (MAD_ESTATE otherwise).
+ * Either pointer may be NULL. */
+MAD_API mad_status mad_observe(mad_ctx *ctx, int32_t series, double *gap, double *tlb);
 
 /* Human-readable description of the last error on ctx (or of the calling
  * thread's last mad_create* or mad_mth_nn_dist_noalloc error when ctx is

@@ -31,13 +31,15 @@ STATUS_NAMES = {0: "MAD_OK", 1: "MAD_EINVAL", 2: "MAD_ENOMEM", 3: "MAD_ECUDA", 4
                 5: "MAD_ETIMEOUT", 6: "MAD_EINTERNAL"}
 ABI_FUNCTIONS = ("mad_create", "mad_create_device", "mad_create_batch", "mad_profile", "mad_profile_batch",
                  "mad_motifs", "mad_discords", "mad_valmp", "mad_matrix_profile", "mad_stats",
-                 "mad_mth_nn_dist_noalloc", "mad_motif_sets", "mad_last_error", "mad_destroy")
+                 "mad_mth_nn_dist_noalloc", "mad_motif_sets", "mad_observe", "mad_last_error",
+                 "mad_destroy")
 
 
 class mad_options(C.Structure):
     _fields_ = [("excl_num", C.c_int32), ("excl_den", C.c_int32), ("precision", C.c_int32),
                 ("k_max", C.c_int32), ("m_max", C.c_int32), ("keep_profiles", C.c_int32),
-                ("mode", C.c_int32), ("band_form", C.c_int32), ("stream", C.c_void_p)]
+                ("mode", C.c_int32), ("band_form", C.c_int32), ("observe_len", C.c_int32),
+                ("stream", C.c_void_p)]
 
 
 class mad_motif(C.Structure):
@@ -96,6 +98,7 @@ def library() -> C.CDLL:
             "mad_stats": [P, i32, C.POINTER(mad_length_stats), i32, C.POINTER(i32)],
             "mad_mth_nn_dist_noalloc": [P, i64, P, i32, i32, i32, i32, P, P],
             "mad_motif_sets": [P, i32, i32, C.c_double, i32, C.POINTER(mad_motif_set), P, C.POINTER(i32)],
+            "mad_observe": [P, i32, P, P],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -115,7 +118,7 @@ def _check(status, ctx):
 
 
 def _options(precision=MAD_FP64, excl=(1, 4), k_max=10, m_max=1, keep_profiles=False, stream=None, band_form=0,
-             mode=0):
+             mode=0, observe_len=0):
     o = mad_options()
     o.excl_num, o.excl_den = excl
     o.precision = precision
@@ -124,6 +127,7 @@ def _options(precision=MAD_FP64, excl=(1, 4), k_max=10, m_max=1, keep_profiles=F
     o.keep_profiles = 1 if keep_profiles else 0
     o.band_form = band_form
     o.mode = mode
+    o.observe_len = observe_len
     if stream is not None:
         o.stream = stream if isinstance(stream, int) else stream.cuda_stream
     return o
@@ -194,6 +198,13 @@ def mad_motif_sets(ctx, series, k, D, cap):
     _check(library().mad_motif_sets(ctx, series, k, float(D), cap, sets, _p(mem), C.byref(n)), ctx)
     return [dict(a=s.a, b=s.b, len=s.len, radius=s.radius, members=list(mem[i, :s.count]))
             for i, s in enumerate(sets[:n.value])]
+
+
+def mad_observe(ctx, series, n_rows):
+    """(gap, tlb) arrays of n_rows = n - observe_len + 1 entries."""
+    gap, tlb = np.empty(n_rows), np.empty(n_rows)
+    _check(library().mad_observe(ctx, series, _p(gap), _p(tlb)), ctx)
+    return gap, tlb
 
 
 def mad_discords(ctx, series, k, m):

@@ -290,6 +290,10 @@ __device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i, double
             A.lbmax[i] = 0.0;
             lb = 0.0;
         }
+        if (A.obs_gap) {
+            A.obs_gap[i] = __longlong_as_double(0x7ff8000000000000LL);
+            A.obs_tlb[i] = __longlong_as_double(0x7ff8000000000000LL);
+        }
         return 2;
     }
     const double m2i = A.m2[i];
@@ -332,6 +336,27 @@ __device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i, double
     const double sig = sqrt(m2i / l);
     const double B = A.st.bnum[i] / sig;
     const int m = A.m_max;
+    if (A.obs_gap) {
+        // maxLB - minED and the mean tightness LB / ED of the stored entries
+        // (Eq. LB with each entry's correlation at the row's base length)
+        const double lbb = (double)A.st.base[i], sb = A.st.sigb[i];
+        double dmin = pinf(), tsum = 0.0;
+        int tc = 0;
+        for_pm<PM>([&](int a) {
+            if (r.j[a] < 0) return;
+            const double d = dist_from_q(r.q[a], l);
+            dmin = fmin(dmin, d);
+            if (d > 0.0) {
+                const double qb = A.st.ent_qb[(int64_t)a * n0 + i];
+                const double base = qb <= 0.0 ? sqrt(lbb) : sqrt(lbb * (1.0 - qb * qb));
+                tsum += base * sb / sig / d;
+                ++tc;
+            }
+        });
+        const double nan = __longlong_as_double(0x7ff8000000000000LL);
+        A.obs_gap[i] = cnt > 0 ? B - dmin : nan;
+        A.obs_tlb[i] = tc > 0 ? tsum / tc : nan;
+    }
     // the m-th smallest true distance is at most the m-th smallest pessimistic
     // one (compared as squared distances 2 l (1 - q))
     bool ok = false;
@@ -621,9 +646,13 @@ __global__ void k_merge(MergeArgs<T> A)
     refine_reported<PM>(A.x, A.xh, A.xl, i, l, A.mu[i], isdi, A.mu, A.isd, A.em, A.st, n0, r, A.m_max,
                         &A.out.stats[3]);
     report_row<PM>(A.out, A.vm, n0, i, l, r, nb, A.m_max);
+    for_pm<PM>([&](int e) {
+        if (r.j[e] >= 0) A.st.ent_qb[(int64_t)e * n0 + i] = r.q[e];
+    });
     A.st.base[i] = l;
     const double sqm2i = sqrt(A.m2[i]);
     const double sig = sqm2i / sqrt((double)l);
+    A.st.sigb[i] = sig;
     if (ntc <= p) {
         A.st.bnum[i] = pinf();
     } else {

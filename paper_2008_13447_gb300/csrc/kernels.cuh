@@ -113,6 +113,8 @@ void launch_kappa(const double *m2, const int32_t *run, int64_t nl, int l, int R
 struct RowState {
     int32_t *ent_j;
     double *ent_c;
+    double *ent_qb;         // correlation of each entry at the row's base length
+    double *sigb;           // sigma_i(l_b)
     float *ent_dq;          // correlation error bound of each entry (0 once re-evaluated in FP64)
     int32_t *base;
     double *bnum;
@@ -140,6 +142,8 @@ template <typename T> struct ExtArgs {
     // doubles, reduced with atomicMin)
     double *lbmax;
     unsigned long long *min_dist_abs, *min_lb_abs;
+    // observation at one length (NULL otherwise): maxLB - minED, mean LB / ED
+    double *obs_gap, *obs_tlb;
     const float *xh, *xl;   // x as FP32 pairs (compensated re-evaluation)
     const double *isd;      // 1 / sqrt(M2) at l (0: flat)
     int64_t n0, nl;

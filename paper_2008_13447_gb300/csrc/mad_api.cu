@@ -44,6 +44,8 @@ struct Series {
     Valmp vm{};
     DiscTable tab{};
     double *keep_nnd = nullptr;
+    int obs_len = 0;                 // observation length of the last profile (0: none)
+    double *obs_gap = nullptr, *obs_tlb = nullptr;
     int32_t *keep_nnj = nullptr;
     std::vector<mad_length_stats> stats;
 };
@@ -119,6 +121,8 @@ void free_profile(Series &s)
     s.profiled = false;
     s.keep_nnd = nullptr;
     s.keep_nnj = nullptr;
+    s.obs_len = 0;
+    s.obs_gap = s.obs_tlb = nullptr;
 }
 
 int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
@@ -216,8 +220,14 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
     T *seedb[2] = {dalloc<T>(ctx, s, K * spitch), dalloc<T>(ctx, s, K * spitch)};
     T *thr = dalloc<T>(ctx, s, npad);
     RowState rs{dalloc<int32_t>(ctx, s, (size_t)p * n0), dalloc<double>(ctx, s, (size_t)p * n0),
+                dalloc<double>(ctx, s, (size_t)p * n0), dalloc<double>(ctx, s, n0),
                 dalloc<float>(ctx, s, (size_t)p * n0), dalloc<int32_t>(ctx, s, n0), dalloc<double>(ctx, s, n0),
                 dalloc<int32_t>(ctx, s, n0)};
+    // pruning observation at one length (options.observe_len)
+    const bool observe = o.observe_len > lmin && o.observe_len <= lmax;
+    s.obs_len = observe ? o.observe_len : 0;
+    s.obs_gap = observe ? dalloc<double>(ctx, s, n0) : nullptr;
+    s.obs_tlb = observe ? dalloc<double>(ctx, s, n0) : nullptr;
     float *kappab[2] = {dalloc<float>(ctx, s, n0), dalloc<float>(ctx, s, n0)};
     float *kmaxb[2] = {dalloc<float>(ctx, s, 1), dalloc<float>(ctx, s, 1)};
     double *m2blk = dalloc<double>(ctx, s, (n0 + 255) / 256);
@@ -451,6 +461,10 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
             ea.out = lo;
             ea.thr = thr;
             ea.em = em;
+            if (observe && l == o.observe_len) {
+                ea.obs_gap = s.obs_gap;
+                ea.obs_tlb = s.obs_tlb;
+            }
             if (motif_mode) {
                 ea.lbmax = lbmax;
                 ea.min_dist_abs = reinterpret_cast<unsigned long long *>(mm + 2 * li);
@@ -984,6 +998,23 @@ MAD_API mad_status mad_motif_sets(mad_ctx *ctx, int32_t series, int32_t k, doubl
             throw;
         }
         for (void *p : tmp) cudaFree(p);
+    });
+}
+
+MAD_API mad_status mad_observe(mad_ctx *ctx, int32_t series, double *gap, double *tlb)
+{
+    if (!ctx) { g_create_err = "ctx is NULL"; return MAD_EINVAL; }
+    return run_guarded(ctx, [&] {
+        Series &s = get_series(ctx, series);
+        if (!s.profiled || s.obs_len == 0) {
+            set_err(ctx, "no observation: set options.observe_len to a length in (lmin, lmax] and profile");
+            throw Fail{MAD_ESTATE};
+        }
+        const int64_t nl = s.n - s.obs_len + 1;
+        cudaStream_t st = ctx->stream;
+        if (gap) CK(cudaMemcpyAsync(gap, s.obs_gap, sizeof(double) * nl, cudaMemcpyDeviceToHost, st));
+        if (tlb) CK(cudaMemcpyAsync(tlb, s.obs_tlb, sizeof(double) * nl, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
     });
 }
 
