@@ -73,6 +73,8 @@ def _L():
             "orc_discords_one_length": (C.c_int, [i64, P, P, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P]),
             "orc_discords": (None, [i64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P, P,
                                     P, P, P, P, P]),
+            "orc_discords_global": (C.c_int, [i64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                              C.c_int, P, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -272,6 +274,18 @@ def discords_one_length(score, l, k, nbr=None, num=1, den=4):
     off, dd, nn = np.empty(k, np.int64), np.empty(k), np.empty(k, np.int64)
     got = _L().orc_discords_one_length(len(score), _p(score), _p(nb), l, num, den, k, _p(off), _p(dd), _p(nn))
     return [(int(off[r]), float(dd[r]), int(nn[r])) for r in range(got)]
+
+
+def discords_global(n, lmin, lmax, k, m_max, m, nnd_all, nnj_all, num=1, den=4):
+    """Global-greedy variable-length m-th discords: list of (off, len, dist,
+    norm_dist, nn), at most k."""
+    nnd_all = _f64(nnd_all)
+    nnj_all = np.ascontiguousarray(nnj_all, np.int64)
+    off, ln = np.empty(k, np.int64), np.empty(k, np.int32)
+    dd, nd, nn = np.empty(k), np.empty(k), np.empty(k, np.int64)
+    got = _L().orc_discords_global(n, lmin, lmax, num, den, k, m_max, m, _p(nnd_all), _p(nnj_all),
+                                   _p(off), _p(ln), _p(dd), _p(nd), _p(nn))
+    return [(int(off[r]), int(ln[r]), float(dd[r]), float(nd[r]), int(nn[r])) for r in range(got)]
 
 
 def discords(n, lmin, lmax, k, m_max, nnd_all, nnj_all, num=1, den=4):

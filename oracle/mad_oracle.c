@@ -810,6 +810,69 @@ int orc_discords_one_length(i64 nl, const double *score, const i64 *nbr, int l, 
     return got;
 }
 
+/* Global-greedy variable-length m-th discords (the variant of Algorithm 9's
+ * per-rank merge): for column m, every (i, l) with an m-th best match is a
+ * candidate with score NN_l^m[i] / sqrt(l); candidates are visited by score
+ * descending, then length descending (the ">=" of Algorithm 9), then offset
+ * ascending, and accepted unless within max(E(l), E(l')) of an accepted
+ * (i', l'); the first k accepted. nnd_all / nnj_all as for orc_discords.
+ * Outputs k entries: off, len, raw d, normalised d, neighbour; returns the
+ * number accepted. */
+typedef struct { double s; int l; i64 i; } sli_t;
+
+static int cmp_sli(const void *a, const void *b)
+{
+    const sli_t *u = (const sli_t *)a, *v = (const sli_t *)b;
+    if (u->s > v->s) return -1;
+    if (u->s < v->s) return 1;
+    if (u->l > v->l) return -1;
+    if (u->l < v->l) return 1;
+    return (u->i < v->i) ? -1 : (u->i > v->i);
+}
+
+int orc_discords_global(i64 n, int lmin, int lmax, int num, int den, int k, int m_max, int m,
+                        const double *nnd_all, const i64 *nnj_all,
+                        i64 *out_off, int32_t *out_len, double *out_d, double *out_nd, i64 *out_nn)
+{
+    i64 n0 = n - lmin + 1;
+    i64 cap = n0 * (i64)(lmax - lmin + 1);
+    sli_t *c = (sli_t *)malloc(sizeof(sli_t) * (size_t)cap);
+    i64 cnt = 0;
+    for (int l = lmin; l <= lmax; ++l) {
+        i64 nl = n - l + 1;
+        const double *nd = nnd_all + (i64)(l - lmin) * n0 * m_max;
+        for (i64 i = 0; i < nl; ++i) {
+            double d = nd[i * m_max + m - 1];
+            if (!isfinite(d)) continue;
+            c[cnt].s = d / sqrt((double)l);
+            c[cnt].l = l;
+            c[cnt].i = i;
+            ++cnt;
+        }
+    }
+    qsort(c, (size_t)cnt, sizeof(sli_t), cmp_sli);
+    int got = 0;
+    for (i64 t = 0; t < cnt && got < k; ++t) {
+        int ok = 1;
+        i64 E = orc_excl(c[t].l, num, den);
+        for (int g = 0; g < got && ok; ++g) {
+            i64 Eg = orc_excl(out_len[g], num, den);
+            i64 Em = E > Eg ? E : Eg;
+            if (iabs64(c[t].i - out_off[g]) <= Em) ok = 0;
+        }
+        if (!ok) continue;
+        i64 at = (i64)(c[t].l - lmin) * n0 * m_max + c[t].i * m_max + m - 1;
+        out_off[got] = c[t].i;
+        out_len[got] = c[t].l;
+        out_d[got] = nnd_all[at];
+        out_nd[got] = c[t].s;
+        out_nn[got] = nnj_all[at];
+        ++got;
+    }
+    free(c);
+    return got;
+}
+
 /* Variable-length Top-k m-th discords dkm_{lmin,lmax} (Algorithm 7 driving
  * Algorithm 9): for every length, every column m = 1..m_max and every rank
  * r = 1..k, keep the entry with the largest d / sqrt(l); ties go to the later

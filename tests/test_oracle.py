@@ -455,6 +455,40 @@ def test_observation_gap_and_tlb(gen):
     assert np.all(t > 0) and np.all(t <= 1 + 1e-12)
 
 
+def test_global_discords_brute_force():
+    # the global greedy restated over all (i, l) with numpy on a small series
+    x = workloads.ar2(400, 95)
+    lmin, lmax, m_max, k = 16, 22, 2, 4
+    pl = oracle.valmp_plain(x, lmin, lmax, m_max=m_max, keep_nn=True)
+    n = len(x)
+    for m in (1, 2):
+        got = oracle.discords_global(n, lmin, lmax, k, m_max, m, pl["nnd"], pl["nnj"])
+        cand = []
+        for li, l in enumerate(range(lmin, lmax + 1)):
+            for i in range(n - l + 1):
+                d = pl["nnd"][li, i, m - 1]
+                if np.isfinite(d):
+                    cand.append((-d / np.sqrt(l), -l, i, d))
+        cand.sort()
+        acc = []
+        for s_, nl_, i, d in cand:
+            l = -nl_
+            if all(abs(i - a) > max(oracle.excl(l), oracle.excl(b)) for a, b, _ in acc):
+                acc.append((i, l, d))
+            if len(acc) == k:
+                break
+        assert [(g[0], g[1]) for g in got] == [(a, b) for a, b, _ in acc]
+        assert np.allclose([g[2] for g in got], [d for _, _, d in acc])
+
+
+def test_global_discords_planted_spike():
+    x = workloads.random_walk(1500, 96)
+    x[700] += 25.0
+    pl = oracle.valmp_plain(x, 20, 30, keep_nn=True)
+    top = oracle.discords_global(len(x), 20, 30, 1, 1, 1, pl["nnd"], pl["nnj"])[0]
+    assert top[0] <= 700 < top[0] + top[1]
+
+
 # ---------------------------------------------------------------- read-outs
 
 def test_topk_motif_planted_pair():
