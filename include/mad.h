@@ -216,6 +216,24 @@ MAD_API mad_status mad_motif_sets(mad_ctx *ctx, int32_t series, int32_t k, doubl
 MAD_API mad_status mad_discords(mad_ctx *ctx, int32_t series, int32_t k, int32_t m,
                                 mad_discord *out, int32_t *n_out);
 
+/* Global-greedy variable-length m-th discords (a variant of Sec. 6's
+ * Top-k m-th discords with the per-rank merge of Algorithm 9 replaced by one
+ * ranking over all lengths): for each column c in 1..m, every (offset i,
+ * length l) with a c-th best match is a candidate of score
+ * NN_l^c[i] / sqrt(l); candidates are taken by score descending, then longer
+ * length, then smaller offset, each accepted unless |i - i'| <=
+ * max(E(l), E(l')) for an accepted (i', l'), until k are accepted. Unlike
+ * mad_discords, two picks never overlap by more than the exclusion zone,
+ * whatever their lengths. Needs a mode-0 profile made with keep_profiles.
+ * out must hold k * m entries, rank-major as for mad_discords (cells without
+ * a candidate have off = -1, len = 0, NaN distances); dist_recheck is the
+ * FP64 re-check. Requires 1 <= k <= 64, 1 <= m <= m_max. Errors: MAD_EINVAL
+ * for bad arguments or a profile without keep_profiles, MAD_ESTATE before
+ * mad_profile or in motif mode, MAD_ENOMEM when the scratch
+ * (16 B per (column, length, 256 offsets) tile) cannot be allocated. */
+MAD_API mad_status mad_discords_global(mad_ctx *ctx, int32_t series, int32_t k, int32_t m,
+                                       mad_discord *out, int32_t *n_out);
+
 /* Copy VALMP of series `series` to host arrays of n - lmin + 1 entries:
  * raw distance, normalised distance, length, nearest-neighbour offset. */
 MAD_API mad_status mad_valmp(mad_ctx *ctx, int32_t series, double *dist, double *norm,

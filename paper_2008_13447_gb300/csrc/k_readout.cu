@@ -53,6 +53,7 @@ __device__ void block_best(double &v, int32_t &i)
 // ------------------------------------------------------------- discords
 
 constexpr int DBLK = 256;
+static_assert(GDISC_TILE == DBLK, "host tile count must match the kernels' tile");
 
 // Per block of DBLK offsets and column m: the best (score desc, offset asc)
 // m-th best-match distance. Offsets without an m-th best match are skipped.
@@ -148,6 +149,137 @@ void launch_discords_length(const double *nnd, const int32_t *nnj, int64_t n0, i
     static std::once_flag once[64];
     smem_optin_max((const void *)k_disc_greedy, once);
     k_disc_greedy<<<m_max, 1024, sm, s>>>(nnd, nnj, n0, nl, l, E, k_max, m_max, bval, bidx, nblk, tab);
+}
+
+// ------------------------------------------------ global-greedy discords
+
+// Variable-length m-th discords ranked over every (offset, length) at once:
+// candidates by score NN_l^m[i] / sqrt(l) descending, then longer length, then
+// smaller offset, each accepted unless within max(E(l), E(l')) of an accepted
+// (i', l'). A candidate's key (nL - 1 - li) * n0 + i orders the ties. The
+// kept profiles are cut into tiles of DBLK offsets of one length; a tile's
+// best free candidate is kept in (tv, tk), and after each pick only the tiles
+// that meet its zone are re-scanned.
+__device__ __forceinline__ bool better_key(double v, int64_t a, double w, int64_t b)
+{
+    return v > w || (v == w && a >= 0 && (b < 0 || a < b));
+}
+
+__device__ __forceinline__ void warp_best_key(double &v, int64_t &k)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const double w = __shfl_xor_sync(0xffffffffu, v, o);
+        const int64_t b = __shfl_xor_sync(0xffffffffu, k, o);
+        if (better_key(w, b, v, k)) { v = w; k = b; }
+    }
+}
+
+// One warp re-scans tile (li, blk) of column c, skipping the np picks' zones.
+__device__ void gdisc_tile(const GDiscArgs &A, int c, int li, int blk, const int64_t *po, const int64_t *pe, int np)
+{
+    const int lane = threadIdx.x & 31;
+    const int l = A.lmin + li;
+    const int64_t nl = A.n - l + 1;
+    const int64_t E = excl_zone(l, A.num, A.den);
+    const double f = sqrt((double)l);
+    const double *sc = A.nnd + ((int64_t)li * A.m_max + c) * A.n0;
+    double v = ninf();
+    int64_t key = -1;
+    for (int t = lane; t < DBLK; t += 32) {
+        const int64_t e = (int64_t)blk * DBLK + t;
+        if (e >= nl) break;
+        const double d = sc[e];
+        if (!isfinite(d)) continue;
+        bool ok = true;
+        for (int q = 0; q < np && ok; ++q) {
+            const int64_t Em = E > pe[q] ? E : pe[q];
+            const int64_t dd = e - po[q];
+            ok = dd > Em || -dd > Em;
+        }
+        if (!ok) continue;
+        const double s = d / f;
+        const int64_t kk = (int64_t)(A.nL - 1 - li) * A.n0 + e;
+        if (better_key(s, kk, v, key)) { v = s; key = kk; }
+    }
+    warp_best_key(v, key);
+    if (lane == 0) {
+        const int64_t t = (int64_t)c * A.nL * A.nblk + (int64_t)li * A.nblk + blk;
+        A.tv[t] = v;
+        A.tk[t] = key;
+    }
+}
+
+__global__ void k_gdisc_tiles(GDiscArgs A)
+{
+    const int c = blockIdx.y;
+    const int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (t >= (int64_t)A.nL * A.nblk) return;
+    gdisc_tile(A, c, (int)(t / A.nblk), (int)(t % A.nblk), nullptr, nullptr, 0);
+}
+
+// One block per column: k rounds of argmax over the tile table, then the
+// re-scan of the tiles within max(E(l), E(l_pick)) of the pick, per length.
+__global__ void __launch_bounds__(1024) k_gdisc_greedy(GDiscArgs A)
+{
+    __shared__ int64_t po[KMAX], pe[KMAX];
+    __shared__ double rv[32];
+    __shared__ int64_t rk[32];
+    const int c = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t nt = (int64_t)A.nL * A.nblk;
+    const double *tv = A.tv + c * nt;
+    const int64_t *tk = A.tk + c * nt;
+    for (int r = 0; r < A.k; ++r) {
+        double v = ninf();
+        int64_t key = -1;
+        for (int64_t t = threadIdx.x; t < nt; t += blockDim.x)
+            if (better_key(tv[t], tk[t], v, key)) { v = tv[t]; key = tk[t]; }
+        warp_best_key(v, key);
+        if (lane == 0) { rv[wid] = v; rk[wid] = key; }
+        __syncthreads();
+        if (wid == 0) {
+            v = lane < nw ? rv[lane] : ninf();
+            key = lane < nw ? rk[lane] : -1;
+            warp_best_key(v, key);
+            if (lane == 0) { rv[0] = v; rk[0] = key; }
+        }
+        __syncthreads();
+        v = rv[0];
+        key = rk[0];
+        if (key < 0) break;
+        const int li = A.nL - 1 - (int)(key / A.n0);
+        const int64_t i = key % A.n0;
+        const int l = A.lmin + li;
+        if (threadIdx.x == 0) {
+            po[r] = i;
+            pe[r] = excl_zone(l, A.num, A.den);
+            const int cell = r * A.mcols + c;
+            const int64_t at = ((int64_t)li * A.m_max + c) * A.n0 + i;
+            A.out.norm[cell] = v;
+            A.out.dist[cell] = A.nnd[at];
+            A.out.off[cell] = (int32_t)i;
+            A.out.len[cell] = l;
+            A.out.nn[cell] = A.nnj[at];
+        }
+        __syncthreads();
+        for (int l2i = wid; l2i < A.nL; l2i += nw) {
+            const int l2 = A.lmin + l2i;
+            const int64_t nl2 = A.n - l2 + 1;
+            const int64_t E2 = excl_zone(l2, A.num, A.den), Em = E2 > pe[r] ? E2 : pe[r];
+            const int64_t lo = i - Em < 0 ? 0 : i - Em;
+            const int64_t hi = i + Em >= nl2 ? nl2 - 1 : i + Em;
+            for (int64_t blk = lo / DBLK; lo <= hi && blk <= hi / DBLK; ++blk)
+                gdisc_tile(A, c, l2i, (int)blk, po, pe, r + 1);
+        }
+        __syncthreads();
+    }
+}
+
+void launch_discords_global(const GDiscArgs &a, cudaStream_t s)
+{
+    const int64_t nt = (int64_t)a.nL * a.nblk;
+    k_gdisc_tiles<<<dim3((unsigned)((nt + 7) / 8), a.mcols), 256, 0, s>>>(a);
+    k_gdisc_greedy<<<a.mcols, 1024, 0, s>>>(a);
 }
 
 // --------------------------------------------------------------- motifs

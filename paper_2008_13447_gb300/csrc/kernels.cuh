@@ -322,6 +322,19 @@ struct DiscTable {          // k_max x m_max cells, rank-major
     int32_t *len;
     int32_t *nn;
 };
+struct GDiscArgs {          // global-greedy discords over the kept profiles
+    const double *nnd;      // [nL][m_max][n0] m-th best-match distances
+    const int32_t *nnj;
+    int64_t n, n0;
+    int lmin, nL, m_max, num, den;
+    int nblk;               // tiles of DBLK offsets per length
+    int k, mcols;           // ranks, columns 1..mcols
+    double *tv;             // [mcols][nL][nblk] best free score per tile
+    int64_t *tk;            // its key
+    DiscTable out;          // k x mcols cells, rank-major
+};
+constexpr int GDISC_TILE = 256;
+void launch_discords_global(const GDiscArgs &a, cudaStream_t s);
 void launch_discords_length(const double *nnd, const int32_t *nnj, int64_t n0, int64_t nl, int l, int64_t E,
                             int k_max, int m_max, double *bval, int32_t *bidx, DiscTable tab, cudaStream_t s);
 

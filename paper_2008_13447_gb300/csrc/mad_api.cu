@@ -1018,6 +1018,77 @@ MAD_API mad_status mad_observe(mad_ctx *ctx, int32_t series, double *gap, double
     });
 }
 
+// Host side of a discord read-out: the k x m cells (rank-major, row stride
+// `stride` cells) already copied to the host, each re-checked in FP64 from a
+// full distance profile, written to out.
+static void finish_discords(mad_ctx *ctx, Series &s, int k, int m, int stride, const std::vector<double> &nd,
+                            const std::vector<double> &dd, const std::vector<int32_t> &off,
+                            const std::vector<int32_t> &len, const std::vector<int32_t> &nn, mad_discord *out)
+{
+    cudaStream_t st = ctx->stream;
+    std::vector<int32_t> req;
+    std::vector<int> where;
+    for (int r = 0; r < k; ++r)
+        for (int c = 0; c < m; ++c) {
+            const size_t cell = (size_t)r * stride + c;
+            if (len[cell] > 0) {
+                req.push_back(off[cell]);
+                req.push_back(len[cell]);
+                req.push_back(c + 1);
+                where.push_back(r * m + c);
+            }
+        }
+    std::vector<double> rec(where.size(), NAN);
+    if (!where.empty()) {
+        const int nc = (int)where.size();
+        const size_t ns = recheck_scratch(nc, m);
+        void *dreq = nullptr, *dout = nullptr, *dsd = nullptr, *dsj = nullptr;
+        cudaError_t e1 = cudaMalloc(&dreq, req.size() * sizeof(int32_t));
+        if (e1 == cudaSuccess) e1 = cudaMalloc(&dout, nc * sizeof(double));
+        if (e1 == cudaSuccess) e1 = cudaMalloc(&dsd, ns * sizeof(double));
+        if (e1 == cudaSuccess) e1 = cudaMalloc(&dsj, ns * sizeof(int32_t));
+        cudaError_t e3 = e1, e4 = cudaSuccess;
+        if (e1 == cudaSuccess) {
+            cudaMemcpyAsync(dreq, req.data(), req.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+            launch_recheck_discords(s.x, s.n, (const int32_t *)dreq, nc, ctx->opt.excl_num, ctx->opt.excl_den,
+                                    (double *)dout, (double *)dsd, (int32_t *)dsj, m, st);
+            e3 = cudaMemcpyAsync(rec.data(), dout, nc * sizeof(double), cudaMemcpyDeviceToHost, st);
+            e4 = cudaStreamSynchronize(st);
+        }
+        cudaFree(dreq);
+        cudaFree(dout);
+        cudaFree(dsd);
+        cudaFree(dsj);
+        CK(e3);
+        CK(e4);
+        CK(cudaGetLastError());
+    }
+    size_t w = 0;
+    for (int r = 0; r < k; ++r)
+        for (int c = 0; c < m; ++c) {
+            const size_t cell = (size_t)r * stride + c;
+            mad_discord &q = out[r * m + c];
+            q.rank = r + 1;
+            q.m = c + 1;
+            q.reserved = 0;
+            if (len[cell] > 0) {
+                q.off = off[cell];
+                q.nn = nn[cell];
+                q.len = len[cell];
+                q.dist = dd[cell];
+                q.norm_dist = nd[cell];
+                q.dist_recheck = rec[w++];
+            } else {
+                q.off = -1;
+                q.nn = -1;
+                q.len = 0;
+                q.dist = NAN;
+                q.norm_dist = NAN;
+                q.dist_recheck = NAN;
+            }
+        }
+}
+
 MAD_API mad_status mad_discords(mad_ctx *ctx, int32_t series, int32_t k, int32_t m, mad_discord *out,
                                 int32_t *n_out)
 {
@@ -1045,67 +1116,84 @@ MAD_API mad_status mad_discords(mad_ctx *ctx, int32_t series, int32_t k, int32_t
         CK(cudaMemcpyAsync(len.data(), s.tab.len, cells * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(nn.data(), s.tab.nn, cells * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        std::vector<int32_t> req;
-        std::vector<int> where;
-        for (int r = 0; r < k; ++r)
-            for (int c = 0; c < m; ++c) {
-                const size_t cell = (size_t)r * s.m_max + c;
-                if (len[cell] > 0) {
-                    req.push_back(off[cell]);
-                    req.push_back(len[cell]);
-                    req.push_back(c + 1);
-                    where.push_back(r * m + c);
-                }
-            }
-        std::vector<double> rec(where.size(), NAN);
-        if (!where.empty()) {
-            const int nc = (int)where.size();
-            const size_t ns = recheck_scratch(nc, m);
-            void *dreq = nullptr, *dout = nullptr, *dsd = nullptr, *dsj = nullptr;
-            cudaError_t e1 = cudaMalloc(&dreq, req.size() * sizeof(int32_t));
-            if (e1 == cudaSuccess) e1 = cudaMalloc(&dout, nc * sizeof(double));
-            if (e1 == cudaSuccess) e1 = cudaMalloc(&dsd, ns * sizeof(double));
-            if (e1 == cudaSuccess) e1 = cudaMalloc(&dsj, ns * sizeof(int32_t));
-            cudaError_t e3 = e1, e4 = cudaSuccess;
-            if (e1 == cudaSuccess) {
-                cudaMemcpyAsync(dreq, req.data(), req.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
-                launch_recheck_discords(s.x, s.n, (const int32_t *)dreq, nc, ctx->opt.excl_num, ctx->opt.excl_den,
-                                        (double *)dout, (double *)dsd, (int32_t *)dsj, m, st);
-                e3 = cudaMemcpyAsync(rec.data(), dout, nc * sizeof(double), cudaMemcpyDeviceToHost, st);
-                e4 = cudaStreamSynchronize(st);
-            }
-            cudaFree(dreq);
-            cudaFree(dout);
-            cudaFree(dsd);
-            cudaFree(dsj);
-            CK(e3);
-            CK(e4);
-            CK(cudaGetLastError());
+        finish_discords(ctx, s, k, m, s.m_max, nd, dd, off, len, nn, out);
+        *n_out = k * m;
+    });
+}
+
+MAD_API mad_status mad_discords_global(mad_ctx *ctx, int32_t series, int32_t k, int32_t m, mad_discord *out,
+                                       int32_t *n_out)
+{
+    if (!ctx) { g_create_err = "ctx is NULL"; return MAD_EINVAL; }
+    return run_guarded(ctx, [&] {
+        Series &s = get_series(ctx, series);
+        REQUIRE(out != nullptr && n_out != nullptr, "output pointers are NULL");
+        if (!s.profiled) {
+            set_err(ctx, "mad_discords_global before mad_profile");
+            throw Fail{MAD_ESTATE};
         }
-        size_t w = 0;
-        for (int r = 0; r < k; ++r)
-            for (int c = 0; c < m; ++c) {
-                const size_t cell = (size_t)r * s.m_max + c;
-                mad_discord &q = out[r * m + c];
-                q.rank = r + 1;
-                q.m = c + 1;
-                q.reserved = 0;
-                if (len[cell] > 0) {
-                    q.off = off[cell];
-                    q.nn = nn[cell];
-                    q.len = len[cell];
-                    q.dist = dd[cell];
-                    q.norm_dist = nd[cell];
-                    q.dist_recheck = rec[w++];
-                } else {
-                    q.off = -1;
-                    q.nn = -1;
-                    q.len = 0;
-                    q.dist = NAN;
-                    q.norm_dist = NAN;
-                    q.dist_recheck = NAN;
-                }
-            }
+        REQUIRE(k >= 1 && k <= KMAX, "k must be in [1, 64]");
+        REQUIRE(m >= 1 && m <= s.m_max, "m must be in [1, m_max]");
+        if (ctx->opt.mode == 1) {
+            set_err(ctx, "global discords need mode 0 (exact rows)");
+            throw Fail{MAD_ESTATE};
+        }
+        REQUIRE(s.keep_nnd != nullptr, "profile was computed without keep_profiles");
+        cudaStream_t st = ctx->stream;
+        GDiscArgs a{};
+        a.nnd = s.keep_nnd;
+        a.nnj = s.keep_nnj;
+        a.n = s.n;
+        a.n0 = s.n0;
+        a.lmin = s.lmin;
+        a.nL = s.lmax - s.lmin + 1;
+        a.m_max = s.m_max;
+        a.num = ctx->opt.excl_num;
+        a.den = ctx->opt.excl_den;
+        a.nblk = (int)((s.n0 + GDISC_TILE - 1) / GDISC_TILE);
+        a.k = k;
+        a.mcols = m;
+        const size_t cells = (size_t)k * m, nt = (size_t)m * a.nL * a.nblk;
+        // one allocation: tile table, then the k x m cells
+        const size_t bytes = nt * (sizeof(double) + sizeof(int64_t)) + cells * (2 * sizeof(double) + 3 * sizeof(int32_t));
+        void *buf = nullptr;
+        cudaError_t e = cudaMalloc(&buf, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_err(ctx, "cudaMalloc failed for the global discord scratch");
+            throw Fail{MAD_ENOMEM};
+        }
+        char *p = (char *)buf;
+        a.tv = (double *)p;
+        p += nt * sizeof(double);
+        a.tk = (int64_t *)p;
+        p += nt * sizeof(int64_t);
+        a.out.norm = (double *)p;
+        p += cells * sizeof(double);
+        a.out.dist = (double *)p;
+        p += cells * sizeof(double);
+        a.out.off = (int32_t *)p;
+        p += cells * sizeof(int32_t);
+        a.out.len = (int32_t *)p;
+        p += cells * sizeof(int32_t);
+        a.out.nn = (int32_t *)p;
+        std::vector<double> nd(cells), dd(cells);
+        std::vector<int32_t> off(cells), len(cells), nn(cells);
+        cudaError_t e2 = cudaMemsetAsync(a.out.len, 0, cells * sizeof(int32_t), st);
+        if (e2 == cudaSuccess) {
+            launch_discords_global(a, st);
+            e2 = cudaGetLastError();
+        }
+        if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(nd.data(), a.out.norm, cells * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(dd.data(), a.out.dist, cells * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(off.data(), a.out.off, cells * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(len.data(), a.out.len, cells * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(nn.data(), a.out.nn, cells * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        cudaError_t e3 = cudaStreamSynchronize(st);
+        cudaFree(buf);
+        CK(e2);
+        CK(e3);
+        finish_discords(ctx, s, k, m, m, nd, dd, off, len, nn, out);
         *n_out = k * m;
     });
 }
