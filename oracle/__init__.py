@@ -75,6 +75,10 @@ def _L():
                                     P, P, P, P, P]),
             "orc_discords_global": (C.c_int, [i64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                               C.c_int, P, P, P, P, P, P, P]),
+            "orc_dkm_streamed": (None, [i64, P, P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                        P, P, P]),
+            "orc_discords_streamed": (None, [i64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                             C.c_int, P, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -286,6 +290,29 @@ def discords_global(n, lmin, lmax, k, m_max, m, nnd_all, nnj_all, num=1, den=4):
     got = _L().orc_discords_global(n, lmin, lmax, num, den, k, m_max, m, _p(nnd_all), _p(nnj_all),
                                    _p(off), _p(ln), _p(dd), _p(nd), _p(nn))
     return [(int(off[r]), int(ln[r]), float(dd[r]), float(nd[r]), int(nn[r])) for r in range(got)]
+
+
+def dkm_streamed(nnd, nnj, l, k, m, num=1, den=4):
+    """dkm_l as Algorithms 7 and 8 print it, from n_l x m_max best-match
+    tables: arrays (k, m) off (-1 = empty), dist, nn."""
+    nnd = _f64(nnd)
+    nnj = np.ascontiguousarray(nnj, np.int64)
+    nl, m_max = nnd.shape
+    off, dd, nn = np.empty((k, m), np.int64), np.empty((k, m)), np.empty((k, m), np.int64)
+    _L().orc_dkm_streamed(nl, _p(nnd), _p(nnj), m_max, l, num, den, k, m, _p(off), _p(dd), _p(nn))
+    return dict(off=off, dist=dd, nn=nn)
+
+
+def discords_streamed(n, lmin, lmax, k, m_max, m, nnd_all, nnj_all, num=1, den=4):
+    """dkm_{lmin,lmax} from the streamed dkm_l, merged by Algorithm 9:
+    arrays of shape (k, m) as discords()."""
+    nnd_all = _f64(nnd_all)
+    nnj_all = np.ascontiguousarray(nnj_all, np.int64)
+    off, ln = np.empty((k, m), np.int64), np.empty((k, m), np.int32)
+    dd, nd, nn = np.empty((k, m)), np.empty((k, m)), np.empty((k, m), np.int64)
+    _L().orc_discords_streamed(n, lmin, lmax, num, den, k, m_max, m, _p(nnd_all), _p(nnj_all),
+                               _p(off), _p(ln), _p(dd), _p(nd), _p(nn))
+    return dict(off=off, len=ln, dist=dd, norm=nd, nn=nn)
 
 
 def discords(n, lmin, lmax, k, m_max, nnd_all, nnj_all, num=1, den=4):

@@ -873,6 +873,91 @@ int orc_discords_global(i64 n, int lmin, int lmax, int num, int den, int k, int 
     return got;
 }
 
+/* dkm_l built as Algorithms 7 and 8 print it (the "streamed" form): windows
+ * visited by offset ascending; a window with a trivial match (|i - o| <= E(l))
+ * among the offsets currently anywhere in the matrix is skipped; otherwise
+ * columns are tried from m down to 1 with the window's j-th best-match
+ * distance, and it enters the first column where it is larger than some
+ * entry, at the first such rank, the entries below moving down one rank (the
+ * last one leaves). A window enters at most one cell. Empty cells hold -inf;
+ * a column value that is not finite is not tried. nd / nq: n_l x m_max
+ * (row-major) best-match distances and neighbours; outputs k x m (rank-major):
+ * off (-1 = empty), d, nn. */
+void orc_dkm_streamed(i64 nl, const double *nd, const i64 *nq, int m_max, int l, int num, int den, int k, int m,
+                      i64 *out_off, double *out_d, i64 *out_nn)
+{
+    i64 E = orc_excl(l, num, den);
+    for (int c = 0; c < k * m; ++c) {
+        out_off[c] = -1;
+        out_d[c] = -INFINITY;
+        out_nn[c] = -1;
+    }
+    for (i64 i = 0; i < nl; ++i) {
+        int trivial = 0;
+        for (int c = 0; c < k * m && !trivial; ++c)
+            if (out_off[c] >= 0 && iabs64(i - out_off[c]) <= E) trivial = 1;
+        if (trivial) continue;
+        int placed = 0;
+        for (int j = m - 1; j >= 0 && !placed; --j) {
+            double v = nd[i * m_max + j];
+            if (!isfinite(v)) continue;
+            for (int r = 0; r < k; ++r) {
+                if (!(v > out_d[r * m + j])) continue;
+                for (int q = k - 1; q > r; --q) {
+                    out_off[q * m + j] = out_off[(q - 1) * m + j];
+                    out_d[q * m + j] = out_d[(q - 1) * m + j];
+                    out_nn[q * m + j] = out_nn[(q - 1) * m + j];
+                }
+                out_off[r * m + j] = i;
+                out_d[r * m + j] = v;
+                out_nn[r * m + j] = nq[i * m_max + j];
+                placed = 1;
+                break;
+            }
+        }
+    }
+}
+
+/* dkm_{lmin,lmax} from the streamed dkm_l of every length, merged cell by
+ * cell as Algorithm 9 does (largest d / sqrt(l), ties to the later length).
+ * nnd_all / nnj_all as for orc_discords; outputs k x m as orc_discords. */
+void orc_discords_streamed(i64 n, int lmin, int lmax, int num, int den, int k, int m_max, int m,
+                           const double *nnd_all, const i64 *nnj_all,
+                           i64 *out_off, int32_t *out_len, double *out_d, double *out_nd, i64 *out_nn)
+{
+    i64 n0 = n - lmin + 1;
+    i64 *off = (i64 *)malloc(sizeof(i64) * (size_t)(k * m));
+    double *dd = (double *)malloc(sizeof(double) * (size_t)(k * m));
+    i64 *nj = (i64 *)malloc(sizeof(i64) * (size_t)(k * m));
+    for (int c = 0; c < k * m; ++c) {
+        out_len[c] = 0;
+        out_off[c] = -1;
+        out_nn[c] = -1;
+        out_d[c] = -INFINITY;
+        out_nd[c] = -INFINITY;
+    }
+    for (int l = lmin; l <= lmax; ++l) {
+        const double *nd = nnd_all + (i64)(l - lmin) * n0 * m_max;
+        const i64 *nq = nnj_all + (i64)(l - lmin) * n0 * m_max;
+        orc_dkm_streamed(n - l + 1, nd, nq, m_max, l, num, den, k, m, off, dd, nj);
+        double f = sqrt((double)l);
+        for (int c = 0; c < k * m; ++c) {
+            if (off[c] < 0) continue;
+            double v = dd[c] / f;
+            if (out_len[c] == 0 || v >= out_nd[c]) {
+                out_nd[c] = v;
+                out_d[c] = dd[c];
+                out_off[c] = off[c];
+                out_len[c] = l;
+                out_nn[c] = nj[c];
+            }
+        }
+    }
+    free(off);
+    free(dd);
+    free(nj);
+}
+
 /* Variable-length Top-k m-th discords dkm_{lmin,lmax} (Algorithm 7 driving
  * Algorithm 9): for every length, every column m = 1..m_max and every rank
  * r = 1..k, keep the entry with the largest d / sqrt(l); ties go to the later

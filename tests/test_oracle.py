@@ -489,6 +489,68 @@ def test_global_discords_planted_spike():
     assert top[0] <= 700 < top[0] + top[1]
 
 
+def _streamed_invariants(t, E):
+    offs = [int(o) for o in t["off"].ravel() if o >= 0]
+    assert len(offs) == len(set(offs))                      # a window in at most one cell
+    for a in range(len(offs)):
+        for b in range(a):
+            assert abs(offs[a] - offs[b]) > E                # pairwise non-trivial
+    for c in range(t["dist"].shape[1]):
+        col = t["dist"][:, c]
+        assert np.all(col[:-1] >= col[1:])                   # ranked within a column
+
+
+def test_streamed_dkm_pins():
+    x = workloads.ar2(700, 101)
+    lmin, lmax, m_max, k = 20, 23, 3, 5
+    pl = oracle.valmp_plain(x, lmin, lmax, m_max=m_max, keep_nn=True)
+    n = len(x)
+    for li, l in enumerate(range(lmin, lmax + 1)):
+        nl = n - l + 1
+        nd, nj = pl["nnd"][li, :nl], pl["nnj"][li, :nl]
+        for m in (1, 2, 3):
+            t = oracle.dkm_streamed(nd, nj, l, k, m)
+            _streamed_invariants(t, oracle.excl(l))
+            assert np.all(t["off"] >= 0)
+            # no exclusion zone: the last column tried first is the exact top-k
+            t0 = oracle.dkm_streamed(nd, nj, l, k, m, num=0, den=1)
+            top = np.argsort(-nd[:, m - 1], kind="stable")[:k]
+            assert list(t0["off"][:, m - 1]) == list(top)
+            assert np.array_equal(t0["dist"][:, m - 1], nd[top, m - 1])
+            assert np.array_equal(t0["nn"][:, m - 1], nj[top, m - 1])
+            _streamed_invariants(t0, 0)
+    # Algorithm 9's merge: per cell the largest d / sqrt(l) over the lengths
+    for m in (1, 3):
+        g = oracle.discords_streamed(n, lmin, lmax, k, m_max, m, pl["nnd"], pl["nnj"])
+        for r in range(k):
+            for c in range(m):
+                best = None
+                for li, l in enumerate(range(lmin, lmax + 1)):
+                    nl = n - l + 1
+                    t = oracle.dkm_streamed(pl["nnd"][li, :nl], pl["nnj"][li, :nl], l, k, m)
+                    v = t["dist"][r, c] / np.sqrt(l)
+                    if best is None or v >= best[0]:
+                        best = (v, int(t["off"][r, c]), l)
+                assert (g["norm"][r, c], int(g["off"][r, c]), int(g["len"][r, c])) == best
+
+
+def test_streamed_dkm_planted_spike():
+    # a spike on a noisy sine: the window at rank 1 of column 1 covers it
+    # (windows over it that are more than E apart may follow at lower ranks:
+    # the streamed form only keeps present entries pairwise non-trivial)
+    rng = np.random.default_rng(102)
+    t_ = np.arange(3000)
+    x = np.sin(2 * np.pi * t_ / 50) + 0.05 * rng.standard_normal(3000)
+    x[1300] += 3.0
+    l = 24
+    pl = oracle.valmp_plain(x, l, l, keep_nn=True)
+    nl = len(x) - l + 1
+    t = oracle.dkm_streamed(pl["nnd"][0, :nl], pl["nnj"][0, :nl], l, 3, 1)
+    offs = [int(o) for o in t["off"][:, 0]]
+    assert offs[0] <= 1300 < offs[0] + l, offs
+    _streamed_invariants(t, oracle.excl(l))
+
+
 # ---------------------------------------------------------------- read-outs
 
 def test_topk_motif_planted_pair():
