@@ -234,6 +234,25 @@ MAD_API mad_status mad_discords(mad_ctx *ctx, int32_t series, int32_t k, int32_t
 MAD_API mad_status mad_discords_global(mad_ctx *ctx, int32_t series, int32_t k, int32_t m,
                                        mad_discord *out, int32_t *n_out);
 
+/* dkm_{lmin,lmax} built the way Algorithms 7 and 8 print it (the
+ * "streamed" form), then merged across lengths by Algorithm 9: per length,
+ * windows are visited by offset ascending; a window with a trivial match
+ * (|i - o| <= E(l)) among the offsets present anywhere in the k x m matrix is
+ * skipped; otherwise columns m down to 1 are tried with its j-th best-match
+ * distance, and it enters the first column where it is larger than some
+ * entry, at the first such rank (the entries below move down one rank, the
+ * last leaves), so a window holds at most one cell. The result depends on
+ * the visiting order and on m; mad_discords ranks each column on its own
+ * instead. Needs a mode-0 profile made with keep_profiles. out: k * m
+ * entries, rank-major as for mad_discords (an empty cell has off = -1,
+ * len = 0); dist_recheck is the FP64 re-check. Requires 1 <= k <= 64,
+ * 1 <= m <= m_max. Errors: MAD_EINVAL for bad arguments or a profile without
+ * keep_profiles, MAD_ESTATE before mad_profile or in motif mode, MAD_ENOMEM
+ * when the per-length tables (16 B per cell and length) cannot be
+ * allocated. */
+MAD_API mad_status mad_discords_streamed(mad_ctx *ctx, int32_t series, int32_t k, int32_t m,
+                                         mad_discord *out, int32_t *n_out);
+
 /* Copy VALMP of series `series` to host arrays of n - lmin + 1 entries:
  * raw distance, normalised distance, length, nearest-neighbour offset. */
 MAD_API mad_status mad_valmp(mad_ctx *ctx, int32_t series, double *dist, double *norm,

@@ -30,7 +30,8 @@ MAD_NOALLOC_MAX_SLOTS = 1024
 STATUS_NAMES = {0: "MAD_OK", 1: "MAD_EINVAL", 2: "MAD_ENOMEM", 3: "MAD_ECUDA", 4: "MAD_ESTATE",
                 5: "MAD_ETIMEOUT", 6: "MAD_EINTERNAL"}
 ABI_FUNCTIONS = ("mad_create", "mad_create_device", "mad_create_batch", "mad_profile", "mad_profile_batch",
-                 "mad_motifs", "mad_discords", "mad_discords_global", "mad_valmp", "mad_matrix_profile", "mad_stats",
+                 "mad_motifs", "mad_discords", "mad_discords_global", "mad_discords_streamed",
+                 "mad_valmp", "mad_matrix_profile", "mad_stats",
                  "mad_mth_nn_dist_noalloc", "mad_motif_sets", "mad_observe", "mad_last_error",
                  "mad_destroy")
 
@@ -94,6 +95,7 @@ def library() -> C.CDLL:
             "mad_motifs": [P, i32, i32, C.POINTER(mad_motif), C.POINTER(i32)],
             "mad_discords": [P, i32, i32, i32, C.POINTER(mad_discord), C.POINTER(i32)],
             "mad_discords_global": [P, i32, i32, i32, C.POINTER(mad_discord), C.POINTER(i32)],
+            "mad_discords_streamed": [P, i32, i32, i32, C.POINTER(mad_discord), C.POINTER(i32)],
             "mad_valmp": [P, i32, P, P, P, P],
             "mad_matrix_profile": [P, i32, i32, P, P, P, P],
             "mad_stats": [P, i32, C.POINTER(mad_length_stats), i32, C.POINTER(i32)],
@@ -223,6 +225,16 @@ def mad_discords_global(ctx, series, k, m):
     out = (mad_discord * (k * m))()
     n = C.c_int32()
     _check(library().mad_discords_global(ctx, series, k, m, out, C.byref(n)), ctx)
+    return [dict(off=d.off, nn=d.nn, len=d.len, rank=d.rank, m=d.m, dist=d.dist, norm_dist=d.norm_dist,
+                 dist_recheck=d.dist_recheck) for d in out[:n.value]]
+
+
+def mad_discords_streamed(ctx, series, k, m):
+    """dkm_{lmin,lmax} in the streamed form of Algorithms 7 and 8 (needs
+    keep_profiles=True): list (rank-major) of dicts like mad_discords."""
+    out = (mad_discord * (k * m))()
+    n = C.c_int32()
+    _check(library().mad_discords_streamed(ctx, series, k, m, out, C.byref(n)), ctx)
     return [dict(off=d.off, nn=d.nn, len=d.len, rank=d.rank, m=d.m, dist=d.dist, norm_dist=d.norm_dist,
                  dist_recheck=d.dist_recheck) for d in out[:n.value]]
 

@@ -282,6 +282,138 @@ void launch_discords_global(const GDiscArgs &a, cudaStream_t s)
     k_gdisc_greedy<<<a.mcols, 1024, 0, s>>>(a);
 }
 
+// ------------------------------------------------------ streamed dkm_l
+
+// dkm_l as Algorithms 7 and 8 print it, one warp per length: windows in
+// offset order; one with a trivial match among the offsets present anywhere
+// in the matrix is skipped; else columns m..1 are tried and the window
+// enters the first column where it beats an entry, at the first rank it
+// beats, the rest of the column moving down one rank. A column's last entry
+// (its minimum, -inf while not full) only grows, so a batch of 32 windows is
+// screened against it first and only the windows above some column's minimum
+// run the exact steps, one at a time in offset order.
+constexpr int STREAM_WARPS = 4;
+
+__global__ void __launch_bounds__(STREAM_WARPS * 32) k_dkm_streamed(StreamArgs A)
+{
+    __shared__ double cmin_all[STREAM_WARPS][KMAX];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int li = blockIdx.x * STREAM_WARPS + wid;
+    if (li >= A.nL) return;
+    double *cmin = cmin_all[wid];
+    const int l = A.lmin + li, k = A.k, m = A.m;
+    const int64_t nl = A.n - l + 1;
+    const int64_t E = excl_zone(l, A.num, A.den);
+    const int cells = k * m;
+    double *D = A.d + (int64_t)li * cells;
+    int32_t *O = A.o + (int64_t)li * cells;
+    int32_t *N = A.nn + (int64_t)li * cells;
+    const double *sc = A.nnd + (int64_t)li * A.m_max * A.n0;      // column c at sc + c * n0
+    const int32_t *sj = A.nnj + (int64_t)li * A.m_max * A.n0;
+    for (int c = lane; c < cells; c += 32) {
+        D[c] = ninf();
+        O[c] = -1;
+        N[c] = -1;
+    }
+    for (int c = lane; c < m; c += 32) cmin[c] = ninf();
+    __syncwarp();
+    for (int64_t base = 0; base < nl; base += 32) {
+        const int64_t i = base + lane;
+        bool cand = false;
+        if (i < nl)
+            for (int c = 0; c < m && !cand; ++c) {
+                const double v = sc[(int64_t)c * A.n0 + i];
+                cand = isfinite(v) && v > cmin[c];
+            }
+        unsigned mask = __ballot_sync(0xffffffffu, cand);
+        while (mask) {
+            const int t = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int64_t ii = base + t;
+            bool triv = false;
+            for (int c = lane; c < cells; c += 32) {
+                const int64_t o = O[c];
+                triv |= o >= 0 && ii - o <= E && o - ii <= E;
+            }
+            if (__any_sync(0xffffffffu, triv)) continue;
+            for (int j = m - 1; j >= 0; --j) {
+                const double v = sc[(int64_t)j * A.n0 + ii];
+                if (!isfinite(v) || !(v > cmin[j])) continue;
+                // first rank r0 with v > D[r0][j] (exists: v beats the last entry)
+                const unsigned lo = __ballot_sync(0xffffffffu, lane < k && v > D[lane * m + j]);
+                const unsigned hi = __ballot_sync(0xffffffffu, lane + 32 < k && v > D[(lane + 32) * m + j]);
+                if (!lo && !hi) break;    // cannot happen while cmin[j] mirrors the last entry
+                const int r0 = lo ? __ffs(lo) - 1 : 32 + __ffs(hi) - 1;
+                double sd[2];
+                int32_t so[2], sn[2];
+                for (int h = 0; h < 2; ++h) {
+                    const int rr = lane + 32 * h;
+                    if (rr >= r0 && rr < k - 1) {
+                        sd[h] = D[rr * m + j];
+                        so[h] = O[rr * m + j];
+                        sn[h] = N[rr * m + j];
+                    }
+                }
+                __syncwarp();
+                for (int h = 0; h < 2; ++h) {
+                    const int rr = lane + 32 * h;
+                    if (rr >= r0 && rr < k - 1) {
+                        D[(rr + 1) * m + j] = sd[h];
+                        O[(rr + 1) * m + j] = so[h];
+                        N[(rr + 1) * m + j] = sn[h];
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    D[r0 * m + j] = v;
+                    O[r0 * m + j] = (int32_t)ii;
+                    N[r0 * m + j] = sj[(int64_t)j * A.n0 + ii];
+                }
+                __syncwarp();
+                if (lane == 0) cmin[j] = D[(k - 1) * m + j];
+                __syncwarp();
+                break;
+            }
+        }
+    }
+}
+
+// Algorithm 9 over the streamed tables: per cell the largest d / sqrt(l),
+// ties to the later length.
+__global__ void k_dkm_streamed_merge(StreamArgs A)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cells = A.k * A.m;
+    if (c >= cells) return;
+    double best = ninf(), bd = 0.0;
+    int32_t bo = -1, bl = 0, bn = -1;
+    for (int li = 0; li < A.nL; ++li) {
+        const int64_t at = (int64_t)li * cells + c;
+        if (A.o[at] < 0) continue;
+        const int l = A.lmin + li;
+        const double v = A.d[at] / sqrt((double)l);
+        if (bl == 0 || v >= best) {
+            best = v;
+            bd = A.d[at];
+            bo = A.o[at];
+            bl = l;
+            bn = A.nn[at];
+        }
+    }
+    A.out.norm[c] = best;
+    A.out.dist[c] = bd;
+    A.out.off[c] = bo;
+    A.out.len[c] = bl;
+    A.out.nn[c] = bn;
+}
+
+void launch_discords_streamed(const StreamArgs &a, cudaStream_t s)
+{
+    k_dkm_streamed<<<(a.nL + STREAM_WARPS - 1) / STREAM_WARPS, STREAM_WARPS * 32, 0, s>>>(a);
+    const int cells = a.k * a.m;
+    k_dkm_streamed_merge<<<(cells + 255) / 256, 256, 0, s>>>(a);
+}
+
 // --------------------------------------------------------------- motifs
 
 // One greedy round over VALMP: the best (normalised distance asc, offset asc)

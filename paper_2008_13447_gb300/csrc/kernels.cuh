@@ -333,6 +333,17 @@ struct GDiscArgs {          // global-greedy discords over the kept profiles
     int64_t *tk;            // its key
     DiscTable out;          // k x mcols cells, rank-major
 };
+struct StreamArgs {         // dkm_l streamed (Algorithms 7 and 8) and merged (Algorithm 9)
+    const double *nnd;      // kept profiles [nL][m_max][n0]
+    const int32_t *nnj;
+    int64_t n, n0;
+    int lmin, nL, m_max, num, den;
+    int k, m;               // ranks and columns 1..m
+    double *d;              // [nL][k][m] per-length tables
+    int32_t *o, *nn;
+    DiscTable out;          // k x m cells, rank-major
+};
+void launch_discords_streamed(const StreamArgs &a, cudaStream_t s);
 constexpr int GDISC_TILE = 256;
 void launch_discords_global(const GDiscArgs &a, cudaStream_t s);
 void launch_discords_length(const double *nnd, const int32_t *nnj, int64_t n0, int64_t nl, int l, int64_t E,

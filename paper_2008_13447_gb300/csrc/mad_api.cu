@@ -1198,6 +1198,80 @@ MAD_API mad_status mad_discords_global(mad_ctx *ctx, int32_t series, int32_t k, 
     });
 }
 
+MAD_API mad_status mad_discords_streamed(mad_ctx *ctx, int32_t series, int32_t k, int32_t m, mad_discord *out,
+                                         int32_t *n_out)
+{
+    if (!ctx) { g_create_err = "ctx is NULL"; return MAD_EINVAL; }
+    return run_guarded(ctx, [&] {
+        Series &s = get_series(ctx, series);
+        REQUIRE(out != nullptr && n_out != nullptr, "output pointers are NULL");
+        if (!s.profiled) {
+            set_err(ctx, "mad_discords_streamed before mad_profile");
+            throw Fail{MAD_ESTATE};
+        }
+        REQUIRE(k >= 1 && k <= KMAX, "k must be in [1, 64]");
+        REQUIRE(m >= 1 && m <= s.m_max, "m must be in [1, m_max]");
+        if (ctx->opt.mode == 1) {
+            set_err(ctx, "streamed discords need mode 0 (exact rows)");
+            throw Fail{MAD_ESTATE};
+        }
+        REQUIRE(s.keep_nnd != nullptr, "profile was computed without keep_profiles");
+        cudaStream_t st = ctx->stream;
+        StreamArgs a{};
+        a.nnd = s.keep_nnd;
+        a.nnj = s.keep_nnj;
+        a.n = s.n;
+        a.n0 = s.n0;
+        a.lmin = s.lmin;
+        a.nL = s.lmax - s.lmin + 1;
+        a.m_max = s.m_max;
+        a.num = ctx->opt.excl_num;
+        a.den = ctx->opt.excl_den;
+        a.k = k;
+        a.m = m;
+        const size_t cells = (size_t)k * m, tab = (size_t)a.nL * cells;
+        const size_t bytes = tab * (sizeof(double) + 2 * sizeof(int32_t)) + cells * (2 * sizeof(double) + 3 * sizeof(int32_t));
+        void *buf = nullptr;
+        cudaError_t e = cudaMalloc(&buf, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_err(ctx, "cudaMalloc failed for the streamed discord tables");
+            throw Fail{MAD_ENOMEM};
+        }
+        char *p = (char *)buf;
+        a.d = (double *)p;
+        p += tab * sizeof(double);
+        a.out.norm = (double *)p;
+        p += cells * sizeof(double);
+        a.out.dist = (double *)p;
+        p += cells * sizeof(double);
+        a.o = (int32_t *)p;
+        p += tab * sizeof(int32_t);
+        a.nn = (int32_t *)p;
+        p += tab * sizeof(int32_t);
+        a.out.off = (int32_t *)p;
+        p += cells * sizeof(int32_t);
+        a.out.len = (int32_t *)p;
+        p += cells * sizeof(int32_t);
+        a.out.nn = (int32_t *)p;
+        std::vector<double> nd(cells), dd(cells);
+        std::vector<int32_t> off(cells), len(cells), nn(cells);
+        launch_discords_streamed(a, st);
+        cudaError_t e2 = cudaGetLastError();
+        if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(nd.data(), a.out.norm, cells * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(dd.data(), a.out.dist, cells * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(off.data(), a.out.off, cells * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(len.data(), a.out.len, cells * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(nn.data(), a.out.nn, cells * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        cudaError_t e3 = cudaStreamSynchronize(st);
+        cudaFree(buf);
+        CK(e2);
+        CK(e3);
+        finish_discords(ctx, s, k, m, m, nd, dd, off, len, nn, out);
+        *n_out = k * m;
+    });
+}
+
 MAD_API mad_status mad_valmp(mad_ctx *ctx, int32_t series, double *dist, double *norm, int32_t *len, int64_t *nn)
 {
     if (!ctx) { g_create_err = "ctx is NULL"; return MAD_EINVAL; }

@@ -1,8 +1,14 @@
-"""Global-greedy variable-length discords on the GPU: the ranking over the
-GPU's own kept profiles identical to the oracle's ranking of the same
-profiles; against the oracle's own profiles, identical picks (FP64) or the
-same scores within the distance tolerance (FP32); pairwise separation by the
-larger exclusion zone; a planted spike; argument and state errors."""
+"""Discord read-out variants on the GPU.
+
+Global-greedy variable-length discords: the ranking over the GPU's own kept
+profiles identical to the oracle's ranking of the same profiles; against the
+oracle's own profiles, identical picks (FP64) or the same scores within the
+distance tolerance (FP32); pairwise separation by the larger exclusion zone;
+a planted spike; argument and state errors.
+
+Streamed dkm (Algorithms 7 and 8 as printed, merged by Algorithm 9): identical
+to the oracle given the same kept profiles, for k on both sides of one warp's
+32 ranks; FP64 also identical to the oracle's own profiles; errors."""
 import numpy as np
 import pytest
 
@@ -41,13 +47,14 @@ def as_cols(got, k, m):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_global_discords_match_oracle(prec):
+def test_discord_variants_match_oracle(prec):
     x = workloads.ar2(2500, 97)
     n, lmin, lmax, m_max, k = len(x), 24, 40, 2, 8
     ctx = mad.mad_create(x, precision=prec, k_max=4, m_max=m_max, keep_profiles=True)
     try:
         mad.mad_profile(ctx, lmin, lmax, 5)
         got = mad.mad_discords_global(ctx, 0, k, m_max)
+        streamed = {(k2, m): mad.mad_discords_streamed(ctx, 0, k2, m) for k2 in (6, 40) for m in (1, 2)}
         assert len(got) == k * m_max
         assert [(g["rank"], g["m"]) for g in got] == [(r + 1, c + 1) for r in range(k) for c in range(m_max)]
         nnd, nnj = kept_profiles(ctx, n, lmin, lmax, m_max)
@@ -75,6 +82,29 @@ def test_global_discords_match_oracle(prec):
                 assert g[:2] == r[:2]
         for g in got[c::m_max]:
             assert abs(g["dist"] - g["dist_recheck"]) <= tol * np.sqrt(g["len"]) * max(1.0, g["dist"])
+    for (k2, m), st in streamed.items():
+        assert [(g["rank"], g["m"]) for g in st] == [(r + 1, c + 1) for r in range(k2) for c in range(m)]
+        got_t = [(g["off"], g["len"], g["dist"], g["norm_dist"], g["nn"]) for g in st]
+        # the same profiles: identical
+        ref = oracle.discords_streamed(n, lmin, lmax, k2, m_max, m, nnd, nnj)
+        want = [(int(ref["off"][r, c]), int(ref["len"][r, c]), float(ref["dist"][r, c]),
+                 float(ref["norm"][r, c]), int(ref["nn"][r, c])) if ref["len"][r, c] > 0
+                else (-1, 0, None, None, -1) for r in range(k2) for c in range(m)]
+        for g, w in zip(got_t, want):
+            if w[1] == 0:
+                assert (g[0], g[1], g[4]) == (-1, 0, -1)
+            else:
+                assert g == w
+        assert sum(w[1] > 0 for w in want) >= min(k2, 6)
+        if prec == mad.MAD_FP64:
+            # the oracle's own profiles: the same cells, values within FP64 rounding
+            ref = oracle.discords_streamed(n, lmin, lmax, k2, m_max, m, pl["nnd"], pl["nnj"])
+            for r in range(k2):
+                for c in range(m):
+                    g = st[r * m + c]
+                    assert (g["off"], g["len"]) == (ref["off"][r, c], ref["len"][r, c])
+                    if g["len"] > 0:
+                        assert abs(g["norm_dist"] - ref["norm"][r, c]) <= 1e-9 * max(1.0, ref["norm"][r, c])
 
 
 def test_global_discords_planted_spike():
@@ -108,25 +138,27 @@ def test_global_discords_more_ranks_than_candidates():
     assert all(g["off"] == -1 and np.isnan(g["dist"]) for g in got[len(filled):])
 
 
-def test_global_discords_arguments():
+@pytest.mark.parametrize("fn", [mad.mad_discords_global, mad.mad_discords_streamed], ids=["global", "streamed"])
+def test_discord_variants_arguments(fn):
     x = workloads.random_walk(600, 100)
     ctx = mad.mad_create(x, precision=mad.MAD_FP32, k_max=2, m_max=2, keep_profiles=True)
     try:
         with pytest.raises(mad.MadError) as e:
-            mad.mad_discords_global(ctx, 0, 2, 1)           # before mad_profile
+            fn(ctx, 0, 2, 1)                                # before mad_profile
         assert e.value.status == mad.MAD_ESTATE
         mad.mad_profile(ctx, 20, 24, 3)
         for k, m in ((0, 1), (65, 1), (2, 0), (2, 3)):
             with pytest.raises(mad.MadError) as e:
-                mad.mad_discords_global(ctx, 0, k, m)
+                fn(ctx, 0, k, m)
             assert e.value.status == mad.MAD_EINVAL
+        assert len(fn(ctx, 0, 64, 2)) == 128                # k above k_max is allowed here
     finally:
         mad.mad_destroy(ctx)
     ctx = mad.mad_create(x, precision=mad.MAD_FP32, k_max=2, m_max=1)
     try:
         mad.mad_profile(ctx, 20, 24, 3)
         with pytest.raises(mad.MadError) as e:
-            mad.mad_discords_global(ctx, 0, 2, 1)           # no kept profiles
+            fn(ctx, 0, 2, 1)                                # no kept profiles
         assert e.value.status == mad.MAD_EINVAL
     finally:
         mad.mad_destroy(ctx)
@@ -134,7 +166,7 @@ def test_global_discords_arguments():
     try:
         mad.mad_profile(ctx, 20, 24, 3)
         with pytest.raises(mad.MadError) as e:
-            mad.mad_discords_global(ctx, 0, 2, 1)           # motif mode
+            fn(ctx, 0, 2, 1)                                # motif mode
         assert e.value.status == mad.MAD_ESTATE
     finally:
         mad.mad_destroy(ctx)
