@@ -47,6 +47,51 @@ void launch_seed<double>(const SeedArgs<double> &a, cudaStream_t s)
     smem_optin_max((const void *)k_seed<double>, once);
     k_seed<double><<<grid, B, sm, s>>>(a);
 }
+// Seed rows from length l to l + 1 without recomputing them: the centred
+// co-moment of two windows gains one pair of elements (the Welford
+// co-moment step), C_{l+1}(a, c) = C_l(a, c) + l/(l+1) (x[a+l] - mu_l[a])
+// (x[c+l] - mu_l[c]), applied in FP64 to the master copy in place; entries
+// whose windows no longer exist at l + 1 become 0 (as the direct kernel
+// writes them). The band kernel's copy in T is written from the master.
+// Entry (k, j) of the table: row 0 holds C(0, j); row k >= 1 holds C(kS, 0)
+// at j = 0 and C(kS - 1, j - 1) for j >= 1.
+template <typename T>
+__global__ void k_seed_step(const double *x, const double *mu, int64_t nl, int l, int S, int64_t spitch,
+                            double *master, T *seed, int update)
+{
+    const int k = blockIdx.y;
+    const int64_t kS = (int64_t)k * S;
+    const double f = (double)l / (double)(l + 1);
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < spitch;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t at = (int64_t)k * spitch + j;
+        double v = master[at];
+        if (update) {
+            int64_t ra, c;
+            if (k == 0) { ra = 0; c = j; }
+            else if (j == 0) { ra = kS; c = 0; }
+            else { ra = kS - 1; c = j - 1; }
+            v = (ra < nl && c < nl) ? fma(f * (x[ra + l] - mu[ra]), x[c + l] - mu[c], v) : 0.0;
+            master[at] = v;
+        }
+        seed[at] = (T)v;
+    }
+}
+
+template <typename T>
+void launch_seed_step(const double *x, const double *mu, int64_t nl, int l, int S, int64_t K, int64_t spitch,
+                      double *master, T *seed, bool update, cudaStream_t s)
+{
+    const int B = 256;
+    int64_t gx = (spitch + B - 1) / B;
+    if (gx > 1024) gx = 1024;
+    k_seed_step<T><<<dim3((unsigned)gx, (unsigned)K), B, 0, s>>>(x, mu, nl, l, S, spitch, master, seed, update ? 1 : 0);
+}
+template void launch_seed_step<float>(const double *, const double *, int64_t, int, int, int64_t, int64_t, double *,
+                                      float *, bool, cudaStream_t);
+template void launch_seed_step<double>(const double *, const double *, int64_t, int, int, int64_t, int64_t, double *,
+                                       double *, bool, cudaStream_t);
+
 template void launch_band<double>(const BandArgs<double> &, bool, int, cudaStream_t);
 template int band_occupancy<double>(bool, int, int);
 template size_t band_smem<double>(bool, int, int);

@@ -42,8 +42,13 @@ template <typename T> struct SeedArgs {
     const int32_t *nbands;  // nothing to do when the device count is 0
 };
 template <typename T> void launch_seed(const SeedArgs<T> &a, cudaStream_t s);
-template <> void launch_seed<float>(const SeedArgs<float> &a, cudaStream_t s);
 template <> void launch_seed<double>(const SeedArgs<double> &a, cudaStream_t s);
+// Seed rows stepped from length l to l + 1 (update) or only copied to T:
+// mu = window means at l, nl = windows at l + 1, master = FP64 seed rows
+// (updated in place), seed = the band kernel's copy.
+template <typename T>
+void launch_seed_step(const double *x, const double *mu, int64_t nl, int l, int S, int64_t K, int64_t spitch,
+                      double *master, T *seed, bool update, cudaStream_t s);
 
 template <typename T> struct BandArgs {
     const Col<T> *col;      // per-window recurrence data, rows and columns

@@ -218,6 +218,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
     // while length l's band kernel runs
     Col<T> *colb[2] = {dalloc<Col<T>>(ctx, s, npad), dalloc<Col<T>>(ctx, s, npad)};
     T *seedb[2] = {dalloc<T>(ctx, s, K * spitch), dalloc<T>(ctx, s, K * spitch)};
+    double *seedm = dalloc<double>(ctx, s, K * spitch);   // FP64 master of the seed rows
     T *thr = dalloc<T>(ctx, s, npad);
     RowState rs{dalloc<int32_t>(ctx, s, (size_t)p * n0), dalloc<double>(ctx, s, (size_t)p * n0),
                 dalloc<double>(ctx, s, (size_t)p * n0), dalloc<double>(ctx, s, n0),
@@ -399,7 +400,8 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
     cudaEvent_t *ev_prep = side.ev + 6;   // [2], length prepared (by parity)
     cudaEvent_t *ev_ext = side.ev + 8;    // [2], extension done (by parity)
     // Preparation of length l on the side stream: window statistics (one
-    // Welford step), column data and 1/sqrt(M2), contrast factors, seed rows.
+    // Welford step), column data and 1/sqrt(M2), contrast factors, seed rows
+    // (one FP64 co-moment step from the previous length).
     // Its buffers (parity of l) held length l-2, whose last readers (band,
     // direct and merge kernels of l-2, extension of l-1 for the means) are
     // done once the extension of l-1 is.
@@ -412,8 +414,15 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
                                                                              mu[b], m2[b]);
         launch_coldata<T>(s.x, nl, npad, l, mu[b], m2[b], run, colb[b], isdb[b], side.prep);
         launch_kappa(m2[b], run, nl, l, R, m2blk, kappab[b], kmaxb[b], side.prep);
-        SeedArgs<T> sa{s.x, mu[b], nl, l, SP, krows, (int)K, spitch, seedb[b], nullptr};
-        launch_seed<T>(sa, side.prep);
+        if (l == lmin) {
+            // seed rows computed directly once, in FP64; every later length
+            // steps them by one co-moment update
+            SeedArgs<double> sa{s.x, mu[b], nl, l, SP, krows, (int)K, spitch, seedm, nullptr};
+            launch_seed<double>(sa, side.prep);
+            launch_seed_step<T>(s.x, mu[b], nl, l, SP, K, spitch, seedm, seedb[b], false, side.prep);
+        } else {
+            launch_seed_step<T>(s.x, mu[b ^ 1], nl, l - 1, SP, K, spitch, seedm, seedb[b], true, side.prep);
+        }
         CK(cudaEventRecord(ev_prep[b], side.prep));
         CK(cudaGetLastError());
     };
