@@ -883,39 +883,225 @@ int orc_discords_global(i64 n, int lmin, int lmax, int num, int den, int k, int 
  * a column value that is not finite is not tried. nd / nq: n_l x m_max
  * (row-major) best-match distances and neighbours; outputs k x m (rank-major):
  * off (-1 = empty), d, nn. */
+static void dkm_clear(int k, int m, i64 *off, double *d, i64 *nn)
+{
+    for (int c = 0; c < k * m; ++c) {
+        off[c] = -1;
+        d[c] = -INFINITY;
+        nn[c] = -1;
+    }
+}
+
+/* Has window i a trivial match among the offsets present in the matrix? */
+static int dkm_trivial(int k, int m, const i64 *off, i64 i, i64 E)
+{
+    for (int c = 0; c < k * m; ++c)
+        if (off[c] >= 0 && iabs64(i - off[c]) <= E) return 1;
+    return 0;
+}
+
+/* Algorithm 8 for window i with j-th best-match distances v[0..m) and
+ * neighbours vj[0..m): columns m..1, the first column and rank where it is
+ * larger, the rest of the column moving down. */
+static void dkm_insert(int k, int m, i64 *off, double *d, i64 *nn, i64 i, const double *v, const i64 *vj)
+{
+    for (int j = m - 1; j >= 0; --j) {
+        if (!isfinite(v[j])) continue;
+        for (int r = 0; r < k; ++r) {
+            if (!(v[j] > d[r * m + j])) continue;
+            for (int q = k - 1; q > r; --q) {
+                off[q * m + j] = off[(q - 1) * m + j];
+                d[q * m + j] = d[(q - 1) * m + j];
+                nn[q * m + j] = nn[(q - 1) * m + j];
+            }
+            off[r * m + j] = i;
+            d[r * m + j] = v[j];
+            nn[r * m + j] = vj[j];
+            return;
+        }
+    }
+}
+
 void orc_dkm_streamed(i64 nl, const double *nd, const i64 *nq, int m_max, int l, int num, int den, int k, int m,
                       i64 *out_off, double *out_d, i64 *out_nn)
 {
     i64 E = orc_excl(l, num, den);
-    for (int c = 0; c < k * m; ++c) {
-        out_off[c] = -1;
-        out_d[c] = -INFINITY;
-        out_nn[c] = -1;
-    }
+    dkm_clear(k, m, out_off, out_d, out_nn);
     for (i64 i = 0; i < nl; ++i) {
-        int trivial = 0;
-        for (int c = 0; c < k * m && !trivial; ++c)
-            if (out_off[c] >= 0 && iabs64(i - out_off[c]) <= E) trivial = 1;
-        if (trivial) continue;
-        int placed = 0;
-        for (int j = m - 1; j >= 0 && !placed; --j) {
-            double v = nd[i * m_max + j];
-            if (!isfinite(v)) continue;
-            for (int r = 0; r < k; ++r) {
-                if (!(v > out_d[r * m + j])) continue;
-                for (int q = k - 1; q > r; --q) {
-                    out_off[q * m + j] = out_off[(q - 1) * m + j];
-                    out_d[q * m + j] = out_d[(q - 1) * m + j];
-                    out_nn[q * m + j] = out_nn[(q - 1) * m + j];
-                }
-                out_off[r * m + j] = i;
-                out_d[r * m + j] = v;
-                out_nn[r * m + j] = nq[i * m_max + j];
-                placed = 1;
-                break;
-            }
+        if (dkm_trivial(k, m, out_off, i, E)) continue;
+        dkm_insert(k, m, out_off, out_d, out_nn, i, nd + i * m_max, nq + i * m_max);
+    }
+}
+
+/* Algorithm 9: cell by cell, the largest d / sqrt(l), ties to the later
+ * length. */
+static void dkm_merge(int k, int m, int l, const i64 *off, const double *d, const i64 *nn, i64 *out_off,
+                      int32_t *out_len, double *out_d, double *out_nd, i64 *out_nn)
+{
+    double f = sqrt((double)l);
+    for (int c = 0; c < k * m; ++c) {
+        if (off[c] < 0) continue;
+        double v = d[c] / f;
+        if (out_len[c] == 0 || v >= out_nd[c]) {
+            out_nd[c] = v;
+            out_d[c] = d[c];
+            out_off[c] = off[c];
+            out_len[c] = l;
+            out_nn[c] = nn[c];
         }
     }
+}
+
+/* Top-k m-th discords with the paper's pruning (Algorithm 7 driving
+ * Algorithm 10, each dkm_l merged by Algorithm 9):
+ *  - lmin: every row's full profile (Algorithm 3), then windows in offset
+ *    order, each without a trivial match in dkm_lmin inserted by
+ *    Algorithm 8 with its exact 1st..m-th best-match distances;
+ *  - every longer length, first pass in offset order: each row's stored
+ *    entries are re-evaluated (trivial / out-of-range ones skipped) and
+ *    sorted; s_j is the j-th smallest (+inf when fewer than j); a window
+ *    with a trivial match in dkm_l is skipped; otherwise it is valid iff
+ *    s_m < B (its bound, Eq. LB; a flat row is never valid) and then
+ *    inserted with s_1..s_m (exact, as the bound certifies them), else it
+ *    joins the non-valid list with its s_1..s_m;
+ *  - second pass over the list in order: a window with a trivial match in
+ *    dkm_l is skipped; otherwise, for j = m down to 1, the first s_j larger
+ *    than the k-th entry of column j triggers the row's full profile
+ *    (stored entries, bound base and base length renewed) and its insertion
+ *    with the exact distances;
+ *  - rows neither valid nor recomputed keep their extended stored entries.
+ * Outputs: the merged k x m table (as orc_discords), optionally every
+ * dkm_l (dkm_off / dkm_d [(l - lmin) * k * m + cell]) and per-length stats
+ * [(l - lmin) * 4 + {0..3}] = rows, valid, listed, recomputed. */
+void orc_valmod_discord(const double *x, i64 n, int lmin, int lmax, int num, int den, int p, int k, int m,
+                        i64 *out_off, int32_t *out_len, double *out_d, double *out_nd, i64 *out_nn,
+                        i64 *dkm_off, double *dkm_d, i64 *stats)
+{
+    i64 n0 = n - lmin + 1;
+    row_state *st = (row_state *)calloc((size_t)n0, sizeof(row_state));
+    i64 *jstore = (i64 *)malloc(sizeof(i64) * (size_t)(n0 * p));
+    for (i64 i = 0; i < n0; ++i) st[i].j = jstore + i * p;
+    double *mp = (double *)malloc(sizeof(double) * (size_t)n0);
+    i64 *ip = (i64 *)malloc(sizeof(i64) * (size_t)n0);
+    double *nnd = (double *)malloc(sizeof(double) * (size_t)(n0 * m));
+    i64 *nnj = (i64 *)malloc(sizeof(i64) * (size_t)(n0 * m));
+    double *sv = (double *)malloc(sizeof(double) * (size_t)(n0 * m));   /* s_1..s_m per row */
+    i64 *svj = (i64 *)malloc(sizeof(i64) * (size_t)(n0 * m));
+    signed char *valid = (signed char *)malloc((size_t)n0);
+    i64 *list = (i64 *)malloc(sizeof(i64) * (size_t)n0);
+    i64 *off = (i64 *)malloc(sizeof(i64) * (size_t)(k * m));
+    double *dd = (double *)malloc(sizeof(double) * (size_t)(k * m));
+    i64 *nj = (i64 *)malloc(sizeof(i64) * (size_t)(k * m));
+    double *prof = (double *)malloc(sizeof(double) * (size_t)n0);
+    dj_t *dbuf = (dj_t *)malloc(sizeof(dj_t) * (size_t)n0);
+    qj_t *qbuf = (qj_t *)malloc(sizeof(qj_t) * (size_t)n0);
+    for (int c = 0; c < k * m; ++c) {
+        out_len[c] = 0;
+        out_off[c] = -1;
+        out_nn[c] = -1;
+        out_d[c] = -INFINITY;
+        out_nd[c] = -INFINITY;
+    }
+    for (int l = lmin; l <= lmax; ++l) {
+        i64 nl = n - l + 1, E = orc_excl(l, num, den);
+        i64 nvalid = 0, nlist = 0, nrecomp = 0;
+        dkm_clear(k, m, off, dd, nj);
+        if (l == lmin) {
+#pragma omp parallel
+            {
+                double *pr = (double *)malloc(sizeof(double) * (size_t)n0);
+                dj_t *db = (dj_t *)malloc(sizeof(dj_t) * (size_t)n0);
+                qj_t *qb = (qj_t *)malloc(sizeof(qj_t) * (size_t)n0);
+#pragma omp for schedule(dynamic, 8)
+                for (i64 i = 0; i < nl; ++i)
+                    recompute_row(x, n, l, num, den, p, m, i, &st[i], mp, ip, nnd, nnj, pr, db, qb);
+                free(pr);
+                free(db);
+                free(qb);
+            }
+            nrecomp = nl;
+            for (i64 i = 0; i < nl; ++i) {
+                if (dkm_trivial(k, m, off, i, E)) continue;
+                dkm_insert(k, m, off, dd, nj, i, nnd + i * m, nnj + i * m);
+            }
+        } else {
+            /* re-evaluate every row's stored entries (independent of dkm) */
+#pragma omp parallel for schedule(dynamic, 16)
+            for (i64 i = 0; i < nl; ++i) {
+                dj_t e[64];
+                int c = 0;
+                for (int a = 0; a < st[i].cnt; ++a) {
+                    i64 j = st[i].j[a];
+                    if (j >= nl || iabs64(i - j) <= E) continue;
+                    e[c].d = orc_dist(x, n, l, i, j);
+                    e[c].j = j;
+                    ++c;
+                }
+                qsort(e, (size_t)c, sizeof(dj_t), cmp_dj);
+                for (int j = 0; j < m; ++j) {
+                    sv[i * m + j] = j < c ? e[j].d : INFINITY;
+                    svj[i * m + j] = j < c ? e[j].j : -1;
+                }
+                valid[i] = 0;
+                if (!orc_is_flat(x, n, l, i) && c >= m) {
+                    double mu, sig;
+                    orc_window_stats(x, n, l, i, &mu, &sig);
+                    double B = st[i].bound_base * st[i].sig_b / sig;
+                    valid[i] = sv[i * m + m - 1] < B;
+                }
+            }
+            for (i64 i = 0; i < nl; ++i) {
+                if (dkm_trivial(k, m, off, i, E)) continue;
+                if (valid[i]) {
+                    ++nvalid;
+                    dkm_insert(k, m, off, dd, nj, i, sv + i * m, svj + i * m);
+                } else {
+                    list[nlist++] = i;
+                }
+            }
+            for (i64 t = 0; t < nlist; ++t) {
+                i64 i = list[t];
+                if (dkm_trivial(k, m, off, i, E)) continue;
+                for (int j = m - 1; j >= 0; --j) {
+                    if (!(sv[i * m + j] > dd[(k - 1) * m + j])) continue;
+                    recompute_row(x, n, l, num, den, p, m, i, &st[i], mp, ip, nnd, nnj, prof, dbuf, qbuf);
+                    ++nrecomp;
+                    dkm_insert(k, m, off, dd, nj, i, nnd + i * m, nnj + i * m);
+                    break;
+                }
+            }
+        }
+        dkm_merge(k, m, l, off, dd, nj, out_off, out_len, out_d, out_nd, out_nn);
+        if (dkm_off) {
+            for (int c = 0; c < k * m; ++c) {
+                dkm_off[(i64)(l - lmin) * k * m + c] = off[c];
+                dkm_d[(i64)(l - lmin) * k * m + c] = dd[c];
+            }
+        }
+        if (stats) {
+            i64 *s4 = stats + (i64)(l - lmin) * 4;
+            s4[0] = nl;
+            s4[1] = nvalid;
+            s4[2] = nlist;
+            s4[3] = nrecomp;
+        }
+    }
+    free(st);
+    free(jstore);
+    free(mp);
+    free(ip);
+    free(nnd);
+    free(nnj);
+    free(sv);
+    free(svj);
+    free(valid);
+    free(list);
+    free(off);
+    free(dd);
+    free(nj);
+    free(prof);
+    free(dbuf);
+    free(qbuf);
 }
 
 /* dkm_{lmin,lmax} from the streamed dkm_l of every length, merged cell by
@@ -940,18 +1126,7 @@ void orc_discords_streamed(i64 n, int lmin, int lmax, int num, int den, int k, i
         const double *nd = nnd_all + (i64)(l - lmin) * n0 * m_max;
         const i64 *nq = nnj_all + (i64)(l - lmin) * n0 * m_max;
         orc_dkm_streamed(n - l + 1, nd, nq, m_max, l, num, den, k, m, off, dd, nj);
-        double f = sqrt((double)l);
-        for (int c = 0; c < k * m; ++c) {
-            if (off[c] < 0) continue;
-            double v = dd[c] / f;
-            if (out_len[c] == 0 || v >= out_nd[c]) {
-                out_nd[c] = v;
-                out_d[c] = dd[c];
-                out_off[c] = off[c];
-                out_len[c] = l;
-                out_nn[c] = nj[c];
-            }
-        }
+        dkm_merge(k, m, l, off, dd, nj, out_off, out_len, out_d, out_nd, out_nn);
     }
     free(off);
     free(dd);

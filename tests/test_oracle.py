@@ -551,6 +551,66 @@ def test_streamed_dkm_planted_spike():
     _streamed_invariants(t, oracle.excl(l))
 
 
+def test_pruned_discords_all_valid_equals_streamed():
+    # every window stored (p at least the non-trivial count): every row is
+    # valid at every length, so the pruned iteration is the streamed form on
+    # exact profiles, length by length
+    x = workloads.ar2(70, 103)
+    lmin, lmax, k = 10, 14, 4
+    pl = oracle.valmp_plain(x, lmin, lmax, m_max=2, keep_nn=True)
+    n = len(x)
+    for m in (1, 2):
+        g = oracle.valmod_discord(x, lmin, lmax, 64, k, m)
+        assert np.array_equal(g["stats"][1:, 3], np.zeros(lmax - lmin, np.int64))   # nothing recomputed
+        for li, l in enumerate(range(lmin, lmax + 1)):
+            nl = n - l + 1
+            t = oracle.dkm_streamed(pl["nnd"][li, :nl, :m], pl["nnj"][li, :nl, :m], l, k, m)
+            assert np.array_equal(g["dkm_off"][li], t["off"])
+            assert np.allclose(g["dkm_d"][li], t["dist"], rtol=1e-12, atol=0)
+        ref = oracle.discords_streamed(n, lmin, lmax, k, 2, m, pl["nnd"], pl["nnj"])
+        assert np.array_equal(g["off"], ref["off"]) and np.array_equal(g["len"], ref["len"])
+
+
+def test_pruned_discords_exact_values_and_invariants():
+    x = workloads.ar2(1200, 104)
+    lmin, lmax, p, k, m = 20, 30, 5, 4, 2
+    g = oracle.valmod_discord(x, lmin, lmax, p, k, m)
+    pl = oracle.valmp_plain(x, lmin, lmax, m_max=m, keep_nn=True)
+    st = g["stats"]
+    assert st[0, 3] == st[0, 0]                                  # lmin: every row
+    assert np.all(st[1:, 1] + st[1:, 2] <= st[1:, 0])
+    assert np.all(st[1:, 3] <= st[1:, 2])
+    assert st[1:, 2].sum() > st[1:, 3].sum() > 0                 # the second pass prunes
+    for li, l in enumerate(range(lmin, lmax + 1)):
+        t = dict(off=g["dkm_off"][li], dist=g["dkm_d"][li])
+        _streamed_invariants(t, oracle.excl(l))
+        for r in range(k):
+            for c in range(m):
+                o = t["off"][r, c]
+                if o >= 0:                                       # only exact distances enter
+                    assert abs(t["dist"][r, c] - pl["nnd"][li, o, c]) <= 1e-12 * pl["nnd"][li, o, c]
+    # lmin = lmax: the streamed form
+    g1 = oracle.valmod_discord(x, lmin, lmin, p, k, m)
+    nl = len(x) - lmin + 1
+    t = oracle.dkm_streamed(pl["nnd"][0, :nl], pl["nnj"][0, :nl], lmin, k, m)
+    assert np.array_equal(g1["dkm_off"][0], t["off"])
+
+
+def test_pruned_discords_planted_spike():
+    # the spike's windows are far from their stored partners: non-valid, then
+    # recomputed in the second pass and placed at rank 1 of column 1
+    rng = np.random.default_rng(105)
+    t_ = np.arange(2500)
+    x = np.sin(2 * np.pi * t_ / 50) + 0.05 * rng.standard_normal(2500)
+    x[1300] += 3.0
+    lmin, lmax = 24, 30
+    g = oracle.valmod_discord(x, lmin, lmax, 5, 3, 1)
+    for li, l in enumerate(range(lmin, lmax + 1)):
+        o = g["dkm_off"][li, 0, 0]
+        assert o <= 1300 < o + l, (l, o)
+    assert g["stats"][1:, 3].sum() < g["stats"][1:, 0].sum() // 10   # few rows recomputed
+
+
 # ---------------------------------------------------------------- read-outs
 
 def test_topk_motif_planted_pair():
