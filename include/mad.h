@@ -87,7 +87,16 @@ typedef struct mad_options {
                                rows are non-valid (n log p / log n or more) the full profile is
                                computed. The best length-normalised VALMP entry (the top-1
                                variable-length motif) is exact. Needs m_max = 1; no discord
-                               table (mad_discords returns MAD_ESTATE). */
+                               table (mad_discords returns MAD_ESTATE);
+                               2 (discord mode, Algorithm 7 driving Algorithm 10): per length,
+                               windows in offset order; one with a trivial match in dkm_l is
+                               skipped, a valid row (stored entries certify its 1st..m_max-th best
+                               matches) enters dkm_l by Algorithm 8, a non-valid row is listed;
+                               then each listed row whose upper values can still beat a column's
+                               k_max-th entry (m_max down to 1) is recomputed and entered; dkm_l
+                               is merged by Algorithm 9. mad_discords returns that table; rows
+                               neither valid nor recomputed are undefined at that length (NaN in
+                               the kept profiles, no VALMP update). */
     int32_t band_form;      /* matrix-profile kernel form: 0 = full rows (each row band walks every
                                column; the faster form on GB300), 1 = symmetric (upper triangle only,
                                each pair computed once and fed to both windows, used for the lengths
@@ -229,7 +238,7 @@ MAD_API mad_status mad_discords(mad_ctx *ctx, int32_t series, int32_t k, int32_t
  * a candidate have off = -1, len = 0, NaN distances); dist_recheck is the
  * FP64 re-check. Requires 1 <= k <= 64, 1 <= m <= m_max. Errors: MAD_EINVAL
  * for bad arguments or a profile without keep_profiles, MAD_ESTATE before
- * mad_profile or in motif mode, MAD_ENOMEM when the scratch
+ * mad_profile or in mode 1 or 2, MAD_ENOMEM when the scratch
  * (16 B per (column, length, 256 offsets) tile) cannot be allocated. */
 MAD_API mad_status mad_discords_global(mad_ctx *ctx, int32_t series, int32_t k, int32_t m,
                                        mad_discord *out, int32_t *n_out);
@@ -247,7 +256,7 @@ MAD_API mad_status mad_discords_global(mad_ctx *ctx, int32_t series, int32_t k, 
  * entries, rank-major as for mad_discords (an empty cell has off = -1,
  * len = 0); dist_recheck is the FP64 re-check. Requires 1 <= k <= 64,
  * 1 <= m <= m_max. Errors: MAD_EINVAL for bad arguments or a profile without
- * keep_profiles, MAD_ESTATE before mad_profile or in motif mode, MAD_ENOMEM
+ * keep_profiles, MAD_ESTATE before mad_profile or in mode 1 or 2, MAD_ENOMEM
  * when the per-length tables (16 B per cell and length) cannot be
  * allocated. */
 MAD_API mad_status mad_discords_streamed(mad_ctx *ctx, int32_t series, int32_t k, int32_t m,

@@ -294,6 +294,64 @@ void launch_discords_global(const GDiscArgs &a, cudaStream_t s)
 // run the exact steps, one at a time in offset order.
 constexpr int STREAM_WARPS = 4;
 
+// One warp: has window ii a trivial match among the offsets present in the
+// k x m matrix (cells entries of O)?
+__device__ __forceinline__ bool dkm_trivial_warp(const int32_t *O, int cells, int64_t ii, int64_t E, int lane)
+{
+    bool triv = false;
+    for (int c = lane; c < cells; c += 32) {
+        const int64_t o = O[c];
+        triv |= o >= 0 && ii - o <= E && o - ii <= E;
+    }
+    return __any_sync(0xffffffffu, triv);
+}
+
+// One warp: Algorithm 8 for window ii, whose c-th best-match distance and
+// neighbour are v[c * vs] and vj[c * vs]; cmin[c] mirrors the last entry of
+// column c. Every lane takes the same path.
+__device__ void dkm_insert_warp(double *D, int32_t *O, int32_t *N, double *cmin, int k, int m, int64_t ii,
+                                const double *v, const int32_t *vj, int64_t vs, int lane)
+{
+    for (int j = m - 1; j >= 0; --j) {
+        const double vv = v[(int64_t)j * vs];
+        if (!isfinite(vv) || !(vv > cmin[j])) continue;
+        // first rank r0 with vv > D[r0][j] (exists: vv beats the last entry)
+        const unsigned lo = __ballot_sync(0xffffffffu, lane < k && vv > D[lane * m + j]);
+        const unsigned hi = __ballot_sync(0xffffffffu, lane + 32 < k && vv > D[(lane + 32) * m + j]);
+        if (!lo && !hi) break;    // cannot happen while cmin[j] mirrors the last entry
+        const int r0 = lo ? __ffs(lo) - 1 : 32 + __ffs(hi) - 1;
+        double sd[2];
+        int32_t so[2], sn[2];
+        for (int h = 0; h < 2; ++h) {
+            const int rr = lane + 32 * h;
+            if (rr >= r0 && rr < k - 1) {
+                sd[h] = D[rr * m + j];
+                so[h] = O[rr * m + j];
+                sn[h] = N[rr * m + j];
+            }
+        }
+        __syncwarp();
+        for (int h = 0; h < 2; ++h) {
+            const int rr = lane + 32 * h;
+            if (rr >= r0 && rr < k - 1) {
+                D[(rr + 1) * m + j] = sd[h];
+                O[(rr + 1) * m + j] = so[h];
+                N[(rr + 1) * m + j] = sn[h];
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            D[r0 * m + j] = vv;
+            O[r0 * m + j] = (int32_t)ii;
+            N[r0 * m + j] = vj[(int64_t)j * vs];
+        }
+        __syncwarp();
+        if (lane == 0) cmin[j] = D[(k - 1) * m + j];
+        __syncwarp();
+        return;
+    }
+}
+
 __global__ void __launch_bounds__(STREAM_WARPS * 32) k_dkm_streamed(StreamArgs A)
 {
     __shared__ double cmin_all[STREAM_WARPS][KMAX];
@@ -330,53 +388,197 @@ __global__ void __launch_bounds__(STREAM_WARPS * 32) k_dkm_streamed(StreamArgs A
             const int t = __ffs(mask) - 1;
             mask &= mask - 1;
             const int64_t ii = base + t;
-            bool triv = false;
-            for (int c = lane; c < cells; c += 32) {
-                const int64_t o = O[c];
-                triv |= o >= 0 && ii - o <= E && o - ii <= E;
-            }
-            if (__any_sync(0xffffffffu, triv)) continue;
-            for (int j = m - 1; j >= 0; --j) {
-                const double v = sc[(int64_t)j * A.n0 + ii];
-                if (!isfinite(v) || !(v > cmin[j])) continue;
-                // first rank r0 with v > D[r0][j] (exists: v beats the last entry)
-                const unsigned lo = __ballot_sync(0xffffffffu, lane < k && v > D[lane * m + j]);
-                const unsigned hi = __ballot_sync(0xffffffffu, lane + 32 < k && v > D[(lane + 32) * m + j]);
-                if (!lo && !hi) break;    // cannot happen while cmin[j] mirrors the last entry
-                const int r0 = lo ? __ffs(lo) - 1 : 32 + __ffs(hi) - 1;
-                double sd[2];
-                int32_t so[2], sn[2];
-                for (int h = 0; h < 2; ++h) {
-                    const int rr = lane + 32 * h;
-                    if (rr >= r0 && rr < k - 1) {
-                        sd[h] = D[rr * m + j];
-                        so[h] = O[rr * m + j];
-                        sn[h] = N[rr * m + j];
-                    }
-                }
-                __syncwarp();
-                for (int h = 0; h < 2; ++h) {
-                    const int rr = lane + 32 * h;
-                    if (rr >= r0 && rr < k - 1) {
-                        D[(rr + 1) * m + j] = sd[h];
-                        O[(rr + 1) * m + j] = so[h];
-                        N[(rr + 1) * m + j] = sn[h];
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    D[r0 * m + j] = v;
-                    O[r0 * m + j] = (int32_t)ii;
-                    N[r0 * m + j] = sj[(int64_t)j * A.n0 + ii];
-                }
-                __syncwarp();
-                if (lane == 0) cmin[j] = D[(k - 1) * m + j];
-                __syncwarp();
-                break;
-            }
+            if (dkm_trivial_warp(O, cells, ii, E, lane)) continue;
+            dkm_insert_warp(D, O, N, cmin, k, m, ii, sc + ii, sj + ii, A.n0, lane);
         }
     }
 }
+
+// ------------------------------------- discord mode (Algorithms 7 and 10)
+//
+// First pass (one warp, windows in offset order): a window with a trivial
+// match in dkm_l is skipped; a valid row (its stored entries certify its
+// 1st..m-th best matches; every row at lmin) is inserted by Algorithm 8
+// with its exact distances; a non-valid row joins the list with its upper
+// values (the j-th smallest pessimistic stored distances). Valid rows that
+// cannot beat any column minimum are screened out 32 at a time; the
+// non-valid rows between two insertions see the same matrix and are
+// checked together.
+__global__ void __launch_bounds__(32) k_dpass1(DiscPassArgs A)
+{
+    __shared__ double cmin[KMAX];
+    const int lane = threadIdx.x;
+    const int k = A.k, m = A.m, cells = k * m;
+    for (int c = lane; c < cells; c += 32) {
+        A.D[c] = ninf();
+        A.O[c] = -1;
+        A.N[c] = -1;
+    }
+    for (int c = lane; c < m; c += 32) cmin[c] = ninf();
+    __syncwarp();
+    int nls = 0;
+    for (int64_t base = 0; base < A.nl; base += 32) {
+        const int64_t i = base + lane;
+        const bool in = i < A.nl;
+        const int32_t fl = in ? A.flag[i] : ROW_DONE;
+        const bool valid = in && (A.all_valid || fl == ROW_DONE);
+        const bool nonv = in && !A.all_valid && (fl == ROW_RECOMPUTE || fl == ROW_FLAT);
+        bool cand = false;
+        if (valid)
+            for (int c = 0; c < m && !cand; ++c) {
+                const double v = A.nnd[(int64_t)c * A.n0 + i];
+                cand = isfinite(v) && v > cmin[c];
+            }
+        const unsigned cmask = __ballot_sync(0xffffffffu, cand);
+        const unsigned nmask = __ballot_sync(0xffffffffu, nonv);
+        int pos = 0;
+        while (true) {
+            const unsigned rem = pos < 32 ? (cmask & (0xffffffffu << pos)) : 0u;
+            const int t = rem ? __ffs(rem) - 1 : 32;
+            const unsigned below_t = t < 32 ? ((1u << t) - 1u) : 0xffffffffu;
+            const unsigned below_pos = pos < 32 ? ((1u << pos) - 1u) : 0xffffffffu;
+            const unsigned seg = nmask & below_t & ~below_pos;
+            if (seg) {
+                const bool mine = (seg >> lane) & 1u;
+                bool triv = false;
+                if (mine)
+                    for (int c = 0; c < cells && !triv; ++c) {
+                        const int64_t o = A.O[c];
+                        triv = o >= 0 && i - o <= A.E && o - i <= A.E;
+                    }
+                const unsigned lmask = __ballot_sync(0xffffffffu, mine && !triv);
+                if (mine && !triv) {
+                    const int q = nls + __popc(lmask & ((1u << lane) - 1u));
+                    A.lst[q] = (int32_t)i;
+                    A.lpos[i] = q;
+                    for (int c = 0; c < m; ++c) A.lub[(int64_t)q * m + c] = A.nnd[(int64_t)c * A.n0 + i];
+                }
+                nls += __popc(lmask);
+            }
+            if (t == 32) break;
+            const int64_t ii = base + t;
+            if (!dkm_trivial_warp(A.O, cells, ii, A.E, lane))
+                dkm_insert_warp(A.D, A.O, A.N, cmin, k, m, ii, A.nnd + ii, A.nnj + ii, A.n0, lane);
+            pos = t + 1;
+        }
+    }
+    if (lane == 0) *A.nlist = nls;
+}
+
+// The non-valid rows to recompute: listed rows with an upper value above
+// its column's current last entry (the last entries only grow, so every row
+// the second pass will recompute is among them). The others are left
+// undefined at this length (ROW_SKIP, NaN distances) and keep their
+// extended entries.
+__global__ void k_dmark(DiscPassArgs A)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool skip = false;
+    if (i < A.nl) {
+        const int32_t fl = A.flag[i];
+        const int q = A.lpos[i];
+        if (fl == ROW_RECOMPUTE || fl == ROW_FLAT) {
+            bool keep = false;
+            if (q >= 0)
+                for (int c = 0; c < A.m && !keep; ++c)
+                    keep = A.lub[(int64_t)q * A.m + c] > A.D[(A.k - 1) * A.m + c];
+            if (!keep) {
+                skip = true;
+                A.flag[i] = ROW_SKIP;
+                if (A.thr32) A.thr32[i] = __int_as_float(0x7f800000);
+                else A.thr64[i] = dinf();
+                for (int c = 0; c < A.m; ++c) {
+                    A.nnd[(int64_t)c * A.n0 + i] = __longlong_as_double(0x7ff8000000000000LL);
+                    A.nnj[(int64_t)c * A.n0 + i] = -1;
+                }
+            }
+        }
+        if (skip || q < 0 || (fl != ROW_RECOMPUTE && fl != ROW_FLAT)) A.lpos[i] = -1;
+    }
+    const int c = __syncthreads_count(skip);
+    if (threadIdx.x == 0 && c) atomicAdd(&A.stats[10], (unsigned long long)c);
+}
+
+// Second pass (one warp, list order): a window with a trivial match in dkm_l
+// is skipped; else the first column (m down to 1) whose upper value beats
+// its last entry has the row (recomputed, so exact now) inserted by
+// Algorithm 8. Then Algorithm 9 folds dkm_l into dkm_{lmin,lmax}.
+__global__ void __launch_bounds__(32) k_dpass2(DiscPassArgs A)
+{
+    __shared__ double cmin[KMAX];
+    const int lane = threadIdx.x;
+    const int k = A.k, m = A.m, cells = k * m;
+    for (int c = lane; c < m; c += 32) cmin[c] = A.D[(k - 1) * m + c];
+    __syncwarp();
+    const int nls = *A.nlist;
+    for (int base = 0; base < nls; base += 32) {
+        const int t = base + lane;
+        bool cand = false;
+        if (t < nls)
+            for (int c = 0; c < m && !cand; ++c) cand = A.lub[(int64_t)t * m + c] > cmin[c];
+        unsigned mask = __ballot_sync(0xffffffffu, cand);
+        while (mask) {
+            const int u = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int tt = base + u;
+            const int64_t ii = A.lst[tt];
+            if (dkm_trivial_warp(A.O, cells, ii, A.E, lane)) continue;
+            bool pass = false;
+            for (int c = m - 1; c >= 0 && !pass; --c) pass = A.lub[(int64_t)tt * m + c] > cmin[c];
+            if (pass) {
+                if (lane == 0) A.used[ii] = 1;
+                dkm_insert_warp(A.D, A.O, A.N, cmin, k, m, ii, A.nnd + ii, A.nnj + ii, A.n0, lane);
+            }
+        }
+    }
+    const double f = sqrt((double)A.l);
+    for (int c = lane; c < cells; c += 32) {
+        if (A.O[c] < 0) continue;
+        const double v = A.D[c] / f;
+        if (A.tab.len[c] == 0 || v >= A.tab.norm[c]) {
+            A.tab.norm[c] = v;
+            A.tab.dist[c] = A.D[c];
+            A.tab.off[c] = A.O[c];
+            A.tab.len[c] = A.l;
+            A.tab.nn[c] = A.N[c];
+        }
+    }
+}
+
+// Rows recomputed ahead of the second pass that it did not need take back
+// their state from before the recompute (extended entries, bound base and
+// base length), as if never recomputed; list positions and marks are
+// cleared for the next length.
+__global__ void k_drestore(DiscPassArgs A)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= A.nl || A.lpos[i] < 0) return;
+    if (!A.used[i]) {
+        for (int e = 0; e < A.p; ++e) {
+            const int64_t at = (int64_t)e * A.n0 + i;
+            A.st.ent_j[at] = A.saved.ent_j[at];
+            A.st.ent_c[at] = A.saved.ent_c[at];
+            A.st.ent_qb[at] = A.saved.ent_qb[at];
+            A.st.ent_dq[at] = A.saved.ent_dq[at];
+        }
+        A.st.sigb[i] = A.saved.sigb[i];
+        A.st.base[i] = A.saved.base[i];
+        A.st.bnum[i] = A.saved.bnum[i];
+    }
+    A.lpos[i] = -1;
+    A.used[i] = 0;
+}
+
+void launch_discord_pass1(const DiscPassArgs &a, cudaStream_t s) { k_dpass1<<<1, 32, 0, s>>>(a); }
+void launch_discord_restore(const DiscPassArgs &a, cudaStream_t s)
+{
+    k_drestore<<<(unsigned)((a.nl + 255) / 256), 256, 0, s>>>(a);
+}
+void launch_discord_mark(const DiscPassArgs &a, cudaStream_t s)
+{
+    k_dmark<<<(unsigned)((a.nl + 255) / 256), 256, 0, s>>>(a);
+}
+void launch_discord_pass2(const DiscPassArgs &a, cudaStream_t s) { k_dpass2<<<1, 32, 0, s>>>(a); }
 
 // Algorithm 9 over the streamed tables: per cell the largest d / sqrt(l),
 // ties to the later length.

@@ -294,6 +294,8 @@ __device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i, double
             A.obs_gap[i] = __longlong_as_double(0x7ff8000000000000LL);
             A.obs_tlb[i] = __longlong_as_double(0x7ff8000000000000LL);
         }
+        if (A.ub_out)
+            for (int c = 0; c < A.m_max; ++c) A.out.nnd[(int64_t)c * n0 + i] = pinf();
         return 2;
     }
     const double m2i = A.m2[i];
@@ -386,6 +388,22 @@ __device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i, double
     if (A.lbmax) {
         A.lbmax[i] = B;
         lb = B;
+    }
+    if (A.ub_out) {
+        // upper values: the c-th smallest pessimistic stored distance
+        for (int c = 0; c < m; ++c) A.out.nnd[(int64_t)c * n0 + i] = pinf();
+        double dp[PM];
+        long long dk[PM];
+        for_pm<PM>([&](int a) {
+            dp[a] = r.j[a] >= 0 ? 2.0 * l * (1.0 - clamp_q(r.q[a] - r.dq[a])) : pinf();
+            dk[a] = ord64(dp[a]);
+        });
+        for_pm<PM>([&](int a) {
+            if (r.j[a] < 0) return;
+            int k = 0;
+            for_pm<PM>([&](int b) { k += (r.j[b] >= 0 && (dk[b] < dk[a] || (dk[b] == dk[a] && b < a))); });
+            if (k < m) A.out.nnd[(int64_t)k * n0 + i] = sqrt(dp[a]);
+        });
     }
     // theta_q: p-th best among p distinct partners with known lower bounds
     // on their correlation (the remaining entries lowered by their error

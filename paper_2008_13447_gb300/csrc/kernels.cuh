@@ -149,6 +149,9 @@ template <typename T> struct ExtArgs {
     unsigned long long *min_dist_abs, *min_lb_abs;
     // observation at one length (NULL otherwise): maxLB - minED, mean LB / ED
     double *obs_gap, *obs_tlb;
+    // discord mode: non-valid rows write their 1st..m-th smallest pessimistic
+    // stored distances (+inf past the stored count; flat rows +inf) to out.nnd
+    int ub_out;
     const float *xh, *xl;   // x as FP32 pairs (compensated re-evaluation)
     const double *isd;      // 1 / sqrt(M2) at l (0: flat)
     int64_t n0, nl;
@@ -349,6 +352,33 @@ struct StreamArgs {         // dkm_l streamed (Algorithms 7 and 8) and merged (A
     DiscTable out;          // k x m cells, rank-major
 };
 void launch_discords_streamed(const StreamArgs &a, cudaStream_t s);
+struct DiscPassArgs {       // discord mode: Algorithm 10's two passes at one length
+    int64_t n0, nl;
+    int l;
+    int64_t E;
+    int k, m;               // k_max, m_max
+    int all_valid;          // lmin: every row's distances are exact
+    int32_t *flag;          // row state after the extension
+    float *thr32;           // the row thresholds (one of the two, by precision)
+    double *thr64;
+    double *nnd;            // [m][n0] exact (valid / recomputed rows) or upper values (non-valid)
+    int32_t *nnj;
+    double *D;              // dkm_l [k][m]
+    int32_t *O, *N;
+    int32_t *lst;           // non-valid list: row, in offset order
+    double *lub;            // its upper values [list][m]
+    int32_t *lpos;          // row -> list position (-1: not listed)
+    int32_t *nlist;
+    int32_t *used;          // rows the second pass recomputed and entered (0 / 1)
+    DiscTable tab;          // dkm_{lmin,lmax}
+    unsigned long long *stats;
+    RowState st, saved;     // row state and its copy from before the recomputes
+    int p;
+};
+void launch_discord_pass1(const DiscPassArgs &a, cudaStream_t s);
+void launch_discord_mark(const DiscPassArgs &a, cudaStream_t s);
+void launch_discord_pass2(const DiscPassArgs &a, cudaStream_t s);
+void launch_discord_restore(const DiscPassArgs &a, cudaStream_t s);
 constexpr int GDISC_TILE = 256;
 void launch_discords_global(const GDiscArgs &a, cudaStream_t s);
 void launch_discords_length(const double *nnd, const int32_t *nnj, int64_t n0, int64_t nl, int l, int64_t E,

@@ -143,8 +143,8 @@ void check_options(mad_ctx *ctx, const mad_options &o)
     REQUIRE(o.precision == MAD_FP64 || o.precision == MAD_FP32, "precision must be MAD_FP64 or MAD_FP32");
     REQUIRE(o.k_max >= 1 && o.k_max <= KMAX, "k_max must be in [1, 64]");
     REQUIRE(o.m_max >= 1 && o.m_max <= MAXP, "m_max must be in [1, 64]");
-    REQUIRE(o.mode == 0 || o.mode == 1, "mode must be 0 (exact rows) or 1 (motif mode)");
-    REQUIRE(o.mode == 0 || o.m_max == 1, "motif mode reports the motif of each length only: m_max must be 1");
+    REQUIRE(o.mode >= 0 && o.mode <= 2, "mode must be 0 (exact rows), 1 (motif mode) or 2 (discord mode)");
+    REQUIRE(o.mode != 1 || o.m_max == 1, "motif mode reports the motif of each length only: m_max must be 1");
     REQUIRE(o.band_form == 0 || o.band_form == 1, "band_form must be 0 or 1");
 }
 
@@ -259,6 +259,22 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
     // motif mode: per-row bound of non-valid rows; per length the smallest
     // certified distance and non-valid bound (+inf until reduced)
     const bool motif_mode = o.mode == 1;
+    const bool disc_mode = o.mode == 2;
+    // discord mode: dkm_l, the non-valid list with its upper values, list positions
+    double *dkm_d = disc_mode ? dalloc<double>(ctx, s, (size_t)k_max * m_max) : nullptr;
+    int32_t *dkm_o = disc_mode ? dalloc<int32_t>(ctx, s, (size_t)k_max * m_max) : nullptr;
+    int32_t *dkm_n = disc_mode ? dalloc<int32_t>(ctx, s, (size_t)k_max * m_max) : nullptr;
+    int32_t *dlst = disc_mode ? dalloc<int32_t>(ctx, s, n0) : nullptr;
+    double *dlub = disc_mode ? dalloc<double>(ctx, s, (size_t)n0 * m_max) : nullptr;
+    int32_t *dlpos = disc_mode ? dalloc<int32_t>(ctx, s, n0) : nullptr;
+    int32_t *dnlist = disc_mode ? dalloc<int32_t>(ctx, s, 1) : nullptr;
+    int32_t *dused = disc_mode ? dalloc<int32_t>(ctx, s, n0) : nullptr;
+    RowState rs_saved{};
+    if (disc_mode)
+        rs_saved = RowState{dalloc<int32_t>(ctx, s, (size_t)p * n0), dalloc<double>(ctx, s, (size_t)p * n0),
+                            dalloc<double>(ctx, s, (size_t)p * n0), dalloc<double>(ctx, s, n0),
+                            dalloc<float>(ctx, s, (size_t)p * n0), dalloc<int32_t>(ctx, s, n0),
+                            dalloc<double>(ctx, s, n0), nullptr};
     double *lbmax = motif_mode ? dalloc<double>(ctx, s, n0) : nullptr;
     double *mm = motif_mode ? dalloc<double>(ctx, s, (size_t)2 * nL) : nullptr;
     const double motif_limit = (double)n * std::log((double)p) / std::log((double)n);
@@ -281,6 +297,10 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
     }
     CK(cudaMemsetAsync(dstats, 0, (size_t)nL * NSTAT * sizeof(unsigned long long), st));
     if (motif_mode) launch_fill<double>(mm, (int64_t)2 * nL, INFINITY, st);
+    if (disc_mode) {
+        launch_fill<int32_t>(dlpos, n0, -1, st);
+        CK(cudaMemsetAsync(dused, 0, n0 * sizeof(int32_t), st));
+    }
     CK(cudaMemsetAsync(counters, 0, 4 * sizeof(int32_t), st));
     CK(cudaMemsetAsync(vm.len, 0, n0 * sizeof(int32_t), st));
     CK(cudaMemsetAsync(tab.len, 0, (size_t)k_max * m_max * sizeof(int32_t), st));
@@ -426,6 +446,45 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
         CK(cudaEventRecord(ev_prep[b], side.prep));
         CK(cudaGetLastError());
     };
+    auto disc_args = [&](int64_t nl, int l, int64_t E, int all_valid, const LenOut &lo) {
+        DiscPassArgs d{};
+        d.n0 = n0;
+        d.nl = nl;
+        d.l = l;
+        d.E = E;
+        d.k = k_max;
+        d.m = m_max;
+        d.all_valid = all_valid;
+        d.flag = rs.flag;
+        if (sizeof(T) == 4) d.thr32 = reinterpret_cast<float *>(thr);
+        else d.thr64 = reinterpret_cast<double *>(thr);
+        d.nnd = lo.nnd;
+        d.nnj = lo.nnj;
+        d.D = dkm_d;
+        d.O = dkm_o;
+        d.N = dkm_n;
+        d.lst = dlst;
+        d.lub = dlub;
+        d.lpos = dlpos;
+        d.nlist = dnlist;
+        d.tab = tab;
+        d.stats = lo.stats;
+        d.used = dused;
+        d.st = rs;
+        d.saved = rs_saved;
+        d.p = p;
+        return d;
+    };
+    // the row state before a length's recomputes (discord mode)
+    auto save_rows = [&]() {
+        CK(cudaMemcpyAsync(rs_saved.ent_j, rs.ent_j, (size_t)p * n0 * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(rs_saved.ent_c, rs.ent_c, (size_t)p * n0 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(rs_saved.ent_qb, rs.ent_qb, (size_t)p * n0 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(rs_saved.ent_dq, rs.ent_dq, (size_t)p * n0 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(rs_saved.sigb, rs.sigb, (size_t)n0 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(rs_saved.base, rs.base, (size_t)n0 * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(rs_saved.bnum, rs.bnum, (size_t)n0 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    };
     // length lmin: after the one-off initialisation on the context's stream
     CK(cudaEventRecord(ev_ext[1], st));
     prep(lmin);
@@ -479,7 +538,16 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
                 ea.min_dist_abs = reinterpret_cast<unsigned long long *>(mm + 2 * li);
                 ea.min_lb_abs = reinterpret_cast<unsigned long long *>(mm + 2 * li + 1);
             }
+            ea.ub_out = disc_mode ? 1 : 0;
             launch_extend<T>(ea, st);
+            if (disc_mode) {
+                // Algorithm 10's first pass, then the rows its second pass can need
+                DiscPassArgs dp = disc_args(nl, l, E, 0, lo);
+                launch_discord_pass1(dp, st);
+                launch_discord_mark(dp, st);
+                save_rows();
+                nlaunch += 2;
+            }
             if (motif_mode) {
                 SubmpArgs<T> sm{nl, rs.flag, thr, lbmax, ea.min_dist_abs, ea.min_lb_abs, lo.stats + 2, motif_limit,
                                 nnd, nnj, lo.stats};
@@ -602,9 +670,18 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
         }
         FlatArgs fa{n0, nl, l, E, p, m_max, run, rs, vm, lo, wait_err + 0 /* same error word */};
         launch_flat_rows(fa, st);
+        if (disc_mode) {
+            // lmin: every row exact, one pass in offset order (Algorithm 7);
+            // later lengths: Algorithm 10's second pass; then Algorithm 9
+            DiscPassArgs dp = disc_args(nl, l, E, l == lmin ? 1 : 0, lo);
+            if (l == lmin) launch_discord_pass1(dp, st);
+            launch_discord_pass2(dp, st);
+            if (l > lmin) launch_discord_restore(dp, st);
+            nlaunch += 2;
+        }
         CK(cudaEventRecord(ev_nnd, st));
         CK(cudaStreamWaitEvent(side.disc, ev_nnd, 0));
-        if (!motif_mode) launch_discords_length(nnd, nnj, n0, nl, l, E, k_max, m_max, bval, bidx, tab, side.disc);
+        if (!motif_mode && !disc_mode) launch_discords_length(nnd, nnj, n0, nl, l, E, k_max, m_max, bval, bidx, tab, side.disc);
         nlaunch += 3;
         if (o.keep_profiles) {
             CK(cudaMemcpyAsync(s.keep_nnd + (size_t)li * m_max * n0, nnd, (size_t)m_max * n0 * sizeof(double),
@@ -641,6 +718,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
         q.skipped = (int64_t)h[10];
         q.full_profile = (int32_t)h[11];
         if (motif_mode && li > 0) q.recomputed = q.full_profile ? q.rows : (int64_t)(h[2] - h[10]);
+        if (disc_mode && li > 0) q.recomputed = (int64_t)(h[2] - h[10]);
         q.tiles = (int64_t)h[5];
         q.passes = q.recomputed > 0 ? (h[0] > 0 ? 2 : 1) : 0;
         unsigned long long bits = h[3];
@@ -1143,7 +1221,7 @@ MAD_API mad_status mad_discords_global(mad_ctx *ctx, int32_t series, int32_t k, 
         }
         REQUIRE(k >= 1 && k <= KMAX, "k must be in [1, 64]");
         REQUIRE(m >= 1 && m <= s.m_max, "m must be in [1, m_max]");
-        if (ctx->opt.mode == 1) {
+        if (ctx->opt.mode != 0) {
             set_err(ctx, "global discords need mode 0 (exact rows)");
             throw Fail{MAD_ESTATE};
         }
@@ -1220,7 +1298,7 @@ MAD_API mad_status mad_discords_streamed(mad_ctx *ctx, int32_t series, int32_t k
         }
         REQUIRE(k >= 1 && k <= KMAX, "k must be in [1, 64]");
         REQUIRE(m >= 1 && m <= s.m_max, "m must be in [1, m_max]");
-        if (ctx->opt.mode == 1) {
+        if (ctx->opt.mode != 0) {
             set_err(ctx, "streamed discords need mode 0 (exact rows)");
             throw Fail{MAD_ESTATE};
         }
