@@ -53,6 +53,7 @@ def parse():
                     help="0: full rows; 1: symmetric band form when most bands are active")
     ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the plain FP64 GPU path")
     ap.add_argument("--no-motif-path", action="store_true", help="skip timing the motif mode (mode 1)")
+    ap.add_argument("--no-discord-path", action="store_true", help="skip timing the discord mode (mode 2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
     ap.add_argument("--p-sweep", default=None, metavar="LMIN:LMAX",
@@ -403,6 +404,31 @@ def main():
                 "top_motif": {kk: mot1[0][kk] for kk in ("a", "b", "len", "dist", "dist_recheck")} if mot1 else None}
         finally:
             mad.mad_destroy(cm)
+
+    # discord mode (Algorithm 7 driving Algorithm 10): the same workload, the
+    # Top-k m-th discords with the paper's pruning; one warm-up, one timed step
+    if rank == 0 and not args.no_discord_path:
+        cd = mad.mad_create_device(xt, precision=prec, k_max=k, m_max=m, stream=stream, mode=2)
+        try:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for rep in range(2):
+                flush.fill_(7)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                mad.mad_profile(cd, lmin, lmax, p)
+                dis2 = mad.mad_discords(cd, 0, k, m)
+                e1.record(stream)
+                torch.cuda.synchronize()
+            ms2 = e0.elapsed_time(e1)
+            st2 = mad.mad_stats(cd, 0)
+            rows = sum(s["rows"] for s in st2)
+            comp = st2[0]["rows"] + sum(s["recomputed"] for s in st2[1:])
+            out["discord_mode_path"] = {
+                "value": cells / (ms2 / 1e3), "ms_per_step": ms2,
+                "rows_computed_frac": comp / rows,
+                "top_discord": {kk: dis2[0][kk] for kk in ("off", "len", "dist", "dist_recheck")} if dis2 else None}
+        finally:
+            mad.mad_destroy(cd)
 
     # end to end through the public API with host buffers (pinned input)
     pinned = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()

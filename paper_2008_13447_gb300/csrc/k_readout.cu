@@ -308,18 +308,21 @@ __device__ __forceinline__ bool dkm_trivial_warp(const int32_t *O, int cells, in
 
 // One warp: Algorithm 8 for window ii, whose c-th best-match distance and
 // neighbour are v[c * vs] and vj[c * vs]; cmin[c] mirrors the last entry of
-// column c. Every lane takes the same path.
-__device__ void dkm_insert_warp(double *D, int32_t *O, int32_t *N, double *cmin, int k, int m, int64_t ii,
-                                const double *v, const int32_t *vj, int64_t vs, int lane)
+// column c. Every lane takes the same path. Returns the column entered (-1:
+// none) and in *dropped the offset that left it (-1: none).
+__device__ int dkm_insert_warp(double *D, int32_t *O, int32_t *N, double *cmin, int k, int m, int64_t ii,
+                               const double *v, const int32_t *vj, int64_t vs, int lane, int32_t *dropped)
 {
+    *dropped = -1;
     for (int j = m - 1; j >= 0; --j) {
         const double vv = v[(int64_t)j * vs];
         if (!isfinite(vv) || !(vv > cmin[j])) continue;
         // first rank r0 with vv > D[r0][j] (exists: vv beats the last entry)
         const unsigned lo = __ballot_sync(0xffffffffu, lane < k && vv > D[lane * m + j]);
         const unsigned hi = __ballot_sync(0xffffffffu, lane + 32 < k && vv > D[(lane + 32) * m + j]);
-        if (!lo && !hi) break;    // cannot happen while cmin[j] mirrors the last entry
+        if (!lo && !hi) return -1;   // cannot happen while cmin[j] mirrors the last entry
         const int r0 = lo ? __ffs(lo) - 1 : 32 + __ffs(hi) - 1;
+        *dropped = O[(k - 1) * m + j];
         double sd[2];
         int32_t so[2], sn[2];
         for (int h = 0; h < 2; ++h) {
@@ -348,8 +351,9 @@ __device__ void dkm_insert_warp(double *D, int32_t *O, int32_t *N, double *cmin,
         __syncwarp();
         if (lane == 0) cmin[j] = D[(k - 1) * m + j];
         __syncwarp();
-        return;
+        return j;
     }
+    return -1;
 }
 
 __global__ void __launch_bounds__(STREAM_WARPS * 32) k_dkm_streamed(StreamArgs A)
@@ -389,100 +393,265 @@ __global__ void __launch_bounds__(STREAM_WARPS * 32) k_dkm_streamed(StreamArgs A
             mask &= mask - 1;
             const int64_t ii = base + t;
             if (dkm_trivial_warp(O, cells, ii, E, lane)) continue;
-            dkm_insert_warp(D, O, N, cmin, k, m, ii, sc + ii, sj + ii, A.n0, lane);
+            int32_t dropped;
+            dkm_insert_warp(D, O, N, cmin, k, m, ii, sc + ii, sj + ii, A.n0, lane, &dropped);
         }
     }
 }
 
 // ------------------------------------- discord mode (Algorithms 7 and 10)
 //
-// First pass (one warp, windows in offset order): a window with a trivial
-// match in dkm_l is skipped; a valid row (its stored entries certify its
-// 1st..m-th best matches; every row at lmin) is inserted by Algorithm 8
-// with its exact distances; a non-valid row joins the list with its upper
-// values (the j-th smallest pessimistic stored distances). Valid rows that
-// cannot beat any column minimum are screened out 32 at a time; the
-// non-valid rows between two insertions see the same matrix and are
-// checked together.
-__global__ void __launch_bounds__(32) k_dpass1(DiscPassArgs A)
+// Only the windows that change dkm_l need to be visited one at a time: a
+// window enters by Algorithm 8 only if one of its distances beats its
+// column's last entry, and non-valid rows never change dkm_l in the first
+// pass. So each pass is
+//  - a sequential kernel (one block): chunks of DP_CHUNK windows are
+//    screened in parallel against the column minima as they stand, the
+//    windows that might enter are compacted in order, and warp 0 takes them
+//    one by one (trivial-match test, Algorithm 8), logging every entry and
+//    every exit: ins[o] = l for a window that entered at this length,
+//    drop[o] = the window whose entry pushed it out (INT32_MAX: never);
+//  - a parallel kernel that decides every other window from the log: the
+//    offsets present when window i is visited are those that entered before
+//    i (so within [i - E, i - 1] for a trivial match) and left after it.
+// First pass: valid rows (exact 1st..m-th distances; every row at lmin) in
+// offset order; non-valid rows without a trivial match are listed. Only the
+// listed rows whose upper values still beat a column's last entry after the
+// first pass can be recomputed by the second pass (the last entries only
+// grow): they are kept (ROW_RECOMPUTE / ROW_FLAT), the rest are left
+// undefined (ROW_SKIP, NaN distances). Second pass over the kept rows in
+// offset order: a row enters with its exact distances only if one beats its
+// column's last entry (its upper value then does too); the rows it would
+// have recomputed are those without a trivial match whose upper value beats
+// the last entry as it stood at their visit (kept in the log of the column
+// minima); the other kept rows take back their row state.
+constexpr int DP_THREADS = 1024;
+constexpr int DP_RPT = 4;                       // consecutive windows per thread
+constexpr int DP_CHUNK = DP_THREADS * DP_RPT;
+constexpr int DP_STAGE = 2;                     // columns staged in shared memory (m <= DP_STAGE)
+
+// Ordered compaction within the block: thread t contributes c (its flagged
+// windows, in order); returns its first output position; *total = sum.
+__device__ int block_excl_scan(int c, int *wsum, int *total)
 {
-    __shared__ double cmin[KMAX];
-    const int lane = threadIdx.x;
-    const int k = A.k, m = A.m, cells = k * m;
-    for (int c = lane; c < cells; c += 32) {
-        A.D[c] = ninf();
-        A.O[c] = -1;
-        A.N[c] = -1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
     }
-    for (int c = lane; c < m; c += 32) cmin[c] = ninf();
-    __syncwarp();
-    int nls = 0;
-    for (int64_t base = 0; base < A.nl; base += 32) {
-        const int64_t i = base + lane;
-        const bool in = i < A.nl;
-        const int32_t fl = in ? A.flag[i] : ROW_DONE;
-        const bool valid = in && (A.all_valid || fl == ROW_DONE);
-        const bool nonv = in && !A.all_valid && (fl == ROW_RECOMPUTE || fl == ROW_FLAT);
-        bool cand = false;
-        if (valid)
-            for (int c = 0; c < m && !cand; ++c) {
-                const double v = A.nnd[(int64_t)c * A.n0 + i];
-                cand = isfinite(v) && v > cmin[c];
-            }
-        const unsigned cmask = __ballot_sync(0xffffffffu, cand);
-        const unsigned nmask = __ballot_sync(0xffffffffu, nonv);
-        int pos = 0;
-        while (true) {
-            const unsigned rem = pos < 32 ? (cmask & (0xffffffffu << pos)) : 0u;
-            const int t = rem ? __ffs(rem) - 1 : 32;
-            const unsigned below_t = t < 32 ? ((1u << t) - 1u) : 0xffffffffu;
-            const unsigned below_pos = pos < 32 ? ((1u << pos) - 1u) : 0xffffffffu;
-            const unsigned seg = nmask & below_t & ~below_pos;
-            if (seg) {
-                const bool mine = (seg >> lane) & 1u;
-                bool triv = false;
-                if (mine)
-                    for (int c = 0; c < cells && !triv; ++c) {
-                        const int64_t o = A.O[c];
-                        triv = o >= 0 && i - o <= A.E && o - i <= A.E;
-                    }
-                const unsigned lmask = __ballot_sync(0xffffffffu, mine && !triv);
-                if (mine && !triv) {
-                    const int q = nls + __popc(lmask & ((1u << lane) - 1u));
-                    A.lst[q] = (int32_t)i;
-                    A.lpos[i] = q;
-                    for (int c = 0; c < m; ++c) A.lub[(int64_t)q * m + c] = A.nnd[(int64_t)c * A.n0 + i];
-                }
-                nls += __popc(lmask);
-            }
-            if (t == 32) break;
-            const int64_t ii = base + t;
-            if (!dkm_trivial_warp(A.O, cells, ii, A.E, lane))
-                dkm_insert_warp(A.D, A.O, A.N, cmin, k, m, ii, A.nnd + ii, A.nnj + ii, A.n0, lane);
-            pos = t + 1;
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        const int v = wsum[lane];
+        int z = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o) z += y;
         }
+        wsum[lane] = z - v;                 // exclusive offsets of the warps
+        if (lane == 31) wsum[32] = z;
     }
-    if (lane == 0) *A.nlist = nls;
+    __syncthreads();
+    const int pos = wsum[w] + x - c;
+    *total = wsum[32];
+    __syncthreads();
+    return pos;
 }
 
-// The non-valid rows to recompute: listed rows with an upper value above
-// its column's current last entry (the last entries only grow, so every row
-// the second pass will recompute is among them). The others are left
-// undefined at this length (ROW_SKIP, NaN distances) and keep their
-// extended entries.
-__global__ void k_dmark(DiscPassArgs A)
+struct DpSmem {
+    double *D, *cmin;
+    int32_t *O, *N, *cand;
+    double *cv;             // the candidates' distances [DP_CHUNK][DP_STAGE]
+    int *wsum;
+};
+
+__device__ DpSmem dp_smem(unsigned char *raw, int cells, int m)
+{
+    DpSmem s;
+    s.D = reinterpret_cast<double *>(raw);
+    s.cmin = s.D + cells;
+    s.O = reinterpret_cast<int32_t *>(s.cmin + m);
+    s.N = s.O + cells;
+    s.cand = s.N + cells;
+    s.cv = reinterpret_cast<double *>(s.cand + DP_CHUNK);
+    s.wsum = reinterpret_cast<int *>(s.cv + DP_CHUNK * DP_STAGE);
+    return s;
+}
+
+size_t dp_smem_bytes(int k, int m)
+{
+    const size_t cells = (size_t)k * m;
+    return cells * sizeof(double) + m * sizeof(double) + 2 * cells * sizeof(int32_t) + DP_CHUNK * sizeof(int32_t) +
+           (size_t)DP_CHUNK * DP_STAGE * sizeof(double) + 33 * sizeof(int);
+}
+
+// pass = 1: first pass (screen: valid rows); pass = 2: second pass (screen:
+// kept rows, exact distances). Entries / exits are logged in ins/drop of the
+// pass; the second pass also logs the column minima after each entry.
+template <int PASS>
+__global__ void __launch_bounds__(DP_THREADS) k_dp_seq(DiscPassArgs A)
+{
+    extern __shared__ __align__(16) unsigned char dp_raw[];
+    const int k = A.k, m = A.m, cells = k * m;
+    DpSmem sm = dp_smem(dp_raw, cells, m);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t *ins = PASS == 1 ? A.ins1 : A.ins2;
+    int32_t *drop = PASS == 1 ? A.drop1 : A.drop2;
+    if (PASS == 1) {
+        for (int c = threadIdx.x; c < cells; c += DP_THREADS) {
+            sm.D[c] = ninf();
+            sm.O[c] = -1;
+            sm.N[c] = -1;
+        }
+    } else {
+        for (int c = threadIdx.x; c < cells; c += DP_THREADS) {
+            sm.D[c] = A.D[c];
+            sm.O[c] = A.O[c];
+            sm.N[c] = A.N[c];
+            if (sm.O[c] >= 0) drop[sm.O[c]] = INT32_MAX;   // present at the start of the pass
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < m; c += DP_THREADS) sm.cmin[c] = sm.D[(k - 1) * m + c];
+    int nev = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < A.nl; base += DP_CHUNK) {
+        // screen this thread's windows against the column minima as they
+        // stand (every load issued before the tests)
+        const int64_t i0 = base + (int64_t)threadIdx.x * DP_RPT;
+        const bool stage = m <= DP_STAGE;
+        bool okr[DP_RPT];
+#pragma unroll
+        for (int r = 0; r < DP_RPT; ++r) {
+            const int64_t i = i0 + r;
+            okr[r] = i < A.nl && (PASS == 1 ? (A.all_valid || A.flag[i] == ROW_DONE) : A.kept[i] != 0);
+        }
+        double vr[DP_RPT][DP_STAGE];
+        unsigned flags = 0;
+#pragma unroll
+        for (int r = 0; r < DP_RPT; ++r) {
+            bool cand = false;
+            if (okr[r]) {
+                if (stage) {
+#pragma unroll
+                    for (int c = 0; c < DP_STAGE; ++c) vr[r][c] = c < m ? A.nnd[(int64_t)c * A.n0 + i0 + r] : ninf();
+#pragma unroll
+                    for (int c = 0; c < DP_STAGE; ++c) cand |= c < m && isfinite(vr[r][c]) && vr[r][c] > sm.cmin[c];
+                } else {
+                    for (int c = 0; c < m && !cand; ++c) {
+                        const double v = A.nnd[(int64_t)c * A.n0 + i0 + r];
+                        cand = isfinite(v) && v > sm.cmin[c];
+                    }
+                }
+            }
+            if (cand) flags |= 1u << r;
+        }
+        int total;
+        int pos = block_excl_scan(__popc(flags), sm.wsum, &total);
+#pragma unroll
+        for (int r = 0; r < DP_RPT; ++r)
+            if ((flags >> r) & 1u) {
+                sm.cand[pos] = (int32_t)(i0 + r);
+                if (stage)
+#pragma unroll
+                    for (int c = 0; c < DP_STAGE; ++c) sm.cv[pos * DP_STAGE + c] = vr[r][c];
+                ++pos;
+            }
+        __syncthreads();
+        if (w == 0) {
+            // 32 candidates at a time: every lane re-tests its own against
+            // the minima as they stand, and the first that still beats one
+            // is taken (those before it cannot change dkm_l)
+            for (int t0 = 0; t0 < total; t0 += 32) {
+                const int64_t ci = t0 + lane < total ? sm.cand[t0 + lane] : -1;
+                int after = -1;
+                // (with a small matrix each lane also tests its own window for
+                // a trivial match, so a round takes the first window that enters)
+                const bool own_triv = cells <= 64;
+                while (true) {
+                    bool beat = false;
+                    if (ci >= 0 && lane > after)
+                        for (int c = 0; c < m && !beat; ++c) {
+                            const double v = stage ? sm.cv[(t0 + lane) * DP_STAGE + c] : A.nnd[(int64_t)c * A.n0 + ci];
+                            beat = isfinite(v) && v > sm.cmin[c];
+                        }
+                    if (beat && own_triv)
+                        for (int c = 0; c < cells && beat; ++c) {
+                            const int64_t o = sm.O[c];
+                            beat = !(o >= 0 && ci - o <= A.E && o - ci <= A.E);
+                        }
+                    const unsigned bm = __ballot_sync(0xffffffffu, beat);
+                    if (!bm) break;
+                    after = __ffs(bm) - 1;
+                    const int64_t ii = __shfl_sync(0xffffffffu, ci, after);
+                    if (!own_triv && dkm_trivial_warp(sm.O, cells, ii, A.E, lane)) continue;
+                    int32_t dropped;
+                    const int j = dkm_insert_warp(sm.D, sm.O, sm.N, sm.cmin, k, m, ii, A.nnd + ii, A.nnj + ii, A.n0,
+                                                  lane, &dropped);
+                    if (j >= 0 && lane == 0) {
+                        ins[ii] = A.l;
+                        drop[ii] = INT32_MAX;
+                        if (dropped >= 0) drop[dropped] = (int32_t)ii;
+                        if (PASS == 2) {
+                            A.ev_t[nev] = (int32_t)ii;
+                            A.ev_j[nev] = j;
+                            A.ev_v[nev] = sm.cmin[j];
+                        }
+                    }
+                    if (j >= 0) ++nev;
+                    __syncwarp();
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int c = threadIdx.x; c < cells; c += DP_THREADS) {
+        A.D[c] = sm.D[c];
+        A.O[c] = sm.O[c];
+        A.N[c] = sm.N[c];
+        if (PASS == 1) A.O1[c] = sm.O[c];
+    }
+    if (PASS == 1)
+        for (int c = threadIdx.x; c < m; c += DP_THREADS) A.cmin1[c] = sm.cmin[c];
+    if (PASS == 2) {
+        if (threadIdx.x == 0) *A.nev = nev;
+        // Algorithm 9: fold dkm_l into dkm_{lmin,lmax}
+        const double f = sqrt((double)A.l);
+        for (int c = threadIdx.x; c < cells; c += DP_THREADS) {
+            if (sm.O[c] < 0) continue;
+            const double v = sm.D[c] / f;
+            if (A.tab.len[c] == 0 || v >= A.tab.norm[c]) {
+                A.tab.norm[c] = v;
+                A.tab.dist[c] = sm.D[c];
+                A.tab.off[c] = sm.O[c];
+                A.tab.len[c] = A.l;
+                A.tab.nn[c] = sm.N[c];
+            }
+        }
+    }
+}
+
+// First-pass decisions of the non-valid rows: listed unless an offset that
+// entered before it and had not left is within E; kept if listed and an
+// upper value beats its column's last entry after the first pass.
+__global__ void k_dp1_list(DiscPassArgs A)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool skip = false;
     if (i < A.nl) {
         const int32_t fl = A.flag[i];
-        const int q = A.lpos[i];
         if (fl == ROW_RECOMPUTE || fl == ROW_FLAT) {
+            bool blocked = false;
+            for (int64_t o = i - A.E < 0 ? 0 : i - A.E; o < i && !blocked; ++o)
+                blocked = A.ins1[o] == A.l && A.drop1[o] > i;
             bool keep = false;
-            if (q >= 0)
-                for (int c = 0; c < A.m && !keep; ++c)
-                    keep = A.lub[(int64_t)q * A.m + c] > A.D[(A.k - 1) * A.m + c];
-            if (!keep) {
+            if (!blocked)
+                for (int c = 0; c < A.m && !keep; ++c) keep = A.nnd[(int64_t)c * A.n0 + i] > A.cmin1[c];
+            if (keep) {
+                A.kept[i] = 1;
+                for (int c = 0; c < A.m; ++c) A.lub[(int64_t)c * A.n0 + i] = A.nnd[(int64_t)c * A.n0 + i];
+            } else {
                 skip = true;
                 A.flag[i] = ROW_SKIP;
                 if (A.thr32) A.thr32[i] = __int_as_float(0x7f800000);
@@ -493,67 +662,55 @@ __global__ void k_dmark(DiscPassArgs A)
                 }
             }
         }
-        if (skip || q < 0 || (fl != ROW_RECOMPUTE && fl != ROW_FLAT)) A.lpos[i] = -1;
     }
     const int c = __syncthreads_count(skip);
     if (threadIdx.x == 0 && c) atomicAdd(&A.stats[10], (unsigned long long)c);
 }
 
-// Second pass (one warp, list order): a window with a trivial match in dkm_l
-// is skipped; else the first column (m down to 1) whose upper value beats
-// its last entry has the row (recomputed, so exact now) inserted by
-// Algorithm 8. Then Algorithm 9 folds dkm_l into dkm_{lmin,lmax}.
-__global__ void __launch_bounds__(32) k_dpass2(DiscPassArgs A)
-{
-    __shared__ double cmin[KMAX];
-    const int lane = threadIdx.x;
-    const int k = A.k, m = A.m, cells = k * m;
-    for (int c = lane; c < m; c += 32) cmin[c] = A.D[(k - 1) * m + c];
-    __syncwarp();
-    const int nls = *A.nlist;
-    for (int base = 0; base < nls; base += 32) {
-        const int t = base + lane;
-        bool cand = false;
-        if (t < nls)
-            for (int c = 0; c < m && !cand; ++c) cand = A.lub[(int64_t)t * m + c] > cmin[c];
-        unsigned mask = __ballot_sync(0xffffffffu, cand);
-        while (mask) {
-            const int u = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const int tt = base + u;
-            const int64_t ii = A.lst[tt];
-            if (dkm_trivial_warp(A.O, cells, ii, A.E, lane)) continue;
-            bool pass = false;
-            for (int c = m - 1; c >= 0 && !pass; --c) pass = A.lub[(int64_t)tt * m + c] > cmin[c];
-            if (pass) {
-                if (lane == 0) A.used[ii] = 1;
-                dkm_insert_warp(A.D, A.O, A.N, cmin, k, m, ii, A.nnd + ii, A.nnj + ii, A.n0, lane);
-            }
-        }
-    }
-    const double f = sqrt((double)A.l);
-    for (int c = lane; c < cells; c += 32) {
-        if (A.O[c] < 0) continue;
-        const double v = A.D[c] / f;
-        if (A.tab.len[c] == 0 || v >= A.tab.norm[c]) {
-            A.tab.norm[c] = v;
-            A.tab.dist[c] = A.D[c];
-            A.tab.off[c] = A.O[c];
-            A.tab.len[c] = A.l;
-            A.tab.nn[c] = A.N[c];
-        }
-    }
-}
-
-// Rows recomputed ahead of the second pass that it did not need take back
-// their state from before the recompute (extended entries, bound base and
-// base length), as if never recomputed; list positions and marks are
-// cleared for the next length.
-__global__ void k_drestore(DiscPassArgs A)
+// Second-pass decisions of the kept rows: recomputed by the second pass iff
+// no offset present at its visit is within E (the first pass's entries that
+// had not left, and the second pass's earlier entries that had not) and an
+// upper value beats the column's last entry at its visit. The others take
+// back their row state from before the recomputes.
+__global__ void k_dp2_used(DiscPassArgs A)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= A.nl || A.lpos[i] < 0) return;
-    if (!A.used[i]) {
+    if (i >= A.nl || !A.kept[i]) return;
+    A.kept[i] = 0;
+    bool blocked = false;
+    for (int c = 0; c < A.k * A.m && !blocked; ++c) {
+        const int64_t o = A.O1[c];
+        blocked = o >= 0 && i - o <= A.E && o - i <= A.E && A.drop2[o] > i;
+    }
+    for (int64_t o = i - A.E < 0 ? 0 : i - A.E; o < i && !blocked; ++o)
+        blocked = A.ins2[o] == A.l && A.drop2[o] > i;
+    bool used = false;
+    if (!blocked) {
+        // events before visit i: ev_t is increasing
+        int lo = 0, hi = *A.nev;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (A.ev_t[mid] < i) lo = mid + 1;
+            else hi = mid;
+        }
+        for (int c = 0; c < A.m && !used; ++c) {
+            double cm = A.cmin1[c];
+            for (int e = lo - 1; e >= 0; --e)
+                if (A.ev_j[e] == c) {
+                    cm = A.ev_v[e];
+                    break;
+                }
+            used = A.lub[(int64_t)c * A.n0 + i] > cm;
+        }
+    }
+    if (!used) {
+        // the recompute's top-p stay on as threshold hints
+        for (int e = 0; e < A.p; ++e) {
+            const int64_t at = (int64_t)e * A.n0 + i;
+            A.hint_j[at] = A.st.ent_j[at];
+            A.hint_c[at] = A.st.ent_c[at];
+            A.hint_dq[at] = A.st.ent_dq[at];
+        }
         for (int e = 0; e < A.p; ++e) {
             const int64_t at = (int64_t)e * A.n0 + i;
             A.st.ent_j[at] = A.saved.ent_j[at];
@@ -564,21 +721,28 @@ __global__ void k_drestore(DiscPassArgs A)
         A.st.sigb[i] = A.saved.sigb[i];
         A.st.base[i] = A.saved.base[i];
         A.st.bnum[i] = A.saved.bnum[i];
+    } else {
+        for (int e = 0; e < A.p; ++e) A.hint_j[(int64_t)e * A.n0 + i] = -1;   // the entries are new
     }
-    A.lpos[i] = -1;
-    A.used[i] = 0;
 }
 
-void launch_discord_pass1(const DiscPassArgs &a, cudaStream_t s) { k_dpass1<<<1, 32, 0, s>>>(a); }
-void launch_discord_restore(const DiscPassArgs &a, cudaStream_t s)
+template <int PASS>
+static void launch_dp_seq(const DiscPassArgs &a, cudaStream_t s)
 {
-    k_drestore<<<(unsigned)((a.nl + 255) / 256), 256, 0, s>>>(a);
+    static std::once_flag once[64];
+    smem_optin_max((const void *)k_dp_seq<PASS>, once);
+    k_dp_seq<PASS><<<1, DP_THREADS, dp_smem_bytes(a.k, a.m), s>>>(a);
 }
+void launch_discord_pass1(const DiscPassArgs &a, cudaStream_t s) { launch_dp_seq<1>(a, s); }
 void launch_discord_mark(const DiscPassArgs &a, cudaStream_t s)
 {
-    k_dmark<<<(unsigned)((a.nl + 255) / 256), 256, 0, s>>>(a);
+    k_dp1_list<<<(unsigned)((a.nl + 255) / 256), 256, 0, s>>>(a);
 }
-void launch_discord_pass2(const DiscPassArgs &a, cudaStream_t s) { k_dpass2<<<1, 32, 0, s>>>(a); }
+void launch_discord_pass2(const DiscPassArgs &a, cudaStream_t s) { launch_dp_seq<2>(a, s); }
+void launch_discord_restore(const DiscPassArgs &a, cudaStream_t s)
+{
+    k_dp2_used<<<(unsigned)((a.nl + 255) / 256), 256, 0, s>>>(a);
+}
 
 // Algorithm 9 over the streamed tables: per cell the largest d / sqrt(l),
 // ties to the later length.

@@ -417,7 +417,66 @@ __device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i, double
     int nlow = cnt;
     const int64_t ntc = nontrivial_count(i, A.nl, E);
     double theta = -pinf();
-    if (ntc > p) {
+    if (A.hint_j) {
+        // hint partners not among the entries: their extended correlations,
+        // lowered by their error bounds, are further known lower bounds
+        double hq[PM];
+        int nh = 0;
+        for_pm<PM>([&](int e) {
+            hq[e] = -pinf();
+            if (e >= p) return;
+            const int64_t at = (int64_t)e * n0 + i;
+            const int32_t j = A.hint_j[at];
+            if (j < 0) return;
+            if (j >= A.nl || !nontrivial(i, j, E)) {
+                A.hint_j[at] = -1;
+                return;
+            }
+            const double c = fma(wgt * xi, A.x[j + l - 1] - A.mu_prev[j], A.hint_c[at]);
+            A.hint_c[at] = c;
+            bool dup = false;
+            for_pm<PM>([&](int a) { dup |= (r.j[a] == j); });
+            if (dup) return;
+            const bool flat_j = A.run[j] >= l;
+            hq[e] = corr_isd(c, isdi, A.isd[j], flat_j) - (flat_j ? 0.0 : (double)A.hint_dq[at]);
+            ++nh;
+        });
+        if (cnt + nh >= p && ntc > p) {
+            // the p-th largest of the union (ties by position, entries first)
+            double pth = -pinf();
+            for_pm<PM>([&](int a) {
+                if (r.j[a] < 0) return;
+                const double v = r.q[a] - r.dq[a];
+                int rank = 0;
+                for_pm<PM>([&](int b) {
+                    if (r.j[b] >= 0) {
+                        const double u = r.q[b] - r.dq[b];
+                        rank += (u > v || (u == v && b < a));
+                    }
+                    rank += (hq[b] > v);
+                });
+                if (rank == p - 1) pth = v;
+            });
+            for_pm<PM>([&](int e) {
+                if (hq[e] == -pinf()) return;
+                const double v = hq[e];
+                int rank = 0;
+                for_pm<PM>([&](int b) {
+                    if (r.j[b] >= 0) rank += (r.q[b] - r.dq[b] >= v);
+                    rank += (hq[b] > v || (hq[b] == v && b < e));
+                });
+                if (rank == p - 1) pth = v;
+            });
+            theta = pth - dq_row(A.em, i);
+            nlow = p;            // no partners next to the exclusion zone needed
+        } else {
+            for_pm<PM>([&](int e) {
+                if (hq[e] != -pinf()) qmin = fmin(qmin, hq[e]);
+            });
+            nlow += nh;
+        }
+    }
+    if (ntc > p && theta == -pinf()) {
         const double mui = A.mu[i];
         for (int64_t t = 1; nlow < p && t <= A.nl; ++t) {
             for (int side = 0; side < 2 && nlow < p; ++side) {
@@ -425,6 +484,8 @@ __device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i, double
                 if (j < 0 || j >= A.nl) continue;
                 bool have = false;
                 for_pm<PM>([&](int a) { have |= (r.j[a] == j); });
+                if (A.hint_j)
+                    for (int e = 0; e < p; ++e) have |= (A.hint_j[(int64_t)e * n0 + i] == j);
                 if (have) continue;
                 const bool flat_j = A.run[j] >= l;
                 const double c = flat_j ? 0.0 : comoment(A.x, i, j, l, mui, A.mu[j]);

@@ -152,6 +152,12 @@ template <typename T> struct ExtArgs {
     // discord mode: non-valid rows write their 1st..m-th smallest pessimistic
     // stored distances (+inf past the stored count; flat rows +inf) to out.nnd
     int ub_out;
+    // discord mode (NULL otherwise): per row, p hint partners (the top-p of a
+    // recompute whose state was given back), extended like the entries and
+    // used only to tighten the band kernel's threshold
+    int32_t *hint_j;
+    double *hint_c;
+    float *hint_dq;
     const float *xh, *xl;   // x as FP32 pairs (compensated re-evaluation)
     const double *isd;      // 1 / sqrt(M2) at l (0: flat)
     int64_t n0, nl;
@@ -363,17 +369,24 @@ struct DiscPassArgs {       // discord mode: Algorithm 10's two passes at one le
     double *thr64;
     double *nnd;            // [m][n0] exact (valid / recomputed rows) or upper values (non-valid)
     int32_t *nnj;
-    double *D;              // dkm_l [k][m]
+    double *D;              // dkm_l [k][m] (between the passes)
     int32_t *O, *N;
-    int32_t *lst;           // non-valid list: row, in offset order
-    double *lub;            // its upper values [list][m]
-    int32_t *lpos;          // row -> list position (-1: not listed)
-    int32_t *nlist;
-    int32_t *used;          // rows the second pass recomputed and entered (0 / 1)
+    int32_t *O1;            // dkm_l's offsets after the first pass
+    double *cmin1;          // its column minima [m]
+    int32_t *ins1, *drop1;  // first-pass log [n0]: ins = l if entered at l; drop = who pushed it out
+    int32_t *ins2, *drop2;  // second-pass log [n0]
+    int32_t *ev_t, *ev_j;   // second-pass entries: window, column, the column's new minimum
+    double *ev_v;
+    int32_t *nev;
+    double *lub;            // [m][n0] upper values of the kept rows
+    int32_t *kept;          // [n0] 1: kept for the second pass
     DiscTable tab;          // dkm_{lmin,lmax}
     unsigned long long *stats;
     RowState st, saved;     // row state and its copy from before the recomputes
     int p;
+    int32_t *hint_j;        // [p][n0] threshold hints (see ExtArgs)
+    double *hint_c;
+    float *hint_dq;
 };
 void launch_discord_pass1(const DiscPassArgs &a, cudaStream_t s);
 void launch_discord_mark(const DiscPassArgs &a, cudaStream_t s);

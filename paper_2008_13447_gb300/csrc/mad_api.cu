@@ -264,11 +264,16 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
     double *dkm_d = disc_mode ? dalloc<double>(ctx, s, (size_t)k_max * m_max) : nullptr;
     int32_t *dkm_o = disc_mode ? dalloc<int32_t>(ctx, s, (size_t)k_max * m_max) : nullptr;
     int32_t *dkm_n = disc_mode ? dalloc<int32_t>(ctx, s, (size_t)k_max * m_max) : nullptr;
-    int32_t *dlst = disc_mode ? dalloc<int32_t>(ctx, s, n0) : nullptr;
     double *dlub = disc_mode ? dalloc<double>(ctx, s, (size_t)n0 * m_max) : nullptr;
-    int32_t *dlpos = disc_mode ? dalloc<int32_t>(ctx, s, n0) : nullptr;
-    int32_t *dnlist = disc_mode ? dalloc<int32_t>(ctx, s, 1) : nullptr;
-    int32_t *dused = disc_mode ? dalloc<int32_t>(ctx, s, n0) : nullptr;
+    int32_t *dkept = disc_mode ? dalloc<int32_t>(ctx, s, n0) : nullptr;
+    int32_t *dO1 = disc_mode ? dalloc<int32_t>(ctx, s, (size_t)k_max * m_max) : nullptr;
+    double *dcmin1 = disc_mode ? dalloc<double>(ctx, s, m_max) : nullptr;
+    // entry / exit logs of the two passes (4 x n0) and the second pass's minima log
+    int32_t *dlog = disc_mode ? dalloc<int32_t>(ctx, s, (size_t)6 * n0 + 1) : nullptr;
+    double *dev_v = disc_mode ? dalloc<double>(ctx, s, n0) : nullptr;
+    int32_t *hint_j = disc_mode ? dalloc<int32_t>(ctx, s, (size_t)p * n0) : nullptr;
+    double *hint_c = disc_mode ? dalloc<double>(ctx, s, (size_t)p * n0) : nullptr;
+    float *hint_dq = disc_mode ? dalloc<float>(ctx, s, (size_t)p * n0) : nullptr;
     RowState rs_saved{};
     if (disc_mode)
         rs_saved = RowState{dalloc<int32_t>(ctx, s, (size_t)p * n0), dalloc<double>(ctx, s, (size_t)p * n0),
@@ -298,8 +303,9 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
     CK(cudaMemsetAsync(dstats, 0, (size_t)nL * NSTAT * sizeof(unsigned long long), st));
     if (motif_mode) launch_fill<double>(mm, (int64_t)2 * nL, INFINITY, st);
     if (disc_mode) {
-        launch_fill<int32_t>(dlpos, n0, -1, st);
-        CK(cudaMemsetAsync(dused, 0, n0 * sizeof(int32_t), st));
+        CK(cudaMemsetAsync(dkept, 0, n0 * sizeof(int32_t), st));
+        CK(cudaMemsetAsync(dlog, 0, ((size_t)6 * n0 + 1) * sizeof(int32_t), st));
+        CK(cudaMemsetAsync(hint_j, 0xff, (size_t)p * n0 * sizeof(int32_t), st));   // -1: no hint
     }
     CK(cudaMemsetAsync(counters, 0, 4 * sizeof(int32_t), st));
     CK(cudaMemsetAsync(vm.len, 0, n0 * sizeof(int32_t), st));
@@ -463,13 +469,23 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
         d.D = dkm_d;
         d.O = dkm_o;
         d.N = dkm_n;
-        d.lst = dlst;
         d.lub = dlub;
-        d.lpos = dlpos;
-        d.nlist = dnlist;
+        d.kept = dkept;
+        d.O1 = dO1;
+        d.cmin1 = dcmin1;
+        d.ins1 = dlog;
+        d.drop1 = dlog + n0;
+        d.ins2 = dlog + 2 * n0;
+        d.drop2 = dlog + 3 * n0;
+        d.ev_t = dlog + 4 * n0;
+        d.ev_j = dlog + 5 * n0;
+        d.nev = dlog + 6 * n0;
+        d.ev_v = dev_v;
+        d.hint_j = hint_j;
+        d.hint_c = hint_c;
+        d.hint_dq = hint_dq;
         d.tab = tab;
         d.stats = lo.stats;
-        d.used = dused;
         d.st = rs;
         d.saved = rs_saved;
         d.p = p;
@@ -539,6 +555,9 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
                 ea.min_lb_abs = reinterpret_cast<unsigned long long *>(mm + 2 * li + 1);
             }
             ea.ub_out = disc_mode ? 1 : 0;
+            ea.hint_j = hint_j;
+            ea.hint_c = hint_c;
+            ea.hint_dq = hint_dq;
             launch_extend<T>(ea, st);
             if (disc_mode) {
                 // Algorithm 10's first pass, then the rows its second pass can need
