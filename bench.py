@@ -112,6 +112,22 @@ def run_ncu_case(args):
     return 0
 
 
+def max_over_ranks(ms, pg, device):
+    """The slowest rank's time, on every rank (ms itself with one rank)."""
+    if pg is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(cells_per_rank, world, ms_per_step):
+    """Whole-job cells/s: every rank processes its own replica of the
+    workload in the step time of the slowest rank."""
+    return cells_per_rank * world / (ms_per_step / 1e3)
+
+
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -325,14 +341,10 @@ def main():
         pg.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if pg:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), pg, dev)
     ms_per_step = total_ms / args.steps
     cells = w.cells
-    value = cells * world / (ms_per_step / 1e3)
+    value = job_throughput(cells, world, ms_per_step)
 
     # read-out launches per step (motif rounds, pair re-check, discord re-check)
     launches_per_step = launches / args.steps + 2 * k + 1 + 1
@@ -447,9 +459,9 @@ def main():
         finally:
             mad.mad_destroy(c2)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e = min(e2e_ms)
+    e2e = max_over_ranks(min(e2e_ms), pg, dev)
     d2h = n0 * (8 + 8 + 4 + 4) + k * 56 + k * m * 56
-    out["e2e"] = {"value": cells * world / (e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": n * 8,
+    out["e2e"] = {"value": job_throughput(cells, world, e2e), "unit": UNIT, "h2d_bytes_per_step": n * 8,
                   "d2h_bytes_per_step": d2h, "ms_per_step": e2e}
     out["result"] = {"top_motif": {k2: mot[0][k2] for k2 in ("a", "b", "len", "dist", "dist_recheck")} if mot else None,
                      "top_discord": {k2: dis[0][k2] for k2 in ("off", "len", "dist", "dist_recheck")} if dis else None,
