@@ -61,6 +61,8 @@ def parse():
                          "JSON line (certified / recomputed fractions, time)")
     ap.add_argument("--ncu-case", default=None, metavar="LMIN:LMAX",
                     help="profile the workload once over [LMIN, LMAX] and exit (a small case for ncu captures)")
+    ap.add_argument("--mode", type=int, default=0, choices=[0, 1, 2],
+                    help="with --ncu-case: 0 exact rows, 1 motif mode, 2 discord mode")
     return ap.parse_args()
 
 
@@ -102,7 +104,8 @@ def run_ncu_case(args):
     w = workloads.make(args.workload)
     a, b = (int(v) for v in args.ncu_case.split(":"))
     prec = mad.MAD_FP32 if args.precision == "fp32" else mad.MAD_FP64
-    ctx = mad.mad_create(w.series[0], precision=prec, k_max=w.k, m_max=w.m, band_form=args.band_form)
+    ctx = mad.mad_create(w.series[0], precision=prec, k_max=w.k, m_max=w.m, band_form=args.band_form,
+                         mode=args.mode)
     try:
         mad.mad_profile(ctx, a, b, w.p)
         for s in mad.mad_stats(ctx, 0):

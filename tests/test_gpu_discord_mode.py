@@ -63,6 +63,22 @@ def test_discord_mode_matches_oracle(prec):
     assert st[0]["recomputed"] == st[0]["rows"]
 
 
+def test_discord_mode_many_ranks_matches_oracle():
+    # k above one warp's 32 ranks and three columns, a ragged series length
+    x = workloads.ar2(1333, 109)
+    lmin, lmax, p, k, m = 18, 26, 6, 40, 3
+    dis, _ = run_mode2(x, lmin, lmax, p, k, m, mad.MAD_FP64)
+    ref = oracle.valmod_discord(x, lmin, lmax, p, k, m)
+    for r in range(k):
+        for c in range(m):
+            d = dis[r * m + c]
+            if ref["len"][r, c] == 0:
+                assert d["len"] == 0 and d["off"] == -1
+                continue
+            assert (d["off"], d["len"]) == (int(ref["off"][r, c]), int(ref["len"][r, c]))
+            assert abs(d["dist"] - ref["dist"][r, c]) <= 1e-9 * ref["dist"][r, c]
+
+
 def test_discord_mode_all_valid_is_streamed_form():
     # p = 64 stores every window of a short series: every row is valid, and
     # the table is the streamed form of the exact profiles
