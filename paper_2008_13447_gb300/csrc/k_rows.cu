@@ -508,8 +508,13 @@ __device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i, double
     return 2;
 }
 
+// Row kernels: 128 threads per block. With at most 8 entries per row, four
+// blocks per SM (at most 128 registers) hold every row of a 65,536-point
+// series in one wave.
+template <int PM> constexpr int row_min_blocks() { return PM <= 8 ? 4 : 1; }
+
 template <typename T, int PM>
-__global__ void k_extend(ExtArgs<T> A)
+__global__ void __launch_bounds__(128, row_min_blocks<PM>()) k_extend(ExtArgs<T> A)
 {
     __shared__ unsigned sc[2];
     __shared__ unsigned long long smin[2];
@@ -597,7 +602,7 @@ __device__ __forceinline__ bool key_before(T ka, int32_t ja, T kb, int32_t jb)
 }
 
 template <typename T, int PM>
-__global__ void k_merge(MergeArgs<T> A)
+__global__ void __launch_bounds__(128, row_min_blocks<PM>()) k_merge(MergeArgs<T> A)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= A.nl) return;
