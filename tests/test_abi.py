@@ -84,6 +84,10 @@ def test_argument_errors_before_gpu_work(lib):
     assert lib.mad_create(mad._p(x), 3, C.byref(o), None) == mad.MAD_EINVAL
     assert lib.mad_profile(None, 8, 16, 5) == mad.MAD_EINVAL
     assert lib.mad_motifs(None, 0, 5, None, None) == mad.MAD_EINVAL
+    for fn in (lib.mad_discords, lib.mad_discords_global, lib.mad_discords_streamed):
+        assert fn(None, 0, 2, 1, None, None) == mad.MAD_EINVAL
+    assert lib.mad_motif_sets(None, 0, 2, 1.0, 8, None, None, None) == mad.MAD_EINVAL
+    assert lib.mad_observe(None, 0, None, None) == mad.MAD_EINVAL
     lib.mad_destroy(None)   # NULL-safe
     assert isinstance(lib.mad_last_error(None), bytes)
 
