@@ -251,6 +251,13 @@ def cpu_oracle_sample(w, seconds):
 
 # ------------------------------------------------------------ reference arm
 
+def workload_config(name, w):
+    """The workload fields of the JSON line's config, shared by both arms."""
+    x = w.series[0]
+    return {"workload": name, "n": len(x), "lmin": w.lmin[0], "lmax": w.lmax[0], "p": w.p, "k": w.k, "m": w.m,
+            "exclusion": "ceil(l/4)", "cells_per_step": w.cells}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -270,7 +277,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": args.workload},
+           "data": "synthetic", "config": workload_config(args.workload, w),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": samp["cores"], "kind": "oracle",
                             "sample": samp["sample"]},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -368,9 +375,9 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32" if prec == mad.MAD_FP32 else "f64", "data": "synthetic",
-           "config": {"workload": args.workload, "n": n, "lmin": lmin, "lmax": lmax, "p": p, "k": k, "m": m,
-                      "exclusion": "ceil(l/4)", "precision": args.precision, "band_form": args.band_form, "cells_per_step": cells,
-                      "l2": "flushed between timed steps (512 MB write)", "parallelism": "replicas"},
+           "config": {**workload_config(args.workload, w), "precision": args.precision,
+                      "band_form": args.band_form, "l2": "flushed between timed steps (512 MB write)",
+                      "parallelism": "replicas"},
            "roofline": roof, "gpu_launches": int(round(launches_per_step * args.steps)),
            "clocks": clk}
 
