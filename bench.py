@@ -67,7 +67,7 @@ def parse():
 
 
 def run_p_sweep(args):
-    """Pruning versus the number p of stored entries per row (Sec. 6.3): the
+    """Pruning versus the number p of stored entries per row (Sec. 7.2): the
     fractions of rows certified and recomputed after lmin, and the time."""
     import time
     import paper_2008_13447_gb300 as mad

@@ -132,7 +132,7 @@ typedef struct {
                                full FP64 distance profile (two-pass statistics per window) */
 } mad_discord;
 
-/* Pruning counters of one length (Sec. 6.3 "valid / non-valid / recomputed"). */
+/* Pruning counters of one length (Sec. 7.2 "valid / non-valid / recomputed"). */
 typedef struct {
     int32_t len;
     int32_t reserved;
@@ -314,7 +314,7 @@ MAD_API mad_status mad_mth_nn_dist_noalloc(const double *x, int64_t n, const int
                                            int32_t ncells, int32_t m_max, int32_t excl_num,
                                            int32_t excl_den, double *out, void *stream);
 
-/* Pruning observation at options.observe_len (Sec. 6.3 diagnostics), for
+/* Pruning observation at options.observe_len (Sec. 7.2 diagnostics), for
  * the n - observe_len + 1 rows at that length, host arrays:
  *   gap[i] = maxLB - minED: the row's bound (Eq. LB from its p-th stored
  *            entry) minus its smallest stored distance; > 0 exactly when

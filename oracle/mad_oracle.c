@@ -9,7 +9,7 @@
  *
  * Every result with a plain definition is that definition written out:
  *   - window mean / population standard deviation by a two-pass loop
- *     (Sec. 4.2, the mu and sigma used by the distance formula);
+ *     (Sec. 4.3, the mu and sigma used by the distance formula);
  *   - the z-normalised Euclidean distance through the Pearson correlation
  *     (Eq. DIST), and directly from z-normalised windows (Def. of a motif
  *     pair, "z-normalized Euclidean distance");
@@ -20,7 +20,7 @@
  *   - the variable-length matrix profile VALMP (Algorithm 2 updateVALMP);
  *   - the lower bound of Eq. LB and the pruned VALMOD iteration that uses it
  *     (Algorithms 1, 3, 4 and 10), restated in the reading documented below;
- *   - the top-k motif and Top-k m-th discord read-outs (Sec. 5, Algorithms
+ *   - the top-k motif and Top-k m-th discord read-outs (Sec. 5-6, Algorithms
  *     5, 8 and 9, in the deterministic reading documented below).
  *
  * Conventions: offsets are 0-based; a window of length l starts at i and
@@ -47,7 +47,7 @@ i64 orc_excl(int l, int num, int den)
 }
 
 /* Mean and population standard deviation of x[i .. i+l-1], two passes
- * (mu = s / l and sigma = sqrt(ss / l - mu^2) in Sec. 4.2, computed here
+ * (mu = s / l and sigma = sqrt(ss / l - mu^2) in Sec. 4.3, computed here
  * without running sums). */
 void orc_window_stats(const double *x, i64 n, int l, i64 i, double *mu, double *sigma)
 {
@@ -393,7 +393,7 @@ static void recompute_row(const double *x, i64 n, int l, int num, int den, int p
 }
 
 /* Observation at one length obs_len (> lmin, optional; the paper's
- * pruning diagnostics, Sec. 6.3): for every row with stored entries, before
+ * pruning diagnostics, Sec. 7.2): for every row with stored entries, before
  * its recompute decision, obs_gap[i] = maxLB - minED = B - (smallest stored
  * distance) (> 0 exactly when the row is certified for its motif) and
  * obs_tlb[i] = mean over its stored entries of LB / ED, the tightness of

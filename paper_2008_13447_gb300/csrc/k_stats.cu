@@ -1,7 +1,7 @@
 // k_stats.cu -- window statistics (mean, centred second moment) and the
 // per-window data of the diagonal recurrence.
 //
-// Sec. 4.2 computes mu and sigma of every window from running sums (Eq. DIST
+// Sec. 4.3 computes mu and sigma of every window from running sums (Eq. DIST
 // needs them). Running sums of raw values cancel badly on drifting series,
 // so here every window's mean and M2 = l sigma^2 are formed once at lmin by
 // a two-pass loop over the window and then carried from length l-1 to l by

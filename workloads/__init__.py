@@ -4,7 +4,7 @@ This module only *generates* float64 series (and the length-range parameters
 that go with them). It holds none of the method's arithmetic, so both the CPU
 oracle (``oracle/``) and the CUDA path may use it without sharing code.
 
-The paper evaluates on real recordings (GAP, CAP/EEG, ECG, EMG, ASTRO, Sec. 6
+The paper evaluates on real recordings (GAP, CAP/EEG, ECG, EMG, ASTRO, Sec. 7
 "Datasets"); none of them is available here, so every workload below is a
 synthetic stand-in with the shape, size and structure of the paper's series:
 random walks (the paper's default synthetic model), ECG-like quasi-periodic
