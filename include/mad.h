@@ -285,7 +285,7 @@ MAD_API mad_status mad_stats(mad_ctx *ctx, int32_t series, mad_length_stats *out
 
 /* The m-th best-match distance of listed windows, recomputed directly in
  * FP64 from a full distance profile (Eq. DIST with two-pass window
- * statistics; the m-th best match of Definition 6), i.e. the computation
+ * statistics; Def. "m-th best match"), i.e. the computation
  * behind mad_discords' dist_recheck, without allocating any memory. The
  * paper has no counterpart of this function: it serves callers that cannot
  * allocate device memory during the call (memory held in a caching

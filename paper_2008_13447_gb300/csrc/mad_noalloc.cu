@@ -11,7 +11,7 @@
 // found once per device.
 //
 // The paper has no counterpart of this function; the quantity it computes is
-// the m-th best-match distance of Definition 6 at one length, from a full
+// the m-th best-match distance (Def. "m-th best match") at one length, from a full
 // FP64 distance profile (Eq. DIST, two-pass window statistics).
 #include <mutex>
 #include <string>

@@ -102,7 +102,7 @@ def test_seismic2m_first_lengths():
             with ThreadPoolExecutor(len(rows)) as ex:
                 profs = list(ex.map(lambda r: oracle.distance_profile(x, l, r), rows))
             for r, dp in zip(rows, profs):
-                ref = np.sort(dp[np.isfinite(dp)])[:m]       # the m best matches (Def. 6)
+                ref = np.sort(dp[np.isfinite(dp)])[:m]       # the m best matches (Def. "m-th best match")
                 assert np.all(np.abs(nnd[r] - ref) <= tol(l)), (l, r, nnd[r], ref)
                 for c in range(m):                          # partners: valid, distance as reported
                     j = int(nnj[r, c])
