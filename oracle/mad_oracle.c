@@ -21,7 +21,13 @@
  *   - the lower bound of Eq. LB and the pruned VALMOD iteration that uses it
  *     (Algorithms 1, 3, 4 and 10), restated in the reading documented below;
  *   - the top-k motif and Top-k m-th discord read-outs (Sec. 5-6, Algorithms
- *     5, 8 and 9, in the deterministic reading documented below).
+ *     5, 8 and 9, in the deterministic reading documented below);
+ *   - the paper-literal pruned iterations: motif mode (Algorithm 1 with
+ *     ComputeSubMP, Algorithm 4) and the discords with Algorithm 10's
+ *     pruning (driven by Algorithm 7);
+ *   - motif sets (Algorithm 6), the pruning observation (Sec. 7.2), and the
+ *     discord ranking variants (a global greedy over every offset and length,
+ *     and dkm_l streamed as Algorithms 7 and 8 print it).
  *
  * Conventions: offsets are 0-based; a window of length l starts at i and
  * covers x[i .. i+l-1]; n_l = n - l + 1 windows exist. A pair (i, j) is a
