@@ -80,7 +80,7 @@ def _L():
             "orc_discords_streamed": (None, [i64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                              C.c_int, P, P, P, P, P, P, P]),
             "orc_valmod_discord": (None, [P, i64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
-                                          C.c_int, P, P, P, P, P, P, P, P]),
+                                          C.c_int, P, P, P, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -320,17 +320,20 @@ def discords_streamed(n, lmin, lmax, k, m_max, m, nnd_all, nnj_all, num=1, den=4
 def valmod_discord(x, lmin, lmax, p, k, m, num=1, den=4):
     """Top-k m-th discords with the paper's pruning (Algorithms 7, 10, 8, 9):
     dict(off, len, dist, norm, nn) of shape (k, m) (the merged table),
-    dkm_off / dkm_d of shape (|L|, k, m) (every dkm_l) and stats (|L|, 4) =
-    rows, valid, listed, recomputed."""
+    dkm_off / dkm_d of shape (|L|, k, m) (every dkm_l), stats (|L|, 4) =
+    rows, valid, listed, recomputed, and recomp (|L|, n - lmin + 1) bool: the
+    rows whose full profile was computed at each length."""
     x = _f64(x)
     nL = lmax - lmin + 1
     off, ln = np.empty((k, m), np.int64), np.empty((k, m), np.int32)
     dd, nd, nn = np.empty((k, m)), np.empty((k, m)), np.empty((k, m), np.int64)
     doff, dd_l = np.empty((nL, k, m), np.int64), np.empty((nL, k, m))
     st = np.empty((nL, 4), np.int64)
+    rc = np.empty((nL, len(x) - lmin + 1), np.int8)
     _L().orc_valmod_discord(_p(x), len(x), lmin, lmax, num, den, p, k, m, _p(off), _p(ln), _p(dd), _p(nd),
-                            _p(nn), _p(doff), _p(dd_l), _p(st))
-    return dict(off=off, len=ln, dist=dd, norm=nd, nn=nn, dkm_off=doff, dkm_d=dd_l, stats=st)
+                            _p(nn), _p(doff), _p(dd_l), _p(st), _p(rc))
+    return dict(off=off, len=ln, dist=dd, norm=nd, nn=nn, dkm_off=doff, dkm_d=dd_l, stats=st,
+                recomp=rc.astype(bool))
 
 
 def discords(n, lmin, lmax, k, m_max, nnd_all, nnj_all, num=1, den=4):

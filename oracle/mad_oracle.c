@@ -977,11 +977,12 @@ static void dkm_merge(int k, int m, int l, const i64 *off, const double *d, cons
  *    with the exact distances;
  *  - rows neither valid nor recomputed keep their extended stored entries.
  * Outputs: the merged k x m table (as orc_discords), optionally every
- * dkm_l (dkm_off / dkm_d [(l - lmin) * k * m + cell]) and per-length stats
- * [(l - lmin) * 4 + {0..3}] = rows, valid, listed, recomputed. */
+ * dkm_l (dkm_off / dkm_d [(l - lmin) * k * m + cell]), per-length stats
+ * [(l - lmin) * 4 + {0..3}] = rows, valid, listed, recomputed, and which rows
+ * had their full profile computed (recomp[(l - lmin) * n0 + i] = 1, else 0). */
 void orc_valmod_discord(const double *x, i64 n, int lmin, int lmax, int num, int den, int p, int k, int m,
                         i64 *out_off, int32_t *out_len, double *out_d, double *out_nd, i64 *out_nn,
-                        i64 *dkm_off, double *dkm_d, i64 *stats)
+                        i64 *dkm_off, double *dkm_d, i64 *stats, signed char *recomp)
 {
     i64 n0 = n - lmin + 1;
     row_state *st = (row_state *)calloc((size_t)n0, sizeof(row_state));
@@ -1011,6 +1012,8 @@ void orc_valmod_discord(const double *x, i64 n, int lmin, int lmax, int num, int
     for (int l = lmin; l <= lmax; ++l) {
         i64 nl = n - l + 1, E = orc_excl(l, num, den);
         i64 nvalid = 0, nlist = 0, nrecomp = 0;
+        signed char *rc = recomp ? recomp + (i64)(l - lmin) * n0 : NULL;
+        if (rc) memset(rc, 0, (size_t)n0);
         dkm_clear(k, m, off, dd, nj);
         if (l == lmin) {
 #pragma omp parallel
@@ -1026,6 +1029,7 @@ void orc_valmod_discord(const double *x, i64 n, int lmin, int lmax, int num, int
                 free(qb);
             }
             nrecomp = nl;
+            if (rc) memset(rc, 1, (size_t)nl);
             for (i64 i = 0; i < nl; ++i) {
                 if (dkm_trivial(k, m, off, i, E)) continue;
                 dkm_insert(k, m, off, dd, nj, i, nnd + i * m, nnj + i * m);
@@ -1072,6 +1076,7 @@ void orc_valmod_discord(const double *x, i64 n, int lmin, int lmax, int num, int
                     if (!(sv[i * m + j] > dd[(k - 1) * m + j])) continue;
                     recompute_row(x, n, l, num, den, p, m, i, &st[i], mp, ip, nnd, nnj, prof, dbuf, qbuf);
                     ++nrecomp;
+                    if (rc) rc[i] = 1;
                     dkm_insert(k, m, off, dd, nj, i, nnd + i * m, nnj + i * m);
                     break;
                 }
