@@ -157,6 +157,10 @@ typedef struct {
     int64_t skipped;        /* motif mode: non-valid rows left undefined at this length */
     int32_t full_profile;   /* motif mode: 1 if the full profile was computed at this length */
     int32_t reserved2;
+    double dq_ratio_max;    /* largest observed error of a re-evaluated stored entry's correlation
+                               divided by the error bound the library kept for it (the bound holds
+                               while this is <= 1; against a compensated re-evaluation the
+                               observation is an upper estimate); 0 when nothing was re-evaluated */
 } mad_length_stats;
 
 /* Create a context for one series copied from host memory (FP64, n values).
@@ -303,11 +307,13 @@ MAD_API mad_status mad_stats(mad_ctx *ctx, int32_t series, mad_length_stats *out
  * Errors: MAD_EINVAL for a bad argument or cell (checked on the host before
  * any GPU work, or x / out not device memory of the current device),
  * MAD_ECUDA for a failed CUDA call; mad_last_error(NULL) gives the text.
+ * n must not exceed 2^31 (offsets are 32-bit in the kernels; else MAD_EINVAL).
  * The call makes no cudaMalloc / cudaFree or other allocating call. Its
- * scratch is one statically sized device array per device; the first call
- * on each device (with that device current) looks up the array's address,
- * which is set-up work: make that first call before any stream capture
- * begins. The scratch needs no zero initialisation. All calls on a device
+ * scratch is one statically sized device array per device; every call looks
+ * up the array's address in the calling context (so a cudaDeviceReset in
+ * between is harmless), and the first call in a context loads the library's
+ * device code there, which is set-up work: make that first call before any
+ * stream capture begins. The scratch needs no zero initialisation. All calls on a device
  * share the one scratch, so calls that overlap in time (other streams or
  * host threads) race: order them. Synchronous with respect to the host. */
 MAD_API mad_status mad_mth_nn_dist_noalloc(const double *x, int64_t n, const int32_t *cells,
@@ -326,6 +332,26 @@ MAD_API mad_status mad_mth_nn_dist_noalloc(const double *x, int64_t n, const int
  * range contains observe_len with lmin < observe_len (MAD_ESTATE otherwise).
  * Either pointer may be NULL. */
 MAD_API mad_status mad_observe(mad_ctx *ctx, int32_t series, double *gap, double *tlb);
+
+/* Test hook for the failure path (no counterpart in the paper). Sets, for
+ * the whole process, how many times each wavefront wait of the
+ * matrix-profile kernel (the hand-over of boundary values between the warps
+ * of a block) tries before it gives up; a negative value restores the
+ * kernel's own limit (the default, about 10^6 tries). With 0 every such wait
+ * gives up at once: the kernel still keeps every access in bounds and runs
+ * to its end, the results of that profile are meaningless, and mad_profile
+ * returns MAD_ETIMEOUT. The waits that hand out work units keep their own
+ * limit. Meant for tests; takes effect at the next mad_profile. */
+MAD_API void mad_debug_wavefront_wait_limit(int32_t tries);
+
+/* Test hook for the error model (no counterpart in the paper). When on (for
+ * the whole process, from the next mad_profile), every stored entry whose
+ * correlation carries an error bound -- the FP32 recurrence's, or the direct
+ * path's -- is re-evaluated in FP64 as soon as it is selected, so that
+ * mad_length_stats.dq_ratio_max records the largest observed error over
+ * its bound for all of them, not only for the reported entries near
+ * distance 0. Results stay exact; the profile is slower. */
+MAD_API void mad_debug_audit_error_bounds(int32_t on);
 
 /* Human-readable description of the last error on ctx (or of the calling
  * thread's last mad_create* or mad_mth_nn_dist_noalloc error when ctx is

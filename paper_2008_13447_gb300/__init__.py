@@ -33,7 +33,7 @@ ABI_FUNCTIONS = ("mad_create", "mad_create_device", "mad_create_batch", "mad_pro
                  "mad_motifs", "mad_discords", "mad_discords_global", "mad_discords_streamed",
                  "mad_valmp", "mad_matrix_profile", "mad_stats",
                  "mad_mth_nn_dist_noalloc", "mad_motif_sets", "mad_observe", "mad_last_error",
-                 "mad_destroy")
+                 "mad_destroy", "mad_debug_wavefront_wait_limit", "mad_debug_audit_error_bounds")
 
 
 class mad_options(C.Structure):
@@ -61,7 +61,7 @@ class mad_length_stats(C.Structure):
                 ("col_appends", C.c_int64), ("second_pass_rows", C.c_int64), ("direct_rows", C.c_int64),
                 ("band_ms", C.c_double),
                 ("fp32_dq_max", C.c_double), ("skipped", C.c_int64), ("full_profile", C.c_int32),
-                ("reserved2", C.c_int32)]
+                ("reserved2", C.c_int32), ("dq_ratio_max", C.c_double)]
 
 
 class mad_motif_set(C.Structure):
@@ -111,6 +111,10 @@ def library() -> C.CDLL:
         lib.mad_last_error.restype = C.c_char_p
         lib.mad_destroy.argtypes = [P]
         lib.mad_destroy.restype = None
+        lib.mad_debug_wavefront_wait_limit.argtypes = [i32]
+        lib.mad_debug_wavefront_wait_limit.restype = None
+        lib.mad_debug_audit_error_bounds.argtypes = [i32]
+        lib.mad_debug_audit_error_bounds.restype = None
         _lib = lib
     return _lib
 
@@ -265,7 +269,7 @@ def mad_stats(ctx, series, cap=1 << 16):
                  passes=s.passes, band_cells=s.band_cells, launches=s.launches, inserts=s.inserts,
                  col_appends=s.col_appends, second_pass_rows=s.second_pass_rows, direct_rows=s.direct_rows,
                  band_ms=s.band_ms, fp32_dq_max=s.fp32_dq_max, skipped=s.skipped,
-                 full_profile=s.full_profile) for s in out[:min(n.value, cap)]]
+                 full_profile=s.full_profile, dq_ratio_max=s.dq_ratio_max) for s in out[:min(n.value, cap)]]
 
 
 def mad_mth_nn_dist_noalloc(x_ptr, n, cells, m_max, out_ptr, excl=(1, 4), stream=None):
@@ -277,6 +281,16 @@ def mad_mth_nn_dist_noalloc(x_ptr, n, cells, m_max, out_ptr, excl=(1, 4), stream
     st = None if stream is None else C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
     _check(library().mad_mth_nn_dist_noalloc(C.c_void_p(x_ptr), n, _p(c), len(c), m_max, excl[0], excl[1],
                                              C.c_void_p(out_ptr), st), None)
+
+
+def mad_debug_wavefront_wait_limit(tries):
+    """Test hook: tries of the band kernel's wavefront waits (< 0: default)."""
+    library().mad_debug_wavefront_wait_limit(int(tries))
+
+
+def mad_debug_audit_error_bounds(on):
+    """Test hook: re-evaluate every bounded stored entry in FP64 (records dq_ratio_max)."""
+    library().mad_debug_audit_error_bounds(1 if on else 0)
 
 
 def mad_last_error(ctx=None):

@@ -312,9 +312,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *b, unsigned parity)
                  : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ void mbar_wait(uint64_t *b, unsigned parity, int *err)
+__device__ __forceinline__ void mbar_wait(uint64_t *b, unsigned parity, int *err, int limit = WAIT_LIMIT)
 {
-    for (int it = 0; it < WAIT_LIMIT; ++it)
+    for (int it = 0; it < limit; ++it)
         if (mbar_try_wait(b, parity)) return;
     atomicExch(err, 1);
 }
@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(NW * 32, band_min_blocks<T, RPL>()) k_band(con
                 tp = ntop;
                 if (q + 1 < nchunk) ntop = stop[cs + CH + lane];
             } else {
-                mbar_wait(&mfull[w * NSLOT + slot], par, A.err);        // chunk q from warp w-1
+                mbar_wait(&mfull[w * NSLOT + slot], par, A.err, A.wave_limit);   // chunk q from warp w-1
                 const T *bb = bbuf + (w * NSLOT + slot) * CH;
                 const T prev = bb[lane == 0 ? 0 : lane - 1];
                 tp = lane == 0 ? carry : prev;
@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(NW * 32, band_min_blocks<T, RPL>()) k_band(con
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&mempty[w * NSLOT + slot]);   // slot free again
             }
-            if (w < NW - 1) mbar_wait(&mempty[(w + 1) * NSLOT + slot], par ^ 1u, A.err);  // slot free
+            if (w < NW - 1) mbar_wait(&mempty[(w + 1) * NSLOT + slot], par ^ 1u, A.err, A.wave_limit);  // slot free
             __syncwarp();
             T *bout = bbuf + ((w + 1 < NW ? w + 1 : 0) * NSLOT + slot) * CH;
             // does this warp's row range meet the exclusion zone in this chunk?

@@ -112,6 +112,7 @@ __device__ __forceinline__ double dist_err(double d, double dq, int l)
 __device__ __forceinline__ bool needs_refine(const ErrModel &em, double d, double dq, int l)
 {
     if (!(dq > 0.0)) return false;
+    if (em.audit) return true;
     const double tol = em.rel_tol * d + em.abs_coef * sqrt((double)l);
     return dist_err(d, dq, l) > 0.5 * tol;
 }
@@ -184,9 +185,10 @@ __device__ __forceinline__ void corr_ranks(const RowEnts<PM> &r, int (&rk)[PM])
 template <int PM>
 __device__ void refine_reported(const double *x, const float *xh, const float *xl, int64_t i, int l, double mui,
                                 double isdi, const double *mu, const double *isd, const ErrModel &em, RowState st,
-                                int64_t n0, RowEnts<PM> &r, int m, unsigned long long *stat_dq)
+                                int64_t n0, RowEnts<PM> &r, int m, unsigned long long *stat_dq,
+                                unsigned long long *stat_ratio)
 {
-    double dqmax = 0.0;
+    double dqmax = 0.0, ratio = 0.0;
     for (int pass = 0; pass <= PM; ++pass) {
         int rk[PM];
         corr_ranks(r, rk);
@@ -194,7 +196,8 @@ __device__ void refine_reported(const double *x, const float *xh, const float *x
         int32_t j = -1;
         double qold = 0.0;
         for_pm<PM>([&](int a) {
-            if (r.j[a] >= 0 && rk[a] < m && rk[a] < hr && needs_refine(em, dist_from_q(r.q[a], l), r.dq[a], l)) {
+            if (r.j[a] >= 0 && (rk[a] < m || em.audit) && rk[a] < hr &&
+                needs_refine(em, dist_from_q(r.q[a], l), r.dq[a], l)) {
                 hit = a;
                 hr = rk[a];
                 j = r.j[a];
@@ -205,7 +208,7 @@ __device__ void refine_reported(const double *x, const float *xh, const float *x
         double c = 0.0, q = 0.0;
         float dqn = 0.0f;
         bool done = false;
-        if (em.abs_coef > 0.0) {
+        if (em.abs_coef > 0.0 && !em.audit) {
             c = comoment_comp(xh, xl, i, j, l, mui, mu[j]);
             q = clamp_q(c * isdi * isd[j]);
             dqn = (float)DQ_COMP;
@@ -217,6 +220,12 @@ __device__ void refine_reported(const double *x, const float *xh, const float *x
             dqn = 0.0f;
         }
         dqmax = fmax(dqmax, fabs(q - qold));
+        // the entry's observed error over its own bound (<= 1 while the bound
+        // holds); against the compensated value the error is known to within
+        // DQ_COMP, which is added (an upper estimate)
+        float dqb = 0.0f;
+        for_pm<PM>([&](int a) { if (a == hit) dqb = r.dq[a]; });
+        if (dqb > 0.0f) ratio = fmax(ratio, (fabs(q - qold) + (double)dqn) / (double)dqb);
         st.ent_c[(int64_t)hit * n0 + i] = c;
         st.ent_dq[(int64_t)hit * n0 + i] = dqn;
         for_pm<PM>([&](int a) {
@@ -228,6 +237,7 @@ __device__ void refine_reported(const double *x, const float *xh, const float *x
         });
     }
     if (dqmax > 0.0 && stat_dq) atomicMax(stat_dq, (unsigned long long)__double_as_longlong(dqmax));
+    if (ratio > 0.0 && stat_ratio) atomicMax(stat_ratio, (unsigned long long)__double_as_longlong(ratio));
 }
 
 // The row's m-th best matches (first m entries in correlation order), +inf
@@ -379,7 +389,7 @@ __device__ __forceinline__ int extend_row(const ExtArgs<T> &A, int64_t i, double
     }
     if (ok) {
         refine_reported<PM>(A.x, A.xh, A.xl, i, l, A.mu[i], isdi, A.mu, A.isd, A.em, A.st, n0, r, m,
-                            &A.out.stats[3]);
+                            &A.out.stats[3], &A.out.stats[12]);
         dbest = report_row<PM>(A.out, A.vm, n0, i, l, r, cnt, m);
         A.st.flag[i] = ROW_DONE;
         A.thr[i] = T(pinf());
@@ -728,7 +738,7 @@ __global__ void __launch_bounds__(128, row_min_blocks<PM>()) k_merge(MergeArgs<T
         }
     });
     refine_reported<PM>(A.x, A.xh, A.xl, i, l, A.mu[i], isdi, A.mu, A.isd, A.em, A.st, n0, r, A.m_max,
-                        &A.out.stats[3]);
+                        &A.out.stats[3], &A.out.stats[12]);
     report_row<PM>(A.out, A.vm, n0, i, l, r, nb, A.m_max);
     for_pm<PM>([&](int e) {
         if (r.j[e] >= 0) A.st.ent_qb[(int64_t)e * n0 + i] = r.q[e];

@@ -74,6 +74,8 @@ template <typename T> struct BandArgs {
     int *bins;              // [row][nbins] order-preserving ints
     int nbins;
     int *err;               // set to 1 if a bounded wait ran out
+    int wave_limit;         // tries of each wavefront wait (the hand-over between warps) before it
+                            // gives up; the unit-queue waits always use the full limit
     unsigned long long *ninsert;  // top-p list insertions (diagnostic counter)
     unsigned long long *stats;    // this length's counters ([5] units, [6] cells)
     // symmetric form
@@ -103,6 +105,8 @@ struct ErrModel {
     double dq0;
     double rel_tol;         // distance tolerance = rel_tol * d + abs_coef * sqrt(l)
     double abs_coef;
+    int audit;              // test hook: re-evaluate every stored entry that carries a bound, in
+                            // FP64, so that the observed error over its bound is recorded
 };
 void launch_kappa(const double *m2, const int32_t *run, int64_t nl, int l, int R, double *blkmax, float *kappa,
                   float *kappa_max, cudaStream_t s);
@@ -137,7 +141,8 @@ struct LenOut {
     double *nnd;            // [m][n0] m-th best-match distance at the current length
     int32_t *nnj;           // [m][n0] its offset
     unsigned long long *stats;  // this length's counters: [1] certified, [2] recomputed,
-                                //   [3] largest |q_band - q_FP64| seen on re-evaluated entries (bits)
+                                //   [3] largest |q_band - q_FP64| seen on re-evaluated entries (bits),
+                                //   [12] largest such error over the entry's own bound (bits)
 };
 
 template <typename T> struct ExtArgs {

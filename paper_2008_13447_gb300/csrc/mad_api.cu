@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <string>
@@ -31,6 +32,12 @@ using namespace mad;
 namespace {
 
 thread_local std::string g_create_err;
+
+// Tries of the band kernel's wavefront waits (mad_debug_wavefront_wait_limit;
+// negative: the kernel's own limit).
+std::atomic<int> g_wave_limit{-1};
+// mad_debug_audit_error_bounds
+std::atomic<int> g_audit{0};
 
 struct Series {
     int64_t n = 0;
@@ -234,8 +241,10 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
     double *m2blk = dalloc<double>(ctx, s, (n0 + 255) / 256);
     double *isdb[2] = {dalloc<double>(ctx, s, n0), dalloc<double>(ctx, s, n0)};
     float *xh = dalloc<float>(ctx, s, n), *xl = dalloc<float>(ctx, s, n);
-    const ErrModel emb[2] = {{kappab[0], kmaxb[0], Precision<T>::dq0, Precision<T>::rel_tol, Precision<T>::abs_coef},
-                             {kappab[1], kmaxb[1], Precision<T>::dq0, Precision<T>::rel_tol, Precision<T>::abs_coef}};
+    const int audit = g_audit.load() ? 1 : 0;
+    const ErrModel emb[2] = {
+        {kappab[0], kmaxb[0], Precision<T>::dq0, Precision<T>::rel_tol, Precision<T>::abs_coef, audit},
+        {kappab[1], kmaxb[1], Precision<T>::dq0, Precision<T>::rel_tol, Precision<T>::abs_coef, audit}};
     Valmp vm{dalloc<double>(ctx, s, n0), dalloc<double>(ctx, s, n0), dalloc<int32_t>(ctx, s, n0),
              dalloc<int32_t>(ctx, s, n0)};
     int *bins = dalloc<int>(ctx, s, (size_t)n0 * nbins);
@@ -253,8 +262,9 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
     // per-length device counters: [0] rows left for a second pass, [1] certified,
     // [2] recomputed, [3] largest FP32-vs-FP64 correlation gap (bits),
     // [4] top-p insertions, [5] band units, [6] band cells
-    // [10] motif mode: rows left undefined, [11] motif mode: full profile
-    constexpr int NSTAT = 12;
+    // [10] motif mode: rows left undefined, [11] motif mode: full profile,
+    // [12] largest observed error of a re-evaluated entry over its bound (bits)
+    constexpr int NSTAT = 16;
     unsigned long long *dstats = dalloc<unsigned long long>(ctx, s, (size_t)nL * NSTAT);
     // motif mode: per-row bound of non-valid rows; per length the smallest
     // certified distance and non-valid bound (+inf until reduced)
@@ -375,6 +385,10 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
     ba.bins = bins;
     ba.nbins = nbins;
     ba.err = wait_err;
+    {
+        const int wl = g_wave_limit.load();
+        ba.wave_limit = wl < 0 ? (1 << 20) : wl;
+    }
     ba.ckey = ckey;
     ba.cj = cjj;
     ba.ccnt = ccnt;
@@ -742,6 +756,8 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
         q.passes = q.recomputed > 0 ? (h[0] > 0 ? 2 : 1) : 0;
         unsigned long long bits = h[3];
         std::memcpy(&q.fp32_dq_max, &bits, sizeof(double));
+        bits = h[12];
+        std::memcpy(&q.dq_ratio_max, &bits, sizeof(double));
         q.band_cells = (int64_t)h[6];
         q.inserts = (int64_t)h[4];
         q.col_appends = (int64_t)h[7];
@@ -899,6 +915,10 @@ MAD_API mad_status mad_create_device(const void *dev_series, int32_t dtype, int6
     *out = c;
     return MAD_OK;
 }
+
+MAD_API void mad_debug_wavefront_wait_limit(int32_t tries) { g_wave_limit.store(tries); }
+
+MAD_API void mad_debug_audit_error_bounds(int32_t on) { g_audit.store(on ? 1 : 0); }
 
 MAD_API mad_status mad_profile(mad_ctx *ctx, int32_t lmin, int32_t lmax, int32_t p)
 {

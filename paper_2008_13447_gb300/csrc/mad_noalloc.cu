@@ -8,12 +8,12 @@
 // device, which stalls unrelated streams of a latency-bound caller; and some
 // callers must know their memory footprint before they start. The entry
 // point below allocates nothing: its scratch is linked into the library and
-// found once per device.
+// its address is looked up in the calling context.
 //
 // The paper has no counterpart of this function; the quantity it computes is
 // the m-th best-match distance (Def. "m-th best match") at one length, from a full
 // FP64 distance profile (Eq. DIST, two-pass window statistics).
-#include <mutex>
+#include <climits>
 #include <string>
 
 #include "kernels.cuh"
@@ -41,21 +41,20 @@ constexpr size_t SCRATCH_BYTES = CELLS_BYTES + SD_BYTES + SJ_BYTES;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
 constexpr int MAX_DEVICES = 64;
-std::mutex g_setup_mu;
-unsigned char *g_scratch_ptr[MAX_DEVICES] = {};
 
-// Address of this device's scratch; looked up on the first call made with
-// `dev` current, then cached.
-cudaError_t scratch_for(int dev, unsigned char **out)
+// Device address of the scratch in the current context. Looked up on every
+// call rather than cached: after cudaDeviceReset (or in another context on
+// the same device) the module is loaded again, possibly at another address,
+// and a cached pointer would then point at freed memory. Once the module is
+// loaded in the context the lookup allocates nothing; the first call in a
+// context loads it, which is set-up work (make that first call before any
+// stream capture begins).
+cudaError_t scratch_address(unsigned char **out)
 {
-    std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
-    }
-    *out = g_scratch_ptr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    *out = static_cast<unsigned char *>(p);
     return cudaSuccess;
 }
 
@@ -89,6 +88,8 @@ MAD_API mad_status mad_mth_nn_dist_noalloc(const double *x, int64_t n, const int
     if (ncells == 0) return MAD_OK;
     if (!x || !cells || !out) return fail(MAD_EINVAL, "x, cells and out must not be NULL");
     if (n < 4) return fail(MAD_EINVAL, "series needs at least 4 samples");
+    // offsets and partners are 32-bit in the re-check kernels
+    if (n - 1 > (int64_t)INT32_MAX) return fail(MAD_EINVAL, "series longer than 2^31 samples");
     if (m_max < 1 || m_max > MAXP) return fail(MAD_EINVAL, "m_max must be in [1, 64]");
     if (excl_num < 0 || excl_den < 1) return fail(MAD_EINVAL, "exclusion fraction needs num >= 0 and den >= 1");
     if ((int64_t)ncells * m_max > MAD_NOALLOC_MAX_SLOTS)
@@ -114,7 +115,7 @@ MAD_API mad_status mad_mth_nn_dist_noalloc(const double *x, int64_t n, const int
     if (!is_device_pointer(x, dev) || !is_device_pointer(out, dev))
         return fail(MAD_EINVAL, "x and out must be device memory of the current device");
     unsigned char *base = nullptr;
-    e = scratch_for(dev, &base);
+    e = scratch_address(&base);
     if (e != cudaSuccess) return fail(MAD_ECUDA, std::string("cudaGetSymbolAddress(): ") + cudaGetErrorString(e));
 
     // No part of the scratch has to start at zero: the cells region is
