@@ -59,15 +59,23 @@ typedef enum {
     MAD_EINTERNAL = 6   /* an internal consistency check failed */
 } mad_status;
 
-/* Arithmetic of the dominant matrix-profile kernel.
+/* Arithmetic of the matrix-profile kernels.
  *   MAD_FP64: FP64 everywhere (the plain reference path on the GPU).
  *   MAD_FP32: the O(n^2) diagonal (QT) recurrence in FP32 on centred
- *             co-moments, re-seeded from direct dot products every band of
- *             rows; window statistics, the per-row stored entries, the
- *             length extension, the bound test and the reported distances
- *             of the stored entries stay FP64. Distances agree with FP64
- *             within 1e-4 * sqrt(l). */
-typedef enum { MAD_FP64 = 0, MAD_FP32 = 1 } mad_precision;
+ *             co-moments, re-seeded from FP64 dot products every band of
+ *             rows; rows recomputed on their own (the direct path) use FP32
+ *             dot products. Window statistics, the per-row stored entries,
+ *             the length extension, the bound test and the reported
+ *             distances stay FP64 (or compensated FP32, within the error the
+ *             library bounds). Every kept correlation carries a proven error
+ *             bound; distances agree with FP64 within 1e-4 * sqrt(l).
+ *   MAD_SPLIT_TC: as MAD_FP32, but the direct path runs on the tensor cores
+ *             (tcgen05): each block of co-moments is a dense product of the
+ *             rows' normalised windows and the shifted series (Hankel form),
+ *             both split into FP16 hi + lo pairs (hi*hi + hi*lo + lo*hi),
+ *             accumulated in FP32; more of the rows to recompute take that
+ *             path. Same guarantees as MAD_FP32. */
+typedef enum { MAD_FP64 = 0, MAD_FP32 = 1, MAD_SPLIT_TC = 2 } mad_precision;
 
 typedef struct mad_options {
     int32_t excl_num;       /* exclusion zone numerator   (0 with excl_den 0: 1/4) */
@@ -161,6 +169,12 @@ typedef struct {
                                divided by the error bound the library kept for it (the bound holds
                                while this is <= 1; against a compensated re-evaluation the
                                observation is an upper estimate); 0 when nothing was re-evaluated */
+    double direct_ms;       /* device time of the direct-path recompute launches at this length */
+    double rows_ms;         /* device time of the per-row launches (extension, bound test, merge of
+                               the recomputed rows' candidates) at this length */
+    int32_t graph;          /* 1 if this profile ran as a replayed CUDA graph (a repeat of the
+                               previous profile's shape, see mad_profile) */
+    int32_t reserved3;
 } mad_length_stats;
 
 /* Create a context for one series copied from host memory (FP64, n values).
@@ -183,7 +197,13 @@ MAD_API mad_status mad_create_batch(const double *const *series, const int64_t *
  * p entries per row (Algorithm 1 VALMOD with the Top-k m-th discord table
  * of Algorithm 7). Requires 2 <= lmin <= lmax, 1 <= p <= 64, m_max <= p, and
  * n - lmax + 1 > 2 E(lmax) + 2 (every window keeps a non-trivial neighbour).
- * A context may be profiled again (results are replaced). */
+ * A context may be profiled again (results are replaced). Device memory: the
+ * first profile allocates the workspace; a profile with the same lmin, lmax,
+ * p and options reuses it (no allocation), and from the second such profile
+ * on the whole launch sequence is captured once into a CUDA graph and
+ * replayed (mad_set_graphs(0) turns that off). The series' device data is
+ * read at every profile, so new values written to a caller-owned series
+ * between profiles are used. */
 MAD_API mad_status mad_profile(mad_ctx *ctx, int32_t lmin, int32_t lmax, int32_t p);
 
 /* Batched form: lmin[s], lmax[s] per series of a mad_create_batch context. */
@@ -352,6 +372,11 @@ MAD_API void mad_debug_wavefront_wait_limit(int32_t tries);
  * its bound for all of them, not only for the reported entries near
  * distance 0. Results stay exact; the profile is slower. */
 MAD_API void mad_debug_audit_error_bounds(int32_t on);
+
+/* Process-wide switch for the CUDA-graph replay of repeated profiles
+ * (default on). Off: every profile launches its kernels one by one (the
+ * workspace is still reused). Takes effect at the next mad_profile. */
+MAD_API void mad_set_graphs(int32_t on);
 
 /* Human-readable description of the last error on ctx (or of the calling
  * thread's last mad_create* or mad_mth_nn_dist_noalloc error when ctx is

@@ -25,7 +25,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libmad.so")
 
 MAD_OK, MAD_EINVAL, MAD_ENOMEM, MAD_ECUDA, MAD_ESTATE, MAD_ETIMEOUT, MAD_EINTERNAL = range(7)
-MAD_FP64, MAD_FP32 = 0, 1
+MAD_FP64, MAD_FP32, MAD_SPLIT_TC = 0, 1, 2
 MAD_NOALLOC_MAX_SLOTS = 1024
 STATUS_NAMES = {0: "MAD_OK", 1: "MAD_EINVAL", 2: "MAD_ENOMEM", 3: "MAD_ECUDA", 4: "MAD_ESTATE",
                 5: "MAD_ETIMEOUT", 6: "MAD_EINTERNAL"}
@@ -33,7 +33,8 @@ ABI_FUNCTIONS = ("mad_create", "mad_create_device", "mad_create_batch", "mad_pro
                  "mad_motifs", "mad_discords", "mad_discords_global", "mad_discords_streamed",
                  "mad_valmp", "mad_matrix_profile", "mad_stats",
                  "mad_mth_nn_dist_noalloc", "mad_motif_sets", "mad_observe", "mad_last_error",
-                 "mad_destroy", "mad_debug_wavefront_wait_limit", "mad_debug_audit_error_bounds")
+                 "mad_destroy", "mad_debug_wavefront_wait_limit", "mad_debug_audit_error_bounds",
+                 "mad_set_graphs")
 
 
 class mad_options(C.Structure):
@@ -61,7 +62,8 @@ class mad_length_stats(C.Structure):
                 ("col_appends", C.c_int64), ("second_pass_rows", C.c_int64), ("direct_rows", C.c_int64),
                 ("band_ms", C.c_double),
                 ("fp32_dq_max", C.c_double), ("skipped", C.c_int64), ("full_profile", C.c_int32),
-                ("reserved2", C.c_int32), ("dq_ratio_max", C.c_double)]
+                ("reserved2", C.c_int32), ("dq_ratio_max", C.c_double), ("direct_ms", C.c_double),
+                ("rows_ms", C.c_double), ("graph", C.c_int32), ("reserved3", C.c_int32)]
 
 
 class mad_motif_set(C.Structure):
@@ -115,6 +117,8 @@ def library() -> C.CDLL:
         lib.mad_debug_wavefront_wait_limit.restype = None
         lib.mad_debug_audit_error_bounds.argtypes = [i32]
         lib.mad_debug_audit_error_bounds.restype = None
+        lib.mad_set_graphs.argtypes = [i32]
+        lib.mad_set_graphs.restype = None
         _lib = lib
     return _lib
 
@@ -269,7 +273,8 @@ def mad_stats(ctx, series, cap=1 << 16):
                  passes=s.passes, band_cells=s.band_cells, launches=s.launches, inserts=s.inserts,
                  col_appends=s.col_appends, second_pass_rows=s.second_pass_rows, direct_rows=s.direct_rows,
                  band_ms=s.band_ms, fp32_dq_max=s.fp32_dq_max, skipped=s.skipped,
-                 full_profile=s.full_profile, dq_ratio_max=s.dq_ratio_max) for s in out[:min(n.value, cap)]]
+                 full_profile=s.full_profile, dq_ratio_max=s.dq_ratio_max, direct_ms=s.direct_ms,
+                 rows_ms=s.rows_ms, graph=s.graph) for s in out[:min(n.value, cap)]]
 
 
 def mad_mth_nn_dist_noalloc(x_ptr, n, cells, m_max, out_ptr, excl=(1, 4), stream=None):
@@ -291,6 +296,11 @@ def mad_debug_wavefront_wait_limit(tries):
 def mad_debug_audit_error_bounds(on):
     """Test hook: re-evaluate every bounded stored entry in FP64 (records dq_ratio_max)."""
     library().mad_debug_audit_error_bounds(1 if on else 0)
+
+
+def mad_set_graphs(on):
+    """CUDA-graph replay of repeated profiles (default on)."""
+    library().mad_set_graphs(1 if on else 0)
 
 
 def mad_last_error(ctx=None):

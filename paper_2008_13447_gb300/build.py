@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmad.so")
-SOURCES = ["k_stats.cu", "k_band_f32.cu", "k_band_f64.cu", "k_rows.cu", "k_direct.cu", "k_readout.cu", "mad_api.cu", "mad_noalloc.cu", "k_sets.cu"]
+SOURCES = ["k_stats.cu", "k_band_f32.cu", "k_band_f64.cu", "k_rows.cu", "k_direct.cu", "k_direct_tc.cu", "k_readout.cu", "mad_api.cu", "mad_noalloc.cu", "k_sets.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
          "-I", os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"]

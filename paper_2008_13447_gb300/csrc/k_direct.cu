@@ -12,6 +12,15 @@
 // like the correlation. Each block takes DR rows x DCOLS columns; each thread
 // keeps its rows' best p keys over its columns, and the block reduces them
 // to one list of p per row and column block.
+//
+// Error bound of a key (in correlation units), written with every kept
+// entry: the sum of l products in T has error <= (l + 2) u sum_t |a_t y_t|
+// (each FMA rounds once, each input once), with sum_t |a_t y_t| <=
+// sqrt(M2_r (M2_j + l (mu_j - s)^2)) by Cauchy-Schwarz; the key's own
+// rounding adds u:
+//     dq_j = 1.5 ((l + 3) u sqrt(1 + l (mu_j - s)^2 / M2_j) + u).
+// A column is a candidate when key + dq_j sqrt(M2_r) beats the row's
+// threshold.
 #include "kernels.cuh"
 
 namespace mad {
@@ -24,18 +33,24 @@ constexpr int DCOLS = DTHREADS * DCPT;
 __device__ __forceinline__ double d_pinf() { return __longlong_as_double(0x7ff0000000000000LL); }
 
 template <typename T>
-__device__ __forceinline__ void local_insert(T *K, int32_t *J, int &cnt, int p, T key, int32_t j)
+__device__ __forceinline__ void local_insert(T *K, int32_t *J, float *D, int &cnt, int p, T key, int32_t j, float dq)
 {
     if (cnt == p && !(key > K[p - 1] || (key == K[p - 1] && j < J[p - 1]))) return;
     int b = cnt < p ? cnt++ : p - 1;
     while (b > 0 && (K[b - 1] < key || (K[b - 1] == key && J[b - 1] > j))) {
         K[b] = K[b - 1];
         J[b] = J[b - 1];
+        D[b] = D[b - 1];
         --b;
     }
     K[b] = key;
     J[b] = j;
+    D[b] = dq;
 }
+
+template <typename T> struct Unit;
+template <> struct Unit<float> { static constexpr double u = 0x1p-24; };
+template <> struct Unit<double> { static constexpr double u = 0x1p-53; };
 
 template <typename T>
 __global__ void __launch_bounds__(DTHREADS) k_direct(DirectArgs<T> A)
@@ -78,12 +93,17 @@ __global__ void __launch_bounds__(DTHREADS) k_direct(DirectArgs<T> A)
 
     T K[DR][MAXP];
     int32_t J[DR][MAXP];
+    float D[DR][MAXP];
     int cnt[DR];
     T th[DR];
+    double sqr[DR];
     for (int k = 0; k < DR; ++k) {
         cnt[k] = 0;
         th[k] = rr[k] >= 0 ? A.thr[rr[k]] : T(d_pinf());
+        const double ir = rr[k] >= 0 ? (double)A.col[rr[k]].inv : 0.0;
+        sqr[k] = ir > 0.0 ? 1.0001 / ir : 0.0;
     }
+    float dqmax = 0.0f;
     for (int u = 0; u < DCPT; ++u) {
         const int64_t jl = threadIdx.x + (int64_t)u * DTHREADS;
         const int64_t j = cb0 + jl;
@@ -98,17 +118,23 @@ __global__ void __launch_bounds__(DTHREADS) k_direct(DirectArgs<T> A)
         }
         const Col<T> cj = A.col[j];
         const double dmu = A.mu[j] - shift;
+        const double ij = (double)cj.inv;
+        const float dq = (float)(1.5 * ((l + 3.0) * Unit<T>::u * sqrt(1.0 + (double)l * dmu * dmu * ij * ij) +
+                                        Unit<T>::u));
+        dqmax = fmaxf(dqmax, dq);
         for (int k = 0; k < DR; ++k) {
             const int64_t r = rr[k];
             if (r < 0 || !nontrivial(r, j, A.E)) continue;
             const double c = (double)acc[k] - asum[k] * dmu;
-            const T key = T(c * (double)cj.inv);
-            if (key > th[k]) local_insert<T>(K[k], J[k], cnt[k], A.p, key, (int32_t)j);
+            const T key = T(c * ij);
+            if ((double)key + dq * sqr[k] > (double)th[k])
+                local_insert<T>(K[k], J[k], D[k], cnt[k], A.p, key, (int32_t)j, dq);
         }
     }
     // block-wide: p rounds of "largest head among the threads" per row
     __shared__ T hk[DTHREADS / 32];
     __shared__ int32_t hj[DTHREADS / 32];
+    __shared__ float hd[DTHREADS / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int k = 0; k < DR; ++k) {
         if (rr[k] < 0) break;
@@ -118,37 +144,44 @@ __global__ void __launch_bounds__(DTHREADS) k_direct(DirectArgs<T> A)
         for (int e = 0; e < A.p; ++e) {
             T v = head < cnt[k] ? K[k][head] : T(-d_pinf());
             int32_t jj = head < cnt[k] ? J[k][head] : INT32_MAX;
+            float dd = head < cnt[k] ? D[k][head] : 0.0f;
             for (int o = 16; o > 0; o >>= 1) {
                 const T v2 = __shfl_xor_sync(0xffffffffu, v, o);
                 const int32_t j2 = __shfl_xor_sync(0xffffffffu, jj, o);
-                if (v2 > v || (v2 == v && j2 < jj)) { v = v2; jj = j2; }
+                const float d2 = __shfl_xor_sync(0xffffffffu, dd, o);
+                if (v2 > v || (v2 == v && j2 < jj)) { v = v2; jj = j2; dd = d2; }
             }
-            if (lane == 0) { hk[wid] = v; hj[wid] = jj; }
+            if (lane == 0) { hk[wid] = v; hj[wid] = jj; hd[wid] = dd; }
             __syncthreads();
             if (wid == 0) {
                 v = lane < DTHREADS / 32 ? hk[lane] : T(-d_pinf());
                 jj = lane < DTHREADS / 32 ? hj[lane] : INT32_MAX;
+                dd = lane < DTHREADS / 32 ? hd[lane] : 0.0f;
                 for (int o = 16; o > 0; o >>= 1) {
                     const T v2 = __shfl_xor_sync(0xffffffffu, v, o);
                     const int32_t j2 = __shfl_xor_sync(0xffffffffu, jj, o);
-                    if (v2 > v || (v2 == v && j2 < jj)) { v = v2; jj = j2; }
+                    const float d2 = __shfl_xor_sync(0xffffffffu, dd, o);
+                    if (v2 > v || (v2 == v && j2 < jj)) { v = v2; jj = j2; dd = d2; }
                 }
-                if (lane == 0) { hk[0] = v; hj[0] = jj; }
+                if (lane == 0) { hk[0] = v; hj[0] = jj; hd[0] = dd; }
             }
             __syncthreads();
             v = hk[0];
             jj = hj[0];
+            dd = hd[0];
             __syncthreads();
             if (jj == INT32_MAX) break;
             if (head < cnt[k] && J[k][head] == jj) ++head;
             if (threadIdx.x == 0) {
                 A.okey[slot * A.p + e] = v;
                 A.oj[slot * A.p + e] = jj;
+                A.odq[slot * A.p + e] = dd;
             }
             ++outc;
         }
         if (threadIdx.x == 0) A.ocnt[slot] = outc;
     }
+    if (dqmax > 0.0f) atomicMax(reinterpret_cast<int *>(A.dq_max), __float_as_int(dqmax));
     }
 }
 

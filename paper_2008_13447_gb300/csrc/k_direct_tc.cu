@@ -1,0 +1,439 @@
+// k_direct_tc.cu -- recompute of listed rows' full distance profiles on the
+// 5th-generation tensor cores (tcgen05): Algorithm 4's SlidingDotProduct for
+// the non-valid rows and Algorithm 10's recompute loop, for rows that are too
+// few in their band for the diagonal band kernel to pay off.
+//
+// A block of co-moments is a dense product of two Hankel-shaped matrices:
+//     acc(r, j) = sum_t A_r[t] B_j[t],
+//     A_r[t] = S_a (x[r+t] - mu_r) / sqrt(M2_r)          (row r, centred, unit norm)
+//     B_j[t] = S_b (x[j+t] - s)                          (column j, one shift s per tile)
+// so that C(r, j) sqrt(...) follows from acc by a rank-one correction:
+//     q(r, j) = (acc - S_b (mu_j - s) sum_t A_r[t]) / sqrt(M2_j) / (S_a S_b),
+// the correlation of Eq. DIST. Both operands are split into FP16 pairs
+// (hi + lo, about 22 significant bits) and the product is taken as
+// hi*hi + hi*lo + lo*hi, accumulated in FP32 in tensor memory (TMEM).
+//
+// Per work item (128 listed rows x one block of 4096 columns): for each tile
+// of 256 columns and each chunk of 64 lags, the row operand is copied into
+// shared memory by the bulk-copy engine (cp.async.bulk, from an image the
+// prep kernel wrote in the swizzled layout), the column operand is expanded
+// from the series by the block's threads, and one thread issues 4 x 3 MMAs
+// (M = 128, N = 256, K = 16) into one TMEM accumulator. Then 4 warps read the
+// accumulator back (tcgen05.ld, one row per thread), form the correlation and
+// its error bound, and keep each row's p best keys over the column block.
+//
+// Error bound of a kept correlation (in q units), from the arithmetic above:
+// the pair representation (|a - hi - lo| <= 2^-22 |a| per operand, the
+// omitted lo*lo term <= 2^-22 |a b|), the FP32 accumulation of 3K products
+// (<= 3K 2^-24 sum|A B|, K the padded lag count), and the FP32 correction and
+// scaling, with sum_t |A_r[t] B_j[t]| <= S_a S_b sqrt(M2_j + l (mu_j - s)^2)
+// (Cauchy-Schwarz):
+//     dq_j = 1.5 ((3 2^-22 + (3K + 4) 2^-24) f_j + 2^-23),
+//     f_j  = sqrt(1 + l (mu_j - s)^2 / M2_j).
+// A candidate is kept when q + dq_j could beat the row's threshold, and
+// carries dq_j to the merge.
+#include <cuda_fp16.h>
+
+#include "kernels.cuh"
+
+namespace mad {
+namespace {
+
+constexpr int TC_M = 128;          // rows per tile (TMEM lanes)
+constexpr int TC_N = 256;          // columns per MMA tile (TMEM columns of the accumulator)
+constexpr int TC_KC = 64;          // lags per chunk (one 128-byte swizzle atom of FP16)
+constexpr int TC_THREADS = 256;
+constexpr int TC_COLS = 4096;      // columns per work item (same blocks as the direct kernel)
+constexpr float TC_SA = 256.0f;    // scale of the row operand (|A| <= 256)
+constexpr int TC_WAIT = 1 << 22;   // tries of a bounded mbarrier wait
+constexpr int A_TILE_BYTES = TC_M * TC_KC * 2;   // 16 KB, one of hi / lo
+constexpr int B_TILE_BYTES = TC_N * TC_KC * 2;   // 32 KB
+constexpr int SHIFT_LEN = 312;     // halves per shifted copy of the column values
+
+__device__ __forceinline__ unsigned su32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Byte offset of element (row m, lag k) in a K-major 128-byte-swizzled tile
+// (rows of 64 FP16 at 128 B, the 16-byte chunk index XOR-ed with m mod 8).
+__host__ __device__ __forceinline__ int swz(int m, int k)
+{
+    return m * 128 + ((((k >> 3) ^ (m & 7)) & 7) << 4) + (k & 7) * 2;
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, stride between
+// 8-row groups (1024 B), descriptor version 1, 128-byte swizzle.
+__device__ __forceinline__ uint64_t sdesc(unsigned addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;                 // leading byte offset (unused with this swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+    d |= (uint64_t)1 << 46;                 // version
+    d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor of kind::f16: FP16 A and B, FP32 D, both K-major,
+// N = 256, M = 128.
+constexpr uint32_t IDESC = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                           ((uint32_t)(TC_M >> 4) << 24);
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(su32(b)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// Bounded wait; false (and the error word set) if the phase never completed.
+__device__ __forceinline__ bool mbar_wait_b(uint64_t *b, unsigned parity, int *err)
+{
+    for (int it = 0; it < TC_WAIT; ++it)
+        if (mbar_try(b, parity)) return true;
+    atomicExch(err, 2);
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     su32(dst)),
+                 "l"(src), "r"(bytes), "r"(su32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+                 "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+// 32 consecutive accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                 "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                 "[%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+}
+
+__device__ __forceinline__ void split_half(float v, __half &hi, __half &lo)
+{
+    hi = __float2half_rn(v);
+    lo = __float2half_rn(v - __half2float(hi));
+}
+
+// Row operand images of the listed rows at length l, in the layout the MMA
+// reads: [row tile][lag chunk][hi, lo][128 rows x 64 lags, swizzled], zero
+// past the row's length and past the last listed row; plus per row the sum
+// of its represented values (for the rank-one correction) and sqrt(M2).
+__global__ void k_tc_rows(TcArgs A)
+{
+    const int nrows = *A.nrows;
+    const int l = A.l;
+    const int nkc = A.nkc;
+    const int64_t ntile = (nrows + TC_M - 1) / TC_M;
+    __shared__ float red[TC_THREADS / 32];
+    for (int64_t pos = blockIdx.x; pos < ntile * TC_M; pos += gridDim.x) {
+        const int rt = (int)(pos / TC_M), m = (int)(pos % TC_M);
+        const bool live = pos < nrows;
+        const int64_t r = live ? A.rows[pos] : 0;
+        const double mu = live ? A.mu[r] : 0.0;
+        const double isd = live ? A.isd[r] : 0.0;
+        float part = 0.0f;
+        for (int k = threadIdx.x; k < nkc * TC_KC; k += blockDim.x) {
+            float v = 0.0f;
+            if (live && k < l) v = (float)((A.x[r + k] - mu) * isd) * TC_SA;
+            __half hi, lo;
+            split_half(v, hi, lo);
+            part += __half2float(hi) + __half2float(lo);
+            const int kc = k / TC_KC, kk = k % TC_KC;
+            unsigned char *base = A.aimg + ((size_t)(rt * nkc + kc) * 2) * A_TILE_BYTES;
+            *reinterpret_cast<__half *>(base + swz(m, kk)) = hi;
+            *reinterpret_cast<__half *>(base + A_TILE_BYTES + swz(m, kk)) = lo;
+        }
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float s = 0.0f;
+            for (int w = 0; w < TC_THREADS / 32; ++w) s += red[w];
+            A.asum[pos] = s;
+            A.sqm2[pos] = (live && isd > 0.0) ? (float)(1.0 / isd) : 0.0f;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void list_insert(T *K, int32_t *J, float *D, int &cnt, int p, T key, int32_t j, float dq)
+{
+    if (cnt == p && !(key > K[p - 1])) return;
+    int b = cnt < p ? cnt++ : p - 1;
+    while (b > 0 && K[b - 1] < key) {
+        K[b] = K[b - 1];
+        J[b] = J[b - 1];
+        D[b] = D[b - 1];
+        --b;
+    }
+    K[b] = key;
+    J[b] = j;
+    D[b] = dq;
+}
+
+struct __align__(16) ColC { float c, g, dq, pad; };
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_direct_tc(TcArgs A)
+{
+    const int nrows = *A.nrows;
+    if (nrows <= 0) return;
+    const int l = A.l;
+    const int nkc = A.nkc;
+    const int p = A.p;
+    const int rtiles = (nrows + TC_M - 1) / TC_M;
+    const int64_t items = (int64_t)rtiles * A.nblk;
+    if (blockIdx.x >= items) return;
+
+    extern __shared__ __align__(1024) unsigned char sm_raw[];
+    // 1024-byte aligned tiles first: A hi/lo (16 KB each), B hi/lo (32 KB each)
+    unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)sm_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *sa = sm;                              // [2][A_TILE_BYTES]
+    unsigned char *sb = sa + 2 * A_TILE_BYTES;           // [2][B_TILE_BYTES]
+    __half *shift = reinterpret_cast<__half *>(sb + 2 * B_TILE_BYTES);   // [2][8][SHIFT_LEN]
+    ColC *cc = reinterpret_cast<ColC *>(shift + 2 * 8 * SHIFT_LEN);      // [TC_N]
+    float *lk = reinterpret_cast<float *>(cc + TC_N);                   // [TC_M][p]
+    int32_t *lj = reinterpret_cast<int32_t *>(lk + TC_M * p);
+    float *ld = reinterpret_cast<float *>(lj + TC_M * p);
+    __shared__ __align__(8) uint64_t bar_a, bar_mma;
+    __shared__ uint32_t tmem_base;
+    __shared__ float red[TC_THREADS / 32];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        mbar_init(&bar_a, 1);
+        mbar_init(&bar_mma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                     "r"(TC_N)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    unsigned pa = 0, pm = 0;           // mbarrier phases
+    bool ok = true;
+    float dqmax = 0.0f;
+
+    for (int64_t item = blockIdx.x; item < items && ok; item += gridDim.x) {
+        const int rt = (int)(item / A.nblk);
+        const int cb = (int)(item % A.nblk);
+        const int64_t cb0 = (int64_t)cb * TC_COLS;
+        // this thread's row (epilogue warps 0..3: TMEM lane = tid)
+        const int64_t pos = (int64_t)rt * TC_M + tid;
+        const bool erow = tid < TC_M && pos < nrows;
+        const int64_t r = erow ? A.rows[pos] : -1;
+        const float asum = erow ? A.asum[pos] : 0.0f;
+        const float sq = erow ? A.sqm2[pos] : 0.0f;
+        const float th = erow ? (float)A.thr[r] : 0.0f;
+        int cnt = 0;
+        for (int st0 = 0; st0 < TC_COLS / TC_N && ok; ++st0) {
+            const int64_t j0 = cb0 + (int64_t)st0 * TC_N;
+            if (j0 >= A.nl) break;
+            // ---- column constants of this tile: shift s, scale S_b, correction,
+            // normaliser and error bound per column
+            const int64_t jm = j0 + TC_N / 2 < A.nl ? j0 + TC_N / 2 : A.nl - 1;
+            const double s = A.mu[jm];
+            float spread = 0.0f;
+            {
+                const int64_t j = j0 + tid;
+                if (j < A.nl) {
+                    const double m2 = A.m2[j];
+                    spread = (float)(sqrt(m2 > 0.0 ? m2 : 0.0) + fabs(A.mu[j] - s));
+                }
+                for (int o = 16; o > 0; o >>= 1) spread = fmaxf(spread, __shfl_xor_sync(0xffffffffu, spread, o));
+                if (lane == 0) red[warp] = spread;
+            }
+            __syncthreads();
+            float mx = 0.0f;
+            for (int w = 0; w < TC_THREADS / 32; ++w) mx = fmaxf(mx, red[w]);
+            // S_b: a power of two with max |B| <= 256
+            const float Sb = mx > 0.0f ? exp2f(floorf(log2f(255.0f / mx))) : 1.0f;
+            {
+                const int64_t j = j0 + tid;
+                ColC c{0.0f, 0.0f, 0.0f, 0.0f};
+                if (j < A.nl) {
+                    const double isd = A.isd[j];
+                    const double dm = A.mu[j] - s;
+                    c.c = (float)(Sb * dm);
+                    c.g = (float)(isd / ((double)TC_SA * Sb));
+                    const double f = sqrt(1.0 + (double)l * dm * dm * isd * isd);
+                    const double K = (double)nkc * TC_KC;
+                    c.dq = (float)(1.5 * ((3.0 * 0x1p-22 + (3.0 * K + 4.0) * 0x1p-24) * f + 0x1p-23));
+                    dqmax = fmaxf(dqmax, c.dq);
+                }
+                cc[tid] = c;
+            }
+            // ---- lag chunks: stage A, build B, 12 MMAs
+            for (int kc = 0; kc < nkc; ++kc) {
+                if (tid == 0) {
+                    mbar_expect_tx(&bar_a, 2 * A_TILE_BYTES);
+                    const unsigned char *src = A.aimg + ((size_t)(rt * nkc + kc) * 2) * A_TILE_BYTES;
+                    bulk_g2s(sa, src, A_TILE_BYTES, &bar_a);
+                    bulk_g2s(sa + A_TILE_BYTES, src + A_TILE_BYTES, A_TILE_BYTES, &bar_a);
+                }
+                // column values v[i] = S_b (x[g0 + i] - s), i in [0, 320), as FP16
+                // pairs in eight copies shifted by 0..7 (every row of the tile is
+                // then an aligned 16-byte copy)
+                const int64_t g0 = j0 + (int64_t)kc * TC_KC;
+                for (int e = tid; e < 8 * SHIFT_LEN; e += TC_THREADS) {
+                    const int sft = e / SHIFT_LEN, i = e % SHIFT_LEN;
+                    const int64_t g = g0 + i + sft;
+                    const float v = g < A.n ? (float)(A.x[g] - s) * Sb : 0.0f;
+                    __half hi, lo;
+                    split_half(v, hi, lo);
+                    shift[sft * SHIFT_LEN + i] = hi;
+                    shift[(8 + sft) * SHIFT_LEN + i] = lo;
+                }
+                __syncthreads();
+                for (int e = tid; e < 2 * TC_N * 8; e += TC_THREADS) {
+                    const int hl = e / (TC_N * 8), rem = e % (TC_N * 8);
+                    const int nn = rem / 8, c = rem % 8;
+                    const int sft = nn & 7;
+                    const uint4 v = *reinterpret_cast<const uint4 *>(shift + (hl * 8 + sft) * SHIFT_LEN +
+                                                                     (nn - sft) + 8 * c);
+                    *reinterpret_cast<uint4 *>(sb + hl * B_TILE_BYTES + swz(nn, 8 * c)) = v;
+                }
+                fence_async_smem();
+                tc_fence_before();
+                __syncthreads();
+                if (tid == TC_M) {
+                    tc_fence_after();
+                    if (!mbar_wait_b(&bar_a, pa, A.err)) ok = false;
+                    if (ok) {
+                        const unsigned a0 = su32(sa), b0 = su32(sb);
+#pragma unroll
+                        for (int ks = 0; ks < TC_KC / 16; ++ks) {
+                            const uint64_t ah = sdesc(a0 + ks * 32), al = sdesc(a0 + A_TILE_BYTES + ks * 32);
+                            const uint64_t bh = sdesc(b0 + ks * 32), bl = sdesc(b0 + B_TILE_BYTES + ks * 32);
+                            tc_mma(tmem, ah, bh, (kc > 0 || ks > 0) ? 1u : 0u);
+                            tc_mma(tmem, ah, bl, 1u);
+                            tc_mma(tmem, al, bh, 1u);
+                        }
+                    }
+                    tc_commit(&bar_mma);
+                }
+                pa ^= 1u;
+                // the MMAs have read the tiles (and written the accumulator)
+                // before anything is overwritten
+                if (!mbar_wait_b(&bar_mma, pm, A.err)) ok = false;
+                pm ^= 1u;
+                tc_fence_after();
+                ok = __syncthreads_and(ok);
+                if (!ok) break;
+            }
+            if (!ok) break;
+            // ---- epilogue: one row per thread of warps 0..3, 32 columns at a time
+            if (tid < TC_M) {
+                for (int c0 = 0; c0 < TC_N; c0 += 32) {
+                    float v[32];
+                    __syncwarp();
+                    tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+                    if (!erow) continue;
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) {
+                        const int64_t j = j0 + c0 + c;
+                        const ColC k = cc[c0 + c];
+                        const float q = fmaf(-k.c, asum, v[c]) * k.g;
+                        if ((q + k.dq) * sq > th && j < A.nl && nontrivial(r, j, A.E))
+                            list_insert<float>(lk + tid * p, lj + tid * p, ld + tid * p, cnt, p, q * sq, (int32_t)j,
+                                               k.dq);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+        }
+        // ---- this item's per-row lists
+        if (erow && ok) {
+            const int64_t slot = pos * A.nblk + cb;
+            for (int e = 0; e < cnt; ++e) {
+                A.okey[slot * p + e] = lk[tid * p + e];
+                A.oj[slot * p + e] = lj[tid * p + e];
+                A.odq[slot * p + e] = ld[tid * p + e];
+            }
+            A.ocnt[slot] = cnt;
+        }
+        __syncthreads();
+    }
+    if (dqmax > 0.0f) atomicMax(reinterpret_cast<int *>(A.dq_max), __float_as_int(dqmax));
+    // after a wait that ran out, give the MMAs in flight one more bounded
+    // wait before the accumulator is freed
+    if (!ok && tid == TC_M) mbar_wait_b(&bar_mma, pm ^ 1u, A.err);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N) : "memory");
+    }
+}
+
+}  // namespace
+
+size_t tc_smem_bytes(int p)
+{
+    return 1024 + 2 * (size_t)A_TILE_BYTES + 2 * (size_t)B_TILE_BYTES + 2 * 8 * SHIFT_LEN * sizeof(__half) +
+           TC_N * sizeof(ColC) + (size_t)TC_M * p * (sizeof(float) + sizeof(int32_t) + sizeof(float));
+}
+
+size_t tc_aimg_bytes(int64_t max_rows, int lmax)
+{
+    const int64_t tiles = (max_rows + TC_M - 1) / TC_M;
+    const int64_t nkc = (lmax + TC_KC - 1) / TC_KC;
+    return (size_t)tiles * nkc * 2 * A_TILE_BYTES;
+}
+
+int tc_chunks(int l) { return (l + TC_KC - 1) / TC_KC; }
+
+void launch_direct_tc(const TcArgs &a, int num_sms, cudaStream_t s)
+{
+    static std::once_flag once[64];
+    smem_optin_max((const void *)k_direct_tc, once);
+    k_tc_rows<<<num_sms * 8, TC_THREADS, 0, s>>>(a);
+    k_direct_tc<<<num_sms, TC_THREADS, tc_smem_bytes(a.p), s>>>(a);
+}
+
+}  // namespace mad

@@ -630,24 +630,30 @@ __global__ void __launch_bounds__(128, row_min_blocks<PM>()) k_merge(MergeArgs<T
     const bool sym_on = sym_rule(A.allow_sym, *A.nflagged, A.nl) && fl == ROW_RECOMPUTE;
     T bk[PM];
     int32_t bj[PM];
+    float bd[PM];               // per-entry error bound from the direct paths (< 0: band model)
     for_pm<PM>([&](int t) {
         bk[t] = T(-pinf());
         bj[t] = INT32_MAX;
+        bd[t] = -1.0f;
     });
     T lastk = T(-pinf());       // the p-th kept key (a sentinel until p are kept)
     int32_t lastj = INT32_MAX;
-    auto offer = [&](T v, int32_t j) {
+    auto offer = [&](T v, int32_t j, float dq) {
         if (!key_before(v, j, lastk, lastj)) return;
         T cv = v;
         int32_t cj = j;
+        float cd = dq;
         for_pm<PM>([&](int t) {
             if (t < p && key_before(cv, cj, bk[t], bj[t])) {
                 const T tk = bk[t];
                 const int32_t tj = bj[t];
+                const float td = bd[t];
                 bk[t] = cv;
                 bj[t] = cj;
+                bd[t] = cd;
                 cv = tk;
                 cj = tj;
+                cd = td;
             }
         });
         for_pm<PM>([&](int t) {
@@ -663,7 +669,7 @@ __global__ void __launch_bounds__(128, row_min_blocks<PM>()) k_merge(MergeArgs<T
             const int64_t slot = d * A.dnblk + g;
             if ((int64_t)g * direct_cols_per_block_dev() >= A.nl) break;
             const int cnt = A.dcnt[slot];
-            for (int c = 0; c < cnt; ++c) offer(A.dkey[slot * p + c], A.dj[slot * p + c]);
+            for (int c = 0; c < cnt; ++c) offer(A.dkey[slot * p + c], A.dj[slot * p + c], A.ddq[slot * p + c]);
         }
     } else {
         const int g0 = sym_on ? (int)(((i / A.R) * (int64_t)A.R) / A.group_w) : 0;
@@ -682,7 +688,7 @@ __global__ void __launch_bounds__(128, row_min_blocks<PM>()) k_merge(MergeArgs<T
                     const int g = gq + 4 * u + w;
                     if (g < g0 || g >= gend) continue;
                     const int64_t slot = i * A.ngroups + g;
-                    for (int c = 0; c < cs[w]; ++c) offer(A.skey[slot * p + c], A.sj[slot * p + c]);
+                    for (int c = 0; c < cs[w]; ++c) offer(A.skey[slot * p + c], A.sj[slot * p + c], -1.0f);
                 }
             }
         }
@@ -698,7 +704,7 @@ __global__ void __launch_bounds__(128, row_min_blocks<PM>()) k_merge(MergeArgs<T
             atomicAdd(A.overflow, 1ull);
             return;
         }
-        for (int c = 0; c < cc; ++c) offer(A.ckey[i * A.cap + c], A.cj[i * A.cap + c]);
+        for (int c = 0; c < cc; ++c) offer(A.ckey[i * A.cap + c], A.cj[i * A.cap + c], -1.0f);
     }
     int nb = 0;
     for_pm<PM>([&](int t) { nb += (t < p && bj[t] != INT32_MAX); });
@@ -723,7 +729,7 @@ __global__ void __launch_bounds__(128, row_min_blocks<PM>()) k_merge(MergeArgs<T
             const double inv = (double)A.col[j].inv;
             const bool flat_j = A.run[j] >= l;
             const double c = (flat_j || inv == 0.0) ? 0.0 : (double)bk[e] / inv;
-            const float dq = flat_j ? 0.0f : (float)dq_pair(A.em, i, j);
+            const float dq = flat_j ? 0.0f : (bd[e] >= 0.0f ? bd[e] : (float)dq_pair(A.em, i, j));
             A.st.ent_j[at] = j;
             A.st.ent_c[at] = c;
             A.st.ent_dq[at] = dq;
@@ -750,8 +756,11 @@ __global__ void __launch_bounds__(128, row_min_blocks<PM>()) k_merge(MergeArgs<T
     if (ntc <= p) {
         A.st.bnum[i] = pinf();
     } else {
-        // unstored partners have band keys <= the p-th kept key
-        double qp = (double)lastk / sqm2i + dq_row(A.em, i);
+        // unstored partners have keys <= the p-th kept key, each within its
+        // error bound (band model, or the direct paths' largest at this length)
+        double dqb = dq_row(A.em, i);
+        if (fl == ROW_DIRECT) dqb = fmax(dqb, (double)*A.ddq_max);
+        double qp = (double)lastk / sqm2i + dqb;
         qp = qp > 1.0 ? 1.0 : (qp < 0.0 ? 0.0 : qp);
         A.st.bnum[i] = sqrt((double)l * (1.0 - qp * qp)) * sig;
     }

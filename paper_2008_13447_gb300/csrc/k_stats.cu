@@ -117,14 +117,32 @@ void launch_split_x(const double *x, int64_t n, float *xh, float *xl, cudaStream
     k_split_x<<<(unsigned)g, 256, 0, s>>>(x, n, xh, xl);
 }
 
-// Contrast factor kappa_i (see ErrModel): block maxima of M2 over 256
-// windows, then for each window the maximum over the blocks that cover the R
-// windows ending at it (a superset of them, so kappa is not underestimated).
-__global__ void k_m2_blockmax(const double *__restrict__ m2, int64_t nl, double *__restrict__ blkmax)
+// Contrast factor kappa_i (see ErrModel). Along the diagonal chain of a
+// cell (i, j) of the band kernel (at most R + 1 windows above-left of it,
+// back to its seed), each recurrence step rounds twice relative to the
+// running co-moment (|C| <= sqrt(M2_a M2_b) by Cauchy-Schwarz) and once for
+// each FP32 input df, dg; per step the total is below
+//     2u sqrt(w_a w_b),   w_k = M2_k + 1.5 (df_k^2 + dg_k^2)
+// (Cauchy-Schwarz on (sqrt M2, sqrt 1.5 h) vectors, h^2 = df^2 + dg^2), so the
+// correlation error of the cell is below u (2R + 4) kappa_i kappa_j with
+//     kappa_i = sqrt(max of w over the chain windows of i / M2_i).
+// Block maxima of w over 256 windows are taken, then for each window the
+// maximum over the blocks covering the R + 2 windows ending at it (a
+// superset, so kappa is never underestimated).
+__global__ void k_m2_blockmax(const double *__restrict__ x, const double *__restrict__ mu,
+                              const double *__restrict__ m2, int64_t nl, int l, double *__restrict__ blkmax)
 {
     __shared__ double sh[32];
     const int64_t i = blockIdx.x * (int64_t)256 + threadIdx.x;
-    double v = i < nl ? m2[i] : 0.0;
+    double v = 0.0;
+    if (i < nl) {
+        v = m2[i];
+        if (i + 1 < nl) {
+            const double df = 0.5 * (x[i + l] - x[i]);
+            const double dg = (x[i + l] - mu[i + 1]) + (x[i] - mu[i]);
+            v += 1.5 * (df * df + dg * dg);
+        }
+    }
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
     __syncthreads();
@@ -143,7 +161,7 @@ __global__ void k_kappa(const double *__restrict__ m2, const int32_t *__restrict
     if (i < nl) {
         const double mi = m2[i];
         if (run[i] < l && mi > 0.0) {
-            const int64_t lo = i - R + 1 < 0 ? 0 : i - R + 1;
+            const int64_t lo = i - R - 1 < 0 ? 0 : i - R - 1;
             double mx = mi;
             for (int64_t b = lo / 256; b <= i / 256; ++b) mx = fmax(mx, blkmax[b]);
             k = (float)sqrt(mx / mi) * 1.0001f;
@@ -155,11 +173,11 @@ __global__ void k_kappa(const double *__restrict__ m2, const int32_t *__restrict
     if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(kappa_max), __float_as_int(k));
 }
 
-void launch_kappa(const double *m2, const int32_t *run, int64_t nl, int l, int R, double *blkmax, float *kappa,
-                  float *kappa_max, cudaStream_t s)
+void launch_kappa(const double *x, const double *mu, const double *m2, const int32_t *run, int64_t nl, int l, int R,
+                  double *blkmax, float *kappa, float *kappa_max, cudaStream_t s)
 {
     const unsigned nb = (unsigned)((nl + 255) / 256);
-    k_m2_blockmax<<<nb, 256, 0, s>>>(m2, nl, blkmax);
+    k_m2_blockmax<<<nb, 256, 0, s>>>(x, mu, m2, nl, l, blkmax);
     cudaMemsetAsync(kappa_max, 0, sizeof(float), s);
     k_kappa<<<nb, 256, 0, s>>>(m2, run, nl, l, R, blkmax, kappa, kappa_max);
 }

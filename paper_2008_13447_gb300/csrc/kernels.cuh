@@ -92,13 +92,17 @@ template <typename T> int band_occupancy(bool bins_mode, int p, int rpl);
 template <typename T> size_t band_smem(bool bins_mode, int p, int rpl);
 
 // ------------------------------------------------------------- error model
-// Rounding of the band kernel's recurrence accumulates along a diagonal; its
-// size relative to a cell's normaliser sqrt(M2_i M2_j) grows with the
-// variance met earlier on the chain. kappa_i = sqrt(max M2 over the R windows
-// ending at i / M2_i) (>= 1) measures that contrast, and the correlation of a
-// band key for cell (i, j) is trusted to dq0 * kappa_i * kappa_j. A distance
+// Rounding of the band kernel's recurrence accumulates along a diagonal
+// chain of at most R + 1 steps from its seed. With kappa_i = sqrt(max over
+// the chain windows of w_k / M2_i), w_k = M2_k + 1.5 (df_k^2 + dg_k^2) (see
+// launch_kappa), the correlation of a band key for cell (i, j) is within
+//     dq0 kappa_i kappa_j,   dq0 = u (2R + 4)
+// of the exact one (u the unit roundoff of the recurrence's type; the FP64
+// path adds the error of its seeds, stepped in FP64 from length to length).
+// The direct path (k_direct) and the tensor-core path (k_direct_tc) write
+// their own per-entry bounds, and the largest of them per length. A distance
 // whose resulting error could exceed half its tolerance is re-evaluated
-// directly in FP64.
+// (compensated FP32 or FP64).
 struct ErrModel {
     const float *kappa;     // per window
     const float *kappa_max; // max over windows at this length (device scalar)
@@ -108,8 +112,8 @@ struct ErrModel {
     int audit;              // test hook: re-evaluate every stored entry that carries a bound, in
                             // FP64, so that the observed error over its bound is recorded
 };
-void launch_kappa(const double *m2, const int32_t *run, int64_t nl, int l, int R, double *blkmax, float *kappa,
-                  float *kappa_max, cudaStream_t s);
+void launch_kappa(const double *x, const double *mu, const double *m2, const int32_t *run, int64_t nl, int l, int R,
+                  double *blkmax, float *kappa, float *kappa_max, cudaStream_t s);
 
 // ----------------------------------------------------------------- k_rows.cu
 // Per-row state kept across lengths (structure of arrays, n0 = n - lmin + 1):
@@ -251,6 +255,8 @@ template <typename T> struct MergeArgs {
     const T *dkey;
     const int32_t *dj;
     const int32_t *dcnt;
+    const float *ddq;       // per-entry error bounds of the direct paths
+    const float *ddq_max;   // their largest at this length
     int dnblk;
     const T *ckey;
     const int32_t *cj;
@@ -326,9 +332,42 @@ template <typename T> struct DirectArgs {
     int32_t *oj;
     int32_t *ocnt;          // [list position][nblk]
     int nblk;
+    float *odq;             // [list position][nblk][p] error bound of each key (correlation units)
+    float *dq_max;          // largest bound of any column at this length (device scalar, max-reduced)
 };
 template <typename T> void launch_direct(const DirectArgs<T> &a, int grid, cudaStream_t s);
 int direct_cols_per_block();
+
+// The same recompute on the tensor cores (k_direct_tc.cu): FP16 hi + lo split
+// products of the rows' normalised windows and the shifted series, FP32
+// accumulation in TMEM; same outputs as the direct kernel.
+struct TcArgs {
+    const double *x;
+    int64_t n, nl;
+    int l;
+    int64_t E;
+    int p;
+    const double *mu;       // window means at l
+    const double *m2;       // M2 at l
+    const double *isd;      // 1 / sqrt(M2) (0: flat)
+    const int32_t *rows;    // listed rows
+    const int32_t *nrows;   // their count (device)
+    const float *thr;       // per-row key threshold
+    int nkc;                // lag chunks of 64 covering l
+    unsigned char *aimg;    // row operand images [row tile][chunk][hi, lo][16 KB]
+    float *asum;            // [list position] sum of the represented row operand
+    float *sqm2;            // [list position] sqrt(M2) of the row
+    float *okey;            // outputs as DirectArgs
+    int32_t *oj;
+    int32_t *ocnt;
+    float *odq;
+    float *dq_max;
+    int nblk;
+    int *err;               // set if a bounded wait ran out
+};
+void launch_direct_tc(const TcArgs &a, int num_sms, cudaStream_t s);
+size_t tc_aimg_bytes(int64_t max_rows, int lmax);
+int tc_chunks(int l);
 
 template <typename T>
 void launch_fill(T *p, int64_t n, T v, cudaStream_t s);

@@ -38,6 +38,18 @@ thread_local std::string g_create_err;
 std::atomic<int> g_wave_limit{-1};
 // mad_debug_audit_error_bounds
 std::atomic<int> g_audit{0};
+// mad_set_graphs: capture and replay repeated profiles (default on)
+std::atomic<int> g_graphs{1};
+
+// What a profile's workspace depends on: while a series is profiled again
+// with the same key, its device buffers are reused as they are (no
+// cudaMalloc / cudaFree) and the whole per-length launch sequence is replayed
+// from a CUDA graph.
+struct WsKey {
+    int tsize = 0, lmin = 0, lmax = 0, p = 0, m_max = 0, k_max = 0, mode = 0, band_form = 0, keep = 0,
+        observe = 0, num = 0, den = 0, audit = 0, wave_limit = 0, tc = 0;
+    bool operator==(const WsKey &o) const { return std::memcmp(this, &o, sizeof(WsKey)) == 0; }
+};
 
 struct Series {
     int64_t n = 0;
@@ -47,7 +59,28 @@ struct Series {
     bool profiled = false;
     int lmin = 0, lmax = 0, p = 0, m_max = 1, k_max = 10;
     int64_t n0 = 0;
+    // workspace: device buffers in allocation order; while `reuse` is set,
+    // allocations are handed out again from the list (sizes checked)
     std::vector<void *> allocs;
+    std::vector<size_t> alloc_bytes;
+    size_t cursor = 0;
+    bool reuse = false;
+    bool ws_valid = false;
+    WsKey key{};
+    // side streams and events of the per-length pipeline, kept across profiles
+    cudaStream_t prep = nullptr, disc = nullptr, cap = nullptr;
+    cudaEvent_t sev[10] = {};
+    std::vector<cudaEvent_t> tev;           // timing events of the band kernel (pairs)
+    std::vector<int> tev_li;                // length index of each pair
+    std::vector<unsigned long long> host_launch;
+    cudaGraphExec_t exec = nullptr;         // the captured profile, replayed while the key holds
+    // read-back of the last profile
+    unsigned long long *dstats = nullptr;
+    int32_t *wait_err = nullptr;
+    int nstat = 0;
+    // scratch of the read-outs (grown, never shrunk)
+    void *rscratch = nullptr;
+    size_t rscratch_bytes = 0;
     Valmp vm{};
     DiscTable tab{};
     double *keep_nnd = nullptr;
@@ -115,16 +148,33 @@ void set_err(mad_ctx *c, const std::string &m)
 template <typename P>
 P *dalloc(mad_ctx *ctx, Series &s, size_t count)
 {
+    const size_t bytes = count * sizeof(P) > 0 ? count * sizeof(P) : 1;
+    if (s.reuse) {
+        if (s.cursor >= s.allocs.size() || s.alloc_bytes[s.cursor] != bytes) {
+            set_err(ctx, "workspace reuse out of step with its allocations");
+            throw Fail{MAD_EINTERNAL};
+        }
+        return static_cast<P *>(s.allocs[s.cursor++]);
+    }
     void *p = nullptr;
-    CK(cudaMalloc(&p, count * sizeof(P) > 0 ? count * sizeof(P) : 1));
+    CK(cudaMalloc(&p, bytes));
     s.allocs.push_back(p);
+    s.alloc_bytes.push_back(bytes);
     return static_cast<P *>(p);
 }
 
 void free_profile(Series &s)
 {
+    if (s.exec) cudaGraphExecDestroy(s.exec);
+    s.exec = nullptr;
     for (void *p : s.allocs) cudaFree(p);
     s.allocs.clear();
+    s.alloc_bytes.clear();
+    s.cursor = 0;
+    s.reuse = false;
+    s.ws_valid = false;
+    s.dstats = nullptr;
+    s.wait_err = nullptr;
     s.profiled = false;
     s.keep_nnd = nullptr;
     s.keep_nnj = nullptr;
@@ -133,6 +183,41 @@ void free_profile(Series &s)
 }
 
 int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// Scratch of the read-outs: one device buffer per series, grown when a call
+// needs more and kept (the read-outs then allocate nothing in steady state).
+// Carve hands out 256-byte aligned pieces of it.
+struct Carve {
+    std::vector<size_t> sizes;
+    size_t total() const
+    {
+        size_t t = 0;
+        for (size_t b : sizes) t += (b + 255) / 256 * 256;
+        return t;
+    }
+};
+std::vector<void *> rscratch(mad_ctx *ctx, Series &s, const Carve &c, cudaStream_t st)
+{
+    const size_t need = c.total() > 0 ? c.total() : 256;
+    if (need > s.rscratch_bytes) {
+        if (s.rscratch) {
+            CK(cudaStreamSynchronize(st));
+            cudaFree(s.rscratch);
+            s.rscratch = nullptr;
+            s.rscratch_bytes = 0;
+        }
+        const size_t nb = need + need / 2;
+        CK(cudaMalloc(&s.rscratch, nb));
+        s.rscratch_bytes = nb;
+    }
+    std::vector<void *> out;
+    size_t off = 0;
+    for (size_t b : c.sizes) {
+        out.push_back(static_cast<char *>(s.rscratch) + off);
+        off += (b + 255) / 256 * 256;
+    }
+    return out;
+}
 
 mad_options defaults(const mad_options *o)
 {
@@ -147,7 +232,8 @@ mad_options defaults(const mad_options *o)
 void check_options(mad_ctx *ctx, const mad_options &o)
 {
     REQUIRE(o.excl_num >= 0 && o.excl_den >= 1, "exclusion zone needs excl_num >= 0 and excl_den >= 1");
-    REQUIRE(o.precision == MAD_FP64 || o.precision == MAD_FP32, "precision must be MAD_FP64 or MAD_FP32");
+    REQUIRE(o.precision == MAD_FP64 || o.precision == MAD_FP32 || o.precision == MAD_SPLIT_TC,
+            "precision must be MAD_FP64, MAD_FP32 or MAD_SPLIT_TC");
     REQUIRE(o.k_max >= 1 && o.k_max <= KMAX, "k_max must be in [1, 64]");
     REQUIRE(o.m_max >= 1 && o.m_max <= MAXP, "m_max must be in [1, 64]");
     REQUIRE(o.mode >= 0 && o.mode <= 2, "mode must be 0 (exact rows), 1 (motif mode) or 2 (discord mode)");
@@ -166,38 +252,39 @@ void init_ctx(mad_ctx *ctx, const mad_options *opt)
 
 // ------------------------------------------------------------- profile
 
-// Error model of the band kernel's keys (see ErrModel): base correlation
-// error dq0 (scaled per cell by the contrast factors) and the distance
-// tolerance that decides which reported entries are re-evaluated in FP64.
+// Error model of the band kernel's keys (see ErrModel): dq0 = u (2R + 4)
+// for a chain of at most R + 1 steps (scaled per cell by the contrast
+// factors), plus, on the FP64 path, the error of the FP64 seeds (a direct
+// dot product at lmin, then one Welford step per length); and the distance
+// tolerance that decides which reported entries are re-evaluated.
 template <typename T>
 struct Precision;
 template <>
 struct Precision<double> {
-    // FP64 recurrence over at most one band from FP64 seeds: ~1e-14 observed.
-    static constexpr double dq0 = 5e-14, rel_tol = 1e-9, abs_coef = 0.0;
+    static constexpr double u = 0x1p-53, rel_tol = 1e-9, abs_coef = 0.0;
+    static double dq0(int R, int lmax) { return u * (2.0 * R + 4.0 + 4.0 * lmax + 64.0); }
 };
 template <>
 struct Precision<float> {
-    // FP32 recurrence over at most one band from FP32 seeds: ~1e-6 observed
-    // on smooth data (epsilon_32 * sqrt(R) ~ 1.9e-6 for R = 1024).
-    static constexpr double dq0 = 3e-6, rel_tol = 0.0, abs_coef = 1e-4;
+    static constexpr double u = 0x1p-24, rel_tol = 0.0, abs_coef = 1e-4;
+    static double dq0(int R, int) { return u * (2.0 * R + 4.0) + 0x1p-50; }
 };
 
+// Timed launches of the per-length pipeline (CUDA events recorded on the
+// launching stream around each launch; in a captured profile the records are
+// graph nodes of their own).
+enum { TK_BAND = 0, TK_DIRECT = 1, TK_ROWS = 2 };
+
+// Issue one profile over [lmin, lmax] on stream st: every kernel, copy and
+// cross-stream dependency, and nothing that waits on the host, so that the
+// same sequence can be captured into a CUDA graph. Buffers come from the
+// series' workspace (reused while its key holds).
 template <typename T>
-void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStream_t st)
+void issue_profile(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStream_t st, bool capture)
 {
     const mad_options &o = ctx->opt;
     const int num = o.excl_num, den = o.excl_den;
     const int64_t n = s.n;
-    REQUIRE(lmin >= 2 && lmin <= lmax, "need 2 <= lmin <= lmax");
-    REQUIRE((int64_t)lmax < n, "lmax must be smaller than the series length");
-    REQUIRE(p >= 1 && p <= MAXP, "p must be in [1, 64]");
-    REQUIRE(o.m_max <= p, "m_max must not exceed p (the paper's p >= m)");
-    const int64_t Emax = excl_zone(lmax, num, den);
-    REQUIRE(n - lmax + 1 > 2 * Emax + 2, "series too short for lmax and the exclusion zone (need n-lmax+1 > 2E(lmax)+2)");
-    REQUIRE(n < (int64_t)INT32_MAX - 4096, "series longer than 2^31 - 4096 samples");
-
-    free_profile(s);
     s.lmin = lmin;
     s.lmax = lmax;
     s.p = p;
@@ -242,9 +329,10 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
     double *isdb[2] = {dalloc<double>(ctx, s, n0), dalloc<double>(ctx, s, n0)};
     float *xh = dalloc<float>(ctx, s, n), *xl = dalloc<float>(ctx, s, n);
     const int audit = g_audit.load() ? 1 : 0;
+    const double dq0 = Precision<T>::dq0(R, lmax);
     const ErrModel emb[2] = {
-        {kappab[0], kmaxb[0], Precision<T>::dq0, Precision<T>::rel_tol, Precision<T>::abs_coef, audit},
-        {kappab[1], kmaxb[1], Precision<T>::dq0, Precision<T>::rel_tol, Precision<T>::abs_coef, audit}};
+        {kappab[0], kmaxb[0], dq0, Precision<T>::rel_tol, Precision<T>::abs_coef, audit},
+        {kappab[1], kmaxb[1], dq0, Precision<T>::rel_tol, Precision<T>::abs_coef, audit}};
     Valmp vm{dalloc<double>(ctx, s, n0), dalloc<double>(ctx, s, n0), dalloc<int32_t>(ctx, s, n0),
              dalloc<int32_t>(ctx, s, n0)};
     int *bins = dalloc<int>(ctx, s, (size_t)n0 * nbins);
@@ -304,11 +392,13 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
     int32_t *wait_err = counters + 3;
     int32_t *ndirect = dalloc<int32_t>(ctx, s, 1);
 
-    // ---- one-off initialisation
-    {
+    // ---- one-off initialisation (the seed-row list is constant: written
+    // when the workspace is created, outside any capture)
+    if (!s.reuse) {
         std::vector<int32_t> kr(K);
         for (int64_t k = 0; k < K; ++k) kr[k] = (int32_t)k;
         CK(cudaMemcpyAsync(krows, kr.data(), K * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
     }
     CK(cudaMemsetAsync(dstats, 0, (size_t)nL * NSTAT * sizeof(unsigned long long), st));
     if (motif_mode) launch_fill<double>(mm, (int64_t)2 * nL, INFINITY, st);
@@ -365,6 +455,15 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
     T *dkey = dalloc<T>(ctx, s, (size_t)max_direct * dnblk * p);
     int32_t *djj = dalloc<int32_t>(ctx, s, (size_t)max_direct * dnblk * p);
     int32_t *dcnt = dalloc<int32_t>(ctx, s, (size_t)max_direct * dnblk);
+    float *ddq = dalloc<float>(ctx, s, (size_t)max_direct * dnblk * p);
+    float *ddqmax = dalloc<float>(ctx, s, (size_t)nL);   // per length, max-reduced
+    CK(cudaMemsetAsync(ddqmax, 0, (size_t)nL * sizeof(float), st));
+    // tensor-core direct path: row operand images and per-row sums
+    const bool tc = o.precision == MAD_SPLIT_TC;
+    const int64_t max_direct_pad = (max_direct + 127) / 128 * 128;
+    unsigned char *aimg = tc ? dalloc<unsigned char>(ctx, s, tc_aimg_bytes(max_direct, lmax)) : nullptr;
+    float *tasum = tc ? dalloc<float>(ctx, s, (size_t)max_direct_pad) : nullptr;
+    float *tsq = tc ? dalloc<float>(ctx, s, (size_t)max_direct_pad) : nullptr;
     T *skey = dalloc<T>(ctx, s, (size_t)n0 * ngroups_max * p);
     int32_t *sj = dalloc<int32_t>(ctx, s, (size_t)n0 * ngroups_max * p);
     int32_t *scnt = dalloc<int32_t>(ctx, s, (size_t)n0 * ngroups_max);
@@ -396,23 +495,26 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
 
     // the symmetric band form (upper triangle, both sides of each cell)
     const int use_sym = o.band_form == 1 ? 1 : 0;
-    s.stats.assign(nL, mad_length_stats{});
-    std::vector<unsigned long long> host_launch(nL, 0);
-    // CUDA events around every band-kernel launch (device time of the
-    // dominant kernel, per length)
-    struct Ev { int li; cudaEvent_t a, b; };
-    std::vector<Ev> evs;
-    auto ev_pair = [&](int li) {
-        Ev e{li, nullptr, nullptr};
-        CK(cudaEventCreate(&e.a));
-        CK(cudaEventCreate(&e.b));
-        evs.push_back(e);
-        return evs.size() - 1;
+    s.host_launch.assign(nL, 0);
+    // CUDA events around the band-kernel, direct-path and per-row launches
+    // (device time per kernel and length), from the series' pool
+    s.tev_li.clear();
+    const unsigned ev_flags = capture ? cudaEventRecordExternal : cudaEventRecordDefault;
+    size_t ev_next = 0;
+    auto ev_begin = [&](int li, int kind) {
+        if (s.tev.size() < ev_next + 2) {
+            cudaEvent_t a = nullptr, b = nullptr;
+            CK(cudaEventCreate(&a));
+            CK(cudaEventCreate(&b));
+            s.tev.push_back(a);
+            s.tev.push_back(b);
+        }
+        s.tev_li.push_back(li * 4 + kind);
+        CK(cudaEventRecordWithFlags(s.tev[ev_next], st, ev_flags));
+        ev_next += 2;
+        return ev_next - 1;
     };
-    struct EvGuard {
-        std::vector<Ev> &v;
-        ~EvGuard() { for (Ev &e : v) { if (e.a) cudaEventDestroy(e.a); if (e.b) cudaEventDestroy(e.b); } }
-    } ev_guard{evs};
+    auto ev_end_rec = [&](size_t e) { CK(cudaEventRecordWithFlags(s.tev[e], st, ev_flags)); };
     // launches issued for the current length, counted at each launch site
     unsigned long long nlaunch = 1 /* k_flat_runs */ + 1 /* k_stats_init */ + 1 /* k_split_x */ + 1 /* fill thr */;
 
@@ -421,24 +523,13 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
     // discord tables of length l need only that length's m-th best matches,
     // so they run while the next length proceeds. Events order them against
     // the context's stream.
-    struct Side {
-        cudaStream_t prep = nullptr, disc = nullptr;
-        cudaEvent_t ev[10] = {};
-        ~Side()
-        {
-            if (prep) cudaStreamDestroy(prep);
-            if (disc) cudaStreamDestroy(disc);
-            for (cudaEvent_t e : ev)
-                if (e) cudaEventDestroy(e);
-        }
-    } side;
-    CK(cudaStreamCreateWithFlags(&side.prep, cudaStreamNonBlocking));
-    CK(cudaStreamCreateWithFlags(&side.disc, cudaStreamNonBlocking));
-    for (cudaEvent_t &e : side.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    cudaEvent_t ev_nnd = side.ev[2], ev_end = side.ev[3];
-    cudaEvent_t *ev_disc = side.ev + 4;   // [2], one per m-th NN buffer
-    cudaEvent_t *ev_prep = side.ev + 6;   // [2], length prepared (by parity)
-    cudaEvent_t *ev_ext = side.ev + 8;    // [2], extension done (by parity)
+    struct SideRef {
+        cudaStream_t prep, disc;
+    } side{s.prep, s.disc};
+    cudaEvent_t ev_nnd = s.sev[2], ev_end = s.sev[3];
+    cudaEvent_t *ev_disc = s.sev + 4;   // [2], one per m-th NN buffer
+    cudaEvent_t *ev_prep = s.sev + 6;   // [2], length prepared (by parity)
+    cudaEvent_t *ev_ext = s.sev + 8;    // [2], extension done (by parity)
     // Preparation of length l on the side stream: window statistics (one
     // Welford step), column data and 1/sqrt(M2), contrast factors, seed rows
     // (one FP64 co-moment step from the previous length).
@@ -453,7 +544,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
             k_stats_step<<<(unsigned)((nl + 255) / 256), 256, 0, side.prep>>>(s.x, nl, l, mu[b ^ 1], m2[b ^ 1],
                                                                              mu[b], m2[b]);
         launch_coldata<T>(s.x, nl, npad, l, mu[b], m2[b], run, colb[b], isdb[b], side.prep);
-        launch_kappa(m2[b], run, nl, l, R, m2blk, kappab[b], kmaxb[b], side.prep);
+        launch_kappa(s.x, mu[b], m2[b], run, nl, l, R, m2blk, kappab[b], kmaxb[b], side.prep);
         if (l == lmin) {
             // seed rows computed directly once, in FP64; every later length
             // steps them by one co-moment update
@@ -572,7 +663,11 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
             ea.hint_j = hint_j;
             ea.hint_c = hint_c;
             ea.hint_dq = hint_dq;
-            launch_extend<T>(ea, st);
+            {
+                const size_t e = ev_begin(li, TK_ROWS);
+                launch_extend<T>(ea, st);
+                ev_end_rec(e);
+            }
             if (disc_mode) {
                 // Algorithm 10's first pass, then the rows its second pass can need
                 DiscPassArgs dp = disc_args(nl, l, E, 0, lo);
@@ -604,7 +699,13 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
         sp.flag = rs.flag;
         sp.nl = nl;
         sp.R = R;
-        sp.lim = (4 * R) / l > 1 ? (4 * R) / l : 1;
+        // rows to recompute per band below which they go to the direct path:
+        // the band kernel costs about R n_l cells at ALU speed, a direct row
+        // n_l l multiply-adds (about 50x faster per lag on the tensor cores)
+        {
+            const int per = tc ? 48 * R : 4 * R;
+            sp.lim = per / l > 1 ? per / l : 1;
+        }
         sp.force_direct = 0;
         sp.allow_sym = use_sym;
         sp.nflagged = lo.stats + 2;
@@ -633,17 +734,43 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
             launch_fill<int32_t>(bins, (int64_t)n0 * nbins, (int32_t)0x807fffff, st);  // ord(-inf)
             CK(cudaMemsetAsync(unit_ctr, 0, sizeof(int32_t), st));
             {
-                const size_t e = ev_pair(li);
-                CK(cudaEventRecord(evs[e].a, st));
+                const size_t e = ev_begin(li, TK_BAND);
                 launch_band<T>(ba, true, grid_bins, st);
-                CK(cudaEventRecord(evs[e].b, st));
+                ev_end_rec(e);
             }
             launch_theta_bins<T>(bins, nbins, nl, p, m2[b], em, thr, st);
             launch_mask_thr<T>(rs.flag, n0, thr, st);
             nlaunch += 4;
             CK(cudaGetLastError());
         }
-        DirectArgs<T> da{s.x, mu[b], colb[b], nl, l, E, p, drows, ndirect, thr, dkey, djj, dcnt, dnblk};
+        DirectArgs<T> da{s.x, mu[b], colb[b], nl, l, E, p, drows, ndirect, thr, dkey, djj, dcnt, dnblk,
+                         ddq, ddqmax + li};
+        TcArgs ta{};
+        if (tc) {
+            ta.x = s.x;
+            ta.n = n;
+            ta.nl = nl;
+            ta.l = l;
+            ta.E = E;
+            ta.p = p;
+            ta.mu = mu[b];
+            ta.m2 = m2[b];
+            ta.isd = isdb[b];
+            ta.rows = drows;
+            ta.nrows = ndirect;
+            ta.thr = reinterpret_cast<const float *>(thr);
+            ta.nkc = tc_chunks(l);
+            ta.aimg = aimg;
+            ta.asum = tasum;
+            ta.sqm2 = tsq;
+            ta.okey = reinterpret_cast<float *>(dkey);
+            ta.oj = djj;
+            ta.ocnt = dcnt;
+            ta.odq = ddq;
+            ta.dq_max = ddqmax + li;
+            ta.nblk = dnblk;
+            ta.err = wait_err;
+        }
         MergeArgs<T> ma{};
         ma.x = s.x;
         ma.mu = mu[b];
@@ -680,15 +807,16 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
         ma.dkey = dkey;
         ma.dj = djj;
         ma.dcnt = dcnt;
+        ma.ddq = ddq;
+        ma.ddq_max = ddqmax + li;
         ma.dnblk = dnblk;
         for (int pass = 0; pass < 2; ++pass) {
             ma.allow_sym = pass == 0 ? use_sym : 0;
             if (pass == 0) {
                 CK(cudaMemsetAsync(unit_ctr, 0, sizeof(int32_t), st));
-                const size_t e = ev_pair(li);
-                CK(cudaEventRecord(evs[e].a, st));
+                const size_t e = ev_begin(li, TK_BAND);
                 launch_band<T>(ba, false, grid_band, st);
-                CK(cudaEventRecord(evs[e].b, st));
+                ev_end_rec(e);
                 nlaunch += use_sym ? 2 : 1;
             } else {
                 sp.force_direct = 1;
@@ -696,8 +824,17 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
                 launch_split(sp, st);
                 ++nlaunch;
             }
-            launch_direct<T>(da, grid_direct, st);
-            launch_merge<T>(ma, st);
+            {
+                const size_t e = ev_begin(li, TK_DIRECT);
+                if (tc && pass == 0) launch_direct_tc(ta, ctx->num_sms, st);
+                else launch_direct<T>(da, grid_direct, st);
+                ev_end_rec(e);
+            }
+            {
+                const size_t e = ev_begin(li, TK_ROWS);
+                launch_merge<T>(ma, st);
+                ev_end_rec(e);
+            }
             nlaunch += 2;
             CK(cudaGetLastError());
         }
@@ -724,7 +861,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
         }
         CK(cudaEventRecord(ev_disc[li & 1], side.disc));
         CK(cudaGetLastError());
-        host_launch[li] = nlaunch;
+        s.host_launch[li] = nlaunch;
         nlaunch = 0;
     }
     // the side streams' last work is done before the read-back
@@ -732,11 +869,102 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
     CK(cudaStreamWaitEvent(st, ev_end, 0));
     CK(cudaEventRecord(ev_end, side.prep));
     CK(cudaStreamWaitEvent(st, ev_end, 0));
+    s.dstats = dstats;
+    s.wait_err = wait_err;
+    s.nstat = NSTAT;
+    s.vm = vm;
+    s.tab = tab;
+}
+
+// Profile one series: validate, reuse the workspace while the key holds,
+// and issue the profile -- eagerly the first time (buffers allocated), into
+// a CUDA graph the second time with the same key (captured, instantiated,
+// launched), and by replaying that graph after. Then read back the error
+// word, the per-length counters and the kernel timings.
+template <typename T>
+void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStream_t st)
+{
+    const mad_options &o = ctx->opt;
+    const int num = o.excl_num, den = o.excl_den;
+    const int64_t n = s.n;
+    REQUIRE(lmin >= 2 && lmin <= lmax, "need 2 <= lmin <= lmax");
+    REQUIRE((int64_t)lmax < n, "lmax must be smaller than the series length");
+    REQUIRE(p >= 1 && p <= MAXP, "p must be in [1, 64]");
+    REQUIRE(o.m_max <= p, "m_max must not exceed p (the paper's p >= m)");
+    const int64_t Emax = excl_zone(lmax, num, den);
+    REQUIRE(n - lmax + 1 > 2 * Emax + 2, "series too short for lmax and the exclusion zone (need n-lmax+1 > 2E(lmax)+2)");
+    REQUIRE(n < (int64_t)INT32_MAX - 4096, "series longer than 2^31 - 4096 samples");
+
+    WsKey key{};
+    key.tsize = (int)sizeof(T);
+    key.tc = o.precision == MAD_SPLIT_TC ? 1 : 0;
+    key.lmin = lmin;
+    key.lmax = lmax;
+    key.p = p;
+    key.m_max = o.m_max;
+    key.k_max = o.k_max;
+    key.mode = o.mode;
+    key.band_form = o.band_form;
+    key.keep = o.keep_profiles ? 1 : 0;
+    key.observe = o.observe_len;
+    key.num = num;
+    key.den = den;
+    key.audit = g_audit.load();
+    key.wave_limit = g_wave_limit.load();
+    const bool same = s.ws_valid && s.key == key;
+    if (!same) {
+        free_profile(s);
+        s.key = key;
+    }
+    s.profiled = false;
+    const int nL = lmax - lmin + 1;
+    s.stats.assign(nL, mad_length_stats{});
+    // streams and events of the pipeline, created once per series
+    if (!s.prep) {
+        CK(cudaStreamCreateWithFlags(&s.prep, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&s.disc, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&s.cap, cudaStreamNonBlocking));
+        for (cudaEvent_t &e : s.sev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    if (same && s.exec) {
+        CK(cudaGraphLaunch(s.exec, st));
+    } else {
+        s.reuse = same;
+        s.cursor = 0;
+        const bool capture = same && g_graphs.load();
+        if (!capture) {
+            issue_profile<T>(ctx, s, lmin, lmax, p, st, false);
+        } else {
+            // capture on the series' own stream (the caller's may be the
+            // legacy default stream, which cannot be captured), then launch
+            // the instantiated graph on the caller's stream
+            CK(cudaStreamBeginCapture(s.cap, cudaStreamCaptureModeThreadLocal));
+            cudaGraph_t g = nullptr;
+            try {
+                issue_profile<T>(ctx, s, lmin, lmax, p, s.cap, true);
+            } catch (...) {
+                cudaStreamEndCapture(s.cap, &g);
+                if (g) cudaGraphDestroy(g);
+                s.ws_valid = false;
+                throw;
+            }
+            CK(cudaStreamEndCapture(s.cap, &g));
+            const cudaError_t ei = cudaGraphInstantiateWithFlags(&s.exec, g, 0);
+            cudaGraphDestroy(g);
+            CK(ei);
+            CK(cudaGraphLaunch(s.exec, st));
+        }
+        s.ws_valid = true;
+        s.reuse = false;
+    }
     int32_t herr = 0;
-    CK(cudaMemcpyAsync(&herr, wait_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&herr, s.wait_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    const int NSTAT = s.nstat;
     std::vector<unsigned long long> hs((size_t)nL * NSTAT);
-    CK(cudaMemcpyAsync(hs.data(), dstats, hs.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hs.data(), s.dstats, hs.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    const bool motif_mode = o.mode == 1;
+    const bool disc_mode = o.mode == 2;
     if (herr != 0) {
         set_err(ctx, "a bounded wait in the band kernel ran out, or a row was left without its recompute");
         throw Fail{MAD_ETIMEOUT};
@@ -763,16 +991,20 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
         q.col_appends = (int64_t)h[7];
         q.second_pass_rows = (int64_t)h[0];
         q.direct_rows = (int64_t)h[9];
-        q.launches = (int64_t)host_launch[li];
-        q.band_ms = 0.0;
+        q.launches = (int64_t)s.host_launch[li];
+        q.band_ms = q.direct_ms = q.rows_ms = 0.0;
+        q.graph = s.exec ? 1 : 0;
     }
-    for (const Ev &e : evs) {
+    for (size_t e = 0; e < s.tev_li.size(); ++e) {
         float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e.a, e.b));
-        s.stats[e.li].band_ms += ms;
+        CK(cudaEventElapsedTime(&ms, s.tev[2 * e], s.tev[2 * e + 1]));
+        mad_length_stats &q = s.stats[s.tev_li[e] / 4];
+        switch (s.tev_li[e] % 4) {
+        case TK_BAND: q.band_ms += ms; break;
+        case TK_DIRECT: q.direct_ms += ms; break;
+        default: q.rows_ms += ms; break;
+        }
     }
-    s.vm = vm;
-    s.tab = tab;
     s.profiled = true;
 }
 
@@ -787,7 +1019,8 @@ Series &get_series(mad_ctx *ctx, int32_t idx)
 
 void profile_one(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStream_t st)
 {
-    if (ctx->opt.precision == MAD_FP32) profile_series<float>(ctx, s, lmin, lmax, p, st);
+    if (ctx->opt.precision == MAD_FP32 || ctx->opt.precision == MAD_SPLIT_TC)
+        profile_series<float>(ctx, s, lmin, lmax, p, st);
     else profile_series<double>(ctx, s, lmin, lmax, p, st);
 }
 
@@ -920,6 +1153,8 @@ MAD_API void mad_debug_wavefront_wait_limit(int32_t tries) { g_wave_limit.store(
 
 MAD_API void mad_debug_audit_error_bounds(int32_t on) { g_audit.store(on ? 1 : 0); }
 
+MAD_API void mad_set_graphs(int32_t on) { g_graphs.store(on ? 1 : 0); }
+
 MAD_API mad_status mad_profile(mad_ctx *ctx, int32_t lmin, int32_t lmax, int32_t p)
 {
     if (!ctx) { g_create_err = "ctx is NULL"; return MAD_EINVAL; }
@@ -995,19 +1230,15 @@ MAD_API mad_status mad_motifs(mad_ctx *ctx, int32_t series, int32_t k, mad_motif
         }
         cudaStream_t st = ctx->stream;
         const int64_t nblk = (s.n0 + 255) / 256;
-        std::vector<void *> tmp;
-        auto talloc = [&](size_t bytes) {
-            void *p = nullptr;
-            CK(cudaMalloc(&p, bytes));
-            tmp.push_back(p);
-            return p;
-        };
-        try {
-            int32_t *acc = (int32_t *)talloc(sizeof(int32_t) * 3 * k);
-            int32_t *picked = (int32_t *)talloc(sizeof(int32_t) * k);
-            double *bval = (double *)talloc(sizeof(double) * nblk);
-            int32_t *bidx = (int32_t *)talloc(sizeof(int32_t) * nblk);
-            double *rd = (double *)talloc(sizeof(double) * k);
+        {
+            Carve cv{{sizeof(int32_t) * 3 * k, sizeof(int32_t) * k, sizeof(double) * nblk, sizeof(int32_t) * nblk,
+                      sizeof(double) * k}};
+            std::vector<void *> b = rscratch(ctx, s, cv, st);
+            int32_t *acc = (int32_t *)b[0];
+            int32_t *picked = (int32_t *)b[1];
+            double *bval = (double *)b[2];
+            int32_t *bidx = (int32_t *)b[3];
+            double *rd = (double *)b[4];
             for (int r = 0; r < k; ++r)
                 launch_motif_round(s.vm, s.n0, ctx->opt.excl_num, ctx->opt.excl_den, acc, r, bval, bidx, picked, st);
             CK(cudaGetLastError());
@@ -1034,11 +1265,7 @@ MAD_API mad_status mad_motifs(mad_ctx *ctx, int32_t series, int32_t k, mad_motif
                 m.dist_recheck = hr[r];
             }
             *n_out = got;
-        } catch (...) {
-            for (void *p : tmp) cudaFree(p);
-            throw;
         }
-        for (void *p : tmp) cudaFree(p);
     });
 }
 
@@ -1168,26 +1395,14 @@ static void finish_discords(mad_ctx *ctx, Series &s, int k, int m, int stride, c
     if (!where.empty()) {
         const int nc = (int)where.size();
         const size_t ns = recheck_scratch(nc, m);
-        void *dreq = nullptr, *dout = nullptr, *dsd = nullptr, *dsj = nullptr;
-        cudaError_t e1 = cudaMalloc(&dreq, req.size() * sizeof(int32_t));
-        if (e1 == cudaSuccess) e1 = cudaMalloc(&dout, nc * sizeof(double));
-        if (e1 == cudaSuccess) e1 = cudaMalloc(&dsd, ns * sizeof(double));
-        if (e1 == cudaSuccess) e1 = cudaMalloc(&dsj, ns * sizeof(int32_t));
-        cudaError_t e3 = e1, e4 = cudaSuccess;
-        if (e1 == cudaSuccess) {
-            cudaMemcpyAsync(dreq, req.data(), req.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
-            launch_recheck_discords(s.x, s.n, (const int32_t *)dreq, nc, ctx->opt.excl_num, ctx->opt.excl_den,
-                                    (double *)dout, (double *)dsd, (int32_t *)dsj, m, st);
-            e3 = cudaMemcpyAsync(rec.data(), dout, nc * sizeof(double), cudaMemcpyDeviceToHost, st);
-            e4 = cudaStreamSynchronize(st);
-        }
-        cudaFree(dreq);
-        cudaFree(dout);
-        cudaFree(dsd);
-        cudaFree(dsj);
-        CK(e3);
-        CK(e4);
+        Carve cv{{req.size() * sizeof(int32_t), nc * sizeof(double), ns * sizeof(double), ns * sizeof(int32_t)}};
+        std::vector<void *> b = rscratch(ctx, s, cv, st);
+        CK(cudaMemcpyAsync(b[0], req.data(), req.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        launch_recheck_discords(s.x, s.n, (const int32_t *)b[0], nc, ctx->opt.excl_num, ctx->opt.excl_den,
+                                (double *)b[1], (double *)b[2], (int32_t *)b[3], m, st);
         CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(rec.data(), b[1], nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
     }
     size_t w = 0;
     for (int r = 0; r < k; ++r)
@@ -1483,6 +1698,13 @@ MAD_API void mad_destroy(mad_ctx *ctx)
         free_profile(s);
         if (s.own_x && s.x) cudaFree(s.x);
         s.x = nullptr;
+        for (cudaEvent_t e : s.tev) cudaEventDestroy(e);
+        for (cudaEvent_t e : s.sev)
+            if (e) cudaEventDestroy(e);
+        if (s.prep) cudaStreamDestroy(s.prep);
+        if (s.disc) cudaStreamDestroy(s.disc);
+        if (s.cap) cudaStreamDestroy(s.cap);
+        if (s.rscratch) cudaFree(s.rscratch);
     }
     delete ctx;
 }

@@ -18,7 +18,7 @@ def _fake_sample(w, seconds):
 def _args(**kw):
     a = dict(gpus=1, steps=2, warmup=3, impl="reference", workload="rw4096", precision="fp32", band_form=0,
              no_fp64_path=True, no_motif_path=True, no_discord_path=True, no_cpu_baseline=True, cpu_seconds=1.0,
-             p_sweep=None, ncu_case=None, mode=0)
+             p_sweep=None, ncu_case=None, mode=0, lrange=None, fp64_steps=3, e2e_steps=3)
     a.update(kw)
     return types.SimpleNamespace(**a)
 
@@ -41,6 +41,21 @@ def test_reference_line(monkeypatch, capsys):
                            "d2h_bytes_per_step": 0}
     import workloads
     assert line["config"] == bench.workload_config("rw4096", workloads.make("rw4096"))
+
+
+def test_reference_line_batch_and_range(monkeypatch, capsys):
+    # the batch workload's config describes its series; a stated sub-range
+    # of lengths shows up in both arms' config
+    monkeypatch.setattr(bench, "cpu_oracle_sample", _fake_sample)
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    assert bench.run_reference(_args(workload="batch256")) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["config"]["series"] == 256 and line["config"]["lengths_total"] > 256
+    assert bench.run_reference(_args(workload="seismic2m")) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert (line["config"]["lmin"], line["config"]["lmax"]) == bench.DEFAULT_RANGE["seismic2m"]
+    assert line["config"]["cells_per_step"] == 2097152 ** 2 * 9
 
 
 def test_reference_other_ranks_print_nothing(monkeypatch, capsys):
