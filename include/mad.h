@@ -174,7 +174,8 @@ typedef struct {
                                the recomputed rows' candidates) at this length */
     int32_t graph;          /* 1 if this profile ran as a replayed CUDA graph (a repeat of the
                                previous profile's shape, see mad_profile) */
-    int32_t reserved3;
+    int32_t band_rows;      /* rows per band of the matrix-profile kernel in this profile (chosen
+                               by the autotuner, see mad_set_autotune) */
 } mad_length_stats;
 
 /* Create a context for one series copied from host memory (FP64, n values).
@@ -377,6 +378,16 @@ MAD_API void mad_debug_audit_error_bounds(int32_t on);
  * (default on). Off: every profile launches its kernels one by one (the
  * workspace is still reused). Takes effect at the next mad_profile. */
 MAD_API void mad_set_graphs(int32_t on);
+
+/* Process-wide switch of the launch autotuner (default on). On: the first
+ * profile of a series of at most 32768 windows in a new size bucket (log2 of
+ * the window count, log2 of lmin, p, precision, mode) times a short trial
+ * profile for each candidate band height (1024, 512, 256 rows) and, on the
+ * tensor-core path, each direct-path routing threshold, and keeps the
+ * fastest for that bucket for the rest of the process. Off: the defaults
+ * (the tallest band that fits, the default routing). Results do not depend
+ * on the choice beyond FP32 rounding within the stated bounds. */
+MAD_API void mad_set_autotune(int32_t on);
 
 /* Human-readable description of the last error on ctx (or of the calling
  * thread's last mad_create* or mad_mth_nn_dist_noalloc error when ctx is

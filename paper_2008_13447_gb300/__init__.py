@@ -34,7 +34,7 @@ ABI_FUNCTIONS = ("mad_create", "mad_create_device", "mad_create_batch", "mad_pro
                  "mad_valmp", "mad_matrix_profile", "mad_stats",
                  "mad_mth_nn_dist_noalloc", "mad_motif_sets", "mad_observe", "mad_last_error",
                  "mad_destroy", "mad_debug_wavefront_wait_limit", "mad_debug_audit_error_bounds",
-                 "mad_set_graphs")
+                 "mad_set_graphs", "mad_set_autotune")
 
 
 class mad_options(C.Structure):
@@ -63,7 +63,7 @@ class mad_length_stats(C.Structure):
                 ("band_ms", C.c_double),
                 ("fp32_dq_max", C.c_double), ("skipped", C.c_int64), ("full_profile", C.c_int32),
                 ("reserved2", C.c_int32), ("dq_ratio_max", C.c_double), ("direct_ms", C.c_double),
-                ("rows_ms", C.c_double), ("graph", C.c_int32), ("reserved3", C.c_int32)]
+                ("rows_ms", C.c_double), ("graph", C.c_int32), ("band_rows", C.c_int32)]
 
 
 class mad_motif_set(C.Structure):
@@ -119,6 +119,8 @@ def library() -> C.CDLL:
         lib.mad_debug_audit_error_bounds.restype = None
         lib.mad_set_graphs.argtypes = [i32]
         lib.mad_set_graphs.restype = None
+        lib.mad_set_autotune.argtypes = [i32]
+        lib.mad_set_autotune.restype = None
         _lib = lib
     return _lib
 
@@ -274,7 +276,7 @@ def mad_stats(ctx, series, cap=1 << 16):
                  col_appends=s.col_appends, second_pass_rows=s.second_pass_rows, direct_rows=s.direct_rows,
                  band_ms=s.band_ms, fp32_dq_max=s.fp32_dq_max, skipped=s.skipped,
                  full_profile=s.full_profile, dq_ratio_max=s.dq_ratio_max, direct_ms=s.direct_ms,
-                 rows_ms=s.rows_ms, graph=s.graph) for s in out[:min(n.value, cap)]]
+                 rows_ms=s.rows_ms, graph=s.graph, band_rows=s.band_rows) for s in out[:min(n.value, cap)]]
 
 
 def mad_mth_nn_dist_noalloc(x_ptr, n, cells, m_max, out_ptr, excl=(1, 4), stream=None):
@@ -301,6 +303,11 @@ def mad_debug_audit_error_bounds(on):
 def mad_set_graphs(on):
     """CUDA-graph replay of repeated profiles (default on)."""
     library().mad_set_graphs(1 if on else 0)
+
+
+def mad_set_autotune(on):
+    """Launch autotuner for small series (default on)."""
+    library().mad_set_autotune(1 if on else 0)
 
 
 def mad_last_error(ctx=None):

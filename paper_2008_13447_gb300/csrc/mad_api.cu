@@ -18,7 +18,9 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <new>
 #include <string>
 #include <thread>
@@ -47,7 +49,7 @@ std::atomic<int> g_graphs{1};
 // from a CUDA graph.
 struct WsKey {
     int tsize = 0, lmin = 0, lmax = 0, p = 0, m_max = 0, k_max = 0, mode = 0, band_form = 0, keep = 0,
-        observe = 0, num = 0, den = 0, audit = 0, wave_limit = 0, tc = 0;
+        observe = 0, num = 0, den = 0, audit = 0, wave_limit = 0, tc = 0, rpl = 0, limf = 0;
     bool operator==(const WsKey &o) const { return std::memcmp(this, &o, sizeof(WsKey)) == 0; }
 };
 
@@ -81,6 +83,11 @@ struct Series {
     // scratch of the read-outs (grown, never shrunk)
     void *rscratch = nullptr;
     size_t rscratch_bytes = 0;
+    // launch parameters of the next profile (chosen by the autotuner)
+    int rpl = 0, limf = 0;
+    // pinned host buffer the error word and the counters are read back into
+    unsigned long long *hbuf = nullptr;
+    size_t hbuf_words = 0;
     Valmp vm{};
     DiscTable tab{};
     double *keep_nnd = nullptr;
@@ -294,7 +301,7 @@ void issue_profile(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStrea
     s.n0 = n0;
     const int m_max = o.m_max, k_max = o.k_max;
     const int nL = lmax - lmin + 1;
-    const int rpl = band_rpl<T>(p);
+    const int rpl = s.rpl;
     const int R = 32 * rpl * BAND_NW;
     const int nbins = band_nbins(p);
     const int SP = R < 1024 ? R : 1024;         // seed-row spacing (every band start)
@@ -703,7 +710,7 @@ void issue_profile(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStrea
         // the band kernel costs about R n_l cells at ALU speed, a direct row
         // n_l l multiply-adds (about 50x faster per lag on the tensor cores)
         {
-            const int per = tc ? 48 * R : 4 * R;
+            const int per = s.limf * R;
             sp.lim = per / l > 1 ? per / l : 1;
         }
         sp.force_direct = 0;
@@ -876,13 +883,103 @@ void issue_profile(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStrea
     s.tab = tab;
 }
 
-// Profile one series: validate, reuse the workspace while the key holds,
-// and issue the profile -- eagerly the first time (buffers allocated), into
-// a CUDA graph the second time with the same key (captured, instantiated,
-// launched), and by replaying that graph after. Then read back the error
-// word, the per-length counters and the kernel timings.
+// ------------------------------------------------------------- autotuner
+//
+// Launch parameters with a measurable effect and no effect on the results
+// (beyond FP32 rounding within the stated bounds): the band height R =
+// 256 * rpl rows (smaller bands give small series more parallel work units,
+// larger ones fewer per-column overheads per cell) and the number of rows to
+// recompute per band below which they take the direct path (limf * R / l;
+// the tensor-core direct path is much cheaper per row than the FP32 one).
+// For each bucket (type, path, log2 of the windows, log2 of lmin, p, mode)
+// the first profile times a short trial profile (lmin .. lmin + 3) for each
+// candidate and keeps the fastest for the rest of the process.
+struct TuneKey {
+    int tsize, tc, nb, lb, p, mode;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(tsize, tc, nb, lb, p, mode) < std::tie(o.tsize, o.tc, o.nb, o.lb, o.p, o.mode);
+    }
+};
+struct TuneVal { int rpl, limf; float ms; };
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+// mad_set_autotune: tune (1, default) or take the defaults (0)
+std::atomic<int> g_autotune{1};
+
+int ilog2(int64_t v)
+{
+    int b = 0;
+    while (((int64_t)1 << (b + 1)) <= v) ++b;
+    return b;
+}
+
+template <typename T> void start_profile(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStream_t st);
+void finish_profile(mad_ctx *ctx, Series &s);
+
 template <typename T>
-void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStream_t st)
+void choose_launch(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStream_t st)
+{
+    const mad_options &o = ctx->opt;
+    const bool tc = o.precision == MAD_SPLIT_TC;
+    const int max_rpl = band_rpl<T>(p);
+    const int def_limf = tc ? 48 : 4;
+    s.rpl = max_rpl;
+    s.limf = def_limf;
+    const int64_t n0 = s.n - lmin + 1;
+    // small series only: large ones always take the full band height (its
+    // seed rows and units already fill the GPU)
+    if (!g_autotune.load() || n0 > 32768) return;
+    const TuneKey key{(int)sizeof(T), tc ? 1 : 0, ilog2(n0), ilog2(lmin), p, o.mode};
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it == g_tune.end()) {
+        std::vector<std::pair<int, int>> cand;
+        for (int r : {4, 2, 1})
+            if (r <= max_rpl)
+                for (int lf : tc ? std::vector<int>{16, 48, 128} : std::vector<int>{4}) cand.push_back({r, lf});
+        const int tmax = lmax < lmin + 3 ? lmax : lmin + 3;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        TuneVal best{max_rpl, def_limf, 1e30f};
+        try {
+            for (auto &c : cand) {
+                s.rpl = c.first;
+                s.limf = c.second;
+                for (int rep = 0; rep < 2; ++rep) {   // the first run allocates and loads modules
+                    CK(cudaEventRecord(e0, st));
+                    start_profile<T>(ctx, s, lmin, tmax, p, st);
+                    CK(cudaEventRecord(e1, st));
+                    CK(cudaStreamSynchronize(st));
+                    finish_profile(ctx, s);
+                }
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best.ms) best = TuneVal{c.first, c.second, ms};
+            }
+        } catch (...) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            throw;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        free_profile(s);
+        it = g_tune.emplace(key, best).first;
+    }
+    s.rpl = it->second.rpl;
+    s.limf = it->second.limf;
+}
+
+// Start one profile of a series on stream st: validate, reuse the workspace
+// while the key holds, and issue the profile -- eagerly the first time
+// (buffers allocated), into a CUDA graph the second time with the same key
+// (captured, instantiated, launched), and by replaying that graph after;
+// then queue the read-back of the error word and the per-length counters
+// into pinned host memory. finish_profile reads them once st is done.
+template <typename T>
+void start_profile(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStream_t st)
 {
     const mad_options &o = ctx->opt;
     const int num = o.excl_num, den = o.excl_den;
@@ -894,6 +991,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
     const int64_t Emax = excl_zone(lmax, num, den);
     REQUIRE(n - lmax + 1 > 2 * Emax + 2, "series too short for lmax and the exclusion zone (need n-lmax+1 > 2E(lmax)+2)");
     REQUIRE(n < (int64_t)INT32_MAX - 4096, "series longer than 2^31 - 4096 samples");
+    REQUIRE(s.rpl >= 1 && s.limf >= 1, "launch parameters not chosen");
 
     WsKey key{};
     key.tsize = (int)sizeof(T);
@@ -911,12 +1009,16 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
     key.den = den;
     key.audit = g_audit.load();
     key.wave_limit = g_wave_limit.load();
+    key.rpl = s.rpl;
+    key.limf = s.limf;
     const bool same = s.ws_valid && s.key == key;
     if (!same) {
         free_profile(s);
         s.key = key;
     }
     s.profiled = false;
+    s.lmin = lmin;
+    s.lmax = lmax;
     const int nL = lmax - lmin + 1;
     s.stats.assign(nL, mad_length_stats{});
     // streams and events of the pipeline, created once per series
@@ -957,12 +1059,30 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
         s.ws_valid = true;
         s.reuse = false;
     }
-    int32_t herr = 0;
-    CK(cudaMemcpyAsync(&herr, s.wait_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    const size_t words = 1 + (size_t)nL * s.nstat;
+    if (words > s.hbuf_words) {
+        if (s.hbuf) cudaFreeHost(s.hbuf);
+        s.hbuf = nullptr;
+        s.hbuf_words = 0;
+        CK(cudaHostAlloc(reinterpret_cast<void **>(&s.hbuf), words * sizeof(unsigned long long), cudaHostAllocDefault));
+        s.hbuf_words = words;
+    }
+    s.hbuf[0] = 0;
+    CK(cudaMemcpyAsync(s.hbuf, s.wait_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(s.hbuf + 1, s.dstats, (size_t)nL * s.nstat * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       st));
+}
+
+// The host side of a finished profile (its stream synchronised): error word,
+// per-length counters, kernel timings.
+void finish_profile(mad_ctx *ctx, Series &s)
+{
+    const mad_options &o = ctx->opt;
+    const int lmin = s.lmin, nL = s.lmax - s.lmin + 1;
+    const int64_t n = s.n;
     const int NSTAT = s.nstat;
-    std::vector<unsigned long long> hs((size_t)nL * NSTAT);
-    CK(cudaMemcpyAsync(hs.data(), s.dstats, hs.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    const int32_t herr = (int32_t)(s.hbuf[0] & 0xffffffffu);
+    const unsigned long long *hs = s.hbuf + 1;
     const bool motif_mode = o.mode == 1;
     const bool disc_mode = o.mode == 2;
     if (herr != 0) {
@@ -994,6 +1114,7 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
         q.launches = (int64_t)s.host_launch[li];
         q.band_ms = q.direct_ms = q.rows_ms = 0.0;
         q.graph = s.exec ? 1 : 0;
+        q.band_rows = 32 * BAND_NW * s.rpl;
     }
     for (size_t e = 0; e < s.tev_li.size(); ++e) {
         float ms = 0.f;
@@ -1008,6 +1129,15 @@ void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStre
     s.profiled = true;
 }
 
+template <typename T>
+void profile_series(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStream_t st)
+{
+    choose_launch<T>(ctx, s, lmin, lmax, p, st);
+    start_profile<T>(ctx, s, lmin, lmax, p, st);
+    CK(cudaStreamSynchronize(st));
+    finish_profile(ctx, s);
+}
+
 Series &get_series(mad_ctx *ctx, int32_t idx)
 {
     if (idx < 0 || idx >= (int32_t)ctx->series.size()) {
@@ -1017,11 +1147,27 @@ Series &get_series(mad_ctx *ctx, int32_t idx)
     return ctx->series[idx];
 }
 
+bool fp32_kernels(const mad_ctx *ctx)
+{
+    return ctx->opt.precision == MAD_FP32 || ctx->opt.precision == MAD_SPLIT_TC;
+}
+
 void profile_one(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStream_t st)
 {
-    if (ctx->opt.precision == MAD_FP32 || ctx->opt.precision == MAD_SPLIT_TC)
-        profile_series<float>(ctx, s, lmin, lmax, p, st);
+    if (fp32_kernels(ctx)) profile_series<float>(ctx, s, lmin, lmax, p, st);
     else profile_series<double>(ctx, s, lmin, lmax, p, st);
+}
+
+// Batch: tune and start (no host wait) one series on stream st.
+void start_one(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStream_t st)
+{
+    if (fp32_kernels(ctx)) {
+        choose_launch<float>(ctx, s, lmin, lmax, p, st);
+        start_profile<float>(ctx, s, lmin, lmax, p, st);
+    } else {
+        choose_launch<double>(ctx, s, lmin, lmax, p, st);
+        start_profile<double>(ctx, s, lmin, lmax, p, st);
+    }
 }
 
 template <typename F>
@@ -1155,6 +1301,8 @@ MAD_API void mad_debug_audit_error_bounds(int32_t on) { g_audit.store(on ? 1 : 0
 
 MAD_API void mad_set_graphs(int32_t on) { g_graphs.store(on ? 1 : 0); }
 
+MAD_API void mad_set_autotune(int32_t on) { g_autotune.store(on ? 1 : 0); }
+
 MAD_API mad_status mad_profile(mad_ctx *ctx, int32_t lmin, int32_t lmax, int32_t p)
 {
     if (!ctx) { g_create_err = "ctx is NULL"; return MAD_EINVAL; }
@@ -1169,12 +1317,14 @@ MAD_API mad_status mad_profile_batch(mad_ctx *ctx, const int32_t *lmin, const in
     if (!ctx) { g_create_err = "ctx is NULL"; return MAD_EINVAL; }
     return run_guarded(ctx, [&] {
         REQUIRE(lmin != nullptr && lmax != nullptr, "lmin / lmax arrays are NULL");
-        // Series are independent: a few host threads, each with its own
-        // stream, profile them concurrently (small series, whose per-length
-        // pipelines are latency-bound, overlap one another). Every stream
-        // first waits for the context's stream (where the inputs were
-        // written); each profile synchronises its own stream before it
-        // returns, so all work is done when the threads are joined.
+        // Series are independent. Eight host threads, each with its own
+        // stream, start the series' profiles without waiting on the device:
+        // a series profiled before with the same shape is one graph launch
+        // (its whole per-length sequence), so the series run back to back on
+        // eight streams and the GPU interleaves them. Every stream first
+        // waits for the context's stream (where the inputs were written);
+        // each thread then waits for its stream and reads its series'
+        // counters back.
         const int count = (int)ctx->series.size();
         const int nw = count < 8 ? count : 8;
         std::vector<cudaStream_t> ws(nw, nullptr);
@@ -1185,7 +1335,10 @@ MAD_API mad_status mad_profile_batch(mad_ctx *ctx, const int32_t *lmin, const in
             ~Guard()
             {
                 for (cudaStream_t q : ws)
-                    if (q) cudaStreamDestroy(q);
+                    if (q) {
+                        cudaStreamSynchronize(q);
+                        cudaStreamDestroy(q);
+                    }
                 if (ev) cudaEventDestroy(ev);
             }
         } guard{ws, ready};
@@ -1200,15 +1353,15 @@ MAD_API mad_status mad_profile_batch(mad_ctx *ctx, const int32_t *lmin, const in
         for (int t = 0; t < nw; ++t)
             th.emplace_back([&, t] {
                 cudaSetDevice(ctx->device);
-                for (int k = t; k < count && res[t] == MAD_OK; k += nw) {
-                    try {
-                        profile_one(ctx, ctx->series[k], lmin[k], lmax[k], p, ws[t]);
-                    } catch (const Fail &e) {
-                        res[t] = e.st;
-                    } catch (...) {
-                        set_err(ctx, "internal error");
-                        res[t] = MAD_EINTERNAL;
-                    }
+                try {
+                    for (int k = t; k < count; k += nw) start_one(ctx, ctx->series[k], lmin[k], lmax[k], p, ws[t]);
+                    CK(cudaStreamSynchronize(ws[t]));
+                    for (int k = t; k < count; k += nw) finish_profile(ctx, ctx->series[k]);
+                } catch (const Fail &e) {
+                    res[t] = e.st;
+                } catch (...) {
+                    set_err(ctx, "internal error");
+                    res[t] = MAD_EINTERNAL;
                 }
             });
         for (std::thread &x : th) x.join();
@@ -1705,6 +1858,7 @@ MAD_API void mad_destroy(mad_ctx *ctx)
         if (s.disc) cudaStreamDestroy(s.disc);
         if (s.cap) cudaStreamDestroy(s.cap);
         if (s.rscratch) cudaFree(s.rscratch);
+        if (s.hbuf) cudaFreeHost(s.hbuf);
     }
     delete ctx;
 }

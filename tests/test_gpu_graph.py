@@ -97,3 +97,52 @@ def test_replayed_profile_reads_new_series_values():
         assert np.allclose(vm["norm"], ref["norm"], rtol=1e-9, atol=1e-12)
     finally:
         mad.mad_destroy(ctx)
+
+
+def test_batch_replays_graphs_and_matches_the_oracle():
+    # uneven series, each with its own range: the second batch profile
+    # replays every series' graph and gives the same results as the first
+    series = [workloads.random_walk(1500 + 700 * s, 160 + s) if s % 2 == 0 else workloads.ar2(1800 + 500 * s, 160 + s)
+              for s in range(10)]
+    lmin = [20 + 3 * s for s in range(10)]
+    lmax = [a + 6 for a in lmin]
+    ctx = mad.mad_create_batch(series, precision=mad.MAD_FP64, k_max=3, m_max=1)
+    try:
+        res = []
+        for rep in range(3):
+            mad.mad_profile_batch(ctx, lmin, lmax, 5)
+            res.append([mad.mad_valmp(ctx, s, len(series[s]) - lmin[s] + 1) for s in range(10)])
+            st = [mad.mad_stats(ctx, s) for s in range(10)]
+            assert all(q["graph"] == (1 if rep > 0 else 0) for sts in st for q in sts)
+        for s in range(10):
+            for key in ("dist", "norm", "len", "nn"):
+                assert np.array_equal(res[0][s][key], res[2][s][key])
+        for s in (0, 3, 9):
+            ref = oracle.valmp_plain(series[s], lmin[s], lmax[s])
+            assert np.allclose(res[2][s]["norm"], ref["norm"], rtol=1e-9, atol=1e-12)
+    finally:
+        mad.mad_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [mad.MAD_FP32, mad.MAD_SPLIT_TC], ids=["fp32", "tc"])
+def test_autotuned_launch_agrees_with_defaults(prec):
+    # the tuner picks a band height (and on the tensor-core path a routing
+    # threshold) per size bucket; the results agree with the defaults'
+    x = workloads.ecg_like(5000, 165, period=55.0)
+    out = {}
+    for tune in (0, 1):
+        mad.mad_set_autotune(tune)
+        try:
+            ctx = mad.mad_create(x, precision=prec, k_max=3, m_max=1)
+            try:
+                mad.mad_profile(ctx, 50, 58, 6)
+                st = mad.mad_stats(ctx, 0)
+                out[tune] = (mad.mad_valmp(ctx, 0, len(x) - 50 + 1), st[0]["band_rows"])
+            finally:
+                mad.mad_destroy(ctx)
+        finally:
+            mad.mad_set_autotune(1)
+    assert out[0][1] == 1024 and out[1][1] in (256, 512, 1024)
+    assert np.all(np.abs(out[0][0]["norm"] - out[1][0]["norm"]) <= 2e-4)
+    ref = oracle.valmp_plain(x, 50, 58)
+    assert np.all(np.abs(out[1][0]["norm"] - ref["norm"]) <= 1e-4)
