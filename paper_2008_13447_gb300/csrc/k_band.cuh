@@ -24,11 +24,12 @@
 // Layout: a band is R = 32 * RPL * NW consecutive rows. Lane t of warp w
 // owns rows rfirst(w) + t*RPL + [0, RPL); all lanes of a warp walk the same
 // column j at a time, so the row r's predecessor C(r-1, j-1) sits in the
-// same lane (previous row, previous column) or in lane t-1 (one shuffle), and
-// the first row of warp w takes it from warp w-1 through shared memory, one
-// chunk of CH columns behind (a wavefront over the warps, one barrier per
-// chunk). Per-column data (df, dg, inv) is staged per chunk in shared memory
-// and read as broadcasts.
+// same lane (previous row, previous column) or in lane t-1 (one shuffle). The
+// first row of warp w takes it from the seed row at rfirst(w) when there is
+// one (seed rows every A.sp rows, down to one per warp), else from warp w-1
+// through shared memory, one chunk of CH columns behind (a wavefront over
+// the unseeded warps, synchronised pairwise by mbarriers). Per-column data
+// (df, dg, inv) is staged per chunk in shared memory and read as broadcasts.
 #pragma once
 #include "kernels.cuh"
 
@@ -134,7 +135,7 @@ constexpr bool BAND_PAIR = true;   // two columns per hit test in the common cas
 //             column's threshold, staged in cd.pad, appended to row j's
 //             candidate list in global memory).
 template <typename T, int RPL, int NW, int MODE, bool DIAG>
-__device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *cbuf, T tp, T *bout, int lane, int w,
+__device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *cbuf, T tp, T *bout, int lane, bool feeds,
                                            int64_t cs, int64_t rbase, int rl0, T (&C)[RPL], const T (&dfr)[RPL],
                                            const T (&dgr)[RPL], T (&th)[RPL], const T (&invr)[RPL],
                                            T (&runmax)[RPL], T *lkey, int32_t *lj, int32_t *lcnt, unsigned &ninsert)
@@ -148,7 +149,7 @@ __device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *c
 #pragma unroll
         for (int a = RPL - 1; a >= 1; --a) C[a] = fma(dfr[a], cd.dg, fma(cd.df, dgr[a], C[a - 1]));
         C[0] = fma(dfr[0], cd.dg, fma(cd.df, dgr[0], v));
-        if (w < NW - 1 && lane == 31) bout[c] = C[RPL - 1];
+        if (feeds && lane == 31) bout[c] = C[RPL - 1];
         if (MODE == MODE_BINS) {
 #pragma unroll
             for (int a = 0; a < RPL; ++a) {
@@ -249,11 +250,11 @@ __device__ __forceinline__ void store_pair(double *p, double a, double b)
 
 template <typename T, int RPL, int NW>
 __device__ __forceinline__ void band_chunk_pair(const BandArgs<T> &A, const Col<T> *cbuf, T tp, T *bout, int lane,
-                                                int w, int64_t cs, int64_t rbase, int rl0, T (&C)[RPL],
+                                                bool feeds, int64_t cs, int64_t rbase, int rl0, T (&C)[RPL],
                                                 const T (&dfr)[RPL], const T (&dgr)[RPL], T (&th)[RPL], T *lkey,
                                                 int32_t *lj, int32_t *lcnt, unsigned &ninsert)
 {
-    const bool send = w < NW - 1 && lane == 31;
+    const bool send = feeds && lane == 31;
 #pragma unroll
     for (int c = 0; c < CH; c += 2) {
         const Col<T> cd0 = cbuf[c];
@@ -341,6 +342,12 @@ __global__ void __launch_bounds__(NW * 32, band_min_blocks<T, RPL>()) k_band(con
     int32_t *lj = reinterpret_cast<int32_t *>(lkey + R * A.p);
     int32_t *lcnt = lj + R * A.p;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // Seed rows sit every A.sp rows (a multiple of the rows per warp): a warp
+    // whose first row is one starts every chain from it; a warp below a
+    // warp that is not seeded takes its top edge from that warp. So every
+    // chain is at most A.sp steps long.
+    const bool seeded = ((int64_t)w * 32 * RPL) % A.sp == 0;
+    const bool feeds = w < NW - 1 && ((int64_t)(w + 1) * 32 * RPL) % A.sp != 0;
     const int nb_active = *A.nbands;
     // The symmetric form walks all bands and only the upper triangle; it is
     // used when at least half of the rows need recomputing.
@@ -410,7 +417,10 @@ __global__ void __launch_bounds__(NW * 32, band_min_blocks<T, RPL>()) k_band(con
         const int64_t rbase = rfirst + lane * RPL;
         const int rl0 = w * 32 * RPL + lane * RPL;
         const T *sleft = A.seed + (c0 / A.sp) * A.spitch;
-        const T *stop = A.seed + (i0 / A.sp) * A.spitch;
+        // a warp whose first row is a seed row starts from it (like the
+        // band's first warp); the others take their top edge from the warp
+        // above through the ring
+        const T *stop = A.seed + (rfirst / A.sp) * A.spitch;
 
         T C[RPL], dfr[RPL], dgr[RPL], th[RPL], runmax[RPL], invr[RPL];
 #pragma unroll
@@ -430,7 +440,7 @@ __global__ void __launch_bounds__(NW * 32, band_min_blocks<T, RPL>()) k_band(con
         // form carries the column's threshold in the spare field)
         Col<T> ncol = A.col[c0 + lane];
         if (SYM) ncol.pad = A.thr[c0 + lane];
-        T ntop = w == 0 ? stop[c0 + lane] : T(0);
+        T ntop = seeded ? stop[c0 + lane] : T(0);
 
         for (int q = 0; q < nchunk; ++q, ++qg) {
             const int slot = (int)(qg % NSLOT);
@@ -443,7 +453,7 @@ __global__ void __launch_bounds__(NW * 32, band_min_blocks<T, RPL>()) k_band(con
                 ncol = A.col[cs + CH + lane];
                 if (SYM) ncol.pad = A.thr[cs + CH + lane];
             }
-            if (w == 0) {
+            if (seeded) {
                 tp = ntop;
                 if (q + 1 < nchunk) ntop = stop[cs + CH + lane];
             } else {
@@ -455,7 +465,7 @@ __global__ void __launch_bounds__(NW * 32, band_min_blocks<T, RPL>()) k_band(con
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&mempty[w * NSLOT + slot]);   // slot free again
             }
-            if (w < NW - 1) mbar_wait(&mempty[(w + 1) * NSLOT + slot], par ^ 1u, A.err, A.wave_limit);  // slot free
+            if (feeds) mbar_wait(&mempty[(w + 1) * NSLOT + slot], par ^ 1u, A.err, A.wave_limit);  // slot free
             __syncwarp();
             T *bout = bbuf + ((w + 1 < NW ? w + 1 : 0) * NSLOT + slot) * CH;
             // does this warp's row range meet the exclusion zone in this chunk?
@@ -463,15 +473,15 @@ __global__ void __launch_bounds__(NW * 32, band_min_blocks<T, RPL>()) k_band(con
             // (symmetric form: everything not wholly above the zone is tested cell by cell)
             const bool diag = SYM ? !(cs > rhi + A.E) : (cs <= rhi + A.E) && (cs + CH - 1 >= rlo - A.E);
             if (diag)
-                band_chunk<T, RPL, NW, MODE, true>(A, cbuf, tp, bout, lane, w, cs, rbase, rl0, C, dfr, dgr, th,
+                band_chunk<T, RPL, NW, MODE, true>(A, cbuf, tp, bout, lane, feeds, cs, rbase, rl0, C, dfr, dgr, th,
                                                    invr, runmax, lkey, lj, lcnt, ninsert);
             else if (MODE == MODE_TOPP && BAND_PAIR)
-                band_chunk_pair<T, RPL, NW>(A, cbuf, tp, bout, lane, w, cs, rbase, rl0, C, dfr, dgr, th, lkey, lj,
+                band_chunk_pair<T, RPL, NW>(A, cbuf, tp, bout, lane, feeds, cs, rbase, rl0, C, dfr, dgr, th, lkey, lj,
                                             lcnt, ninsert);
             else
-                band_chunk<T, RPL, NW, MODE, false>(A, cbuf, tp, bout, lane, w, cs, rbase, rl0, C, dfr, dgr, th,
+                band_chunk<T, RPL, NW, MODE, false>(A, cbuf, tp, bout, lane, feeds, cs, rbase, rl0, C, dfr, dgr, th,
                                                     invr, runmax, lkey, lj, lcnt, ninsert);
-            if (w < NW - 1 && lane == 31) mbar_arrive(&mfull[(w + 1) * NSLOT + slot]);   // chunk q written
+            if (feeds && lane == 31) mbar_arrive(&mfull[(w + 1) * NSLOT + slot]);   // chunk q written
             if (BINS) {
                 const int bin = (int)((cs / CH) % nbins);
 #pragma unroll

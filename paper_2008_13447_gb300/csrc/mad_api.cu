@@ -304,7 +304,20 @@ void issue_profile(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStrea
     const int rpl = s.rpl;
     const int R = 32 * rpl * BAND_NW;
     const int nbins = band_nbins(p);
-    const int SP = R < 1024 ? R : 1024;         // seed-row spacing (every band start)
+    // Seed-row spacing: the smallest power of two from one warp's rows (at
+    // least 128) up to the band height whose seed rows (two copies in T and
+    // the FP64 master) fit in 16 GB. Every chain of the band kernel then has
+    // at most SP steps, which is what its error bound scales with; one seed
+    // row per warp also removes the wavefront between the warps.
+    int SP = R;
+    for (int sp = 32 * rpl > 128 ? 32 * rpl : 128; sp <= R; sp *= 2) {
+        const double rows = (double)((n0 + sp - 1) / sp);
+        const double bytes = rows * (double)(round_up(n0, R) + R + CH) * (2.0 * sizeof(T) + 8.0);
+        if (bytes <= 16e9) {
+            SP = sp;
+            break;
+        }
+    }
     const int64_t K = (n0 + SP - 1) / SP;       // seed rows
     const int64_t KB = (n0 + R - 1) / R;        // bands
     const int64_t npad = round_up(n0, R) + R + CH;
@@ -336,7 +349,7 @@ void issue_profile(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStrea
     double *isdb[2] = {dalloc<double>(ctx, s, n0), dalloc<double>(ctx, s, n0)};
     float *xh = dalloc<float>(ctx, s, n), *xl = dalloc<float>(ctx, s, n);
     const int audit = g_audit.load() ? 1 : 0;
-    const double dq0 = Precision<T>::dq0(R, lmax);
+    const double dq0 = Precision<T>::dq0(SP, lmax);
     const ErrModel emb[2] = {
         {kappab[0], kmaxb[0], dq0, Precision<T>::rel_tol, Precision<T>::abs_coef, audit},
         {kappab[1], kmaxb[1], dq0, Precision<T>::rel_tol, Precision<T>::abs_coef, audit}};
@@ -551,7 +564,7 @@ void issue_profile(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStrea
             k_stats_step<<<(unsigned)((nl + 255) / 256), 256, 0, side.prep>>>(s.x, nl, l, mu[b ^ 1], m2[b ^ 1],
                                                                              mu[b], m2[b]);
         launch_coldata<T>(s.x, nl, npad, l, mu[b], m2[b], run, colb[b], isdb[b], side.prep);
-        launch_kappa(s.x, mu[b], m2[b], run, nl, l, R, m2blk, kappab[b], kmaxb[b], side.prep);
+        launch_kappa(s.x, mu[b], m2[b], run, nl, l, SP, m2blk, kappab[b], kmaxb[b], side.prep);
         if (l == lmin) {
             // seed rows computed directly once, in FP64; every later length
             // steps them by one co-moment update
