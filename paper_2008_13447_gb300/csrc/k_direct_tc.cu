@@ -18,9 +18,12 @@
 // shared memory by the bulk-copy engine (cp.async.bulk, from an image the
 // prep kernel wrote in the swizzled layout), the column operand is expanded
 // from the series by the block's threads, and one thread issues 4 x 3 MMAs
-// (M = 128, N = 256, K = 16) into one TMEM accumulator. Then 4 warps read the
-// accumulator back (tcgen05.ld, one row per thread), form the correlation and
-// its error bound, and keep each row's p best keys over the column block.
+// (M = 128, N = 256, K = 16) into one TMEM accumulator. Then the warps read
+// the accumulator back (tcgen05.ld: warp w reads TMEM lanes 32 (w mod 4) ..,
+// one row per thread; with p <= 32 the eight warps split the 256 columns in
+// two halves), form the correlation and its error bound, and keep each
+// row's p best keys over the column block (the halves' lists merged at the
+// end of the block).
 //
 // Error bound of a kept correlation (in q units), from the arithmetic above:
 // the pair representation (|a - hi - lo| <= 2^-22 |a| per operand, the
@@ -230,9 +233,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_direct_tc(TcArgs A)
     unsigned char *sb = sa + 2 * A_TILE_BYTES;           // [2][B_TILE_BYTES]
     __half *shift = reinterpret_cast<__half *>(sb + 2 * B_TILE_BYTES);   // [2][8][SHIFT_LEN]
     ColC *cc = reinterpret_cast<ColC *>(shift + 2 * 8 * SHIFT_LEN);      // [TC_N]
-    float *lk = reinterpret_cast<float *>(cc + TC_N);                   // [TC_M][p]
-    int32_t *lj = reinterpret_cast<int32_t *>(lk + TC_M * p);
-    float *ld = reinterpret_cast<float *>(lj + TC_M * p);
+    // column halves of the epilogue (threads per row) and each thread's list
+    const int H = p <= 32 ? 2 : 1;
+    float *lk = reinterpret_cast<float *>(cc + TC_N);                   // [H][TC_M][p]
+    int32_t *lj = reinterpret_cast<int32_t *>(lk + H * TC_M * p);
+    float *ld = reinterpret_cast<float *>(lj + H * TC_M * p);
     __shared__ __align__(8) uint64_t bar_a, bar_mma;
     __shared__ uint32_t tmem_base;
     __shared__ float red[TC_THREADS / 32];
@@ -261,13 +266,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_direct_tc(TcArgs A)
         const int rt = (int)(item / A.nblk);
         const int cb = (int)(item % A.nblk);
         const int64_t cb0 = (int64_t)cb * TC_COLS;
-        // this thread's row (epilogue warps 0..3: TMEM lane = tid)
-        const int64_t pos = (int64_t)rt * TC_M + tid;
-        const bool erow = tid < TC_M && pos < nrows;
+        // this thread's row (TMEM lane m = tid mod 128) and column half h
+        const int m = tid & (TC_M - 1), h = tid / TC_M;
+        const bool ethread = h < H;
+        const int64_t pos = (int64_t)rt * TC_M + m;
+        const bool erow = ethread && pos < nrows;
         const int64_t r = erow ? A.rows[pos] : -1;
         const float asum = erow ? A.asum[pos] : 0.0f;
         const float sq = erow ? A.sqm2[pos] : 0.0f;
-        const float th = erow ? (float)A.thr[r] : 0.0f;
+        // threshold in correlation units (listed rows are not flat: sq > 0)
+        const float thq = erow ? (float)A.thr[r] / sq : 0.0f;
+        const int64_t exlo = r - A.E, exhi = r + A.E;   // trivial matches of the row
+        float *mk = lk + (h * TC_M + m) * p;
+        int32_t *mj = lj + (h * TC_M + m) * p;
+        float *md = ld + (h * TC_M + m) * p;
         int cnt = 0;
         for (int st0 = 0; st0 < TC_COLS / TC_N && ok; ++st0) {
             const int64_t j0 = cb0 + (int64_t)st0 * TC_N;
@@ -365,21 +377,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_direct_tc(TcArgs A)
                 if (!ok) break;
             }
             if (!ok) break;
-            // ---- epilogue: one row per thread of warps 0..3, 32 columns at a time
-            if (tid < TC_M) {
-                for (int c0 = 0; c0 < TC_N; c0 += 32) {
+            // ---- epilogue: one row per thread, the thread's column half, 32
+            // columns per TMEM load; candidates where q + dq_j beats the
+            // threshold, then the validity checks
+            if (ethread) {
+                const int cw = TC_N / H;
+                for (int c0 = h * cw; c0 < (h + 1) * cw; c0 += 32) {
                     float v[32];
                     __syncwarp();
-                    tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+                    tc_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0, v);
                     if (!erow) continue;
 #pragma unroll
                     for (int c = 0; c < 32; ++c) {
-                        const int64_t j = j0 + c0 + c;
                         const ColC k = cc[c0 + c];
-                        const float q = fmaf(-k.c, asum, v[c]) * k.g;
-                        if ((q + k.dq) * sq > th && j < A.nl && nontrivial(r, j, A.E))
-                            list_insert<float>(lk + tid * p, lj + tid * p, ld + tid * p, cnt, p, q * sq, (int32_t)j,
-                                               k.dq);
+                        const float t = fmaf(-k.c, asum, v[c]);
+                        if (fmaf(t, k.g, k.dq) > thq) {
+                            const int64_t j = j0 + c0 + c;
+                            if (j < A.nl && (j < exlo || j > exhi))
+                                list_insert<float>(mk, mj, md, cnt, p, t * k.g * sq, (int32_t)j, k.dq);
+                        }
                     }
                 }
             }
@@ -387,15 +403,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_direct_tc(TcArgs A)
             __syncthreads();
             tc_fence_after();
         }
-        // ---- this item's per-row lists
-        if (erow && ok) {
+        // ---- this item's per-row lists: the halves merged by (key desc,
+        // offset asc), the p best written
+        __shared__ int hcnt[TC_M];
+        if (h == 1) hcnt[m] = cnt;
+        __syncthreads();
+        if (erow && h == 0 && ok) {
             const int64_t slot = pos * A.nblk + cb;
-            for (int e = 0; e < cnt; ++e) {
-                A.okey[slot * p + e] = lk[tid * p + e];
-                A.oj[slot * p + e] = lj[tid * p + e];
-                A.odq[slot * p + e] = ld[tid * p + e];
+            const float *bk = lk + (TC_M + m) * p;
+            const int32_t *bj = lj + (TC_M + m) * p;
+            const float *bd = ld + (TC_M + m) * p;
+            const int nb = H > 1 ? hcnt[m] : 0;
+            int ia = 0, ib = 0, e = 0;
+            for (; e < p && (ia < cnt || ib < nb); ++e) {
+                bool takea = ib >= nb;
+                if (!takea && ia < cnt) takea = mk[ia] > bk[ib] || (mk[ia] == bk[ib] && mj[ia] < bj[ib]);
+                if (takea) {
+                    A.okey[slot * p + e] = mk[ia];
+                    A.oj[slot * p + e] = mj[ia];
+                    A.odq[slot * p + e] = md[ia];
+                    ++ia;
+                } else {
+                    A.okey[slot * p + e] = bk[ib];
+                    A.oj[slot * p + e] = bj[ib];
+                    A.odq[slot * p + e] = bd[ib];
+                    ++ib;
+                }
             }
-            A.ocnt[slot] = cnt;
+            A.ocnt[slot] = e;
         }
         __syncthreads();
     }
@@ -415,8 +450,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_direct_tc(TcArgs A)
 
 size_t tc_smem_bytes(int p)
 {
+    const int H = p <= 32 ? 2 : 1;
     return 1024 + 2 * (size_t)A_TILE_BYTES + 2 * (size_t)B_TILE_BYTES + 2 * 8 * SHIFT_LEN * sizeof(__half) +
-           TC_N * sizeof(ColC) + (size_t)TC_M * p * (sizeof(float) + sizeof(int32_t) + sizeof(float));
+           TC_N * sizeof(ColC) + (size_t)H * TC_M * p * (sizeof(float) + sizeof(int32_t) + sizeof(float));
 }
 
 size_t tc_aimg_bytes(int64_t max_rows, int lmax)
