@@ -331,8 +331,18 @@ void issue_profile(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStrea
     // buffered by length parity: length l+1's are prepared on a side stream
     // while length l's band kernel runs
     Col<T> *colb[2] = {dalloc<Col<T>>(ctx, s, npad), dalloc<Col<T>>(ctx, s, npad)};
-    T *seedb[2] = {dalloc<T>(ctx, s, K * spitch), dalloc<T>(ctx, s, K * spitch)};
-    double *seedm = dalloc<double>(ctx, s, K * spitch);   // FP64 master of the seed rows
+    // Seed rows are computed for the K rows that exist; the buffers hold one
+    // per SP rows of every band (the last band runs past n0), the extra rows
+    // zero, so that every seeded warp's top-edge row is in bounds.
+    const int64_t Kalloc = round_up(n0, R) / SP;
+    T *seedb[2] = {dalloc<T>(ctx, s, Kalloc * spitch), dalloc<T>(ctx, s, Kalloc * spitch)};
+    double *seedm = dalloc<double>(ctx, s, Kalloc * spitch);   // FP64 master of the seed rows
+    if (!s.reuse && Kalloc > K) {
+        const size_t tail = (size_t)(Kalloc - K) * spitch;
+        CK(cudaMemsetAsync(seedb[0] + K * spitch, 0, tail * sizeof(T), st));
+        CK(cudaMemsetAsync(seedb[1] + K * spitch, 0, tail * sizeof(T), st));
+        CK(cudaMemsetAsync(seedm + K * spitch, 0, tail * sizeof(double), st));
+    }
     T *thr = dalloc<T>(ctx, s, npad);
     RowState rs{dalloc<int32_t>(ctx, s, (size_t)p * n0), dalloc<double>(ctx, s, (size_t)p * n0),
                 dalloc<double>(ctx, s, (size_t)p * n0), dalloc<double>(ctx, s, n0),
