@@ -81,7 +81,7 @@ def run_p_sweep(args):
     import workloads
     w = workloads.make(args.workload)
     a, b = (int(v) for v in args.p_sweep.split(":"))
-    prec = mad.MAD_FP32 if args.precision == "fp32" else mad.MAD_FP64
+    prec = PRECISIONS[args.precision](mad)
     x = w.series[0]
     res = []
     for p in (5, 10, 20, 40, 64):
@@ -110,13 +110,14 @@ def run_ncu_case(args):
     import workloads
     w = workloads.make(args.workload)
     a, b = (int(v) for v in args.ncu_case.split(":"))
-    prec = mad.MAD_FP32 if args.precision == "fp32" else mad.MAD_FP64
+    prec = PRECISIONS[args.precision](mad)
     ctx = mad.mad_create(w.series[0], precision=prec, k_max=w.k, m_max=w.m, band_form=args.band_form,
                          mode=args.mode)
     try:
         mad.mad_profile(ctx, a, b, w.p)
         for s in mad.mad_stats(ctx, 0):
-            print(json.dumps({k: s[k] for k in ("len", "rows", "certified", "recomputed", "band_cells", "band_ms")}))
+            print(json.dumps({k: s[k] for k in ("len", "rows", "certified", "recomputed", "band_cells", "band_ms",
+                                                "direct_rows", "direct_ms", "rows_ms")}))
     finally:
         mad.mad_destroy(ctx)
     return 0
