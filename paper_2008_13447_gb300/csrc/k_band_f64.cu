@@ -55,23 +55,40 @@ void launch_seed<double>(const SeedArgs<double> &a, cudaStream_t s)
 // writes them). The band kernel's copy in T is written from the master.
 // Entry (k, j) of the table: row 0 holds C(0, j); row k >= 1 holds C(kS, 0)
 // at j = 0 and C(kS - 1, j - 1) for j >= 1.
+// Each thread takes one column j and SEED_ROWS consecutive seed rows, so
+// the column's factor (x[j-1+l] - mu[j-1]) is loaded once for them.
+constexpr int SEED_ROWS = 16;
+
 template <typename T>
-__global__ void k_seed_step(const double *x, const double *mu, int64_t nl, int l, int S, int64_t spitch,
+__global__ void k_seed_step(const double *x, const double *mu, int64_t nl, int l, int S, int64_t K, int64_t spitch,
                             double *master, T *seed, int update)
 {
-    const int k = blockIdx.y;
-    const int64_t kS = (int64_t)k * S;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= spitch) return;
+    const int64_t k0 = (int64_t)blockIdx.y * SEED_ROWS;
     const double f = (double)l / (double)(l + 1);
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < spitch;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t at = (int64_t)k * spitch + j;
+    const int64_t cj = j - 1;   // the column window of rows k >= 1
+    const double bj = (cj >= 0 && cj < nl) ? x[cj + l] - mu[cj] : 0.0;
+    for (int64_t k = k0; k < k0 + SEED_ROWS && k < K; ++k) {
+        const int64_t at = k * spitch + j;
         double v = master[at];
         if (update) {
+            const int64_t kS = k * S;
             int64_t ra, c;
-            if (k == 0) { ra = 0; c = j; }
-            else if (j == 0) { ra = kS; c = 0; }
-            else { ra = kS - 1; c = j - 1; }
-            v = (ra < nl && c < nl) ? fma(f * (x[ra + l] - mu[ra]), x[c + l] - mu[c], v) : 0.0;
+            double b = bj;
+            if (k == 0) {
+                ra = 0;
+                c = j;
+                b = (c < nl) ? x[c + l] - mu[c] : 0.0;
+            } else if (j == 0) {
+                ra = kS;
+                c = 0;
+                b = x[l] - mu[0];
+            } else {
+                ra = kS - 1;
+                c = cj;
+            }
+            v = (ra < nl && c < nl) ? fma(f * (x[ra + l] - mu[ra]), b, v) : 0.0;
             master[at] = v;
         }
         seed[at] = (T)v;
@@ -83,9 +100,10 @@ void launch_seed_step(const double *x, const double *mu, int64_t nl, int l, int 
                       double *master, T *seed, bool update, cudaStream_t s)
 {
     const int B = 256;
-    int64_t gx = (spitch + B - 1) / B;
-    if (gx > 1024) gx = 1024;
-    k_seed_step<T><<<dim3((unsigned)gx, (unsigned)K), B, 0, s>>>(x, mu, nl, l, S, spitch, master, seed, update ? 1 : 0);
+    const int64_t gx = (spitch + B - 1) / B;
+    const int64_t gy = (K + SEED_ROWS - 1) / SEED_ROWS;
+    k_seed_step<T><<<dim3((unsigned)gx, (unsigned)gy), B, 0, s>>>(x, mu, nl, l, S, K, spitch, master, seed,
+                                                                    update ? 1 : 0);
 }
 template void launch_seed_step<float>(const double *, const double *, int64_t, int, int, int64_t, int64_t, double *,
                                       float *, bool, cudaStream_t);

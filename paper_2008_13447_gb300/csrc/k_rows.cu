@@ -844,8 +844,10 @@ __global__ void k_theta_bins(const int *bins, int nbins, int64_t nl, int p, cons
         return;
     }
     double th = (double)top[p - 1];
-    // bins hold keys rounded down; widen by the key error and one FP32 step
-    th -= dq_row(em, i) * sqrt(m2[i]) + fabs(th) * 1e-6;
+    // bins hold computed keys rounded down: the true p-th best key is at least
+    // top[p-1] less one key error, and a cell whose true key reaches that
+    // computes at most one more key error lower; and one FP32 step
+    th -= 2.0 * dq_row(em, i) * sqrt(m2[i]) + fabs(th) * 1e-6;
     thr[i] = T(th);
 }
 
