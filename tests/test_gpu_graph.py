@@ -1,6 +1,7 @@
-"""Repeated profiles: the workspace is reused (no device allocation) and from
-the second profile with the same shape on, the whole launch sequence runs as
-one captured CUDA graph. Results must be identical, bit for bit, to the
+"""Repeated profiles: the workspace is reused (no device allocation by the
+library) and from the second profile with the same shape on, the whole
+launch sequence runs as one captured CUDA graph (its instantiation, at that
+second profile, is the driver's one allocation; replays allocate nothing). Results must be identical, bit for bit, to the
 eager first profile, and to a profile with graphs switched off."""
 import numpy as np
 import pytest
@@ -52,10 +53,12 @@ def test_repeated_profiles_replay_a_graph_and_allocate_nothing(prec):
         mad.mad_profile(ctx, lmin, lmax, p)            # eager, allocates the workspace
         first = snapshot(ctx, n, lmin, lmax, k, m)
         assert all(s["graph"] == 0 for s in first["st"])
+        runs = []
+        mad.mad_profile(ctx, lmin, lmax, p)            # captured (the driver takes memory for the graph)
+        runs.append(snapshot(ctx, n, lmin, lmax, k, m))
         torch.cuda.synchronize()
         free0 = torch.cuda.mem_get_info()[0]
-        runs = []
-        for _ in range(3):                           # captured once, then replayed
+        for _ in range(2):                           # replayed: nothing allocated
             mad.mad_profile(ctx, lmin, lmax, p)
             runs.append(snapshot(ctx, n, lmin, lmax, k, m))
         torch.cuda.synchronize()
@@ -67,8 +70,13 @@ def test_repeated_profiles_replay_a_graph_and_allocate_nothing(prec):
         # graphs off: the same results, launched one by one
         mad.mad_set_graphs(0)
         mad.mad_profile(ctx, lmin, lmax, p + 1)        # another shape: a new workspace
-        mad.mad_profile(ctx, lmin, lmax, p)
+        mad.mad_profile(ctx, lmin, lmax, p)            # and back: allocated again
+        torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
+        mad.mad_profile(ctx, lmin, lmax, p)            # the same shape again: the workspace reused
         off = snapshot(ctx, n, lmin, lmax, k, m)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free1
         assert all(s["graph"] == 0 for s in off["st"])
         same(first, off)
     finally:
