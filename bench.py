@@ -39,6 +39,19 @@ UNIT = "cells/s"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 OPS_PER_CELL = 4            # FFMA, FFMA (recurrence), FMUL (key), FSETP (threshold test)
+# Measured peaks of the GB300s (MEASURED_PEAKS.json when the
+# driver has written it; else the values it wrote earlier, recorded here)
+RECORDED_PEAKS = {"hbm_gbs": 6775.6, "bf16_tflops": 1906.5, "bf16_tflops_sustained": 1723.6}
+
+
+def measured_peaks():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return {k: float(d[k]) for k in RECORDED_PEAKS if k in d} or dict(RECORDED_PEAKS), "MEASURED_PEAKS.json"
+    except (OSError, ValueError, KeyError, TypeError):
+        return dict(RECORDED_PEAKS), "recorded copy of the driver's measurement"
+
+
 PRECISIONS = {"fp32": lambda mad: mad.MAD_FP32, "fp64": lambda mad: mad.MAD_FP64,
               "split_tc": lambda mad: mad.MAD_SPLIT_TC}
 DTYPES = {"fp32": "f32", "fp64": "f64", "split_tc": "f32 (direct path: f16 hi+lo on tensor cores)"}
@@ -390,7 +403,7 @@ def main():
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     acc = dict(band_ms=0.0, direct_ms=0.0, rows_ms=0.0, band_cells=0, launches=0, band_launches=0,
-               rows_after=0, recomputed_after=0, direct_rows=0, graph=0)
+               rows_after=0, recomputed_after=0, direct_rows=0, graph=0, direct_flops=0.0)
     for si in range(args.steps):
         flush.fill_(si & 0xff)
         torch.cuda.synchronize()
@@ -414,6 +427,9 @@ def main():
                     acc["rows_after"] += q["rows"]
                     acc["recomputed_after"] += q["recomputed"]
                     acc["direct_rows"] += q["direct_rows"]
+                # direct path: per listed row and column, l multiply-adds per
+                # product; the split form takes three products (hi*hi, hi*lo, lo*hi)
+                acc["direct_flops"] += q["direct_rows"] * q["rows"] * 2.0 * q["len"]
     torch.cuda.synchronize()
     if pg:
         pg.barrier()
@@ -440,6 +456,20 @@ def main():
             else "k_band (%s)" % args.precision,
             "ops_per_cell": OPS_PER_CELL, "band_cells_per_step": band_cells / K,
             "band_ms_per_step": band_ms / K}
+    if prec == mad.MAD_SPLIT_TC and acc["direct_ms"] > 0:
+        peaks, src = measured_peaks()
+        flops = 3.0 * acc["direct_flops"]
+        ach = flops / (acc["direct_ms"] / 1e3) / 1e12
+        roof_tc = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                   "frac": ach / peaks["bf16_tflops_sustained"], "traffic": None,
+                   "kernel": "k_direct_tc (tcgen05, FP16 hi+lo, 3 products per lag, FP32 accumulation)",
+                   "peak_source": "BF16 dense sustained, " + src + " (FP16 runs at the BF16 rate)",
+                   "flops_per_step": flops / K, "direct_ms_per_step": acc["direct_ms"] / K}
+        if acc["direct_ms"] > band_ms:
+            roof_tc["band_kernel"] = roof
+            roof = roof_tc
+        else:
+            roof["tensor_core_direct_path"] = roof_tc
     kernels = {"band_ms_per_step": band_ms / K, "direct_ms_per_step": acc["direct_ms"] / K,
                "rows_ms_per_step": acc["rows_ms"] / K,
                "other_ms_per_step": ms_per_step - (band_ms + acc["direct_ms"] + acc["rows_ms"]) / K}
