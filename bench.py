@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--lrange", default=None, metavar="LMIN:LMAX",
                     help="override the workload's length range (every series)")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the plain FP64 GPU path")
+    ap.add_argument("--fp64-lrange", default=None, metavar="LMIN:LMAX",
+                    help="time the plain FP64 path (and the chosen path again, for a like-for-like ratio) on this "
+                         "sub-range of lengths only (for workloads whose full FP64 step takes minutes)")
     ap.add_argument("--e2e-steps", type=int, default=3, help="timed end-to-end repetitions (median)")
     ap.add_argument("--band-form", type=int, default=0, choices=[0, 1],
                     help="0: full rows; 1: symmetric band form when most bands are active")
@@ -487,8 +490,36 @@ def main():
            "config": cfg, "roofline": roof, "kernels": kernels, "pruning": pruning,
            "gpu_launches": int(round(launches_per_step * args.steps)), "clocks": clk}
 
-    # plain FP64 GPU path: one warm-up step, then timed steps (median)
+    # plain FP64 GPU path: one warm-up step, then timed steps (median); on a
+    # stated sub-range of lengths for the largest workloads, with the chosen
+    # path timed again on the same sub-range
     if rank == 0 and not args.no_fp64_path and prec != mad.MAD_FP64:
+        sub = parse_range(args.fp64_lrange) if args.fp64_lrange else None
+        lo = [sub[0]] * ns if sub else w.lmin
+        hi = [sub[1]] * ns if sub else w.lmax
+        cells_sub = float(sum(len(sx) ** 2 * (b - a + 1) for sx, a, b in zip(w.series, lo, hi)))
+
+        def step_sub(c):
+            if batch:
+                mad.mad_profile_batch(c, lo, hi, p)
+            else:
+                mad.mad_profile(c, lo[0], hi[0], p)
+            return readouts(c)
+
+        def timed(c, reps):
+            step_sub(c)
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                flush.fill_(7)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                step_sub(c)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return ts
+
         if batch:
             c64 = mad.mad_create_batch(w.series, precision=mad.MAD_FP64, k_max=k, m_max=m, stream=stream,
                                        band_form=args.band_form)
@@ -496,23 +527,17 @@ def main():
             c64 = mad.mad_create_device(xt, precision=mad.MAD_FP64, k_max=k, m_max=m, stream=stream,
                                         band_form=args.band_form)
         try:
-            step(c64)
-            t64 = []
-            for rep in range(args.fp64_steps):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                flush.fill_(7)
-                torch.cuda.synchronize()
-                e0.record(stream)
-                step(c64)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                t64.append(e0.elapsed_time(e1))
-            ms64 = statistics.median(t64)
-            out["fp64_path"] = {"value": cells / (ms64 / 1e3), "ms_per_step": ms64, "steps": len(t64),
-                                "warmup": 1, "ms_all": t64,
-                                "speedup_of_%s" % args.precision: (cells / (ms_per_step / 1e3)) / (cells / (ms64 / 1e3))}
+            t64 = timed(c64, args.fp64_steps)
         finally:
             mad.mad_destroy(c64)
+        ms64 = statistics.median(t64)
+        ms_same = ms_per_step
+        if sub:
+            ms_same = statistics.median(timed(ctx, args.fp64_steps))
+        out["fp64_path"] = {"value": cells_sub / (ms64 / 1e3), "ms_per_step": ms64, "steps": len(t64), "warmup": 1,
+                            "ms_all": t64, "lengths": "all" if not sub else "%d..%d" % sub,
+                            "cells_per_step": cells_sub,
+                            "speedup_of_%s" % args.precision: ms64 / ms_same}
 
     # motif mode (Algorithm 1 with ComputeSubMP): the same workload, only the
     # motif of each length guaranteed; one warm-up step, one timed step
