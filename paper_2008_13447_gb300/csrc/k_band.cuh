@@ -160,7 +160,7 @@ constexpr bool BAND_PAIR = true;   // two columns per hit test in the common cas
 //             column's threshold, staged in cd.pad, appended to row j's
 //             candidate list in global memory).
 template <typename T, int RPL, int NW, int MODE, bool DIAG>
-__device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *cbuf, const T *tw, T *bout, int lane,
+__device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *cbuf, T tp, T *bout, int lane,
                                            bool feeds,
                                            int64_t cs, int64_t rbase, int rl0, T (&C)[RPL], const T (&dfr)[RPL],
                                            const T (&dgr)[RPL], T (&th)[RPL], const T (&invr)[RPL],
@@ -170,7 +170,8 @@ __device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *c
     for (int c = 0; c < CH; ++c) {
         const Col<T> cd = cbuf[c];
         T v = __shfl_up_sync(0xffffffffu, C[RPL - 1], 1);
-        if (lane == 0) v = tw[c];
+        const T vt = __shfl_sync(0xffffffffu, tp, c);
+        if (lane == 0) v = vt;
 #pragma unroll
         for (int a = RPL - 1; a >= 1; --a) C[a] = fma(dfr[a], cd.dg, fma(cd.df, dgr[a], C[a - 1]));
         C[0] = fma(dfr[0], cd.dg, fma(cd.df, dgr[0], v));
@@ -274,7 +275,7 @@ __device__ __forceinline__ void store_pair(double *p, double a, double b)
 }
 
 template <typename T, int RPL, int NW>
-__device__ __forceinline__ void band_chunk_pair(const BandArgs<T> &A, const Col<T> *cbuf, const T *tw, T *bout, int lane,
+__device__ __forceinline__ void band_chunk_pair(const BandArgs<T> &A, const Col<T> *cbuf, T tp, T *bout, int lane,
                                                 bool feeds, int64_t cs, int64_t rbase, int rl0, T (&C)[RPL],
                                                 const T (&dfr)[RPL], const T (&dgr)[RPL], T (&th)[RPL], T *lkey,
                                                 int32_t *lj, int32_t *lcnt, unsigned &ninsert)
@@ -286,12 +287,14 @@ __device__ __forceinline__ void band_chunk_pair(const BandArgs<T> &A, const Col<
         const Col<T> cd1 = cbuf[c + 1];
         T C0[RPL];
         T v = __shfl_up_sync(0xffffffffu, C[RPL - 1], 1);
-        if (lane == 0) v = tw[c];
+        T vt = __shfl_sync(0xffffffffu, tp, c);
+        if (lane == 0) v = vt;
 #pragma unroll
         for (int a = RPL - 1; a >= 1; --a) C0[a] = fma(dfr[a], cd0.dg, fma(cd0.df, dgr[a], C[a - 1]));
         C0[0] = fma(dfr[0], cd0.dg, fma(cd0.df, dgr[0], v));
         v = __shfl_up_sync(0xffffffffu, C0[RPL - 1], 1);
-        if (lane == 0) v = tw[c + 1];
+        vt = __shfl_sync(0xffffffffu, tp, c + 1);
+        if (lane == 0) v = vt;
 #pragma unroll
         for (int a = RPL - 1; a >= 1; --a) C[a] = fma(dfr[a], cd1.dg, fma(cd1.df, dgr[a], C0[a - 1]));
         C[0] = fma(dfr[0], cd1.dg, fma(cd1.df, dgr[0], v));
@@ -359,8 +362,7 @@ __global__ void __launch_bounds__(NW * 32, band_min_blocks<T, RPL>()) k_band(con
     uint64_t *mempty = mfull + NW * NSLOT;                         // [NW][NSLOT]
     Col<T> *colbuf = reinterpret_cast<Col<T> *>(mempty + NW * NSLOT);  // [NW][CH]
     T *bbuf = reinterpret_cast<T *>(colbuf + NW * CH);             // [NW][NSLOT][CH]
-    T *tops = bbuf + NW * NSLOT * CH;                              // [NW][CH] top edge of the chunk
-    unsigned char *tail = reinterpret_cast<unsigned char *>(tops + NW * CH);
+    unsigned char *tail = reinterpret_cast<unsigned char *>(bbuf + NW * NSLOT * CH);
     // bins mode: int [R][nbins];  top-p mode: T [R][p], int32 [R][p], int32 [R]
     int *sbins = reinterpret_cast<int *>(tail);
     T *lkey = reinterpret_cast<T *>(tail);
@@ -491,8 +493,6 @@ __global__ void __launch_bounds__(NW * 32, band_min_blocks<T, RPL>()) k_band(con
                 if (lane == 0) mbar_arrive(&mempty[w * NSLOT + slot]);   // slot free again
             }
             if (feeds) mbar_wait(&mempty[(w + 1) * NSLOT + slot], par ^ 1u, A.err, A.wave_limit);  // slot free
-            T *tw = tops + w * CH;      // lane 0 reads column c's top-edge value from here
-            tw[lane] = tp;
             __syncwarp();
             T *bout = bbuf + ((w + 1 < NW ? w + 1 : 0) * NSLOT + slot) * CH;
             // does this warp's row range meet the exclusion zone in this chunk?
@@ -500,13 +500,13 @@ __global__ void __launch_bounds__(NW * 32, band_min_blocks<T, RPL>()) k_band(con
             // (symmetric form: everything not wholly above the zone is tested cell by cell)
             const bool diag = SYM ? !(cs > rhi + A.E) : (cs <= rhi + A.E) && (cs + CH - 1 >= rlo - A.E);
             if (diag)
-                band_chunk<T, RPL, NW, MODE, true>(A, cbuf, tw, bout, lane, feeds, cs, rbase, rl0, C, dfr, dgr, th,
+                band_chunk<T, RPL, NW, MODE, true>(A, cbuf, tp, bout, lane, feeds, cs, rbase, rl0, C, dfr, dgr, th,
                                                    invr, runmax, lkey, lj, lcnt, ninsert);
             else if (MODE == MODE_TOPP && BAND_PAIR)
-                band_chunk_pair<T, RPL, NW>(A, cbuf, tw, bout, lane, feeds, cs, rbase, rl0, C, dfr, dgr, th, lkey, lj,
+                band_chunk_pair<T, RPL, NW>(A, cbuf, tp, bout, lane, feeds, cs, rbase, rl0, C, dfr, dgr, th, lkey, lj,
                                             lcnt, ninsert);
             else
-                band_chunk<T, RPL, NW, MODE, false>(A, cbuf, tw, bout, lane, feeds, cs, rbase, rl0, C, dfr, dgr, th,
+                band_chunk<T, RPL, NW, MODE, false>(A, cbuf, tp, bout, lane, feeds, cs, rbase, rl0, C, dfr, dgr, th,
                                                     invr, runmax, lkey, lj, lcnt, ninsert);
             if (feeds && lane == 31) mbar_arrive(&mfull[(w + 1) * NSLOT + slot]);   // chunk q written
             if (BINS) {
@@ -563,7 +563,7 @@ size_t band_smem(bool bins_mode, int p, int rpl)
     constexpr int NW = BAND_NW;
     const int R = 32 * rpl * NW;
     size_t s = (size_t)2 * NW * NSLOT * sizeof(uint64_t) + (size_t)NW * CH * sizeof(Col<T>) +
-               (size_t)NW * NSLOT * CH * sizeof(T) + (size_t)NW * CH * sizeof(T);
+               (size_t)NW * NSLOT * CH * sizeof(T);
     if (bins_mode) s += (size_t)R * band_nbins(p) * sizeof(int);
     else s += (size_t)R * p * (sizeof(T) + sizeof(int32_t)) + (size_t)R * sizeof(int32_t);
     return s;
