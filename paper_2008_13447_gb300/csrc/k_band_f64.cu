@@ -60,7 +60,7 @@ void launch_seed<double>(const SeedArgs<double> &a, cudaStream_t s)
 constexpr int SEED_ROWS = 16;
 
 template <typename T>
-__global__ void k_seed_step(const double *x, const double *mu, int64_t nl, int l, int S, int64_t K, int64_t spitch,
+__global__ void __launch_bounds__(128, 16) k_seed_step(const double *x, const double *mu, int64_t nl, int l, int S, int64_t K, int64_t spitch,
                             double *master, T *seed, int update)
 {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -99,7 +99,8 @@ template <typename T>
 void launch_seed_step(const double *x, const double *mu, int64_t nl, int l, int S, int64_t K, int64_t spitch,
                       double *master, T *seed, bool update, cudaStream_t s)
 {
-    const int B = 256;
+    // 128-thread blocks at <= 32 registers: they fit beside the band kernel
+    const int B = 128;
     const int64_t gx = (spitch + B - 1) / B;
     const int64_t gy = (K + SEED_ROWS - 1) / SEED_ROWS;
     k_seed_step<T><<<dim3((unsigned)gx, (unsigned)gy), B, 0, s>>>(x, mu, nl, l, S, K, spitch, master, seed,

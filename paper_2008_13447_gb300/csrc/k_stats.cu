@@ -41,10 +41,18 @@ __global__ void k_stats_init(const double *__restrict__ x, int64_t nl, int l, do
     }
 }
 
+// The per-length preparation kernels run on a side stream beside the band
+// kernel, whose three CTAs per SM leave 4096 registers of each SM free: in
+// blocks of PREP_THREADS threads at no more than 32 registers a block fits
+// in that room, so these kernels overlap the band kernel instead of waiting
+// for its end.
+constexpr int PREP_THREADS = 128;
+
 // Welford step from length l-1 to l for windows i < nl (= n - l + 1):
 // mu_new = mu + (x_{i+l-1} - mu) / l ; M2_new = M2 + (x_{i+l-1} - mu)(x_{i+l-1} - mu_new).
 // Reads mu_o/m2_o, writes mu_n/m2_n (distinct buffers).
-__global__ void k_stats_step(const double *__restrict__ x, int64_t nl, int l, const double *__restrict__ mu_o,
+__global__ void __launch_bounds__(PREP_THREADS, 16)
+k_stats_step(const double *__restrict__ x, int64_t nl, int l, const double *__restrict__ mu_o,
                              const double *__restrict__ m2_o, double *__restrict__ mu_n, double *__restrict__ m2_n)
 {
     const double inv_l = 1.0 / l;
@@ -62,7 +70,7 @@ __global__ void k_stats_step(const double *__restrict__ x, int64_t nl, int l, co
 //   j <  nl: df_{j-1}, dg_{j-1} (0 for j = 0), inv_j (0 if flat)
 //   j >= nl: df = dg = 0, inv = NaN (so no padded column ever passes a test)
 template <typename T>
-__global__ void k_coldata(const double *__restrict__ x, int64_t nl, int64_t npad, int l,
+__global__ void __launch_bounds__(PREP_THREADS, 16) k_coldata(const double *__restrict__ x, int64_t nl, int64_t npad, int l,
                           const double *__restrict__ mu, const double *__restrict__ m2,
                           const int32_t *__restrict__ run, Col<T> *__restrict__ col, double *__restrict__ isd)
 {
@@ -94,7 +102,8 @@ template <typename T>
 void launch_coldata(const double *x, int64_t nl, int64_t npad, int l, const double *mu, const double *m2,
                     const int32_t *run, Col<T> *col, double *isd, cudaStream_t s)
 {
-    k_coldata<T><<<(unsigned)((npad + 255) / 256), 256, 0, s>>>(x, nl, npad, l, mu, m2, run, col, isd);
+    k_coldata<T><<<(unsigned)((npad + PREP_THREADS - 1) / PREP_THREADS), PREP_THREADS, 0, s>>>(x, nl, npad, l, mu, m2,
+                                                                                          run, col, isd);
 }
 template void launch_coldata<float>(const double *, int64_t, int64_t, int, const double *, const double *,
                                     const int32_t *, Col<float> *, double *, cudaStream_t);
@@ -108,6 +117,13 @@ __global__ void k_split_x(const double *__restrict__ x, int64_t n, float *__rest
         xh[k] = h;
         xl[k] = (float)(x[k] - (double)h);
     }
+}
+
+void launch_stats_step(const double *x, int64_t nl, int l, const double *mu_o, const double *m2_o, double *mu_n,
+                       double *m2_n, cudaStream_t s)
+{
+    k_stats_step<<<(unsigned)((nl + PREP_THREADS - 1) / PREP_THREADS), PREP_THREADS, 0, s>>>(x, nl, l, mu_o, m2_o, mu_n,
+                                                                                          m2_n);
 }
 
 void launch_split_x(const double *x, int64_t n, float *xh, float *xl, cudaStream_t s)

@@ -7,8 +7,8 @@ namespace mad {
 // ---------------------------------------------------------------- k_stats.cu
 __global__ void k_flat_runs(const double *x, int64_t n, int cap, int32_t *run);
 __global__ void k_stats_init(const double *x, int64_t nl, int l, double *mu, double *m2);
-__global__ void k_stats_step(const double *x, int64_t nl, int l, const double *mu_o, const double *m2_o,
-                             double *mu_n, double *m2_n);
+void launch_stats_step(const double *x, int64_t nl, int l, const double *mu_o, const double *m2_o, double *mu_n,
+                       double *m2_n, cudaStream_t s);
 // Column data of the band kernel, and isd[j] = 1 / sqrt(M2_j) in FP64 (0 for
 // a flat window) for the per-row kernels.
 template <typename T>

@@ -574,8 +574,7 @@ void issue_profile(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStrea
         const int64_t nl = n - l + 1;
         CK(cudaStreamWaitEvent(side.prep, ev_ext[b ^ 1], 0));
         if (l > lmin)
-            k_stats_step<<<(unsigned)((nl + 255) / 256), 256, 0, side.prep>>>(s.x, nl, l, mu[b ^ 1], m2[b ^ 1],
-                                                                             mu[b], m2[b]);
+            launch_stats_step(s.x, nl, l, mu[b ^ 1], m2[b ^ 1], mu[b], m2[b], side.prep);
         launch_coldata<T>(s.x, nl, npad, l, mu[b], m2[b], run, colb[b], isdb[b], side.prep);
         launch_kappa(s.x, mu[b], m2[b], run, nl, l, SP, m2blk, kappab[b], kmaxb[b], side.prep);
         if (l == lmin) {
