@@ -133,7 +133,7 @@ def run_ncu_case(args):
         mad.mad_profile(ctx, a, b, w.p)
         for s in mad.mad_stats(ctx, 0):
             print(json.dumps({k: s[k] for k in ("len", "rows", "certified", "recomputed", "band_cells", "band_ms",
-                                                "direct_rows", "direct_ms", "rows_ms")}))
+                                                "inserts", "direct_rows", "direct_ms", "rows_ms")}))
     finally:
         mad.mad_destroy(ctx)
     return 0
