@@ -16,6 +16,8 @@
 //  - append: every non-trivial cell whose key exceeds the row's threshold is
 //    appended to the row's candidate list (the threshold is a proven lower
 //    bound on the row's p-th best key, so the list holds the row's top-p);
+//    a work unit that fills a row's list publishes its p-th kept key (an
+//    atomic max per row) and later units of the row start from it;
 //  - bins: per row, the maximum key over the columns of each chunk index
 //    modulo p is recorded; the smallest of those p maxima is a lower bound on
 //    the row's p-th best key (p distinct columns), used as the first
@@ -458,6 +460,11 @@ __global__ void __launch_bounds__(NW * 32, band_min_blocks<T, RPL>()) k_band(con
             dgr[a] = cr.dg;
             invr[a] = cr.inv;
             th[a] = A.thr[r];
+            // the best threshold another unit of this row has established
+            if (MODE == MODE_TOPP && A.rowbest) {
+                const T tb = (T)ord2f(A.rowbest[r]);
+                th[a] = tb > th[a] ? tb : th[a];
+            }
             C[a] = sleft[r + 1];
             runmax[a] = neg_inf<T>();
             if (!BINS) lcnt[rl0 + a] = 0;
@@ -537,6 +544,10 @@ __global__ void __launch_bounds__(NW * 32, band_min_blocks<T, RPL>()) k_band(con
                 const int32_t cnt = lcnt[rl];
                 const int64_t slot = r * A.ngroups + g;
                 A.scnt[slot] = cnt;
+                // a full list's p-th kept key bounds the row's p-th best key
+                // from below: later units of the row start from it
+                if (MODE == MODE_TOPP && A.rowbest && cnt == A.p)
+                    atomicMax(&A.rowbest[r], f2ord(to_float_rd(th[a])));
                 for (int e = 0; e < cnt; ++e) {
                     A.skey[slot * A.p + e] = lkey[rl * A.p + e];
                     A.sj[slot * A.p + e] = lj[rl * A.p + e];

@@ -73,6 +73,8 @@ template <typename T> struct BandArgs {
     // bins mode: per row, the maximum key of each class of column chunks
     int *bins;              // [row][nbins] order-preserving ints
     int nbins;
+    int *rowbest;           // per row: the best p-th kept key of finished units (order-preserving
+                            // int of a float, rounded down; reset before each launch)
     int *err;               // set to 1 if a bounded wait ran out
     int wave_limit;         // tries of each wavefront wait (the hand-over between warps) before it
                             // gives up; the unit-queue waits always use the full limit

@@ -369,6 +369,7 @@ void issue_profile(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStrea
     Valmp vm{dalloc<double>(ctx, s, n0), dalloc<double>(ctx, s, n0), dalloc<int32_t>(ctx, s, n0),
              dalloc<int32_t>(ctx, s, n0)};
     int *bins = dalloc<int>(ctx, s, (size_t)n0 * nbins);
+    int *rowbest = dalloc<int>(ctx, s, (size_t)npad);   // band kernel: per-row threshold shared by units
     int32_t *bands = dalloc<int32_t>(ctx, s, KB);
     int32_t *counters = dalloc<int32_t>(ctx, s, 4);   // nbands, unit counter, overflow
     int32_t *krows = dalloc<int32_t>(ctx, s, K);
@@ -517,6 +518,7 @@ void issue_profile(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStrea
     ba.bins = bins;
     ba.nbins = nbins;
     ba.err = wait_err;
+    ba.rowbest = rowbest;
     {
         const int wl = g_wave_limit.load();
         ba.wave_limit = wl < 0 ? (1 << 20) : wl;
@@ -846,6 +848,8 @@ void issue_profile(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStrea
             ma.allow_sym = pass == 0 ? use_sym : 0;
             if (pass == 0) {
                 CK(cudaMemsetAsync(unit_ctr, 0, sizeof(int32_t), st));
+                launch_fill<int32_t>(rowbest, npad, (int32_t)0x807fffff, st);   // ord(-inf)
+                ++nlaunch;
                 const size_t e = ev_begin(li, TK_BAND);
                 launch_band<T>(ba, false, grid_band, st);
                 ev_end_rec(e);
