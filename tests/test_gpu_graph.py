@@ -37,7 +37,9 @@ def same(a, b):
     assert a["mot"] == b["mot"]
     assert a["dis"] == b["dis"]
     for sa, sb in zip(a["st"], b["st"]):
-        for key in ("certified", "recomputed", "band_cells", "inserts", "direct_rows", "fp32_dq_max"):
+        # (list insertions are left out: units of a row share thresholds in
+        # the order they finish, so the count varies, not the results)
+        for key in ("certified", "recomputed", "band_cells", "direct_rows", "fp32_dq_max"):
             assert sa[key] == sb[key], key
 
 
