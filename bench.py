@@ -72,6 +72,8 @@ def parse():
                     help="time the plain FP64 path (and the chosen path again, for a like-for-like ratio) on this "
                          "sub-range of lengths only (for workloads whose full FP64 step takes minutes)")
     ap.add_argument("--e2e-steps", type=int, default=3, help="timed end-to-end repetitions (median)")
+    ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
+                    help="1: repeated profiles replay a captured CUDA graph (default); 0: launched one by one")
     ap.add_argument("--band-form", type=int, default=0, choices=[0, 1],
                     help="0: full rows; 1: symmetric band form when most bands are active")
     ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the plain FP64 GPU path")
@@ -368,6 +370,7 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     w = make_workload(args)
+    mad.mad_set_graphs(args.graphs)
     batch = len(w.series) > 1
     p, k, m = w.p, w.k, w.m
     prec = PRECISIONS[args.precision](mad)
@@ -483,7 +486,7 @@ def main():
 
     cfg = {**workload_config(args.workload, w), "precision": args.precision, "band_form": args.band_form,
            "l2": "flushed between timed steps (512 MB write)", "parallelism": "replicas",
-           "graph_replay": bool(acc["graph"])}
+           "graph_replay": bool(acc["graph"]), "graphs_option": args.graphs}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",

@@ -446,6 +446,281 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_direct_tc(TcArgs A)
     }
 }
 
+// ------------------------------------------------------------------
+// Pipelined form (p <= TC2_MAXP): the same products and epilogue, with the
+// steps overlapped by warp roles and mbarriers instead of run one after the
+// other:
+//   warps 0..7  (producers): per 64-lag chunk, wait until the chunk's
+//               shared-memory stage is free, start the row operand's bulk
+//               copy, build the column tile, arrive on the stage's "full"
+//               barrier; per 256-column tile, the column constants;
+//   warp 12     (MMA): per chunk, wait for "full", issue the 12 MMAs into the
+//               tile's accumulator, commit to the stage's "free" barrier
+//               (and after the tile's last chunk to the accumulator's "full");
+//   warps 8..11 (epilogue): per tile, wait for the accumulator, read it back
+//               (TMEM lanes 32 (w mod 4) .., one row per thread), keep the
+//               rows' best p keys, arrive on the accumulator's "free".
+// Two stages (row and column operands) and two accumulators (512 TMEM
+// columns): the column tile of chunk c + 1 is built while the MMAs of chunk c
+// run, and the epilogue of tile t runs while the MMAs of tile t + 1 run.
+// Every role walks the same (item, tile, chunk) sequence, so the barriers'
+// phases follow from the counters. Every wait is bounded; after the first
+// one that runs out (error word set) every later wait returns at once, and
+// all threads still walk the whole sequence, so that the producers' named
+// barriers (which cannot time out) are always met by all of them.
+constexpr int TC2_THREADS = 416;   // 8 producer warps, 4 epilogue warps, 1 MMA warp
+constexpr int TC2_PROD = 256;
+constexpr int TC2_EPI0 = 256;      // first epilogue thread (warp 8)
+constexpr int TC2_MMA = 384;       // MMA warp (warp 12)
+constexpr int TC2_MAXP = 10;
+constexpr int TC2_STAGE = 2 * A_TILE_BYTES + 2 * B_TILE_BYTES;   // 96 KB
+
+__device__ __forceinline__ void mbar_arrive1(uint64_t *b)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void prod_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+struct Tc2Bars {
+    uint64_t full[2], freeb[2], accfull[2], accfree[2], ccready[2], fin;
+};
+
+__global__ void __launch_bounds__(TC2_THREADS, 1) k_direct_tc2(TcArgs A)
+{
+    const int nrows = *A.nrows;
+    if (nrows <= 0) return;
+    const int l = A.l;
+    const int nkc = A.nkc;
+    const int p = A.p;
+    const int rtiles = (nrows + TC_M - 1) / TC_M;
+    const int64_t items = (int64_t)rtiles * A.nblk;
+    if (blockIdx.x >= items) return;
+
+    extern __shared__ __align__(1024) unsigned char sm_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)sm_raw + 1023) & ~(uintptr_t)1023);
+    // stage g: A hi, A lo (16 KB each), B hi, B lo (32 KB each)
+    __half *shift = reinterpret_cast<__half *>(sm + 2 * TC2_STAGE);          // [hi, lo][8][SHIFT_LEN]
+    ColC *cc = reinterpret_cast<ColC *>(shift + 2 * 8 * SHIFT_LEN);          // [2][TC_N]
+    float *lk = reinterpret_cast<float *>(cc + 2 * TC_N);                    // [TC_M][p]
+    int32_t *lj = reinterpret_cast<int32_t *>(lk + TC_M * p);
+    float *ld = reinterpret_cast<float *>(lj + TC_M * p);
+    __shared__ __align__(8) Tc2Bars bars;
+    __shared__ uint32_t tmem_base;
+    __shared__ float red[TC2_PROD / 32];
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        for (int g = 0; g < 2; ++g) {
+            mbar_init(&bars.full[g], TC2_PROD + 1);    // producers + the copy's expect-tx
+            mbar_init(&bars.freeb[g], 1);              // MMA commit
+            mbar_init(&bars.accfull[g], 1);            // MMA commit
+            mbar_init(&bars.accfree[g], TC_M);         // epilogue threads
+            mbar_init(&bars.ccready[g], TC2_PROD);     // producers
+        }
+        mbar_init(&bars.fin, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == TC2_MMA / 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                     "r"(2 * TC_N)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    volatile int *abortv = &abort_flag;
+    auto wait = [&](uint64_t *b, unsigned par) {
+        if (*abortv) return false;
+        if (mbar_wait_b(b, par, A.err)) return true;
+        *abortv = 1;
+        return false;
+    };
+
+    if (tid < TC2_PROD) {
+        // ------------------------------------------------------ producers
+        unsigned t = 0, c = 0;
+        float dqmax = 0.0f;
+        for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+            const int rt = (int)(item / A.nblk);
+            const int64_t cb0 = (int64_t)(item % A.nblk) * TC_COLS;
+            for (int st0 = 0; st0 < TC_COLS / TC_N; ++st0, ++t) {
+                const int64_t j0 = cb0 + (int64_t)st0 * TC_N;
+                if (j0 >= A.nl) break;
+                const int a = t & 1;
+                if (t >= 2) wait(&bars.accfree[a], ((t >> 1) - 1) & 1);
+                // tile shift s, scale S_b, per-column constants (one column per thread)
+                const int64_t jm = j0 + TC_N / 2 < A.nl ? j0 + TC_N / 2 : A.nl - 1;
+                const double sft = A.mu[jm];
+                const int64_t jc = j0 + tid;
+                float spread = 0.0f;
+                if (jc < A.nl) {
+                    const double m2 = A.m2[jc];
+                    spread = (float)(sqrt(m2 > 0.0 ? m2 : 0.0) + fabs(A.mu[jc] - sft));
+                }
+                for (int o = 16; o > 0; o >>= 1) spread = fmaxf(spread, __shfl_xor_sync(0xffffffffu, spread, o));
+                if (lane == 0) red[warp] = spread;
+                prod_sync();
+                float mx = 0.0f;
+                for (int w = 0; w < TC2_PROD / 32; ++w) mx = fmaxf(mx, red[w]);
+                const float Sb = mx > 0.0f ? exp2f(floorf(log2f(255.0f / mx))) : 1.0f;
+                {
+                    ColC cv{0.0f, 0.0f, 0.0f, 0.0f};
+                    if (jc < A.nl) {
+                        const double isd = A.isd[jc];
+                        const double dm = A.mu[jc] - sft;
+                        cv.c = (float)(Sb * dm);
+                        cv.g = (float)(isd / ((double)TC_SA * Sb));
+                        const double f = sqrt(1.0 + (double)l * dm * dm * isd * isd);
+                        const double K = (double)nkc * TC_KC;
+                        cv.dq = (float)(1.5 * ((3.0 * 0x1p-22 + (3.0 * K + 4.0) * 0x1p-24) * f + 0x1p-23));
+                        dqmax = fmaxf(dqmax, cv.dq);
+                    }
+                    cc[a * TC_N + tid] = cv;
+                }
+                mbar_arrive1(&bars.ccready[a]);
+                for (int kc = 0; kc < nkc; ++kc, ++c) {
+                    const int g = c & 1;
+                    unsigned char *sa = sm + g * TC2_STAGE;
+                    unsigned char *sb = sa + 2 * A_TILE_BYTES;
+                    if (c >= 2) wait(&bars.freeb[g], ((c >> 1) - 1) & 1);
+                    if (tid == 0) {
+                        mbar_expect_tx(&bars.full[g], 2 * A_TILE_BYTES);
+                        const unsigned char *src = A.aimg + ((size_t)(rt * nkc + kc) * 2) * A_TILE_BYTES;
+                        bulk_g2s(sa, src, A_TILE_BYTES, &bars.full[g]);
+                        bulk_g2s(sa + A_TILE_BYTES, src + A_TILE_BYTES, A_TILE_BYTES, &bars.full[g]);
+                    }
+                    // column values in eight copies shifted by 0..7, then the
+                    // swizzled tile rows (the previous chunk's rows are built
+                    // from the copies before they are overwritten)
+                    if (kc > 0) prod_sync();
+                    __half *sh = shift;
+                    const int64_t gb = j0 + (int64_t)kc * TC_KC;
+                    for (int e = tid; e < 8 * SHIFT_LEN; e += TC2_PROD) {
+                        const int sf = e / SHIFT_LEN, i = e % SHIFT_LEN;
+                        const int64_t gx = gb + i + sf;
+                        const float v = gx < A.n ? (float)(A.x[gx] - sft) * Sb : 0.0f;
+                        __half hi, lo;
+                        split_half(v, hi, lo);
+                        sh[sf * SHIFT_LEN + i] = hi;
+                        sh[(8 + sf) * SHIFT_LEN + i] = lo;
+                    }
+                    prod_sync();
+                    for (int e = tid; e < 2 * TC_N * 8; e += TC2_PROD) {
+                        const int hl = e / (TC_N * 8), rem = e % (TC_N * 8);
+                        const int nn = rem / 8, q = rem % 8;
+                        const int sf = nn & 7;
+                        const uint4 v = *reinterpret_cast<const uint4 *>(sh + (hl * 8 + sf) * SHIFT_LEN + (nn - sf) +
+                                                                         8 * q);
+                        *reinterpret_cast<uint4 *>(sb + hl * B_TILE_BYTES + swz(nn, 8 * q)) = v;
+                    }
+                    fence_async_smem();
+                    mbar_arrive1(&bars.full[g]);
+                }
+            }
+        }
+        if (dqmax > 0.0f) atomicMax(reinterpret_cast<int *>(A.dq_max), __float_as_int(dqmax));
+    } else if (tid == TC2_MMA) {
+        // ----------------------------------------------------------- MMA
+        unsigned t = 0, c = 0;
+        for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+            const int64_t cb0 = (int64_t)(item % A.nblk) * TC_COLS;
+            for (int st0 = 0; st0 < TC_COLS / TC_N; ++st0, ++t) {
+                if (cb0 + (int64_t)st0 * TC_N >= A.nl) break;
+                const int a = t & 1;
+                if (t >= 2) wait(&bars.accfree[a], ((t >> 1) - 1) & 1);
+                tc_fence_after();
+                const uint32_t dacc = tmem + (uint32_t)(a * TC_N);
+                for (int kc = 0; kc < nkc; ++kc, ++c) {
+                    const int g = c & 1;
+                    wait(&bars.full[g], (c >> 1) & 1);
+                    tc_fence_after();
+                    if (!*abortv) {
+                        const unsigned a0 = su32(sm + g * TC2_STAGE), b0 = a0 + 2 * A_TILE_BYTES;
+#pragma unroll
+                        for (int ks = 0; ks < TC_KC / 16; ++ks) {
+                            const uint64_t ah = sdesc(a0 + ks * 32), al = sdesc(a0 + A_TILE_BYTES + ks * 32);
+                            const uint64_t bh = sdesc(b0 + ks * 32), bl = sdesc(b0 + B_TILE_BYTES + ks * 32);
+                            tc_mma(dacc, ah, bh, (kc > 0 || ks > 0) ? 1u : 0u);
+                            tc_mma(dacc, ah, bl, 1u);
+                            tc_mma(dacc, al, bh, 1u);
+                        }
+                    }
+                    tc_commit(&bars.freeb[g]);                 // the stage may be refilled
+                    if (kc == nkc - 1) tc_commit(&bars.accfull[a]);   // the tile's accumulator is complete
+                }
+            }
+        }
+        // every MMA issued has completed before the accumulators are freed
+        tc_commit(&bars.fin);
+        mbar_wait_b(&bars.fin, 0, A.err);
+    } else if (tid >= TC2_EPI0 && tid < TC2_MMA) {
+        // ------------------------------------------------------ epilogue
+        const int m = tid - TC2_EPI0;      // TMEM lane (warps 8..11 read quarters 0..3)
+        float *mk = lk + m * p;
+        int32_t *mj = lj + m * p;
+        float *md = ld + m * p;
+        unsigned t = 0;
+        for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+            const int rt = (int)(item / A.nblk);
+            const int cb = (int)(item % A.nblk);
+            const int64_t cb0 = (int64_t)cb * TC_COLS;
+            const int64_t pos = (int64_t)rt * TC_M + m;
+            const bool erow = pos < nrows;
+            const int64_t r = erow ? A.rows[pos] : -1;
+            const float asum = erow ? A.asum[pos] : 0.0f;
+            const float sq = erow ? A.sqm2[pos] : 0.0f;
+            const float thq = erow ? (float)A.thr[r] / sq : 0.0f;
+            const int64_t exlo = r - A.E, exhi = r + A.E;
+            int cnt = 0;
+            for (int st0 = 0; st0 < TC_COLS / TC_N; ++st0, ++t) {
+                const int64_t j0 = cb0 + (int64_t)st0 * TC_N;
+                if (j0 >= A.nl) break;
+                const int a = t & 1;
+                wait(&bars.accfull[a], (t >> 1) & 1);
+                wait(&bars.ccready[a], (t >> 1) & 1);
+                tc_fence_after();
+                const ColC *ca = cc + a * TC_N;
+                for (int c0 = 0; c0 < TC_N; c0 += 32) {
+                    float v[32];
+                    __syncwarp();
+                    tc_ld32(tmem + ((uint32_t)(m & ~31) << 16) + (uint32_t)(a * TC_N + c0), v);
+                    if (!erow || *abortv) continue;
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const ColC k = ca[c0 + q];
+                        const float tt = fmaf(-k.c, asum, v[q]);
+                        if (fmaf(tt, k.g, k.dq) > thq) {
+                            const int64_t j = j0 + c0 + q;
+                            if (j < A.nl && (j < exlo || j > exhi))
+                                list_insert<float>(mk, mj, md, cnt, p, tt * k.g * sq, (int32_t)j, k.dq);
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive1(&bars.accfree[a]);   // accumulator and column constants released
+            }
+            if (erow && !*abortv) {
+                const int64_t slot = pos * A.nblk + cb;
+                for (int e = 0; e < cnt; ++e) {
+                    A.okey[slot * p + e] = mk[e];
+                    A.oj[slot * p + e] = mj[e];
+                    A.odq[slot * p + e] = md[e];
+                }
+                A.ocnt[slot] = cnt;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == TC2_MMA / 32) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_N) : "memory");
+    }
+}
 }  // namespace
 
 size_t tc_smem_bytes(int p)
@@ -464,12 +739,24 @@ size_t tc_aimg_bytes(int64_t max_rows, int lmax)
 
 int tc_chunks(int l) { return (l + TC_KC - 1) / TC_KC; }
 
+size_t tc2_smem_bytes(int p)
+{
+    return 1024 + 2 * (size_t)TC2_STAGE + 2 * 8 * SHIFT_LEN * sizeof(__half) + 2 * TC_N * sizeof(ColC) +
+           (size_t)TC_M * p * (sizeof(float) + sizeof(int32_t) + sizeof(float));
+}
+
 void launch_direct_tc(const TcArgs &a, int num_sms, cudaStream_t s)
 {
-    static std::once_flag once[64];
-    smem_optin_max((const void *)k_direct_tc, once);
     k_tc_rows<<<num_sms * 8, TC_THREADS, 0, s>>>(a);
-    k_direct_tc<<<num_sms, TC_THREADS, tc_smem_bytes(a.p), s>>>(a);
+    if (a.p <= TC2_MAXP) {
+        static std::once_flag once2[64];
+        smem_optin_max((const void *)k_direct_tc2, once2);
+        k_direct_tc2<<<num_sms, TC2_THREADS, tc2_smem_bytes(a.p), s>>>(a);
+    } else {
+        static std::once_flag once[64];
+        smem_optin_max((const void *)k_direct_tc, once);
+        k_direct_tc<<<num_sms, TC_THREADS, tc_smem_bytes(a.p), s>>>(a);
+    }
 }
 
 }  // namespace mad

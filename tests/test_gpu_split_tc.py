@@ -74,3 +74,11 @@ def test_tc_matches_fp32_readouts():
             mad.mad_destroy(ctx)
     a, b = out[mad.MAD_FP32][0], out[TC][0]
     assert np.all(np.abs(a["norm"] - b["norm"]) <= 2e-4)
+
+
+def test_large_p_takes_the_unpipelined_kernel():
+    # p > 10: the per-row lists no longer fit beside the two pipelined stages;
+    # the one-stage kernel runs instead (same results)
+    x = workloads.ecg_like(5200, 154, period=58.0)
+    r = compare_all(x, 64, 70, 12, TC, m_max=2, k_max=3)
+    assert direct(r["stats"]) > 0
