@@ -207,7 +207,10 @@ MAD_API mad_status mad_create_batch(const double *const *series, const int64_t *
  * between profiles are used. */
 MAD_API mad_status mad_profile(mad_ctx *ctx, int32_t lmin, int32_t lmax, int32_t p);
 
-/* Batched form: lmin[s], lmax[s] per series of a mad_create_batch context. */
+/* Batched form: lmin[s], lmax[s] per series of a mad_create_batch context.
+ * Series are started on eight streams without waiting on the host; a repeat
+ * with the same ranges reuses every series' workspace (launched eagerly, not
+ * replayed as graphs: with many series in flight that measured faster). */
 MAD_API mad_status mad_profile_batch(mad_ctx *ctx, const int32_t *lmin, const int32_t *lmax,
                                      int32_t p);
 

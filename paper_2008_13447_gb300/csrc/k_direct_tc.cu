@@ -32,7 +32,9 @@
 // scaling, with sum_t |A_r[t] B_j[t]| <= S_a S_b sqrt(M2_j + l (mu_j - s)^2)
 // (Cauchy-Schwarz):
 //     dq_j = 1.5 ((3 2^-22 + (3K + 4) 2^-24) f_j + 2^-23),
-//     f_j  = sqrt(1 + l (mu_j - s)^2 / M2_j).
+//     f_j  = sqrt(1 + l (mu_j - s)^2 / M2_j)
+// (the pipelined form forms x - s in FP32 from the series' FP32 pairs, one
+// more rounding of 2^-23 relative to the column operand: 4 2^-22 there).
 // A candidate is kept when q + dq_j could beat the row's threshold, and
 // carries dq_j to the merge.
 #include <cuda_fp16.h>
@@ -576,7 +578,7 @@ __global__ void __launch_bounds__(TC2_THREADS, 1) k_direct_tc2(TcArgs A)
                         cv.g = (float)(isd / ((double)TC_SA * Sb));
                         const double f = sqrt(1.0 + (double)l * dm * dm * isd * isd);
                         const double K = (double)nkc * TC_KC;
-                        cv.dq = (float)(1.5 * ((3.0 * 0x1p-22 + (3.0 * K + 4.0) * 0x1p-24) * f + 0x1p-23));
+                        cv.dq = (float)(1.5 * ((4.0 * 0x1p-22 + (3.0 * K + 4.0) * 0x1p-24) * f + 0x1p-23));
                         dqmax = fmaxf(dqmax, cv.dq);
                     }
                     cc[a * TC_N + tid] = cv;
@@ -599,10 +601,13 @@ __global__ void __launch_bounds__(TC2_THREADS, 1) k_direct_tc2(TcArgs A)
                     if (kc > 0) prod_sync();
                     __half *sh = shift;
                     const int64_t gb = j0 + (int64_t)kc * TC_KC;
+                    // x - s in FP32 from the series' FP32 pairs (GB300's FP64 rate
+                    // is 1/64 of FP32): relative error below 2^-23
+                    const float s_hi = (float)sft, s_lo = (float)(sft - (double)s_hi);
                     for (int e = tid; e < 8 * SHIFT_LEN; e += TC2_PROD) {
                         const int sf = e / SHIFT_LEN, i = e % SHIFT_LEN;
                         const int64_t gx = gb + i + sf;
-                        const float v = gx < A.n ? (float)(A.x[gx] - sft) * Sb : 0.0f;
+                        const float v = gx < A.n ? ((A.xh[gx] - s_hi) + (A.xl[gx] - s_lo)) * Sb : 0.0f;
                         __half hi, lo;
                         split_half(v, hi, lo);
                         sh[sf * SHIFT_LEN + i] = hi;

@@ -345,6 +345,7 @@ int direct_cols_per_block();
 // accumulation in TMEM; same outputs as the direct kernel.
 struct TcArgs {
     const double *x;
+    const float *xh, *xl;   // x as FP32 pairs (x = xh + xl to about 48 bits)
     int64_t n, nl;
     int l;
     int64_t E;
