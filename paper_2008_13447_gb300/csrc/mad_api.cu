@@ -310,11 +310,11 @@ void issue_profile(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStrea
     // the FP64 master) fit in 16 GB. Every chain of the band kernel then has
     // at most SP steps, which is what its error bound scales with; one seed
     // row per warp also removes the wavefront between the warps.
-    // (The paper-literal modes recompute few rows per length, so there the
-    // seed rows' per-length step would cost more than the tighter bound
-    // saves: one seed row per band start.)
+    // (The motif mode recomputes few rows per length, so there the seed
+    // rows' per-length step would cost more than the tighter bound saves:
+    // one seed row per band start.)
     int SP = R < 1024 ? R : 1024;
-    for (int sp = 32 * rpl > 128 ? 32 * rpl : 128; o.mode == 0 && sp <= R; sp *= 2) {
+    for (int sp = 32 * rpl > 128 ? 32 * rpl : 128; o.mode != 1 && sp <= R; sp *= 2) {
         const double rows = (double)((n0 + sp - 1) / sp);
         const double bytes = rows * (double)(round_up(n0, R) + R + CH) * (2.0 * sizeof(T) + 8.0);
         if (bytes <= 16e9) {
