@@ -476,6 +476,7 @@ constexpr int TC2_EPI0 = 256;      // first epilogue thread (warp 8)
 constexpr int TC2_MMA = 384;       // MMA warp (warp 12)
 constexpr int TC2_MAXP = 10;
 constexpr int TC2_STAGE = 2 * A_TILE_BYTES + 2 * B_TILE_BYTES;   // 96 KB
+static_assert(TC2_PROD == TC_N, "one producer thread per tile row");
 
 __device__ __forceinline__ void mbar_arrive1(uint64_t *b)
 {
@@ -604,23 +605,36 @@ __global__ void __launch_bounds__(TC2_THREADS, 1) k_direct_tc2(TcArgs A)
                     // x - s in FP32 from the series' FP32 pairs (GB300's FP64 rate
                     // is 1/64 of FP32): relative error below 2^-23
                     const float s_hi = (float)sft, s_lo = (float)(sft - (double)s_hi);
-                    for (int e = tid; e < 8 * SHIFT_LEN; e += TC2_PROD) {
-                        const int sf = e / SHIFT_LEN, i = e % SHIFT_LEN;
-                        const int64_t gx = gb + i + sf;
+                    // each value v[i] (i < SHIFT_LEN + 7) once, stored to the
+                    // eight copies at i - sf (copy sf holds v[i' + sf] at i')
+                    for (int i = tid; i < SHIFT_LEN + 7; i += TC2_PROD) {
+                        const int64_t gx = gb + i;
                         const float v = gx < A.n ? ((A.xh[gx] - s_hi) + (A.xl[gx] - s_lo)) * Sb : 0.0f;
                         __half hi, lo;
                         split_half(v, hi, lo);
-                        sh[sf * SHIFT_LEN + i] = hi;
-                        sh[(8 + sf) * SHIFT_LEN + i] = lo;
+#pragma unroll
+                        for (int sf = 0; sf < 8; ++sf) {
+                            const int ip = i - sf;
+                            if (ip >= 0 && ip < SHIFT_LEN) {
+                                sh[sf * SHIFT_LEN + ip] = hi;
+                                sh[(8 + sf) * SHIFT_LEN + ip] = lo;
+                            }
+                        }
                     }
                     prod_sync();
-                    for (int e = tid; e < 2 * TC_N * 8; e += TC2_PROD) {
-                        const int hl = e / (TC_N * 8), rem = e % (TC_N * 8);
-                        const int nn = rem / 8, q = rem % 8;
-                        const int sf = nn & 7;
-                        const uint4 v = *reinterpret_cast<const uint4 *>(sh + (hl * 8 + sf) * SHIFT_LEN + (nn - sf) +
-                                                                         8 * q);
-                        *reinterpret_cast<uint4 *>(sb + hl * B_TILE_BYTES + swz(nn, 8 * q)) = v;
+                    // tile row nn (hi and lo): eight aligned 16-byte copies from
+                    // the copy shifted by nn mod 8
+                    {
+                        const int nn = tid, sf = nn & 7;
+#pragma unroll
+                        for (int hl = 0; hl < 2; ++hl) {
+                            const __half *src = sh + (hl * 8 + sf) * SHIFT_LEN + (nn - sf);
+                            unsigned char *dst = sb + hl * B_TILE_BYTES + nn * 128;
+#pragma unroll
+                            for (int q = 0; q < 8; ++q)
+                                *reinterpret_cast<uint4 *>(dst + (((q ^ sf) & 7) << 4)) =
+                                    *reinterpret_cast<const uint4 *>(src + 8 * q);
+                        }
                     }
                     fence_async_smem();
                     mbar_arrive1(&bars.full[g]);
