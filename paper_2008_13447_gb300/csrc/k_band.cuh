@@ -246,16 +246,17 @@ __device__ __forceinline__ void band_chunk(const BandArgs<T> &A, const Col<T> *c
 // gives the scheduler two columns of independent arithmetic per block.
 // Column c's co-moments stay in C0 until its hits are handled; a hit in
 // column c may raise th before column c+1 is handled, which the per-row test
-// inside the insert re-checks.
+// re-checks. The chunks of this form lie outside the exclusion zone of every
+// row of the warp, so every cell is non-trivial. (An out-of-line insertion
+// call measured slower: the registers it saves cost the unrolled chunk.)
 template <typename T, int RPL>
-__device__ __forceinline__ void topp_hits(const BandArgs<T> &A, const T (&Cc)[RPL], T inv, int32_t j, int64_t rbase,
-                                          int rl0, T (&th)[RPL], T *lkey, int32_t *lj, int32_t *lcnt,
-                                          unsigned &ninsert)
+__device__ __forceinline__ void topp_hits(const BandArgs<T> &A, const T (&Cc)[RPL], T inv, int32_t j, int rl0,
+                                          T (&th)[RPL], T *lkey, int32_t *lj, int32_t *lcnt, unsigned &ninsert)
 {
 #pragma unroll
     for (int a = 0; a < RPL; ++a) {
         const T key = Cc[a] * inv;
-        if (key > th[a] && nontrivial(rbase + a, j, A.E)) {
+        if (key > th[a]) {
             const int rl = rl0 + a;
             int32_t cnt = lcnt[rl];
             topp_insert<T>(lkey + rl * A.p, lj + rl * A.p, cnt, A.p, key, j, th[a]);
@@ -277,26 +278,26 @@ __device__ __forceinline__ void store_pair(double *p, double a, double b)
 }
 
 template <typename T, int RPL, int NW>
-__device__ __forceinline__ void band_chunk_pair(const BandArgs<T> &A, const Col<T> *cbuf, T tp, T *bout, int lane,
-                                                bool feeds, int64_t cs, int64_t rbase, int rl0, T (&C)[RPL],
-                                                const T (&dfr)[RPL], const T (&dgr)[RPL], T (&th)[RPL], T *lkey,
-                                                int32_t *lj, int32_t *lcnt, unsigned &ninsert)
+__device__ __forceinline__ void band_chunk_pair(const BandArgs<T> &A, const Col<T> *cbuf, T *bout, int lane,
+                                                bool feeds, int64_t cs, int rl0, T (&C)[RPL], const T (&dfr)[RPL],
+                                                const T (&dgr)[RPL], T (&th)[RPL], T *lkey, int32_t *lj,
+                                                int32_t *lcnt, unsigned &ninsert)
 {
     const bool send = feeds && lane == 31;
 #pragma unroll
     for (int c = 0; c < CH; c += 2) {
+        // (the spare field of a column holds the top edge of its chunk: the
+        // predecessor of the warp's first row in that column)
         const Col<T> cd0 = cbuf[c];
         const Col<T> cd1 = cbuf[c + 1];
         T C0[RPL];
         T v = __shfl_up_sync(0xffffffffu, C[RPL - 1], 1);
-        T vt = __shfl_sync(0xffffffffu, tp, c);
-        if (lane == 0) v = vt;
+        if (lane == 0) v = cd0.pad;
 #pragma unroll
         for (int a = RPL - 1; a >= 1; --a) C0[a] = fma(dfr[a], cd0.dg, fma(cd0.df, dgr[a], C[a - 1]));
         C0[0] = fma(dfr[0], cd0.dg, fma(cd0.df, dgr[0], v));
         v = __shfl_up_sync(0xffffffffu, C0[RPL - 1], 1);
-        vt = __shfl_sync(0xffffffffu, tp, c + 1);
-        if (lane == 0) v = vt;
+        if (lane == 0) v = cd1.pad;
 #pragma unroll
         for (int a = RPL - 1; a >= 1; --a) C[a] = fma(dfr[a], cd1.dg, fma(cd1.df, dgr[a], C0[a - 1]));
         C[0] = fma(dfr[0], cd1.dg, fma(cd1.df, dgr[0], v));
@@ -304,9 +305,9 @@ __device__ __forceinline__ void band_chunk_pair(const BandArgs<T> &A, const Col<
         // one sign test over both columns' keys; the rare hits re-test per column
         if (__any_sync(0xffffffffu, any_positive_pair(C0, cd0.inv, C, cd1.inv, th))) {
             if (any_positive(C0, cd0.inv, th))
-                topp_hits<T, RPL>(A, C0, cd0.inv, (int32_t)(cs + c), rbase, rl0, th, lkey, lj, lcnt, ninsert);
+                topp_hits<T, RPL>(A, C0, cd0.inv, (int32_t)(cs + c), rl0, th, lkey, lj, lcnt, ninsert);
             if (any_positive(C, cd1.inv, th))
-                topp_hits<T, RPL>(A, C, cd1.inv, (int32_t)(cs + c + 1), rbase, rl0, th, lkey, lj, lcnt, ninsert);
+                topp_hits<T, RPL>(A, C, cd1.inv, (int32_t)(cs + c + 1), rl0, th, lkey, lj, lcnt, ninsert);
         }
     }
 }
@@ -437,10 +438,7 @@ __global__ void __launch_bounds__(NW * 32, band_min_blocks<T, RPL>()) k_band(con
         if (c0 >= A.nl) continue;
         if (SYM && c0 + A.group_w <= i0) continue;   // entirely below the diagonal
         const int64_t c1 = c0 + A.group_w < A.nl ? c0 + A.group_w : A.nl;
-        if (threadIdx.x == 0 && A.stats) {
-            atomicAdd(&A.stats[5], 1ull);
-            atomicAdd(&A.stats[6], (unsigned long long)R * (unsigned long long)(c1 - c0));
-        }
+        if (threadIdx.x == 0 && A.stats) atomicAdd(&A.stats[5], 1ull);
         const int nchunk = (int)((c1 - c0 + CH - 1) / CH);
         const int64_t rfirst = i0 + (int64_t)w * 32 * RPL;
         const int64_t rbase = rfirst + lane * RPL;
@@ -469,6 +467,23 @@ __global__ void __launch_bounds__(NW * 32, band_min_blocks<T, RPL>()) k_band(con
             runmax[a] = neg_inf<T>();
             if (!BINS) lcnt[rl0 + a] = 0;
         }
+        // (top-p form) a warp none of whose rows is wanted (threshold +inf:
+        // certified, flat or past the end), and that neither takes its top
+        // edge from the warp above nor hands one to the warp below, skips
+        // the unit: none of its cells could enter a list
+        if (MODE == MODE_TOPP && seeded && !feeds) {
+            bool want = false;
+#pragma unroll
+            for (int a = 0; a < RPL; ++a) want |= th[a] < T(INFINITY);
+            if (!__any_sync(0xffffffffu, want)) {
+#pragma unroll
+                for (int a = 0; a < RPL; ++a)
+                    if (rbase + a < A.nl) A.scnt[(rbase + a) * A.ngroups + g] = 0;
+                qg += nchunk;
+                continue;
+            }
+        }
+        if (lane == 0 && A.stats) atomicAdd(&A.stats[6], (unsigned long long)(32 * RPL) * (unsigned long long)(c1 - c0));
         T carry = sleft[rfirst];
         // prefetched column data / top edge of the next chunk (the symmetric
         // form carries the column's threshold in the spare field)
@@ -481,7 +496,7 @@ __global__ void __launch_bounds__(NW * 32, band_min_blocks<T, RPL>()) k_band(con
             const unsigned par = (qg / NSLOT) & 1u;
             const int64_t cs = c0 + (int64_t)q * CH;
             Col<T> *cbuf = colbuf + w * CH;
-            cbuf[lane] = ncol;
+            Col<T> cw = ncol;
             T tp;
             if (q + 1 < nchunk) {
                 ncol = A.col[cs + CH + lane];
@@ -499,6 +514,10 @@ __global__ void __launch_bounds__(NW * 32, band_min_blocks<T, RPL>()) k_band(con
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&mempty[w * NSLOT + slot]);   // slot free again
             }
+            // the top edge rides in the column's spare field in the append
+            // form (the symmetric form keeps the column threshold there)
+            if (MODE == MODE_TOPP) cw.pad = tp;
+            cbuf[lane] = cw;
             if (feeds) mbar_wait(&mempty[(w + 1) * NSLOT + slot], par ^ 1u, A.err, A.wave_limit);  // slot free
             __syncwarp();
             T *bout = bbuf + ((w + 1 < NW ? w + 1 : 0) * NSLOT + slot) * CH;
@@ -510,8 +529,8 @@ __global__ void __launch_bounds__(NW * 32, band_min_blocks<T, RPL>()) k_band(con
                 band_chunk<T, RPL, NW, MODE, true>(A, cbuf, tp, bout, lane, feeds, cs, rbase, rl0, C, dfr, dgr, th,
                                                    invr, runmax, lkey, lj, lcnt, ninsert);
             else if (MODE == MODE_TOPP && BAND_PAIR)
-                band_chunk_pair<T, RPL, NW>(A, cbuf, tp, bout, lane, feeds, cs, rbase, rl0, C, dfr, dgr, th, lkey, lj,
-                                            lcnt, ninsert);
+                band_chunk_pair<T, RPL, NW>(A, cbuf, bout, lane, feeds, cs, rl0, C, dfr, dgr, th, lkey, lj, lcnt,
+                                            ninsert);
             else
                 band_chunk<T, RPL, NW, MODE, false>(A, cbuf, tp, bout, lane, feeds, cs, rbase, rl0, C, dfr, dgr, th,
                                                     invr, runmax, lkey, lj, lcnt, ninsert);

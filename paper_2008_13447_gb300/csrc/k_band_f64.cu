@@ -56,42 +56,92 @@ void launch_seed<double>(const SeedArgs<double> &a, cudaStream_t s)
 // Entry (k, j) of the table: row 0 holds C(0, j); row k >= 1 holds C(kS, 0)
 // at j = 0 and C(kS - 1, j - 1) for j >= 1.
 // Each thread takes one column j and SEED_ROWS consecutive seed rows, so
-// the column's factor (x[j-1+l] - mu[j-1]) is loaded once for them.
+// the column's factor (x[j-1+l] - mu[j-1]) is loaded once for them; the
+// block's row factors are formed once in shared memory. Away from the first
+// row and column the rows go in batches of SEED_BATCH whose loads are all
+// issued before the first store (several loads in flight per thread: the
+// step is HBM-bound).
 constexpr int SEED_ROWS = 16;
+constexpr int SEED_BATCH = 4;
+
+__device__ __forceinline__ double seed_entry(const double *x, const double *mu, int64_t nl, int l, int S, int64_t k,
+                                             int64_t j, double f, double v)
+{
+    int64_t ra, c;
+    if (k == 0) {
+        ra = 0;
+        c = j;
+    } else if (j == 0) {
+        ra = k * S;
+        c = 0;
+    } else {
+        ra = k * S - 1;
+        c = j - 1;
+    }
+    return (ra < nl && c < nl) ? fma(f * (x[ra + l] - mu[ra]), x[c + l] - mu[c], v) : 0.0;
+}
 
 template <typename T>
-__global__ void __launch_bounds__(128, 16) k_seed_step(const double *x, const double *mu, int64_t nl, int l, int S, int64_t K, int64_t spitch,
-                            double *master, T *seed, int update)
+__global__ void __launch_bounds__(128, 16) k_seed_step(const double *__restrict__ x, const double *__restrict__ mu,
+                                                       int64_t nl, int l, int S, int64_t K, int64_t spitch,
+                                                       double *__restrict__ master, T *__restrict__ seed, int update)
 {
+    // the block's row factors l/(l+1) (x[kS-1+l] - mu[kS-1]) (the same for
+    // every column), and which of its rows still exist at l + 1
+    __shared__ double sa[SEED_ROWS];
+    __shared__ unsigned svalid;
+    const int64_t k0 = (int64_t)blockIdx.y * SEED_ROWS;
+    const int64_t k1 = k0 + SEED_ROWS < K ? k0 + SEED_ROWS : K;
+    const double f = (double)l / (double)(l + 1);
+    if (threadIdx.x < 32) {
+        const int64_t k = k0 + threadIdx.x;
+        const int64_t ra = k * S - 1;
+        const bool ok = threadIdx.x < SEED_ROWS && k >= 1 && k < k1 && ra < nl;
+        if (threadIdx.x < SEED_ROWS) sa[threadIdx.x] = ok ? f * (x[ra + l] - mu[ra]) : 0.0;
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (threadIdx.x == 0) svalid = m;
+    }
+    __syncthreads();
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= spitch) return;
-    const int64_t k0 = (int64_t)blockIdx.y * SEED_ROWS;
-    const double f = (double)l / (double)(l + 1);
-    const int64_t cj = j - 1;   // the column window of rows k >= 1
-    const double bj = (cj >= 0 && cj < nl) ? x[cj + l] - mu[cj] : 0.0;
-    for (int64_t k = k0; k < k0 + SEED_ROWS && k < K; ++k) {
-        const int64_t at = k * spitch + j;
-        double v = master[at];
-        if (update) {
-            const int64_t kS = k * S;
-            int64_t ra, c;
-            double b = bj;
-            if (k == 0) {
-                ra = 0;
-                c = j;
-                b = (c < nl) ? x[c + l] - mu[c] : 0.0;
-            } else if (j == 0) {
-                ra = kS;
-                c = 0;
-                b = x[l] - mu[0];
-            } else {
-                ra = kS - 1;
-                c = cj;
+    if (k0 == 0 || j == 0) {
+        // the first seed row (row 0's windows) and the first column
+#pragma unroll 1
+        for (int64_t k = k0; k < k1; ++k) {
+            const int64_t at = k * spitch + j;
+            double v = master[at];
+            if (update) {
+                v = seed_entry(x, mu, nl, l, S, k, j, f, v);
+                master[at] = v;
             }
-            v = (ra < nl && c < nl) ? fma(f * (x[ra + l] - mu[ra]), b, v) : 0.0;
-            master[at] = v;
+            seed[at] = (T)v;
         }
-        seed[at] = (T)v;
+        return;
+    }
+    // rows k >= 1, column j >= 1: C(kS - 1, j - 1) gains the row factor
+    // times (x[j-1+l] - mu[j-1])
+    const unsigned valid = (j - 1 < nl) ? svalid : 0u;
+    const double bj = (j - 1 < nl) ? x[j - 1 + l] - mu[j - 1] : 0.0;
+    double *mp = master + k0 * spitch + j;
+    T *sp = seed + k0 * spitch + j;
+    const int nrow = (int)(k1 - k0);
+#pragma unroll 1
+    for (int t0 = 0; t0 < nrow; t0 += SEED_BATCH) {
+        double v[SEED_BATCH];
+#pragma unroll
+        for (int t = 0; t < SEED_BATCH; ++t) v[t] = t0 + t < nrow ? mp[(int64_t)t * spitch] : 0.0;
+        if (update) {
+#pragma unroll
+            for (int t = 0; t < SEED_BATCH; ++t) {
+                v[t] = (valid >> (t0 + t)) & 1u ? fma(sa[t0 + t], bj, v[t]) : 0.0;
+                if (t0 + t < nrow) mp[(int64_t)t * spitch] = v[t];
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < SEED_BATCH; ++t)
+            if (t0 + t < nrow) sp[(int64_t)t * spitch] = (T)v[t];
+        mp += SEED_BATCH * spitch;
+        sp += SEED_BATCH * spitch;
     }
 }
 
