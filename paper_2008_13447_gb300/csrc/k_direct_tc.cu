@@ -199,6 +199,10 @@ __global__ void k_tc_rows(TcArgs A)
     }
 }
 
+// Insert (key, j, dq) into a row's list (keys descending, at most p). The
+// callers test key > kmin first, kmin = the p-th kept key once p are kept
+// (else -inf): the same test this insert makes, held in a register so that
+// the columns that cannot enter skip the call.
 template <typename T>
 __device__ __forceinline__ void list_insert(T *K, int32_t *J, float *D, int &cnt, int p, T key, int32_t j, float dq)
 {
@@ -283,6 +287,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_direct_tc(TcArgs A)
         int32_t *mj = lj + (h * TC_M + m) * p;
         float *md = ld + (h * TC_M + m) * p;
         int cnt = 0;
+        float kmin = -INFINITY;   // the p-th kept key once p are kept
         for (int st0 = 0; st0 < TC_COLS / TC_N && ok; ++st0) {
             const int64_t j0 = cb0 + (int64_t)st0 * TC_N;
             if (j0 >= A.nl) break;
@@ -389,14 +394,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_direct_tc(TcArgs A)
                     __syncwarp();
                     tc_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0, v);
                     if (!erow) continue;
+                    unsigned hits = 0;
 #pragma unroll
                     for (int c = 0; c < 32; ++c) {
                         const ColC k = cc[c0 + c];
                         const float t = fmaf(-k.c, asum, v[c]);
-                        if (fmaf(t, k.g, k.dq) > thq) {
+                        hits |= (unsigned)(fmaf(t, k.g, k.dq) > thq && t * k.g * sq > kmin) << c;
+                    }
+                    if (hits) {
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) {
+                            if (!((hits >> c) & 1u)) continue;
+                            const ColC k = cc[c0 + c];
+                            const float key = fmaf(-k.c, asum, v[c]) * k.g * sq;
                             const int64_t j = j0 + c0 + c;
-                            if (j < A.nl && (j < exlo || j > exhi))
-                                list_insert<float>(mk, mj, md, cnt, p, t * k.g * sq, (int32_t)j, k.dq);
+                            if (key > kmin && j < A.nl && (j < exlo || j > exhi)) {
+                                list_insert<float>(mk, mj, md, cnt, p, key, (int32_t)j, k.dq);
+                                if (cnt == p) kmin = mk[p - 1];
+                            }
                         }
                     }
                 }
@@ -585,6 +600,17 @@ __global__ void __launch_bounds__(TC2_THREADS, 1) k_direct_tc2(TcArgs A)
                     cc[a * TC_N + tid] = cv;
                 }
                 mbar_arrive1(&bars.ccready[a]);
+                // x - s in FP32 from the series' FP32 pairs (GB300's FP64 rate
+                // is 1/64 of FP32): relative error below 2^-23
+                const float s_hi = (float)sft, s_lo = (float)(sft - (double)s_hi);
+                // the chunk's values v[i], i = tid and tid + 256 (< SHIFT_LEN + 7),
+                // loaded one chunk ahead so their latency overlaps the tile build
+                float xa_h = 0.0f, xa_l = 0.0f, xb_h = 0.0f, xb_l = 0.0f;
+                {
+                    const int64_t gx = j0 + tid, gy = gx + TC2_PROD;
+                    if (gx < A.n) { xa_h = A.xh[gx]; xa_l = A.xl[gx]; }
+                    if (tid + TC2_PROD < SHIFT_LEN + 7 && gy < A.n) { xb_h = A.xh[gy]; xb_l = A.xl[gy]; }
+                }
                 for (int kc = 0; kc < nkc; ++kc, ++c) {
                     const int g = c & 1;
                     unsigned char *sa = sm + g * TC2_STAGE;
@@ -602,14 +628,14 @@ __global__ void __launch_bounds__(TC2_THREADS, 1) k_direct_tc2(TcArgs A)
                     if (kc > 0) prod_sync();
                     __half *sh = shift;
                     const int64_t gb = j0 + (int64_t)kc * TC_KC;
-                    // x - s in FP32 from the series' FP32 pairs (GB300's FP64 rate
-                    // is 1/64 of FP32): relative error below 2^-23
-                    const float s_hi = (float)sft, s_lo = (float)(sft - (double)s_hi);
                     // each value v[i] (i < SHIFT_LEN + 7) once, stored to the
                     // eight copies at i - sf (copy sf holds v[i' + sf] at i')
-                    for (int i = tid; i < SHIFT_LEN + 7; i += TC2_PROD) {
-                        const int64_t gx = gb + i;
-                        const float v = gx < A.n ? ((A.xh[gx] - s_hi) + (A.xl[gx] - s_lo)) * Sb : 0.0f;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int i = tid + h * TC2_PROD;
+                        if (i >= SHIFT_LEN + 7) break;
+                        const float xh = h ? xb_h : xa_h, xl = h ? xb_l : xa_l;
+                        const float v = gb + i < A.n ? ((xh - s_hi) + (xl - s_lo)) * Sb : 0.0f;
                         __half hi, lo;
                         split_half(v, hi, lo);
 #pragma unroll
@@ -620,6 +646,13 @@ __global__ void __launch_bounds__(TC2_THREADS, 1) k_direct_tc2(TcArgs A)
                                 sh[(8 + sf) * SHIFT_LEN + ip] = lo;
                             }
                         }
+                    }
+                    // the next chunk's values
+                    if (kc + 1 < nkc) {
+                        const int64_t gx = gb + TC_KC + tid, gy = gx + TC2_PROD;
+                        xa_h = xa_l = xb_h = xb_l = 0.0f;
+                        if (gx < A.n) { xa_h = A.xh[gx]; xa_l = A.xl[gx]; }
+                        if (tid + TC2_PROD < SHIFT_LEN + 7 && gy < A.n) { xb_h = A.xh[gy]; xb_l = A.xl[gy]; }
                     }
                     prod_sync();
                     // tile row nn (hi and lo): eight aligned 16-byte copies from
@@ -695,6 +728,7 @@ __global__ void __launch_bounds__(TC2_THREADS, 1) k_direct_tc2(TcArgs A)
             const float thq = erow ? (float)A.thr[r] / sq : 0.0f;
             const int64_t exlo = r - A.E, exhi = r + A.E;
             int cnt = 0;
+            float kmin = -INFINITY;   // the p-th kept key once p are kept
             for (int st0 = 0; st0 < TC_COLS / TC_N; ++st0, ++t) {
                 const int64_t j0 = cb0 + (int64_t)st0 * TC_N;
                 if (j0 >= A.nl) break;
@@ -708,14 +742,26 @@ __global__ void __launch_bounds__(TC2_THREADS, 1) k_direct_tc2(TcArgs A)
                     __syncwarp();
                     tc_ld32(tmem + ((uint32_t)(m & ~31) << 16) + (uint32_t)(a * TC_N + c0), v);
                     if (!erow || *abortv) continue;
+                    // the 32 columns' tests first (independent, no branches),
+                    // then the rare candidates in column order
+                    unsigned hits = 0;
 #pragma unroll
                     for (int q = 0; q < 32; ++q) {
                         const ColC k = ca[c0 + q];
                         const float tt = fmaf(-k.c, asum, v[q]);
-                        if (fmaf(tt, k.g, k.dq) > thq) {
+                        hits |= (unsigned)(fmaf(tt, k.g, k.dq) > thq && tt * k.g * sq > kmin) << q;
+                    }
+                    if (hits) {
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) {
+                            if (!((hits >> q) & 1u)) continue;
+                            const ColC k = ca[c0 + q];
+                            const float key = fmaf(-k.c, asum, v[q]) * k.g * sq;
                             const int64_t j = j0 + c0 + q;
-                            if (j < A.nl && (j < exlo || j > exhi))
-                                list_insert<float>(mk, mj, md, cnt, p, tt * k.g * sq, (int32_t)j, k.dq);
+                            if (key > kmin && j < A.nl && (j < exlo || j > exhi)) {
+                                list_insert<float>(mk, mj, md, cnt, p, key, (int32_t)j, k.dq);
+                                if (cnt == p) kmin = mk[p - 1];
+                            }
                         }
                     }
                 }
