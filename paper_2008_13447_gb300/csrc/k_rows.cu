@@ -84,11 +84,13 @@ __device__ double comoment_comp(const float *__restrict__ xh, const float *__res
     for (int t = 0; t < l; ++t) {
         const float a = (xh[i + t] - mih) + (xl[i + t] - mil);
         const float b = (xh[j + t] - mjh) + (xl[j + t] - mjl);
-        const float pr = a * b;
+        // (explicit roundings: a contraction of S + a*b into an FMA would
+        // break the exactness of TwoProd / TwoSum)
+        const float pr = __fmul_rn(a, b);
         const float pe = fmaf(a, b, -pr);
-        const float sn = S + pr;
-        const float bv = sn - S;
-        const float se = (S - (sn - bv)) + (pr - bv);
+        const float sn = __fadd_rn(S, pr);
+        const float bv = __fsub_rn(sn, S);
+        const float se = __fadd_rn(__fsub_rn(S, __fsub_rn(sn, bv)), __fsub_rn(pr, bv));
         S = sn;
         Er += pe + se;
     }
