@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3, help="timed end-to-end repetitions (median)")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="1: repeated profiles replay a captured CUDA graph (default); 0: launched one by one")
+    ap.add_argument("--tc-tma", type=int, default=0, choices=[0, 1],
+                    help="split_tc: 0 column tiles built by the kernel's producer warps (default); "
+                         "1 loaded by TMA from per-length shifted copies")
     ap.add_argument("--band-form", type=int, default=0, choices=[0, 1],
                     help="0: full rows; 1: symmetric band form when most bands are active")
     ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the plain FP64 GPU path")
@@ -371,6 +374,7 @@ def main():
     stream = torch.cuda.current_stream()
     w = make_workload(args)
     mad.mad_set_graphs(args.graphs)
+    mad.mad_debug_tc_tma(args.tc_tma)
     batch = len(w.series) > 1
     p, k, m = w.p, w.k, w.m
     prec = PRECISIONS[args.precision](mad)
@@ -487,6 +491,8 @@ def main():
     cfg = {**workload_config(args.workload, w), "precision": args.precision, "band_form": args.band_form,
            "l2": "flushed between timed steps (512 MB write)", "parallelism": "replicas",
            "graph_replay": bool(acc["graph"]), "graphs_option": args.graphs}
+    if args.precision == "split_tc":
+        cfg["tc_column_tiles"] = "tma" if args.tc_tma else "built"
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",

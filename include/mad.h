@@ -382,6 +382,23 @@ MAD_API void mad_debug_audit_error_bounds(int32_t on);
  * workspace is still reused). Takes effect at the next mad_profile. */
 MAD_API void mad_set_graphs(int32_t on);
 
+/* Process-wide switch of how the tensor-core path (MAD_SPLIT_TC) forms its
+ * column operand. 0 (default): producer warps of the tensor-core kernel
+ * build each 256 x 64 column tile in shared memory from the series. 1 (p <=
+ * 16): a prep kernel writes each 256-column tile's values once per length
+ * as eight shifted FP16-pair copies, and the tensor-core kernel loads each
+ * chunk's tile by one TMA tensor load (Hankel rows 16 bytes apart), with
+ * eight epilogue warps. Results are the same bit for bit (the same FP16
+ * pairs and products; ties between equal keys go to the smaller column
+ * either way). Form 1 is faster for an isolated launch (3.2 against 4.2 ms
+ * on a 262,144-point series) but slower inside the profile pipeline, where
+ * its 64 KB of column tile per row tile and chunk compete for L2 with the
+ * seed rows streamed beside it. Takes effect at the next mad_profile; form
+ * 1 falls back to form 0 when the driver refuses the TMA descriptor.
+ * Sec. "Computing The Matrix Profile" (the recomputed rows' sliding dot
+ * products). */
+MAD_API void mad_debug_tc_tma(int32_t on);
+
 /* Process-wide switch of the launch autotuner (default on). On: the first
  * profile of a series of at most 32768 windows in a new size bucket (log2 of
  * the window count, log2 of lmin, p, precision, mode) times a short trial

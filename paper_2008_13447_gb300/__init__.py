@@ -34,7 +34,7 @@ ABI_FUNCTIONS = ("mad_create", "mad_create_device", "mad_create_batch", "mad_pro
                  "mad_valmp", "mad_matrix_profile", "mad_stats",
                  "mad_mth_nn_dist_noalloc", "mad_motif_sets", "mad_observe", "mad_last_error",
                  "mad_destroy", "mad_debug_wavefront_wait_limit", "mad_debug_audit_error_bounds",
-                 "mad_set_graphs", "mad_set_autotune")
+                 "mad_set_graphs", "mad_set_autotune", "mad_debug_tc_tma")
 
 
 class mad_options(C.Structure):
@@ -121,6 +121,8 @@ def library() -> C.CDLL:
         lib.mad_set_graphs.restype = None
         lib.mad_set_autotune.argtypes = [i32]
         lib.mad_set_autotune.restype = None
+        lib.mad_debug_tc_tma.argtypes = [i32]
+        lib.mad_debug_tc_tma.restype = None
         _lib = lib
     return _lib
 
@@ -317,3 +319,9 @@ def mad_last_error(ctx=None):
 def mad_destroy(ctx):
     if ctx is not None:
         library().mad_destroy(ctx)
+
+
+def mad_debug_tc_tma(on):
+    """Tensor-core path: column tiles built by the kernel's producer warps
+    (0, default) or loaded by TMA from per-length shifted copies (1)."""
+    library().mad_debug_tc_tma(1 if on else 0)

@@ -37,7 +37,10 @@
 // more rounding of 2^-23 relative to the column operand: 4 2^-22 there).
 // A candidate is kept when q + dq_j could beat the row's threshold, and
 // carries dq_j to the merge.
+#include <cstring>
+#include <cuda.h>
 #include <cuda_fp16.h>
+#include <cudaTypedefs.h>
 
 #include "kernels.cuh"
 
@@ -786,6 +789,390 @@ __global__ void __launch_bounds__(TC2_THREADS, 1) k_direct_tc2(TcArgs A)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_N) : "memory");
     }
 }
+
+// ------------------------------------------------------------------
+// Column tiles by TMA (p <= TC3_MAXP): the same products and error bounds,
+// without building the column operand in shared memory. The column operand
+// of a 256-column tile is a Hankel matrix: for chunk kc its row for column
+// j holds V[j - j0 + 64 kc + k], k < 64, with V = S_b (x - s) the tile's
+// scaled values. k_tc_cols writes, once per length and tile, V as FP16
+// pairs in eight copies shifted by 0..7 values (copy sf holds V[i + sf] at
+// i); the column j = j0 + 8 r + sf then starts at copy sf, offset
+// 8 r + 64 kc: 16-byte aligned rows 16 bytes apart, so one 5-D TMA box
+// {64 lags, 32 rows, 8 copies, tile, hi | lo} lands the 256 x 64 tile in
+// the 128-byte-swizzled K-major layout the MMA reads, its row n' = 32 sf + r
+// holding column j0 + 8 (n' mod 32) + n' / 32 (so do the accumulator's
+// columns and the column constants).
+//   warp 0 (loader): per tile the column constants (bulk copy), per chunk
+//          the row operand (two bulk copies) and the column operand (two
+//          TMA loads), each into a stage freed by the MMA's commit;
+//   warp 1 (MMA):    as in k_direct_tc2;
+//   warps 2..9 (epilogue): warp w reads TMEM lanes 32 (w mod 4) .. and the
+//          column half (w - 2) / 4 of each tile; each thread keeps its row's
+//          best p keys of its half in registers; the halves are merged at
+//          the end of each work item.
+// Every wait is bounded; after the first one that runs out no further copy
+// is issued, every later wait returns at once, and before the block ends
+// the loader waits (bounded) for the copies it issued.
+constexpr int TC3_THREADS = 320;
+constexpr int TC3_EPI0 = 64;          // first epilogue thread (warp 2)
+constexpr int TC3_MAXP = 16;
+constexpr int TC3_STAGE = 2 * A_TILE_BYTES + 2 * B_TILE_BYTES;   // 96 KB
+constexpr int TC3_CC_BYTES = TC_N * 16;                          // column constants of a tile
+
+struct Tc3Params {
+    TcArgs a;
+    CUtensorMap bmap;     // the shifted copies, dims {lc, 32, 8, tiles, 2}
+};
+
+struct Tc3Bars {
+    uint64_t full[2], freeb[2], accfull[2], accfree[2], ccfull[2], fin;
+};
+
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            int c4, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                 "%4, %5, %6}], [%7];" ::"r"(su32(dst)),
+                 "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(su32(bar))
+                 : "memory");
+}
+
+// A row's best p (key, column, bound) in registers, sorted by (key
+// descending, column ascending); empty slots hold (-inf, INT32_MAX).
+__device__ __forceinline__ void top_clear(float (&k)[TC3_MAXP], int32_t (&j)[TC3_MAXP], float (&d)[TC3_MAXP])
+{
+#pragma unroll
+    for (int t = 0; t < TC3_MAXP; ++t) {
+        k[t] = -INFINITY;
+        j[t] = INT32_MAX;
+        d[t] = 0.0f;
+    }
+}
+// one compare-and-swap pass over the p slots (static indices)
+__device__ __forceinline__ void top_insert(float (&k)[TC3_MAXP], int32_t (&j)[TC3_MAXP], float (&d)[TC3_MAXP],
+                                           float key, int32_t jj, float dq, int p)
+{
+#pragma unroll
+    for (int t = 0; t < TC3_MAXP; ++t) {
+        const bool b = t < p && (key > k[t] || (key == k[t] && jj < j[t]));
+        const float tk = k[t], td = d[t];
+        const int32_t tj = j[t];
+        k[t] = b ? key : tk;
+        j[t] = b ? jj : tj;
+        d[t] = b ? dq : td;
+        key = b ? tk : key;
+        jj = b ? tj : jj;
+        dq = b ? td : dq;
+    }
+}
+// the p-th kept key (-inf until p are kept)
+__device__ __forceinline__ float top_last(const float (&k)[TC3_MAXP], int p)
+{
+    float v = -INFINITY;
+#pragma unroll
+    for (int t = 0; t < TC3_MAXP; ++t) v = (t == p - 1) ? k[t] : v;
+    return v;
+}
+
+// Per 256-column tile: shift s, scale S_b, the column constants in
+// accumulator order, and the eight shifted copies of the tile's values as
+// FP16 pairs (lags up to 64 nkc). One block per tile.
+__global__ void __launch_bounds__(TC_N) k_tc_cols(TcArgs A)
+{
+    if (*A.nrows <= 0) return;
+    extern __shared__ __half vsh[];          // [2][lc + 8]: the tile's values, hi and lo
+    __shared__ float red[TC_N / 32];
+    const int tid = threadIdx.x;
+    const int64_t t = blockIdx.x;
+    const int64_t j0 = t * TC_N;
+    const int l = A.l;
+    const int64_t jm = j0 + TC_N / 2 < A.nl ? j0 + TC_N / 2 : A.nl - 1;
+    const double sft = A.mu[jm];
+    const int64_t jc = j0 + tid;
+    float spread = 0.0f;
+    if (jc < A.nl) {
+        const double m2 = A.m2[jc];
+        spread = (float)(sqrt(m2 > 0.0 ? m2 : 0.0) + fabs(A.mu[jc] - sft));
+    }
+    for (int o = 16; o > 0; o >>= 1) spread = fmaxf(spread, __shfl_xor_sync(0xffffffffu, spread, o));
+    if ((tid & 31) == 0) red[tid >> 5] = spread;
+    __syncthreads();
+    float mx = 0.0f;
+    for (int w = 0; w < TC_N / 32; ++w) mx = fmaxf(mx, red[w]);
+    const float Sb = mx > 0.0f ? exp2f(floorf(log2f(255.0f / mx))) : 1.0f;
+    {
+        ColC cv{0.0f, 0.0f, 0.0f, 0.0f};
+        float dqm = 0.0f;
+        if (jc < A.nl) {
+            const double isd = A.isd[jc];
+            const double dm = A.mu[jc] - sft;
+            cv.c = (float)(Sb * dm);
+            cv.g = (float)(isd / ((double)TC_SA * Sb));
+            const double f = sqrt(1.0 + (double)l * dm * dm * isd * isd);
+            const double K = (double)A.nkc * TC_KC;
+            cv.dq = (float)(1.5 * ((4.0 * 0x1p-22 + (3.0 * K + 4.0) * 0x1p-24) * f + 0x1p-23));
+            dqm = cv.dq;
+        }
+        // accumulator column n' = 32 (tid mod 8) + tid / 8
+        reinterpret_cast<ColC *>(A.gcc)[t * TC_N + 32 * (tid & 7) + (tid >> 3)] = cv;
+        for (int o = 16; o > 0; o >>= 1) dqm = fmaxf(dqm, __shfl_xor_sync(0xffffffffu, dqm, o));
+        if ((tid & 31) == 0 && dqm > 0.0f) atomicMax(reinterpret_cast<int *>(A.dq_max), __float_as_int(dqm));
+    }
+    // the tile's values V[i] = S_b (x[j0 + i] - s), i < need + 7, as FP16 pairs
+    const int need = 248 + TC_KC * A.nkc;    // copy length read at this length
+    const int lc = A.lc;
+    __half *vh = vsh, *vl = vsh + lc + 8;
+    const float s_hi = (float)sft, s_lo = (float)(sft - (double)s_hi);
+    for (int i = tid; i < need + 7; i += TC_N) {
+        const int64_t gx = j0 + i;
+        const float v = gx < A.n ? ((A.xh[gx] - s_hi) + (A.xl[gx] - s_lo)) * Sb : 0.0f;
+        __half hi, lo;
+        split_half(v, hi, lo);
+        vh[i] = hi;
+        vl[i] = lo;
+    }
+    __syncthreads();
+    // copy sf of half hl at ((hl * tiles + t) * 8 + sf) * lc
+    __half *dst = reinterpret_cast<__half *>(A.bcopy);
+    for (int e = tid; e < 16 * need; e += TC_N) {
+        const int row = e / need, i = e - row * need;      // row = hl * 8 + sf
+        const int hl = row >> 3, sf = row & 7;
+        dst[((size_t)(hl * A.tiles_ws + t) * 8 + sf) * lc + i] = (hl ? vl : vh)[i + sf];
+    }
+}
+
+__global__ void __launch_bounds__(TC3_THREADS, 1) k_direct_tc3(const __grid_constant__ Tc3Params P)
+{
+    const TcArgs &A = P.a;
+    const int nrows = *A.nrows;
+    if (nrows <= 0) return;
+    const int nkc = A.nkc;
+    const int p = A.p;
+    const int rtiles = (nrows + TC_M - 1) / TC_M;
+    const int64_t items = (int64_t)rtiles * A.nblk;
+    if (blockIdx.x >= items) return;
+
+    extern __shared__ __align__(1024) unsigned char sm_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)sm_raw + 1023) & ~(uintptr_t)1023);
+    // stage g: A hi, A lo (16 KB each), B hi, B lo (32 KB each)
+    ColC *cc = reinterpret_cast<ColC *>(sm + 2 * TC3_STAGE);                 // [2][TC_N]
+    float *xk = reinterpret_cast<float *>(cc + 2 * TC_N);                    // [TC_M][TC3_MAXP] half 1's lists
+    int32_t *xj = reinterpret_cast<int32_t *>(xk + TC_M * TC3_MAXP);
+    float *xd = reinterpret_cast<float *>(xj + TC_M * TC3_MAXP);
+    __shared__ __align__(8) Tc3Bars bars;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    __shared__ int xcnt[TC_M];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        for (int g = 0; g < 2; ++g) {
+            mbar_init(&bars.full[g], 1);               // the loader's expect-tx
+            mbar_init(&bars.freeb[g], 1);              // MMA commit
+            mbar_init(&bars.accfull[g], 1);            // MMA commit
+            mbar_init(&bars.accfree[g], 2 * TC_M);     // epilogue threads
+            mbar_init(&bars.ccfull[g], 1);             // the loader's expect-tx
+        }
+        mbar_init(&bars.fin, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.bmap)) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                     "r"(2 * TC_N)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    volatile int *abortv = &abort_flag;
+    auto wait = [&](uint64_t *b, unsigned par) {
+        if (*abortv) return false;
+        if (mbar_wait_b(b, par, A.err)) return true;
+        *abortv = 1;
+        return false;
+    };
+
+    if (tid == 0) {
+        // ------------------------------------------------------- loader
+        unsigned t = 0, c = 0;
+        int lastc0 = -1, lastc1 = -1, lastt0 = -1, lastt1 = -1;   // last copies issued per buffer
+        for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+            const int rt = (int)(item / A.nblk);
+            const int64_t cb0 = (int64_t)(item % A.nblk) * TC_COLS;
+            for (int st0 = 0; st0 < TC_COLS / TC_N; ++st0, ++t) {
+                const int64_t j0 = cb0 + (int64_t)st0 * TC_N;
+                if (j0 >= A.nl) break;
+                const int a = t & 1;
+                const int tile = (int)(j0 / TC_N);
+                if (t >= 2) wait(&bars.accfree[a], ((t >> 1) - 1) & 1);
+                if (!*abortv) {
+                    mbar_expect_tx(&bars.ccfull[a], TC3_CC_BYTES);
+                    bulk_g2s(cc + a * TC_N, reinterpret_cast<const ColC *>(A.gcc) + (size_t)tile * TC_N,
+                             TC3_CC_BYTES, &bars.ccfull[a]);
+                    if (a) lastt1 = (int)t; else lastt0 = (int)t;
+                }
+                for (int kc = 0; kc < nkc; ++kc, ++c) {
+                    const int g = c & 1;
+                    unsigned char *sa = sm + g * TC3_STAGE;
+                    unsigned char *sb = sa + 2 * A_TILE_BYTES;
+                    if (c >= 2) wait(&bars.freeb[g], ((c >> 1) - 1) & 1);
+                    if (*abortv) continue;
+                    mbar_expect_tx(&bars.full[g], TC3_STAGE);
+                    const unsigned char *src = A.aimg + ((size_t)(rt * nkc + kc) * 2) * A_TILE_BYTES;
+                    bulk_g2s(sa, src, A_TILE_BYTES, &bars.full[g]);
+                    bulk_g2s(sa + A_TILE_BYTES, src + A_TILE_BYTES, A_TILE_BYTES, &bars.full[g]);
+                    tma_load_5d(sb, &P.bmap, kc * TC_KC, 0, 0, tile, 0, &bars.full[g]);
+                    tma_load_5d(sb + B_TILE_BYTES, &P.bmap, kc * TC_KC, 0, 0, tile, 1, &bars.full[g]);
+                    if (g) lastc1 = (int)c; else lastc0 = (int)c;
+                }
+            }
+        }
+        // the copies issued have landed before the block ends
+        if (lastc0 >= 0) mbar_wait_b(&bars.full[0], ((unsigned)lastc0 >> 1) & 1, A.err);
+        if (lastc1 >= 0) mbar_wait_b(&bars.full[1], ((unsigned)lastc1 >> 1) & 1, A.err);
+        if (lastt0 >= 0) mbar_wait_b(&bars.ccfull[0], ((unsigned)lastt0 >> 1) & 1, A.err);
+        if (lastt1 >= 0) mbar_wait_b(&bars.ccfull[1], ((unsigned)lastt1 >> 1) & 1, A.err);
+    } else if (tid == 32) {
+        // ----------------------------------------------------------- MMA
+        unsigned t = 0, c = 0;
+        for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+            const int64_t cb0 = (int64_t)(item % A.nblk) * TC_COLS;
+            for (int st0 = 0; st0 < TC_COLS / TC_N; ++st0, ++t) {
+                if (cb0 + (int64_t)st0 * TC_N >= A.nl) break;
+                const int a = t & 1;
+                if (t >= 2) wait(&bars.accfree[a], ((t >> 1) - 1) & 1);
+                tc_fence_after();
+                const uint32_t dacc = tmem + (uint32_t)(a * TC_N);
+                for (int kc = 0; kc < nkc; ++kc, ++c) {
+                    const int g = c & 1;
+                    wait(&bars.full[g], (c >> 1) & 1);
+                    tc_fence_after();
+                    if (!*abortv) {
+                        const unsigned a0 = su32(sm + g * TC3_STAGE), b0 = a0 + 2 * A_TILE_BYTES;
+#pragma unroll
+                        for (int ks = 0; ks < TC_KC / 16; ++ks) {
+                            const uint64_t ah = sdesc(a0 + ks * 32), al = sdesc(a0 + A_TILE_BYTES + ks * 32);
+                            const uint64_t bh = sdesc(b0 + ks * 32), bl = sdesc(b0 + B_TILE_BYTES + ks * 32);
+                            tc_mma(dacc, ah, bh, (kc > 0 || ks > 0) ? 1u : 0u);
+                            tc_mma(dacc, ah, bl, 1u);
+                            tc_mma(dacc, al, bh, 1u);
+                        }
+                    }
+                    tc_commit(&bars.freeb[g]);                 // the stage may be refilled
+                    if (kc == nkc - 1) tc_commit(&bars.accfull[a]);   // the tile's accumulator is complete
+                }
+            }
+        }
+        // every MMA issued has completed before the accumulators are freed
+        tc_commit(&bars.fin);
+        mbar_wait_b(&bars.fin, 0, A.err);
+    } else if (tid >= TC3_EPI0) {
+        // ------------------------------------------------------ epilogue
+        const int q = warp & 3;                     // TMEM lane quarter of this warp
+        const int h = (warp - 2) >> 2;              // column half of each tile
+        const int m = 32 * q + lane;                // row of the tile (TMEM lane)
+        unsigned t = 0;
+        float Lk[TC3_MAXP], Ld[TC3_MAXP];
+        int32_t Lj[TC3_MAXP];
+        for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+            const int rt = (int)(item / A.nblk);
+            const int cb = (int)(item % A.nblk);
+            const int64_t cb0 = (int64_t)cb * TC_COLS;
+            const int64_t pos = (int64_t)rt * TC_M + m;
+            const bool erow = pos < nrows;
+            const int64_t r = erow ? A.rows[pos] : -1;
+            const float asum = erow ? A.asum[pos] : 0.0f;
+            const float sq = erow ? A.sqm2[pos] : 0.0f;
+            const float thq = erow ? (float)A.thr[r] / sq : 0.0f;
+            const int64_t exlo = r - A.E, exhi = r + A.E;
+            top_clear(Lk, Lj, Ld);
+            int cnt = 0;
+            float kmin = -INFINITY;   // the p-th kept key once p are kept
+            for (int st0 = 0; st0 < TC_COLS / TC_N; ++st0, ++t) {
+                const int64_t j0 = cb0 + (int64_t)st0 * TC_N;
+                if (j0 >= A.nl) break;
+                const int a = t & 1;
+                wait(&bars.accfull[a], (t >> 1) & 1);
+                wait(&bars.ccfull[a], (t >> 1) & 1);
+                tc_fence_after();
+                const ColC *ca = cc + a * TC_N;
+#pragma unroll 1
+                for (int c0 = h * (TC_N / 2); c0 < (h + 1) * (TC_N / 2); c0 += 32) {
+                    const int sf = c0 >> 5;             // accumulator columns 32 sf + r: series column j0 + 8 r + sf
+                    float v[32];
+                    __syncwarp();
+                    tc_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * TC_N + c0), v);
+                    if (!erow || *abortv) continue;
+                    // the 32 columns' tests first (independent, no branches),
+                    // then the rare candidates
+                    unsigned hits = 0;
+#pragma unroll
+                    for (int rr = 0; rr < 32; ++rr) {
+                        const ColC k = ca[c0 + rr];
+                        const float tt = fmaf(-k.c, asum, v[rr]);
+                        hits |= (unsigned)(fmaf(tt, k.g, k.dq) > thq && tt * k.g * sq >= kmin) << rr;
+                    }
+                    if (hits) {
+#pragma unroll
+                        for (int rr = 0; rr < 32; ++rr) {
+                            if (!((hits >> rr) & 1u)) continue;
+                            const ColC k = ca[c0 + rr];
+                            const float key = fmaf(-k.c, asum, v[rr]) * k.g * sq;
+                            const int64_t j = j0 + 8 * rr + sf;
+                            if (key >= kmin && j < A.nl && (j < exlo || j > exhi)) {
+                                top_insert(Lk, Lj, Ld, key, (int32_t)j, k.dq, p);
+                                cnt = cnt < p ? cnt + 1 : p;
+                                kmin = top_last(Lk, p);
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive1(&bars.accfree[a]);   // accumulator and column constants released
+            }
+            // the halves' lists merged: half 1 hands its list over
+            if (h == 1) {
+#pragma unroll
+                for (int e = 0; e < TC3_MAXP; ++e) {
+                    xk[m * TC3_MAXP + e] = Lk[e];
+                    xj[m * TC3_MAXP + e] = Lj[e];
+                    xd[m * TC3_MAXP + e] = Ld[e];
+                }
+                xcnt[m] = cnt;
+            }
+            asm volatile("bar.sync 2, 256;" ::: "memory");
+            if (h == 0 && erow && !*abortv) {
+                const int nb = xcnt[m];
+                for (int e = 0; e < nb; ++e) {
+                    top_insert(Lk, Lj, Ld, xk[m * TC3_MAXP + e], xj[m * TC3_MAXP + e], xd[m * TC3_MAXP + e], p);
+                    cnt = cnt < p ? cnt + 1 : p;
+                }
+                const int64_t slot = pos * A.nblk + cb;
+#pragma unroll
+                for (int e = 0; e < TC3_MAXP; ++e) {
+                    if (e < cnt) {
+                        A.okey[slot * p + e] = Lk[e];
+                        A.oj[slot * p + e] = Lj[e];
+                        A.odq[slot * p + e] = Ld[e];
+                    }
+                }
+                A.ocnt[slot] = cnt;
+            }
+            asm volatile("bar.sync 2, 256;" ::: "memory");
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_N) : "memory");
+    }
+}
 }  // namespace
 
 size_t tc_smem_bytes(int p)
@@ -810,9 +1197,58 @@ size_t tc2_smem_bytes(int p)
            (size_t)TC_M * p * (sizeof(float) + sizeof(int32_t) + sizeof(float));
 }
 
+int tc_copy_len(int lmax) { return 248 + TC_KC * tc_chunks(lmax); }
+
+// (+1 KB: the descriptor's last rows reach 494 bytes past the last copy
+// for lags the kernel never asks for)
+size_t tc_bcopy_bytes(int64_t ntiles, int lmax)
+{
+    return (size_t)2 * ntiles * 8 * tc_copy_len(lmax) * sizeof(__half) + 1024;
+}
+
+size_t tc_gcc_bytes(int64_t ntiles) { return (size_t)ntiles * TC_N * sizeof(ColC); }
+
+int64_t tc_col_tiles(int64_t nl) { return (nl + TC_N - 1) / TC_N; }
+
+size_t tc3_smem_bytes() { return 1024 + 2 * (size_t)TC3_STAGE + 2 * TC3_CC_BYTES + (size_t)TC_M * TC3_MAXP * 12; }
+
+bool tc_encode_bmap(void *map, void *gaddr, int64_t ntiles, int lc)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    if (!encode || !map || !gaddr || ntiles <= 0 || lc % 8 != 0) return false;
+    // dims {lag i, row r (16 B apart: rows overlap, the Hankel form), copy sf, tile, hi|lo}
+    const cuuint64_t dims[5] = {(cuuint64_t)lc, 32, 8, (cuuint64_t)ntiles, 2};
+    const cuuint64_t strides[4] = {16, (cuuint64_t)lc * 2, (cuuint64_t)lc * 16, (cuuint64_t)lc * 16 * ntiles};
+    const cuuint32_t box[5] = {TC_KC, 32, 8, 1, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = encode(reinterpret_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 5, gaddr, dims,
+                              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 void launch_direct_tc(const TcArgs &a, int num_sms, cudaStream_t s)
 {
     k_tc_rows<<<num_sms * 8, TC_THREADS, 0, s>>>(a);
+    if (a.bmap && a.p <= TC3_MAXP && a.ntiles > 0) {
+        k_tc_cols<<<(unsigned)a.ntiles, TC_N, (size_t)2 * (a.lc + 8) * sizeof(__half), s>>>(a);
+        Tc3Params P;
+        P.a = a;
+        memcpy(&P.bmap, a.bmap, sizeof(CUtensorMap));
+        static std::once_flag once3[64];
+        smem_optin_max((const void *)k_direct_tc3, once3);
+        k_direct_tc3<<<num_sms, TC3_THREADS, tc3_smem_bytes(), s>>>(P);
+        return;
+    }
     if (a.p <= TC2_MAXP) {
         static std::once_flag once2[64];
         smem_optin_max((const void *)k_direct_tc2, once2);

@@ -372,9 +372,28 @@ struct TcArgs {
     float *dq_max;
     int nblk;
     int *err;               // set if a bounded wait ran out
+    // column tiles written per length and loaded by TMA (p <= 16): the
+    // tiles' shifted copies [hi, lo][tile][8][lc] (FP16), their column
+    // constants [tile][256] (16 B each), and the TMA descriptor of the
+    // copies (host memory; nullptr: the kernel builds the tiles itself)
+    void *bcopy;
+    void *gcc;
+    int64_t ntiles;         // column tiles at this length
+    int64_t tiles_ws;       // column tiles of the workspace layout (the largest length's count)
+    int lc;
+    const void *bmap;
 };
 void launch_direct_tc(const TcArgs &a, int num_sms, cudaStream_t s);
 size_t tc_aimg_bytes(int64_t max_rows, int lmax);
+// Column tiles by TMA: copy length, byte sizes, and the descriptor of
+// [2][tiles][8][lc] FP16 at gaddr written into map (128 bytes, 64-byte
+// aligned); false if the driver refuses it (the kernel then builds the
+// tiles itself).
+int tc_copy_len(int lmax);
+size_t tc_bcopy_bytes(int64_t ntiles, int lmax);
+size_t tc_gcc_bytes(int64_t ntiles);
+int64_t tc_col_tiles(int64_t nl);
+bool tc_encode_bmap(void *map, void *gaddr, int64_t ntiles, int lc);
 int tc_chunks(int l);
 
 template <typename T>

@@ -42,6 +42,9 @@ std::atomic<int> g_wave_limit{-1};
 std::atomic<int> g_audit{0};
 // mad_set_graphs: capture and replay repeated profiles (default on)
 std::atomic<int> g_graphs{1};
+// mad_debug_tc_tma: the tensor-core path's column tiles by TMA (default off:
+// measured slower inside the profile pipeline, see mad.h)
+std::atomic<int> g_tc_tma{0};
 
 // What a profile's workspace depends on: while a series is profiled again
 // with the same key, its device buffers are reused as they are (no
@@ -49,7 +52,7 @@ std::atomic<int> g_graphs{1};
 // from a CUDA graph.
 struct WsKey {
     int tsize = 0, lmin = 0, lmax = 0, p = 0, m_max = 0, k_max = 0, mode = 0, band_form = 0, keep = 0,
-        observe = 0, num = 0, den = 0, audit = 0, wave_limit = 0, tc = 0, rpl = 0, limf = 0;
+        observe = 0, num = 0, den = 0, audit = 0, wave_limit = 0, tc = 0, rpl = 0, limf = 0, tma = 0;
     bool operator==(const WsKey &o) const { return std::memcmp(this, &o, sizeof(WsKey)) == 0; }
 };
 
@@ -96,6 +99,9 @@ struct Series {
     double *obs_gap = nullptr, *obs_tlb = nullptr;
     int32_t *keep_nnj = nullptr;
     std::vector<mad_length_stats> stats;
+    // TMA descriptor of the tensor-core path's column tiles (a CUtensorMap)
+    alignas(64) unsigned char bmap[128] = {};
+    bool bmap_ok = false;
 };
 
 }  // namespace
@@ -502,6 +508,12 @@ void issue_profile(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStrea
     unsigned char *aimg = tc ? dalloc<unsigned char>(ctx, s, tc_aimg_bytes(max_direct, lmax)) : nullptr;
     float *tasum = tc ? dalloc<float>(ctx, s, (size_t)max_direct_pad) : nullptr;
     float *tsq = tc ? dalloc<float>(ctx, s, (size_t)max_direct_pad) : nullptr;
+    // column tiles of the tensor-core path (p <= 16): eight shifted copies per
+    // tile written per length and loaded by TMA (else built in the kernel)
+    const int64_t col_tiles = tc_col_tiles(n0);
+    void *tcb = (tc && p <= 16) ? dalloc<unsigned char>(ctx, s, tc_bcopy_bytes(col_tiles, lmax)) : nullptr;
+    void *tcc = (tc && p <= 16) ? dalloc<unsigned char>(ctx, s, tc_gcc_bytes(col_tiles)) : nullptr;
+    s.bmap_ok = tcb && g_tc_tma.load() && tc_encode_bmap(s.bmap, tcb, col_tiles, tc_copy_len(lmax));
     T *skey = dalloc<T>(ctx, s, (size_t)n0 * ngroups_max * p);
     int32_t *sj = dalloc<int32_t>(ctx, s, (size_t)n0 * ngroups_max * p);
     int32_t *scnt = dalloc<int32_t>(ctx, s, (size_t)n0 * ngroups_max);
@@ -815,6 +827,12 @@ void issue_profile(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStrea
             ta.dq_max = ddqmax + li;
             ta.nblk = dnblk;
             ta.err = wait_err;
+            ta.bcopy = tcb;
+            ta.gcc = tcc;
+            ta.ntiles = tc_col_tiles(nl);
+            ta.tiles_ws = col_tiles;
+            ta.lc = tc_copy_len(lmax);
+            ta.bmap = s.bmap_ok ? s.bmap : nullptr;
         }
         MergeArgs<T> ma{};
         ma.x = s.x;
@@ -1052,6 +1070,7 @@ void start_profile(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStrea
     key.wave_limit = g_wave_limit.load();
     key.rpl = s.rpl;
     key.limf = s.limf;
+    key.tma = g_tc_tma.load();
     const bool same = s.ws_valid && s.key == key;
     if (!same) {
         free_profile(s);
@@ -1348,6 +1367,8 @@ MAD_API void mad_debug_audit_error_bounds(int32_t on) { g_audit.store(on ? 1 : 0
 MAD_API void mad_set_graphs(int32_t on) { g_graphs.store(on ? 1 : 0); }
 
 MAD_API void mad_set_autotune(int32_t on) { g_autotune.store(on ? 1 : 0); }
+
+MAD_API void mad_debug_tc_tma(int32_t on) { g_tc_tma.store(on ? 1 : 0); }
 
 MAD_API mad_status mad_profile(mad_ctx *ctx, int32_t lmin, int32_t lmax, int32_t p)
 {

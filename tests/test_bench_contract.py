@@ -18,7 +18,7 @@ def _fake_sample(w, seconds):
 def _args(**kw):
     a = dict(gpus=1, steps=2, warmup=3, impl="reference", workload="rw4096", precision="fp32", band_form=0,
              no_fp64_path=True, no_motif_path=True, no_discord_path=True, no_cpu_baseline=True, cpu_seconds=1.0,
-             p_sweep=None, ncu_case=None, mode=0, lrange=None, fp64_steps=3, e2e_steps=3, fp64_lrange=None, graphs=1)
+             p_sweep=None, ncu_case=None, mode=0, lrange=None, fp64_steps=3, e2e_steps=3, fp64_lrange=None, graphs=1, tc_tma=0)
     a.update(kw)
     return types.SimpleNamespace(**a)
 

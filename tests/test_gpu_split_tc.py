@@ -77,8 +77,54 @@ def test_tc_matches_fp32_readouts():
 
 
 def test_large_p_takes_the_unpipelined_kernel():
-    # p > 10: the per-row lists no longer fit beside the two pipelined stages;
-    # the one-stage kernel runs instead (same results)
+    # p > 16: the one-stage kernel (per-row lists in shared memory) runs
     x = workloads.ecg_like(5200, 154, period=58.0)
-    r = compare_all(x, 64, 70, 12, TC, m_max=2, k_max=3)
+    r = compare_all(x, 64, 70, 20, TC, m_max=2, k_max=3)
+    assert direct(r["stats"]) > 0
+
+
+def _tc_profile(x, lmin, lmax, p, tma, m_max=1, k_max=3):
+    mad.mad_debug_tc_tma(tma)
+    try:
+        ctx = mad.mad_create(x, precision=TC, k_max=k_max, m_max=m_max, keep_profiles=True)
+        try:
+            mad.mad_profile(ctx, lmin, lmax, p)
+            n0 = len(x) - lmin + 1
+            return dict(vm=mad.mad_valmp(ctx, 0, n0),
+                        prof=[mad.mad_matrix_profile(ctx, 0, l, len(x), m_max) for l in range(lmin, lmax + 1)],
+                        mot=mad.mad_motifs(ctx, 0, k_max), st=mad.mad_stats(ctx, 0))
+        finally:
+            mad.mad_destroy(ctx)
+    finally:
+        mad.mad_debug_tc_tma(0)
+
+
+@pytest.mark.parametrize("p", [6, 12], ids=["p6_vs_pipelined", "p12_vs_one_stage"])
+def test_tma_column_tiles_match_built_tiles(p):
+    # column tiles loaded by TMA from the per-length shifted copies against
+    # tiles built in shared memory by the kernels without TMA (the default):
+    # the same FP16 pairs and products, so the same results bit for bit
+    # (ties between equal keys go to the smaller column in both)
+    x = workloads.ecg_like(9000, 155, period=47.0)
+    a = _tc_profile(x, 70, 76, p, 1, m_max=2)
+    b = _tc_profile(x, 70, 76, p, 0, m_max=2)
+    assert direct(a["st"]) > 0 and direct(a["st"]) == direct(b["st"])
+    for key in ("dist", "norm", "len", "nn"):
+        assert np.array_equal(a["vm"][key], b["vm"][key]), key
+    for pa, pb in zip(a["prof"], b["prof"]):
+        for u, v in zip(pa, pb):
+            assert np.array_equal(u, v)
+    assert a["mot"] == b["mot"]
+    assert [s["fp32_dq_max"] for s in a["st"]] == [s["fp32_dq_max"] for s in b["st"]]
+
+
+def test_tma_column_tiles_ragged_series_end():
+    # TMA column tiles against the oracle: the last tile's copies run past
+    # the series end (zeros), n_l not a multiple of 256, lags in three chunks
+    x = workloads.ecg_like(8191, 156, period=71.0)
+    mad.mad_debug_tc_tma(1)
+    try:
+        r = compare_all(x, 129, 133, 7, TC, k_max=3)
+    finally:
+        mad.mad_debug_tc_tma(0)
     assert direct(r["stats"]) > 0
