@@ -178,10 +178,7 @@ void launch_seed_pair(const SeedArgs<double> &a, const double *m2, int64_t n, cu
 // Entry (k, j) of the table: row 0 holds C(0, j); row k >= 1 holds C(kS, 0)
 // at j = 0 and C(kS - 1, j - 1) for j >= 1.
 // Each thread takes one column j and SEED_ROWS consecutive seed rows, so
-// the column's factor (x[j-1+l] - mu[j-1]) is loaded once for them (the
-// tables are streamed with evict-first hints: they pass through L2 once per
-// length and would otherwise push out the working sets of the kernels that
-// run beside this one); the
+// the column's factor (x[j-1+l] - mu[j-1]) is loaded once for them; the
 // block's row factors are formed once in shared memory. Away from the first
 // row and column the rows go in batches of SEED_BATCH whose loads are all
 // issued before the first store (several loads in flight per thread: the
@@ -254,17 +251,17 @@ __global__ void __launch_bounds__(128, 16) k_seed_step(const double *__restrict_
     for (int t0 = 0; t0 < nrow; t0 += SEED_BATCH) {
         double v[SEED_BATCH];
 #pragma unroll
-        for (int t = 0; t < SEED_BATCH; ++t) v[t] = t0 + t < nrow ? __ldcs(mp + (int64_t)t * spitch) : 0.0;
+        for (int t = 0; t < SEED_BATCH; ++t) v[t] = t0 + t < nrow ? mp[(int64_t)t * spitch] : 0.0;
         if (update) {
 #pragma unroll
             for (int t = 0; t < SEED_BATCH; ++t) {
                 v[t] = (valid >> (t0 + t)) & 1u ? fma(sa[t0 + t], bj, v[t]) : 0.0;
-                if (t0 + t < nrow) __stcs(mp + (int64_t)t * spitch, v[t]);
+                if (t0 + t < nrow) mp[(int64_t)t * spitch] = v[t];
             }
         }
 #pragma unroll
         for (int t = 0; t < SEED_BATCH; ++t)
-            if (t0 + t < nrow) __stcs(sp + (int64_t)t * spitch, (T)v[t]);
+            if (t0 + t < nrow) sp[(int64_t)t * spitch] = (T)v[t];
         mp += SEED_BATCH * spitch;
         sp += SEED_BATCH * spitch;
     }
