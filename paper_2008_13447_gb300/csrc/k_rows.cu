@@ -990,13 +990,21 @@ __global__ void k_split(SplitArgs A)
     bool direct = A.force_direct || (!sym_on && cnt <= A.lim);
     if (direct) {
         if (threadIdx.x == 0) {
-            base = atomicAdd(A.ndirect, cnt);
-            if (base + cnt > A.max_direct) {
-                atomicSub(A.ndirect, cnt);
-                base = -1;
-            } else if (A.stat_direct) {
-                atomicAdd(A.stat_direct, (unsigned long long)cnt);
+            // reserve cnt list positions only if they fit (compare-and-swap:
+            // an add later undone would let a concurrent block take
+            // positions past a hole of positions nobody writes, which the
+            // direct kernels would then read as rows)
+            int cur = *(volatile int *)A.ndirect;
+            base = -1;
+            while (cur + cnt <= A.max_direct) {
+                const int seen = atomicCAS(A.ndirect, cur, cur + cnt);
+                if (seen == cur) {
+                    base = cur;
+                    break;
+                }
+                cur = seen;
             }
+            if (base >= 0 && A.stat_direct) atomicAdd(A.stat_direct, (unsigned long long)cnt);
         }
         __syncthreads();
         direct = base >= 0;
