@@ -227,9 +227,15 @@ class ClockSampler:
 # -------------------------------------------------------------- helpers
 
 def kernel_source_hash():
+    """Hash of the band kernel's source: its own files and the BandArgs
+    declaration (the rest of kernels.cuh declares other kernels)."""
     h = hashlib.sha256()
-    for f in ("k_band.cuh", "k_band_f32.cu", "kernels.cuh", "mad_internal.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2008_13447_gb300", "csrc", f), "rb").read())
+    csrc = os.path.join(ROOT, "paper_2008_13447_gb300", "csrc")
+    for f in ("k_band.cuh", "k_band_f32.cu", "mad_internal.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    decl = open(os.path.join(csrc, "kernels.cuh")).read()
+    a = decl.index("template <typename T> struct BandArgs {")
+    h.update(decl[a:decl.index("};", a) + 2].encode())
     return h.hexdigest()[:16]
 
 

@@ -990,21 +990,19 @@ __global__ void k_split(SplitArgs A)
     bool direct = A.force_direct || (!sym_on && cnt <= A.lim);
     if (direct) {
         if (threadIdx.x == 0) {
-            // reserve cnt list positions only if they fit (compare-and-swap:
-            // an add later undone would let a concurrent block take
-            // positions past a hole of positions nobody writes, which the
-            // direct kernels would then read as rows)
-            int cur = *(volatile int *)A.ndirect;
-            base = -1;
-            while (cur + cnt <= A.max_direct) {
-                const int seen = atomicCAS(A.ndirect, cur, cur + cnt);
-                if (seen == cur) {
-                    base = cur;
-                    break;
-                }
-                cur = seen;
+            // reserve by one add on a second counter that is never undone:
+            // reservations are handed out in one order and, once one
+            // overflows, every later one does too, so the blocks that fit
+            // hold a prefix of the positions with no hole; ndirect[0] counts
+            // only them. (An add undone on overflow let a concurrent block
+            // take positions past a hole nobody wrote; a compare-and-swap
+            // loop on one counter costs too much under contention.)
+            const int r = atomicAdd(A.ndirect + 1, cnt);
+            base = r + cnt <= A.max_direct ? r : -1;
+            if (base >= 0) {
+                atomicAdd(A.ndirect, cnt);
+                if (A.stat_direct) atomicAdd(A.stat_direct, (unsigned long long)cnt);
             }
-            if (base >= 0 && A.stat_direct) atomicAdd(A.stat_direct, (unsigned long long)cnt);
         }
         __syncthreads();
         direct = base >= 0;
@@ -1050,7 +1048,7 @@ void launch_split(const SplitArgs &a, cudaStream_t s)
 {
     const int64_t nb = (a.nl + a.R - 1) / a.R;
     cudaMemsetAsync(a.nbands, 0, sizeof(int32_t), s);
-    cudaMemsetAsync(a.ndirect, 0, sizeof(int32_t), s);
+    cudaMemsetAsync(a.ndirect, 0, 2 * sizeof(int32_t), s);   // rows taken, positions reserved
     k_split<<<(unsigned)nb, 256, 0, s>>>(a);
 }
 
