@@ -43,11 +43,6 @@ template <typename T> struct SeedArgs {
 };
 template <typename T> void launch_seed(const SeedArgs<T> &a, cudaStream_t s);
 template <> void launch_seed<double>(const SeedArgs<double> &a, cudaStream_t s);
-// Seed rows at lmin for the FP32 paths from FP32-pair dot products (values
-// the pair sum cannot bound to half an FP32 unit are computed in FP64);
-// m2 = window M2 at l, n = series length. seed_pair_smem: its shared memory.
-void launch_seed_pair(const SeedArgs<double> &a, const double *m2, int64_t n, cudaStream_t s);
-size_t seed_pair_smem(int l);
 // Seed rows stepped from length l to l + 1 (update) or only copied to T:
 // mu = window means at l, nl = windows at l + 1, master = FP64 seed rows
 // (updated in place), seed = the band kernel's copy.

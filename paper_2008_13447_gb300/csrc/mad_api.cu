@@ -268,10 +268,8 @@ void init_ctx(mad_ctx *ctx, const mad_options *opt)
 
 // Error model of the band kernel's keys (see ErrModel): dq0 = u (2R + 4)
 // for a chain of at most R + 1 steps (scaled per cell by the contrast
-// factors), on the FP32 paths one unit more for the FP32-pair seeds at
-// lmin (k_seed_pair: within half a unit), on the FP64 path the error of the
-// FP64 seeds (a direct dot product at lmin, then one Welford step per
-// length); and the distance
+// factors), plus, on the FP64 path, the error of the FP64 seeds (a direct
+// dot product at lmin, then one Welford step per length); and the distance
 // tolerance that decides which reported entries are re-evaluated.
 template <typename T>
 struct Precision;
@@ -283,7 +281,7 @@ struct Precision<double> {
 template <>
 struct Precision<float> {
     static constexpr double u = 0x1p-24, rel_tol = 0.0, abs_coef = 1e-4;
-    static double dq0(int R, int) { return u * (2.0 * R + 5.0) + 0x1p-50; }
+    static double dq0(int R, int) { return u * (2.0 * R + 4.0) + 0x1p-50; }
 };
 
 // Timed launches of the per-length pipeline (CUDA events recorded on the
@@ -596,15 +594,10 @@ void issue_profile(mad_ctx *ctx, Series &s, int lmin, int lmax, int p, cudaStrea
         launch_coldata<T>(s.x, nl, npad, l, mu[b], m2[b], run, colb[b], isdb[b], side.prep);
         launch_kappa(s.x, mu[b], m2[b], run, nl, l, SP, m2blk, kappab[b], kmaxb[b], side.prep);
         if (l == lmin) {
-            // seed rows computed directly once (FP32 paths: FP32-pair dot
-            // products within half an FP32 unit, one unit in dq0; FP64 path:
-            // FP64 dot products); every later length steps them by one FP64
-            // co-moment update
+            // seed rows computed directly once, in FP64; every later length
+            // steps them by one co-moment update
             SeedArgs<double> sa{s.x, mu[b], nl, l, SP, krows, (int)K, spitch, seedm, nullptr};
-            if (sizeof(T) == 4 && seed_pair_smem(l) <= 160 * 1024)
-                launch_seed_pair(sa, m2[b], n, side.prep);
-            else
-                launch_seed<double>(sa, side.prep);
+            launch_seed<double>(sa, side.prep);
             launch_seed_step<T>(s.x, mu[b], nl, l, SP, K, spitch, seedm, seedb[b], false, side.prep);
         } else {
             launch_seed_step<T>(s.x, mu[b ^ 1], nl, l - 1, SP, K, spitch, seedm, seedb[b], true, side.prep);
