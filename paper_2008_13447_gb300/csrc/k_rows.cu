@@ -640,7 +640,11 @@ __global__ void __launch_bounds__(128, row_min_blocks<PM>()) k_merge(MergeArgs<T
     });
     T lastk = T(-pinf());       // the p-th kept key (a sentinel until p are kept)
     int32_t lastj = INT32_MAX;
+    // (list entries are partners of this length, 0 <= j < n_l; the guard,
+    // and the clamp of the counts below, keep a slot that no kernel wrote
+    // at this length from sending a read out of range)
     auto offer = [&](T v, int32_t j, float dq) {
+        if (j < 0 || j >= A.nl) return;
         if (!key_before(v, j, lastk, lastj)) return;
         T cv = v;
         int32_t cj = j;
@@ -670,7 +674,7 @@ __global__ void __launch_bounds__(128, row_min_blocks<PM>()) k_merge(MergeArgs<T
         for (int g = 0; g < A.dnblk; ++g) {
             const int64_t slot = d * A.dnblk + g;
             if ((int64_t)g * direct_cols_per_block_dev() >= A.nl) break;
-            const int cnt = A.dcnt[slot];
+            const int cnt = min(max(A.dcnt[slot], 0), p);
             for (int c = 0; c < cnt; ++c) offer(A.dkey[slot * p + c], A.dj[slot * p + c], A.ddq[slot * p + c]);
         }
     } else {
@@ -690,7 +694,8 @@ __global__ void __launch_bounds__(128, row_min_blocks<PM>()) k_merge(MergeArgs<T
                     const int g = gq + 4 * u + w;
                     if (g < g0 || g >= gend) continue;
                     const int64_t slot = i * A.ngroups + g;
-                    for (int c = 0; c < cs[w]; ++c) offer(A.skey[slot * p + c], A.sj[slot * p + c], -1.0f);
+                    const int cnt = min(max(cs[w], 0), p);
+                    for (int c = 0; c < cnt; ++c) offer(A.skey[slot * p + c], A.sj[slot * p + c], -1.0f);
                 }
             }
         }
