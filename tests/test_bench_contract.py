@@ -64,3 +64,18 @@ def test_reference_other_ranks_print_nothing(monkeypatch, capsys):
     monkeypatch.setenv("WORLD_SIZE", "2")
     assert bench.run_reference(_args(gpus=2)) == 0
     assert capsys.readouterr().out.strip() == ""
+
+
+def test_band_traffic_record_matches_the_band_kernel_source():
+    # the DRAM bytes per cell that the bench line reports as the band
+    # kernel's traffic were counted on this kernel source (else it reports
+    # null); a change to the band kernel's files makes this fail until the
+    # record is taken again
+    import json
+    import os
+    import bench
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "band_kernel_traffic.json")))
+    assert rec["kernel_source_sha"] == bench.kernel_source_hash()
+    t = bench.measured_traffic(rec["cells_per_launch"])
+    assert t is not None
+    assert abs(t - (rec["dram_bytes_read"] + rec["dram_bytes_write"])) <= 1e-6 * t
